@@ -1,0 +1,451 @@
+/*
+ * oracle.c -- double-precision CPU oracle for histogram-sampling muon transport
+ * (Cattelan, Qasim, Owen, Serra, "Ultra-Fast Muon Transport via Histogram
+ * Sampling on GPUs", arXiv 2512.10520).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header,
+ * table or constant generator with the CUDA path: it derives its own sampling
+ * thresholds from the raw histogram weights and runs Algorithm 1 step by step
+ * in FP64, one muon at a time, with no blocking, fusion or reordering.
+ *
+ * What it computes, per muon (Algorithm 1, Sec. "Simulation"):
+ *   for k = steps_done .. max_steps-1:
+ *     P = |p|; break with a status if P < p_min, z >= z_max, |x| >= x_max
+ *       or |y| >= y_max                                   (termination test)
+ *     M = GetMaterial(r)                                  (Sec. Simulation, item 1)
+ *     if M is not vacuum:
+ *       i = GetMomentumBin(P), log10 bins                 (Sec. Momentum binning)
+ *       (w0..w3) = Philox4x32-10(key = seed, ctr = (k, id_lo, id_hi, instance))
+ *       cell = #{ j < ncell-1 : T_j <= w0 }               (inverse CDF of H_{M,i})
+ *       f, theta = cell centre axes + uniform jitter      (Sec. Simulation, item 2)
+ *       phi = 2 pi U                                      (isotropic azimuth)
+ *       p <- p + Rot(dp), dp = [dt cos phi, dt sin phi, dz]   (Eq. 3, Rodrigues)
+ *     B = GetField(r)                                     (Sec. Simulation, item 3)
+ *     (r, p) <- RK4Step(r, p, B, d), dP/dt = q v x B      (Eq. 4)
+ *     steps_done = k + 1
+ *
+ * Readings where the paper is silent or garbled:
+ *  - sampler: inverse CDF over uint32 thresholds T_j = floor(2^32 S_j / S_tot)
+ *    with S_j the left-to-right FP64 prefix sum of the cell weights (the paper
+ *    uses Walker's alias method; inverse CDF gives a different but equally
+ *    valid draw -> cell map and makes the cell choice exact in integers);
+ *  - histogram axes are linear: f = dp/p in [0, f_max), theta in [0, theta_max);
+ *    jitter is uniform inside the chosen cell on both axes (draws w1, w2);
+ *  - dz, dt of Algorithm 1 are dz = P((1-f) cos theta - 1), dt = P(1-f) sin theta,
+ *    so the update keeps |p_new| = (1-f) P and angle(p, p_new) = theta exactly;
+ *  - Eq. 3 is read as p <- p + Rot(dp) with Rot(v) = v cos a + (k x v) sin a +
+ *    k (k.v)(1 - cos a), k = z x p^ / |z x p^|, cos a = p^_z, sin a = |z x p^|;
+ *    if |z x p^| < 1e-12, Rot = I for p^_z > 0 and diag(1,-1,-1) otherwise;
+ *  - the field is looked up once per step at the step's start position and held
+ *    fixed over the RK4 stages; trilinear on nodes, zero outside the node box;
+ *  - RK4 integrates dr/ds = p/P0, dp/ds = kappa q (p x B)/P0 over s in [0, d],
+ *    P0 = |p| after the scattering update, kappa = 0.299792458 GeV/(T m);
+ *  - termination uses |x| and |y|, is tested at the start of a step, and a loss
+ *    below the cut mid-step stops the muon at the next test;
+ *  - momentum bins outside [p_lo, p_hi) are clamped to the edge bins;
+ *  - U(w) = (w >> 8) 2^-24 (exact in FP32 and FP64).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_KAPPA 0.299792458           /* GeV / (T m) per unit charge */
+#define OR_TWO_PI 6.283185307179586476925286766559
+
+enum { OR_ALIVE = 0, OR_STOPPED = 1, OR_EXIT_Z = 2, OR_EXIT_XY = 3, OR_MAX_STEPS = 4, OR_INVALID = 5 };
+
+typedef struct or_world {
+    /* geometry */
+    int32_t geom_kind;          /* 0: ordered axis-aligned boxes, 1: voxel grid */
+    int32_t n_box;
+    const double *box_lo;       /* [n_box][3], half-open boxes lo <= r < hi */
+    const double *box_hi;       /* [n_box][3] */
+    const int32_t *box_mat;     /* [n_box] material id (0 = vacuum) */
+    const int32_t *box_block;   /* [n_box] field-scale block id or -1 */
+    const double *box_B;        /* [n_box][3] uniform field inside the box (field_kind 1) */
+    int32_t world_mat;
+    int32_t vox_dims[3];        /* nx, ny, nz */
+    double vox_origin[3];
+    double vox_spacing[3];
+    const uint8_t *vox;         /* [nz][ny][nx] material ids */
+    double x_max, y_max, z_max, p_min;
+    /* field */
+    int32_t field_kind;         /* 0: none, 1: per-box uniform, 2: trilinear node map */
+    int32_t fdims[3];
+    double forigin[3];
+    double fspacing[3];
+    const float *Bmap;          /* [nz][ny][nx][3] */
+    const double *alpha;        /* [n_block][3] field scales, or NULL */
+    int32_t n_block;
+    /* histograms */
+    int32_t n_mat, n_pbin, nf, ntheta;
+    double p_lo, p_hi;
+    const double *f_max;        /* [n_mat][n_pbin] */
+    const double *theta_max;    /* [n_mat][n_pbin] */
+    const uint64_t *T;          /* [n_mat][n_pbin][nf*ntheta-1] from or_build_thresholds */
+} or_world;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11.  Ten rounds of a multiply/xor S-box with a Weyl  */
+/* key schedule.                                                             */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t m0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t m1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(m0 >> 32), lo0 = (uint32_t)m0;
+        uint32_t hi1 = (uint32_t)(m1 >> 32), lo1 = (uint32_t)m1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+double or_uniform(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------------ */
+/* Histogram -> normalised discrete CDF -> uint32 thresholds (Sec. Building  */
+/* histograms: "normalized to obtain a discrete probability distribution").  */
+/* T_j = floor(2^32 * S_j / S_tot), j = 0..ncell-2; stored in 64 bits, since */
+/* a trailing run of empty cells gives T_j = 2^32 (never <= any 32-bit draw). */
+/* Returns 0, or -1 (negative / non-finite weight), -2 (empty histogram).    */
+/* ------------------------------------------------------------------------ */
+int or_build_thresholds(int64_t n_hist, int32_t ncell, const double *w, uint64_t *T)
+{
+    for (int64_t h = 0; h < n_hist; ++h) {
+        const double *wh = w + h * (int64_t)ncell;
+        double total = 0.0;
+        for (int32_t j = 0; j < ncell; ++j) {
+            if (!(wh[j] >= 0.0) || !isfinite(wh[j])) return -1;
+            total += wh[j];
+        }
+        if (!(total > 0.0) || !isfinite(total)) return -2;
+        double S = 0.0;
+        for (int32_t j = 0; j < ncell - 1; ++j) {
+            S += wh[j];
+            double C = S / total;
+            T[h * (int64_t)(ncell - 1) + j] = (uint64_t)floor(C * 4294967296.0);
+        }
+    }
+    return 0;
+}
+
+/* Inverse CDF: the cell whose interval [T_{c-1}, T_c) holds the draw. */
+int32_t or_sample_cell(const uint64_t *T, int32_t ncell, uint32_t w0)
+{
+    int32_t c = 0;
+    for (int32_t j = 0; j < ncell - 1; ++j)
+        if (T[j] <= (uint64_t)w0) ++c;
+    return c;
+}
+
+/* GetMomentumBin: base-10 logarithmic bins on [p_lo, p_hi], clamped. */
+int32_t or_momentum_bin(double P, double p_lo, double p_hi, int32_t n_pbin)
+{
+    double u = (log10(P) - log10(p_lo)) * (double)n_pbin / log10(p_hi / p_lo);
+    double i = floor(u);
+    if (!(i >= 0.0)) return 0;          /* also catches NaN */
+    if (i > (double)(n_pbin - 1)) return n_pbin - 1;
+    return (int32_t)i;
+}
+
+/* GetMaterial: first box (list order) with lo <= r < hi, else the world;
+ * or the voxel holding r, else the world.  *box receives the box index or -1. */
+int32_t or_material(const or_world *w, const double r[3], int32_t *box)
+{
+    *box = -1;
+    if (w->geom_kind == 0) {
+        for (int32_t b = 0; b < w->n_box; ++b) {
+            const double *lo = w->box_lo + 3 * b, *hi = w->box_hi + 3 * b;
+            int inside = 1;
+            for (int a = 0; a < 3; ++a)
+                if (!(r[a] >= lo[a] && r[a] < hi[a])) inside = 0;
+            if (inside) {
+                *box = b;
+                return w->box_mat[b];
+            }
+        }
+        return w->world_mat;
+    }
+    int64_t idx[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = floor((r[a] - w->vox_origin[a]) / w->vox_spacing[a]);
+        if (!(u >= 0.0 && u < (double)w->vox_dims[a])) return w->world_mat;
+        idx[a] = (int64_t)u;
+    }
+    return w->vox[(idx[2] * w->vox_dims[1] + idx[1]) * w->vox_dims[0] + idx[0]];
+}
+
+/* Trilinear interpolation of the node map; zero outside [origin, origin+(dims-1)*spacing]. */
+static void or_field_map(const or_world *w, const double r[3], double B[3])
+{
+    int64_t i0[3];
+    double t[3];
+    B[0] = B[1] = B[2] = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double u = (r[a] - w->forigin[a]) / w->fspacing[a];
+        if (!(u >= 0.0 && u <= (double)(w->fdims[a] - 1))) return;
+        double fl = floor(u);
+        if (fl > (double)(w->fdims[a] - 2)) fl = (double)(w->fdims[a] - 2);
+        i0[a] = (int64_t)fl;
+        t[a] = u - fl;
+    }
+    const int64_t nx = w->fdims[0], ny = w->fdims[1];
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                double wgt = (di ? t[0] : 1.0 - t[0]) * (dj ? t[1] : 1.0 - t[1]) *
+                             (dk ? t[2] : 1.0 - t[2]);
+                const float *node = w->Bmap + 3 * (((i0[2] + dk) * ny + (i0[1] + dj)) * nx + (i0[0] + di));
+                for (int c = 0; c < 3; ++c) B[c] += wgt * (double)node[c];
+            }
+}
+
+/* GetField: none / per-box uniform / trilinear map, then the per-block scale
+ * alpha[block][c] when r lies in a box that carries a block id. */
+void or_field(const or_world *w, const double r[3], int32_t box, double B[3])
+{
+    B[0] = B[1] = B[2] = 0.0;
+    if (w->field_kind == 1) {
+        if (box >= 0)
+            for (int c = 0; c < 3; ++c) B[c] = w->box_B[3 * box + c];
+    } else if (w->field_kind == 2) {
+        or_field_map(w, r, B);
+    }
+    if (w->alpha && box >= 0 && w->box_block) {
+        int32_t blk = w->box_block[box];
+        if (blk >= 0 && blk < w->n_block)
+            for (int c = 0; c < 3; ++c) B[c] *= w->alpha[3 * blk + c];
+    }
+}
+
+/* Eq. 3: p <- p + Rot(dp) with dp = [dt cos phi, dt sin phi, dz] in the frame
+ * whose z axis is the direction of travel. */
+void or_scatter(const double p[3], double f, double theta, double phi, double out[3])
+{
+    double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    double ph[3] = {p[0] / P, p[1] / P, p[2] / P};
+    double dt = P * (1.0 - f) * sin(theta);
+    double dz = P * ((1.0 - f) * cos(theta) - 1.0);
+    double dp[3] = {dt * cos(phi), dt * sin(phi), dz};
+    double rot[3];
+    double s = sqrt(ph[0] * ph[0] + ph[1] * ph[1]);
+    if (s < 1e-12) {
+        if (ph[2] > 0.0) {
+            rot[0] = dp[0]; rot[1] = dp[1]; rot[2] = dp[2];
+        } else {
+            rot[0] = dp[0]; rot[1] = -dp[1]; rot[2] = -dp[2];
+        }
+    } else {
+        double k[3] = {-ph[1] / s, ph[0] / s, 0.0};
+        double ca = ph[2], sa = s;
+        double kxv[3] = {k[1] * dp[2] - k[2] * dp[1], k[2] * dp[0] - k[0] * dp[2], k[0] * dp[1] - k[1] * dp[0]};
+        double kv = k[0] * dp[0] + k[1] * dp[1] + k[2] * dp[2];
+        for (int c = 0; c < 3; ++c) rot[c] = dp[c] * ca + kxv[c] * sa + k[c] * kv * (1.0 - ca);
+    }
+    for (int c = 0; c < 3; ++c) out[c] = p[c] + rot[c];
+}
+
+/* Eq. 4 with E = 0, integrated by classical RK4 over the path length d with B
+ * held fixed: dr/ds = p/P0, dp/ds = kappa q (p x B)/P0. */
+static void or_deriv(const double p[3], const double B[3], double qk, double P0, double dr[3], double dp[3])
+{
+    for (int c = 0; c < 3; ++c) dr[c] = p[c] / P0;
+    dp[0] = qk * (p[1] * B[2] - p[2] * B[1]) / P0;
+    dp[1] = qk * (p[2] * B[0] - p[0] * B[2]) / P0;
+    dp[2] = qk * (p[0] * B[1] - p[1] * B[0]) / P0;
+}
+
+void or_rk4(double r[3], double p[3], const double B[3], int32_t q, double d)
+{
+    double P0 = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    double qk = OR_KAPPA * (double)q;
+    double k1r[3], k1p[3], k2r[3], k2p[3], k3r[3], k3p[3], k4r[3], k4p[3], tmp[3];
+    or_deriv(p, B, qk, P0, k1r, k1p);
+    for (int c = 0; c < 3; ++c) tmp[c] = p[c] + 0.5 * d * k1p[c];
+    or_deriv(tmp, B, qk, P0, k2r, k2p);
+    for (int c = 0; c < 3; ++c) tmp[c] = p[c] + 0.5 * d * k2p[c];
+    or_deriv(tmp, B, qk, P0, k3r, k3p);
+    for (int c = 0; c < 3; ++c) tmp[c] = p[c] + d * k3p[c];
+    or_deriv(tmp, B, qk, P0, k4r, k4p);
+    for (int c = 0; c < 3; ++c) {
+        r[c] += d / 6.0 * (k1r[c] + 2.0 * k2r[c] + 2.0 * k3r[c] + k4r[c]);
+        p[c] += d / 6.0 * (k1p[c] + 2.0 * k2p[c] + 2.0 * k3p[c] + k4p[c]);
+    }
+}
+
+/* One step's random choices (recorded for the adjoint and for tests). */
+typedef struct or_step_draw {
+    int32_t mat, box, pbin, cell;
+    double f, theta, phi;
+} or_step_draw;
+
+/* Material, bin and histogram draw for step k (Algorithm 1, inside "if M is
+ * not vacuum").  Returns 1 if the muon is in matter and d holds the draw. */
+static int or_draw_step(const or_world *w, const double r[3], const double p[3], int32_t k,
+                        uint64_t id, int32_t inst, uint64_t seed, or_step_draw *d)
+{
+    d->mat = or_material(w, r, &d->box);
+    d->pbin = -1;
+    d->cell = -1;
+    d->f = d->theta = d->phi = 0.0;
+    if (d->mat == 0) return 0;
+    double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    int32_t i = or_momentum_bin(P, w->p_lo, w->p_hi, w->n_pbin);
+    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)id, (uint32_t)(id >> 32), (uint32_t)inst};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t u[4];
+    or_philox4x32_10(ctr, key, u);
+    const int32_t ncell = w->nf * w->ntheta;
+    const int64_t hidx = (int64_t)(d->mat - 1) * w->n_pbin + i;
+    int32_t c = or_sample_cell(w->T + hidx * (ncell - 1), ncell, u[0]);
+    int32_t a = c / w->ntheta, b = c % w->ntheta;
+    d->pbin = i;
+    d->cell = c;
+    d->f = ((double)a + or_uniform(u[1])) / (double)w->nf * w->f_max[hidx];
+    d->theta = ((double)b + or_uniform(u[2])) / (double)w->ntheta * w->theta_max[hidx];
+    d->phi = OR_TWO_PI * or_uniform(u[3]);
+    return 1;
+}
+
+/* Termination test at the start of a step; returns a status or OR_ALIVE. */
+static int or_check(const or_world *w, const double r[3], const double p[3])
+{
+    double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    if (P < w->p_min) return OR_STOPPED;
+    if (r[2] >= w->z_max) return OR_EXIT_Z;
+    if (fabs(r[0]) >= w->x_max || fabs(r[1]) >= w->y_max) return OR_EXIT_XY;
+    return OR_ALIVE;
+}
+
+/* Algorithm 1 for one muon.  Muons whose status is terminal (not ALIVE and
+ * not MAX_STEPS) are left unchanged. */
+void or_transport_one(const or_world *w, double r[3], double p[3], int32_t q, int32_t *steps,
+                      uint8_t *status, uint64_t id, int32_t inst, double d, int32_t max_steps,
+                      uint64_t seed)
+{
+    if (*status != OR_ALIVE && *status != OR_MAX_STEPS) return;
+    for (int c = 0; c < 3; ++c)
+        if (!isfinite(r[c]) || !isfinite(p[c])) {
+            *status = OR_INVALID;
+            return;
+        }
+    int st = OR_MAX_STEPS;
+    for (int32_t k = *steps; k < max_steps; ++k) {
+        int t = or_check(w, r, p);
+        if (t != OR_ALIVE) {
+            st = t;
+            break;
+        }
+        or_step_draw dr;
+        if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter(p, dr.f, dr.theta, dr.phi, p);
+        double B[3];
+        or_field(w, r, dr.box, B);
+        or_rk4(r, p, B, q, d);
+        *steps = k + 1;
+    }
+    *status = (uint8_t)st;
+}
+
+typedef struct or_job {
+    const or_world *w;
+    int64_t begin, end;
+    double *x, *y, *z, *px, *py, *pz;
+    const int8_t *q;
+    int32_t *steps;
+    uint8_t *status;
+    int64_t id_offset;
+    int32_t inst;
+    double d;
+    int32_t max_steps;
+    uint64_t seed;
+} or_job;
+
+static void *or_worker(void *arg)
+{
+    or_job *j = (or_job *)arg;
+    for (int64_t m = j->begin; m < j->end; ++m) {
+        double r[3] = {j->x[m], j->y[m], j->z[m]};
+        double p[3] = {j->px[m], j->py[m], j->pz[m]};
+        or_transport_one(j->w, r, p, j->q[m], &j->steps[m], &j->status[m], (uint64_t)(j->id_offset + m),
+                         j->inst, j->d, j->max_steps, j->seed);
+        j->x[m] = r[0]; j->y[m] = r[1]; j->z[m] = r[2];
+        j->px[m] = p[0]; j->py[m] = p[1]; j->pz[m] = p[2];
+    }
+    return NULL;
+}
+
+/* Transport n muons (FP64 SoA, in place) on n_threads POSIX threads.
+ * Muon m has id id_offset + m.  Returns 0 or -1 on bad arguments. */
+int or_transport(const or_world *w, int64_t n, double *x, double *y, double *z, double *px, double *py,
+                 double *pz, const int8_t *q, int32_t *steps, uint8_t *status, int64_t id_offset,
+                 int32_t inst, double d, int32_t max_steps, uint64_t seed, int32_t n_threads)
+{
+    if (!w || n < 0 || n_threads < 1) return -1;
+    if (n == 0) return 0;
+    if (n_threads > 256) n_threads = 256;
+    if ((int64_t)n_threads > n) n_threads = (int32_t)n;
+    pthread_t th[256];
+    or_job jobs[256];
+    for (int32_t t = 0; t < n_threads; ++t) {
+        or_job j = {w, n * t / n_threads, n * (t + 1) / n_threads, x, y, z, px, py, pz, q, steps, status,
+                    id_offset, inst, d, max_steps, seed};
+        jobs[t] = j;
+    }
+    for (int32_t t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, or_worker, &jobs[t]);
+    or_worker(&jobs[0]);
+    for (int32_t t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* Record the draws of one muon's trajectory (tests of the sampler and rotation):
+ * for each executed step s, mat/box/pbin/cell and f/theta/phi.  Returns the
+ * number of steps executed. */
+int32_t or_trace(const or_world *w, double r[3], double p[3], int32_t q, int32_t steps0, uint64_t id,
+                 int32_t inst, double d, int32_t max_steps, uint64_t seed, int32_t *ibuf /* [max][4] */,
+                 double *dbuf /* [max][9]: r before, p after scatter */, double *fbuf /* [max][3] */)
+{
+    int32_t s = 0;
+    for (int32_t k = steps0; k < max_steps; ++k) {
+        if (or_check(w, r, p) != OR_ALIVE) break;
+        or_step_draw dr;
+        for (int c = 0; c < 3; ++c) dbuf[9 * s + c] = r[c];
+        if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter(p, dr.f, dr.theta, dr.phi, p);
+        for (int c = 0; c < 3; ++c) dbuf[9 * s + 3 + c] = p[c];
+        double B[3];
+        or_field(w, r, dr.box, B);
+        for (int c = 0; c < 3; ++c) dbuf[9 * s + 6 + c] = B[c];
+        ibuf[4 * s + 0] = dr.mat; ibuf[4 * s + 1] = dr.box; ibuf[4 * s + 2] = dr.pbin; ibuf[4 * s + 3] = dr.cell;
+        fbuf[3 * s + 0] = dr.f; fbuf[3 * s + 1] = dr.theta; fbuf[3 * s + 2] = dr.phi;
+        or_rk4(r, p, B, q, d);
+        ++s;
+    }
+    return s;
+}
+
+/* The draw of one step at a given state (sampler tests): ibuf = {mat, box,
+ * pbin, cell}, dbuf = {f, theta, phi}.  Returns 1 in matter, 0 in vacuum. */
+int32_t or_draw(const or_world *w, const double r[3], const double p[3], int32_t k, uint64_t id,
+                int32_t inst, uint64_t seed, int32_t *ibuf, double *dbuf)
+{
+    or_step_draw dr;
+    int in_matter = or_draw_step(w, r, p, k, id, inst, seed, &dr);
+    ibuf[0] = dr.mat; ibuf[1] = dr.box; ibuf[2] = dr.pbin; ibuf[3] = dr.cell;
+    dbuf[0] = dr.f; dbuf[1] = dr.theta; dbuf[2] = dr.phi;
+    return in_matter;
+}

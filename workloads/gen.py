@@ -1,0 +1,342 @@
+"""Seeded synthetic workloads standing in for the paper's Geant4/SHiP inputs.
+
+The paper builds its (material, momentum-bin) histograms from Geant4 runs of
+N = 5e6 muons per bin through a slab of thickness d (Sec. "Building
+histograms"), uses 95 log10 momentum bins on 0.18-400 GeV (Sec. "Validation
+and benchmarking") and a Snoopy finite-element field map of the SHiP muon
+shield.  None of that data exists here, so this module makes seeded
+stand-ins with the same shapes and structure:
+
+* histograms: per sample, a Moyal ionisation loss with PDG thin-absorber
+  width/most-probable value, a 1/v^2 radiative tail whose mean matches
+  b*rho*x, and a Highland-width Rayleigh space angle with a 1 % single-scatter
+  1/theta^3 tail; binned on linear axes f = dp/p in [0, f_max) and
+  theta in [0, 5*theta0(p_i)) with theta0 taken at the bin's lower edge;
+* geometries: an iron block in air, and a shield-like layout of six iron
+  magnet blocks with alternating fields plus a concrete wall;
+* a smooth node-based field map (tanh-edged blocks with small fringe
+  components, all three components non-zero somewhere);
+* muon spectra: log-uniform or p^-2.7 momenta with Gaussian/exponential p_T.
+
+Material constants are approximate; they shape the histograms but play no
+part in any parity check (the same arrays feed both sides).
+"""
+from __future__ import annotations
+
+import concurrent.futures
+import dataclasses
+import hashlib
+import json
+import os
+from typing import Dict, List, Optional
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# physical constants (PDG), MeV / cm units inside the histogram fixture
+# --------------------------------------------------------------------------
+_K = 0.307075           # MeV cm^2 / g
+_ME = 0.51099895        # MeV
+_MMU = 105.6583755      # MeV
+
+# rho [g/cm^3], Z/A, I [MeV], X0 [cm], b [g^-1 cm^2] (radiative loss coefficient)
+MATERIALS: Dict[str, Dict[str, float]] = {
+    "iron":     dict(rho=7.874, ZA=0.46557, I=286.0e-6, X0=1.757, b=3.5e-6),
+    "air":      dict(rho=1.205e-3, ZA=0.49919, I=85.7e-6, X0=30390.0, b=3.0e-6),
+    "concrete": dict(rho=2.300, ZA=0.50274, I=135.2e-6, X0=11.55, b=3.0e-6),
+    "lead":     dict(rho=11.35, ZA=0.39575, I=823.0e-6, X0=0.5612, b=6.0e-6),
+}
+
+_CACHE_DIR = os.environ.get(
+    "MT_WORKLOAD_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "mt_workloads"))
+
+
+def _cache_path(tag: str, params: dict) -> str:
+    key = hashlib.sha1(json.dumps(params, sort_keys=True).encode()).hexdigest()[:16]
+    return os.path.join(_CACHE_DIR, f"{tag}_{key}.npz")
+
+
+def pbin_edges(p_lo: float, p_hi: float, n_pbin: int) -> np.ndarray:
+    """Log-spaced momentum-bin edges p_k = p_lo (p_hi/p_lo)^(k/N), k = 0..N."""
+    k = np.arange(n_pbin + 1, dtype=np.float64)
+    return p_lo * (p_hi / p_lo) ** (k / n_pbin)
+
+
+def _highland(p_gev: np.ndarray, x_cm: float, X0: float) -> np.ndarray:
+    """Highland multiple-scattering width theta0 [rad] for a unit-charge muon."""
+    p = p_gev * 1e3
+    E = np.sqrt(p * p + _MMU * _MMU)
+    beta = p / E
+    t = x_cm / X0
+    return 13.6 / (beta * p) * np.sqrt(t) * (1.0 + 0.038 * np.log(t))
+
+
+def _hist_one(rng: np.random.Generator, mat: Dict[str, float], p_a: float, p_b: float,
+              x_cm: float, f_max: float, nf: int, ntheta: int, n_samples: int):
+    """One (material, momentum-bin) histogram of counts [nf][ntheta] plus its theta axis."""
+    p = rng.uniform(p_a, p_b, n_samples)                     # GeV, Pz ~ U(p_i, p_i+1)
+    pm = p * 1e3
+    E = np.sqrt(pm * pm + _MMU * _MMU)
+    beta2 = (pm / E) ** 2
+    bg = pm / _MMU
+    rho, ZA, I = mat["rho"], mat["ZA"], mat["I"]
+    xi = 0.5 * _K * ZA * rho * x_cm / beta2                   # MeV
+    hw = 28.816e-6 * np.sqrt(rho * ZA)                          # plasma energy, MeV
+    delta = np.maximum(0.0, 2.0 * np.log(bg) + 2.0 * np.log(hw / I) - 1.0)
+    dmp = xi * (np.log(2.0 * _ME * bg * bg / I) + np.log(xi / I) + 0.2 - beta2 - delta)
+    z = rng.standard_normal(n_samples)
+    lam = -np.log(np.maximum(z * z, 1e-300))                 # Moyal variate, mode 0
+    dE = np.maximum(dmp + xi * lam, 0.0)                      # MeV
+    f = dE / pm
+    # radiative tail: v ~ v^-2 on [v0, 1), probability matched to mean b*rho*x
+    v0 = 1e-3
+    mean_v = np.log(1.0 / v0) / (1.0 / v0 - 1.0)
+    p_rad = min(1.0, mat["b"] * rho * x_cm / mean_v)
+    rad = rng.random(n_samples) < p_rad
+    u = rng.random(n_samples)
+    v = 1.0 / (1.0 / v0 - u * (1.0 / v0 - 1.0))
+    f = f + np.where(rad, v, 0.0)
+    # scattering: Rayleigh space angle of Highland width, 1 % single-scatter tail
+    th0 = _highland(p, x_cm, mat["X0"])
+    u1 = 1.0 - rng.random(n_samples)
+    u2 = 1.0 - rng.random(n_samples)
+    single = rng.random(n_samples) < 0.01
+    theta = np.where(single, 2.0 * th0 / np.sqrt(u2), th0 * np.sqrt(-2.0 * np.log(u1)))
+    theta_max = 5.0 * float(_highland(np.array([p_a]), x_cm, mat["X0"])[0])
+    a = np.clip(np.floor(f / f_max * nf), 0, nf - 1).astype(np.int64)
+    b = np.clip(np.floor(theta / theta_max * ntheta), 0, ntheta - 1).astype(np.int64)
+    counts = np.bincount(a * ntheta + b, minlength=nf * ntheta).astype(np.float64)
+    return counts.reshape(nf, ntheta), theta_max
+
+
+def histogram_set(materials: List[str], n_pbin: int = 64, p_lo: float = 1.0, p_hi: float = 400.0,
+                  nf: int = 128, ntheta: int = 64, f_max: float = 0.2, n_samples: int = 10**6,
+                  step_len: float = 0.02, seed: int = 42, cache: bool = True) -> dict:
+    """Histogram set H[M][i] for materials 1..len(materials) (material 0 is vacuum).
+
+    Returns a dict with ``weights`` [n_mat][n_pbin][nf][ntheta] (float64 counts),
+    ``f_max`` and ``theta_max`` [n_mat][n_pbin] (float64) and the binning scalars.
+    """
+    params = dict(materials=list(materials), n_pbin=n_pbin, p_lo=p_lo, p_hi=p_hi, nf=nf,
+                  ntheta=ntheta, f_max=f_max, n_samples=n_samples, step_len=step_len, seed=seed, v=1)
+    path = _cache_path("hist", params)
+    if cache and os.path.exists(path):
+        z = np.load(path)
+        W, FM, TM = z["weights"], z["f_max"], z["theta_max"]
+    else:
+        edges = pbin_edges(p_lo, p_hi, n_pbin)
+        x_cm = step_len * 100.0
+        M = len(materials)
+        W = np.zeros((M, n_pbin, nf, ntheta), dtype=np.float64)
+        FM = np.full((M, n_pbin), f_max, dtype=np.float64)
+        TM = np.zeros((M, n_pbin), dtype=np.float64)
+
+        def one(mi):
+            m, i = mi
+            rng = np.random.default_rng([seed, m, i])
+            W[m, i], TM[m, i] = _hist_one(rng, MATERIALS[materials[m]], edges[i], edges[i + 1],
+                                          x_cm, f_max, nf, ntheta, n_samples)
+
+        # each (material, bin) has its own seeded stream, so threading keeps results fixed
+        with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(one, [(m, i) for m in range(M) for i in range(n_pbin)]))
+        if cache:
+            os.makedirs(_CACHE_DIR, exist_ok=True)
+            tmp = path + f".tmp{os.getpid()}.npz"
+            np.savez(tmp, weights=W, f_max=FM, theta_max=TM)
+            os.replace(tmp, path)
+    return dict(n_mat=W.shape[0], n_pbin=n_pbin, p_lo=float(p_lo), p_hi=float(p_hi),
+                nf=nf, ntheta=ntheta, weights=np.ascontiguousarray(W),
+                f_max=np.ascontiguousarray(FM), theta_max=np.ascontiguousarray(TM),
+                materials=list(materials))
+
+
+# --------------------------------------------------------------------------
+# geometries (SI units: m, GeV, T)
+# --------------------------------------------------------------------------
+def _box(lo, hi, mat, block=-1, B=(0.0, 0.0, 0.0)):
+    return dict(lo=[float(v) for v in lo], hi=[float(v) for v in hi], material=int(mat),
+                block_id=int(block), B=[float(v) for v in B])
+
+
+def geometry_config0() -> dict:
+    """Iron block 1x1x2 m (x,y in [-0.5,0.5], z in [0,2]) in air; B = (0,1.7,0) T in iron.
+
+    Materials: 1 = iron, 2 = air.  World bounds |x|,|y| < 2 m, z < 3 m, p_min 0.5 GeV.
+    """
+    return dict(kind="boxes", boxes=[_box((-0.5, -0.5, 0.0), (0.5, 0.5, 2.0), 1, 0, (0.0, 1.7, 0.0))],
+                world_material=2, x_max=2.0, y_max=2.0, z_max=3.0, p_min=0.5)
+
+
+MAGNET_Z0 = [4.5 * k for k in range(6)]
+MAGNET_LEN = 4.0
+MAGNET_HALF = 0.6
+
+
+def geometry_config1() -> dict:
+    """Shield-like layout: six iron blocks 1.2x1.2x4 m with 0.5 m air gaps, alternating
+    B_y = +-1.7 T (+ for even k), then a 2 m concrete wall z in [27,29], |x|,|y| <= 3 m.
+
+    Materials: 1 = iron, 2 = air (world), 3 = concrete.  World |x|,|y| < 3 m, z < 30 m.
+    Block ids 0..5 index the per-magnet field-scale parameters.
+    """
+    boxes = []
+    for k, z0 in enumerate(MAGNET_Z0):
+        s = 1.0 if k % 2 == 0 else -1.0
+        boxes.append(_box((-MAGNET_HALF, -MAGNET_HALF, z0), (MAGNET_HALF, MAGNET_HALF, z0 + MAGNET_LEN),
+                          1, k, (0.0, 1.7 * s, 0.0)))
+    boxes.append(_box((-3.0, -3.0, 27.0), (3.0, 3.0, 29.0), 3, -1))
+    return dict(kind="boxes", boxes=boxes, world_material=2, x_max=3.0, y_max=3.0, z_max=30.0, p_min=0.5)
+
+
+def _smooth_box(u: np.ndarray, a: float, b: float, w: float) -> np.ndarray:
+    return 0.5 * (np.tanh((u - a) / w) - np.tanh((u - b) / w))
+
+
+def _smooth_box_edge(u: np.ndarray, a: float, b: float, w: float) -> np.ndarray:
+    # w * d/du of _smooth_box: peaked at the block ends, used for a fringe B_z
+    return 0.5 * (np.tanh((u - b) / w) ** 2 - np.tanh((u - a) / w) ** 2)
+
+
+def field_map_config1(nx: int = 200, ny: int = 200, nz: int = 600, z_lo: float = -0.5,
+                      z_hi: float = 27.5, half_xy: float = 3.0, magnet_z0=None,
+                      magnet_B=None, edge_w: float = 0.03) -> dict:
+    """Node-based synthetic magnet field, float32 [nz][ny][nx][3].
+
+    Nodes sit at origin + (i,j,k)*spacing over x,y in [-3,3] m and z in [z_lo, z_hi]
+    (the map extends 0.5 m past the magnets at both ends, so the field is ~0 at the
+    map boundary).  Inside each block B_y ~ +-1.7 T with tanh edges of width 3 cm, plus
+    a small quadrupole-like B_x and a fringe B_z at the block ends.
+    """
+    magnet_z0 = MAGNET_Z0 if magnet_z0 is None else magnet_z0
+    if magnet_B is None:
+        magnet_B = [1.7 if k % 2 == 0 else -1.7 for k in range(len(magnet_z0))]
+    x = np.linspace(-half_xy, half_xy, nx)
+    y = np.linspace(-half_xy, half_xy, ny)
+    z = np.linspace(z_lo, z_hi, nz)
+    Sx = _smooth_box(x, -MAGNET_HALF, MAGNET_HALF, edge_w)
+    Sy = _smooth_box(y, -MAGNET_HALF, MAGNET_HALF, edge_w)
+    B = np.zeros((nz, ny, nx, 3), dtype=np.float32)
+    SxSy = (Sy[:, None] * Sx[None, :]).astype(np.float32)
+    quad = ((y[:, None] * x[None, :]) / (MAGNET_HALF * MAGNET_HALF) * SxSy).astype(np.float32)
+    ylin = ((y[:, None] / MAGNET_HALF) * SxSy).astype(np.float32)
+    for z0, b in zip(magnet_z0, magnet_B):
+        Sz = _smooth_box(z, z0, z0 + MAGNET_LEN, edge_w).astype(np.float32)
+        Ez = _smooth_box_edge(z, z0, z0 + MAGNET_LEN, edge_w).astype(np.float32)
+        B[..., 1] += np.float32(b) * Sz[:, None, None] * SxSy[None]
+        B[..., 0] += np.float32(0.1 * b) * Sz[:, None, None] * quad[None]
+        B[..., 2] += np.float32(0.3 * b) * Ez[:, None, None] * ylin[None]
+    spacing = [(2 * half_xy) / (nx - 1), (2 * half_xy) / (ny - 1), (z_hi - z_lo) / (nz - 1)]
+    return dict(kind="map", dims=[nx, ny, nz], origin=[-half_xy, -half_xy, z_lo],
+                spacing=spacing, B=B)
+
+
+# --------------------------------------------------------------------------
+# muon spectra -> float32 SoA
+# --------------------------------------------------------------------------
+def _soa(x, y, z, px, py, pz, q) -> dict:
+    n = len(x)
+    return dict(x=x.astype(np.float32), y=y.astype(np.float32), z=z.astype(np.float32),
+                px=px.astype(np.float32), py=py.astype(np.float32), pz=pz.astype(np.float32),
+                q=q.astype(np.int8), steps=np.zeros(n, np.int32), status=np.zeros(n, np.uint8))
+
+
+def muons_config0(n: int, seed: int = 1234) -> dict:
+    """p log-uniform 5-300 GeV, q = +-1, x,y ~ U(-0.4,0.4) m, z = 0, px,py ~ N(0,0.5) GeV."""
+    rng = np.random.default_rng(seed)
+    p = np.exp(rng.uniform(np.log(5.0), np.log(300.0), n))
+    px = rng.normal(0.0, 0.5, n)
+    py = rng.normal(0.0, 0.5, n)
+    bad = px * px + py * py >= p * p
+    while bad.any():
+        px[bad] = rng.normal(0.0, 0.5, bad.sum())
+        py[bad] = rng.normal(0.0, 0.5, bad.sum())
+        bad = px * px + py * py >= p * p
+    pz = np.sqrt(p * p - px * px - py * py)
+    q = np.where(rng.random(n) < 0.5, -1, 1)
+    x = rng.uniform(-0.4, 0.4, n)
+    y = rng.uniform(-0.4, 0.4, n)
+    return _soa(x, y, np.zeros(n), px, py, pz, q)
+
+
+def muons_config1(n: int, seed: int = 1234, p_lo: float = 10.0, p_hi: float = 350.0) -> dict:
+    """dN/dp ~ p^-2.7 on [10,350] GeV (inverse CDF), p_T ~ Exp(1 GeV), uniform azimuth,
+    random charge, x,y ~ U(-0.4,0.4) m at z = 0."""
+    rng = np.random.default_rng(seed)
+    g = -1.7
+    u = rng.random(n)
+    p = (p_lo ** g + u * (p_hi ** g - p_lo ** g)) ** (1.0 / g)
+    pt = rng.exponential(1.0, n)
+    bad = pt >= p
+    while bad.any():
+        pt[bad] = rng.exponential(1.0, bad.sum())
+        bad = pt >= p
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    px, py = pt * np.cos(phi), pt * np.sin(phi)
+    pz = np.sqrt(p * p - pt * pt)
+    q = np.where(rng.random(n) < 0.5, -1, 1)
+    x = rng.uniform(-0.4, 0.4, n)
+    y = rng.uniform(-0.4, 0.4, n)
+    return _soa(x, y, np.zeros(n), px, py, pz, q)
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Workload:
+    name: str
+    geometry: dict
+    field: dict
+    hist: dict
+    muons: dict
+    step_len: float
+    max_steps: int
+    seed: int
+    id_offset: int = 0
+    instance: int = 0
+
+    @property
+    def n(self) -> int:
+        return len(self.muons["x"])
+
+
+def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = None,
+             field: Optional[str] = None) -> Workload:
+    """Named workloads.
+
+    * ``config0``: 1e4 muons, one iron block in air, analytic per-box field, 200 steps,
+      iron+air histograms (64 log bins on 1-400 GeV, 128x64 cells, 1e6 samples each).
+    * ``config1``: 1e6 muons through the six-magnet shield and concrete wall, trilinear
+      200x200x600 field map, iron/air/concrete histograms, 1500 steps.
+    * ``config4``: config1's spectrum and geometry with a 400x400x1200 map and
+      4 materials x 128 bins x 256x128 cells (a 4th material, lead, is present in the
+      table set but not placed in the geometry).
+
+    ``n`` and ``hist_samples`` shrink a workload for tests; ``field`` = "box" swaps the map
+    for the analytic per-box field.
+    """
+    if name == "config0":
+        h = histogram_set(["iron", "air"], n_samples=hist_samples or 10**6)
+        mu = muons_config0(n or 10_000)
+        geo = geometry_config0()
+        fld = dict(kind="box")
+        return Workload(name, geo, fld, h, mu, 0.02, 200, 7)
+    if name in ("config1", "config3"):
+        h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
+        mu = muons_config1(n or 1_000_000)
+        geo = geometry_config1()
+        fld = dict(kind="box") if field == "box" else field_map_config1()
+        return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
+    if name == "config4":
+        h = histogram_set(["iron", "air", "concrete", "lead"], n_pbin=128, nf=256, ntheta=128,
+                          n_samples=hist_samples or 10**6)
+        mu = muons_config1(n or 100_000_000)
+        geo = geometry_config1()
+        fld = dict(kind="box") if field == "box" else field_map_config1(400, 400, 1200)
+        return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
+    raise KeyError(name)
+
+
+def batched_instances(*args, **kwargs):  # pragma: no cover - filled in with the batched form
+    raise NotImplementedError("batched instance generator not built yet")
