@@ -1,0 +1,330 @@
+"""Benchmark: muon-steps/s of the histogram-sampling muon transport on one GB300.
+
+A "step" of this benchmark is one full transport of one batch: 1e6 muons of the
+p^-2.7 spectrum through the six-magnet shield and concrete wall (trilinear
+200x200x600 FP32 field map, 3 materials x 64 log bins x 128x64 histograms,
+2 cm steps, at most 1500 steps per muon), i.e. every muon runs Algorithm 1
+until it stops, exits or uses its 1500 steps.  The throughput is
+muon-steps/s = (sum of steps taken by all muons) / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank transports its own 1e6
+muons (ids offset by rank, no collective on the data path: weak scaling) and the
+time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "muon-steps/s on 1 GB300: plain, batched, fwd+adjoint; % of memory roofline"
+UNIT = "muon-steps/s"
+BYTES_PER_STEP = 112          # algorithmic bytes per muon-step (8 field corners x 12 B + 16 B sampler)
+WORKLOAD = ("config1: 1e6 muons (p^-2.7 on 10-350 GeV, p_T ~ Exp(1 GeV)), 6 iron magnet blocks "
+            "+/-1.7 T + 2 m concrete wall, trilinear 200x200x600 FP32 field map, 3 materials x 64 log10 "
+            "p-bins x 128x64 (f, theta) histograms, d = 2 cm, max 1500 steps")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _csrc_hash() -> str:
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2512_10520_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        e = t.get(kernel)
+        if e and e.get("csrc_hash") == _csrc_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(value: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier_sum(value: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_run(wl, n_sample: int, threads: int):
+    """Time the FP64 oracle on the first n_sample muons (ids 0..n_sample-1)."""
+    import oracle
+    world = oracle.world_of(wl)
+    mu = {k: v[:n_sample] for k, v in wl.muons.items()}
+    t0 = time.perf_counter()
+    out = oracle.transport(world, mu, wl.step_len, wl.max_steps, wl.seed, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return float(out["steps"].sum()), dt
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    from workloads import gen
+    wl = gen.workload("config1")
+    threads = os.cpu_count() or 1
+    n_sample = args.cpu_sample
+    for _ in range(args.warmup):
+        cpu_oracle_run(wl, max(256, n_sample // 8), threads)
+    steps_tot, t_tot = 0.0, 0.0
+    for _ in range(args.steps):
+        s, dt = cpu_oracle_run(wl, n_sample, threads)
+        steps_tot += s
+        t_tot += dt
+    value = steps_tot / t_tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_muons": n_sample, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {n_sample} muons of config1 per step (FP64 C oracle, "
+                                   f"{threads} POSIX threads)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_mine(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_10520_gb300 as mt
+    from paper_2512_10520_gb300.api import empty_like_soa
+    from workloads import gen
+
+    wl = gen.workload("config1", n=args.muons)
+    n = wl.n
+    id_offset = rank * n
+    stream = torch.cuda.Stream(device=dev)
+    world = mt.World.from_workload(wl)
+    init = mt.muons_to_device(wl.muons, device=dev)
+    work = empty_like_soa(n, device=dev)
+
+    def reset():
+        for k in work:
+            work[k].copy_(init[k], non_blocking=True)
+
+    ev_k = []
+
+    def one_step(timed: bool):
+        reset()
+        if timed:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            b.record(stream)
+            ev_k.append((a, b))
+        else:
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step(False)
+        torch.cuda.synchronize()
+        steps_per_batch = float(work["steps"].sum().item())
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            start.record(stream)
+            for _ in range(args.steps):
+                one_step(True)
+            stop.record(stream)
+            torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+    elapsed = start.elapsed_time(stop) / 1e3
+    elapsed = _barrier_max(elapsed, ws, dev)
+    kernel_s = float(np.mean([a.elapsed_time(b) for a, b in ev_k])) / 1e3
+    total_steps = _barrier_sum(steps_per_batch * args.steps, ws, dev)
+    value = total_steps / elapsed
+
+    # e2e: pinned host buffers -> device -> mt_transport -> host, every step
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(wl.muons[k])).pin_memory() for k in mt._binding.SOA_FIELDS}
+    host_out = empty_like_soa(n, device="cpu", pinned=True)
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    e2e_steps = 0 if args.no_e2e else max(3, args.steps // 2)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e2e_steps):
+            for k in work:
+                work[k].copy_(host_in[k], non_blocking=True)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            for k in work:
+                host_out[k].copy_(work[k], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+    e2e_t = _barrier_max(a.elapsed_time(b) / 1e3, ws, dev)
+    e2e_value = (_barrier_sum(float(host_out["steps"].sum().item()) * e2e_steps, ws, dev) / e2e_t
+                 if e2e_steps else None)
+
+    peaks, peak_kind = _peaks()
+    achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": _traffic("transport_kernel"),
+            "peak_kind": peak_kind, "bytes_per_step": BYTES_PER_STEP,
+            "kernel_ms": kernel_s * 1e3}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        s, dt = cpu_oracle_run(wl, args.cpu_sample, threads)
+        cpu = {"value": s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} muons of config1 (FP64 C oracle, {threads} POSIX threads)"}
+    clocks = clk.summary()
+    world.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "plain", "muons_per_gpu": n, "max_steps": wl.max_steps,
+                       "muon_steps_per_batch_per_gpu": steps_per_batch, "muons_per_s": n * ws * args.steps / elapsed,
+                       "l2": "inputs larger than L2 (field map 764 MB in HBM vs 129 MB L2); no flush",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=20000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--muons", type=int, default=None, help="muons per GPU (default: the workload's 1e6)")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

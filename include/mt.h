@@ -1,0 +1,186 @@
+/*
+ * mt.h -- C ABI of the GB300 (sm_103a) muon transport library libmt.so.
+ *
+ * Implements the online phase of "Ultra-Fast Muon Transport via Histogram
+ * Sampling on GPUs" (arXiv 2512.10520): the per-muon transport loop of
+ * Algorithm 1 (Sec. "Simulation").  Each muon repeatedly
+ *   (1) looks up its material in the geometry        (Sec. Simulation, item 1),
+ *   (2) draws a fractional momentum loss f and a polar scattering angle theta
+ *       from the precomputed histogram H_{M,i} of its material M and log10
+ *       momentum bin i (Sec. Momentum binning), by inverse CDF over a
+ *       Philox4x32-10 draw, plus uniform jitter and an isotropic azimuth, and
+ *       rotates that kick into the global frame with Rodrigues' formula (Eq. 3),
+ *   (3) advances one fixed step d through the magnetic field with an RK4
+ *       Lorentz-force step (Eq. 4), the field looked up once per step,
+ * until its momentum falls below p_min or it leaves the world box.
+ *
+ * Conventions shared by every entry point:
+ *  - Units: metres, GeV/c, tesla.  kappa = 0.299792458 GeV/(T m) per unit charge.
+ *  - Every function returns an mt_status; nothing throws, traps or aborts across
+ *    the ABI.  On failure mt_last_error() returns a thread-local message.
+ *  - Pointers named "host" are host memory; pointers in mt_muon_soa and those
+ *    named "device" are device memory of the handle's GPU.
+ *  - A handle is immutable after mt_create and may be used from several host
+ *    threads and streams at once; results depend only on the inputs, the seed
+ *    and the muon ids, never on launch configuration or chunking.
+ */
+#ifndef MT_H
+#define MT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MT_ABI_VERSION 1
+
+typedef enum mt_status {
+    MT_OK = 0,
+    MT_ERR_INVALID_ARG = 1,  /* a null pointer, a negative size, a bad descriptor field */
+    MT_ERR_CUDA = 2,         /* a CUDA runtime call failed (message says which)       */
+    MT_ERR_OOM = 3,          /* device allocation failed                              */
+    MT_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                    */
+    MT_ERR_TABLE = 5,        /* histogram weights negative, non-finite or all zero    */
+    MT_ERR_DEVICE = 6        /* a device-side check failed (index out of range)       */
+} mt_status;
+
+/* Per-muon status byte (Algorithm 1's break conditions). */
+enum {
+    MT_ALIVE = 0,      /* not terminated; transported by the next call            */
+    MT_STOPPED = 1,    /* |p| < p_min at the start of a step                      */
+    MT_EXIT_Z = 2,     /* z >= z_max at the start of a step                       */
+    MT_EXIT_XY = 3,    /* |x| >= x_max or |y| >= y_max at the start of a step     */
+    MT_MAX_STEPS = 4,  /* ran out of steps; resumable like MT_ALIVE               */
+    MT_INVALID = 5     /* non-finite position or momentum on entry                */
+};
+
+enum { MT_GEOM_BOXES = 0, MT_GEOM_VOXELS = 1 };
+enum { MT_FIELD_NONE = 0, MT_FIELD_BOX = 1, MT_FIELD_MAP = 2 };
+
+#define MT_MAX_BOXES 32
+#define MT_MAX_MATERIALS 15
+#define MT_MAX_PBINS 256
+#define MT_MAX_CELLS 32768
+
+/* Axis-aligned half-open box lo <= r < hi.  Boxes are tested in list order and
+ * the first one containing r gives the material (Sec. Simulation, item 1).
+ * block_id >= 0 marks a magnet block whose field is scaled by alpha[block_id]
+ * in the differentiable form; B is the uniform field inside the box when the
+ * field kind is MT_FIELD_BOX. */
+typedef struct mt_box {
+    double lo[3];
+    double hi[3];
+    int32_t material;   /* 0 = vacuum, 1..n_mat = histogrammed material */
+    int32_t block_id;   /* -1 or a field-scale block index < MT_MAX_BOXES */
+    double B[3];
+} mt_box;
+
+/* Geometry and the break conditions of Algorithm 1 (inputs p_min, r_max). */
+typedef struct mt_geometry_desc {
+    int32_t kind;                 /* MT_GEOM_BOXES or MT_GEOM_VOXELS                     */
+    int32_t n_boxes;              /* boxes: 0..MT_MAX_BOXES                              */
+    const mt_box *boxes;          /* host, n_boxes entries                               */
+    int32_t world_material;       /* material outside every box / voxel grid             */
+    int32_t vox_dims[3];          /* voxels: nx, ny, nz (each >= 1)                      */
+    double vox_origin[3];         /* voxels: corner of voxel (0,0,0)                     */
+    double vox_spacing[3];        /* voxels: edge lengths (> 0)                          */
+    const uint8_t *voxels;        /* host, [nz][ny][nx] material ids                     */
+    double x_max, y_max, z_max;   /* stop when |x| >= x_max, |y| >= y_max or z >= z_max  */
+    double p_min;                 /* stop when |p| < p_min                               */
+} mt_geometry_desc;
+
+/* Magnetic field.  MT_FIELD_MAP: node-based map, node (i,j,k) at
+ * origin + (i,j,k)*spacing, trilinear interpolation, zero outside the node box
+ * (the paper's regular-grid field, Sec. Simulation item 3). */
+typedef struct mt_field_desc {
+    int32_t kind;                 /* MT_FIELD_NONE / MT_FIELD_BOX / MT_FIELD_MAP      */
+    int32_t dims[3];              /* map: nx, ny, nz (each >= 2)                      */
+    double origin[3];
+    double spacing[3];            /* > 0                                             */
+    const float *B;               /* host, [nz][ny][nx][3] float32 (Bx, By, Bz)       */
+} mt_field_desc;
+
+/* Histogram set H_{M,i} (Sec. Building histograms): for materials M = 1..n_mat
+ * and log10 momentum bins i = 0..n_pbin-1 on [p_lo, p_hi] (edges
+ * p_lo (p_hi/p_lo)^(i/n_pbin); momenta outside use the edge bins), a joint
+ * histogram of f = dp/p on [0, f_max) (nf bins) and theta on [0, theta_max)
+ * (ntheta bins).  weights are non-negative counts or probabilities; each
+ * histogram must have a positive, finite sum. */
+typedef struct mt_hist_desc {
+    int32_t n_mat;                /* 1..MT_MAX_MATERIALS                              */
+    int32_t n_pbin;               /* 1..MT_MAX_PBINS                                  */
+    double p_lo, p_hi;            /* 0 < p_lo < p_hi                                  */
+    int32_t nf, ntheta;           /* nf * ntheta in [2, MT_MAX_CELLS]                 */
+    const double *weights;        /* host, [n_mat][n_pbin][nf][ntheta]                */
+    const double *f_max;          /* host, [n_mat][n_pbin], > 0                       */
+    const double *theta_max;      /* host, [n_mat][n_pbin], > 0                       */
+} mt_hist_desc;
+
+/* Muon state, structure of arrays in device memory, caller-owned, updated in
+ * place (Algorithm 1's inputs r and p).  Muon m has the global id
+ * id_offset + m; the Philox counter of step k is (k, id_lo, id_hi, instance). */
+typedef struct mt_muon_soa {
+    float *x, *y, *z;             /* position [m]                                     */
+    float *px, *py, *pz;          /* momentum [GeV/c]                                 */
+    int8_t *q;                    /* charge (+1 mu+, -1 mu-)                          */
+    int32_t *steps;               /* steps already taken; step k runs from here       */
+    uint8_t *status;              /* MT_ALIVE ... MT_INVALID                          */
+    int64_t id_offset;
+    int32_t instance;
+    int32_t reserved;
+} mt_muon_soa;
+
+typedef struct mt_handle mt_handle;
+
+/* Library ABI version (MT_ABI_VERSION of the build). */
+int32_t mt_abi_version(void);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char *mt_last_error(void);
+
+/* Build the device-resident static data of one world: geometry, field map and
+ * sampling tables (the paper pre-loads "geometry definitions, magnetic field
+ * maps, and pre-computed physics histograms" into GPU global memory, Sec.
+ * Simulation).  For each histogram the library normalises the weights into a
+ * discrete CDF and quantises it to uint32 thresholds
+ * T_j = floor(2^32 S_j / S_total) (S_j the left-to-right FP64 prefix sum), so the
+ * cell of a 32-bit draw w is #{j < ncell-1 : T_j <= w}.
+ * Runs on the current CUDA device, synchronously.  The caller keeps ownership
+ * of every descriptor array and may free them when this returns.
+ * Errors: MT_ERR_INVALID_ARG (bad descriptor), MT_ERR_TABLE (bad weights),
+ * MT_ERR_OOM, MT_ERR_CUDA.  *out is NULL on failure. */
+mt_status mt_create(const mt_geometry_desc *geometry, const mt_field_desc *field,
+                    const mt_hist_desc *hist, mt_handle **out);
+
+/* Release a handle and its device memory (NULL is a no-op).  The caller must
+ * make sure no launch that uses it is still running. */
+void mt_destroy(mt_handle *h);
+
+/* Device bytes held by the handle (tables + field map). */
+int64_t mt_device_bytes(const mt_handle *h);
+
+/* Transport n muons in place (Algorithm 1), asynchronously on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  For each muon whose status
+ * is MT_ALIVE or MT_MAX_STEPS it runs steps k = steps .. max_steps-1 and stops
+ * at the first break condition; terminal statuses are left untouched.
+ * step_len is d [m].  seed is the 64-bit Philox key.
+ * Errors (returned before anything is enqueued): MT_ERR_INVALID_ARG for a null
+ * handle/soa, null arrays with n > 0, n < 0, non-finite or non-positive
+ * step_len, max_steps < 0; MT_ERR_CUDA if the launch fails. */
+mt_status mt_transport(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len,
+                       int32_t max_steps, uint64_t seed, void *stream);
+
+/* As mt_transport, with the field inside magnet block b scaled component-wise
+ * by alpha[3*b + c] (device, n_block x 3 floats, n_block <= MT_MAX_BOXES);
+ * alpha = NULL is mt_transport.  This is the forward map of the
+ * differentiable form (field-scale parameters of the paper's Discussion). */
+mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len,
+                              int32_t max_steps, uint64_t seed, const float *alpha, int32_t n_block,
+                              void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MT_H */

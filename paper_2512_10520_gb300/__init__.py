@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) histogram-sampling muon transport.
+
+The compute path is the C-ABI library libmt.so (include/mt.h, sources in csrc/);
+this package is its thin Python binding.  Import does not touch the GPU; the
+first call that needs the library loads it and raises if it was not built.
+"""
+from ._binding import (  # noqa: F401
+    MT_ALIVE, MT_STOPPED, MT_EXIT_Z, MT_EXIT_XY, MT_MAX_STEPS, MT_INVALID,
+    MtError, declared_symbols, library_path, load_library,
+    mt_abi_version, mt_last_error, mt_create, mt_destroy, mt_device_bytes,
+    mt_transport, mt_transport_scaled,
+)
+from .api import World, muons_to_device, muons_to_host  # noqa: F401

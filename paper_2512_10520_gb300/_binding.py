@@ -1,0 +1,257 @@
+"""ctypes binding of libmt.so (include/mt.h): argument marshalling only.
+
+Every step of the transport runs in the library's CUDA kernels; this module only
+turns Python/numpy descriptors into the C structs of mt.h and torch device
+tensors into raw pointers.  It raises if libmt.so has not been built: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+from typing import Dict, Optional
+
+import numpy as np
+
+from . import _build
+
+MT_OK, MT_ERR_INVALID_ARG, MT_ERR_CUDA, MT_ERR_OOM, MT_ERR_TIMEOUT, MT_ERR_TABLE, MT_ERR_DEVICE = range(7)
+MT_ALIVE, MT_STOPPED, MT_EXIT_Z, MT_EXIT_XY, MT_MAX_STEPS, MT_INVALID = range(6)
+MT_GEOM_BOXES, MT_GEOM_VOXELS = 0, 1
+MT_FIELD_NONE, MT_FIELD_BOX, MT_FIELD_MAP = 0, 1, 2
+STATUS_NAMES = {0: "MT_OK", 1: "MT_ERR_INVALID_ARG", 2: "MT_ERR_CUDA", 3: "MT_ERR_OOM", 4: "MT_ERR_TIMEOUT",
+                5: "MT_ERR_TABLE", 6: "MT_ERR_DEVICE"}
+
+
+class MtError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mt_box(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("material", C.c_int32),
+                ("block_id", C.c_int32), ("B", C.c_double * 3)]
+
+
+class mt_geometry_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_boxes", C.c_int32), ("boxes", C.POINTER(mt_box)),
+                ("world_material", C.c_int32), ("vox_dims", C.c_int32 * 3), ("vox_origin", C.c_double * 3),
+                ("vox_spacing", C.c_double * 3), ("voxels", C.c_void_p), ("x_max", C.c_double),
+                ("y_max", C.c_double), ("z_max", C.c_double), ("p_min", C.c_double)]
+
+
+class mt_field_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dims", C.c_int32 * 3), ("origin", C.c_double * 3),
+                ("spacing", C.c_double * 3), ("B", C.c_void_p)]
+
+
+class mt_hist_desc(C.Structure):
+    _fields_ = [("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("p_lo", C.c_double), ("p_hi", C.c_double),
+                ("nf", C.c_int32), ("ntheta", C.c_int32), ("weights", C.c_void_p), ("f_max", C.c_void_p),
+                ("theta_max", C.c_void_p)]
+
+
+class mt_muon_soa(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("px", C.c_void_p),
+                ("py", C.c_void_p), ("pz", C.c_void_p), ("q", C.c_void_p), ("steps", C.c_void_p),
+                ("status", C.c_void_p), ("id_offset", C.c_int64), ("instance", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "mt_abi_version": ([], C.c_int32),
+    "mt_last_error": ([], C.c_char_p),
+    "mt_create": ([C.POINTER(mt_geometry_desc), C.POINTER(mt_field_desc), C.POINTER(mt_hist_desc),
+                   C.POINTER(_P)], C.c_int),
+    "mt_destroy": ([_P], None),
+    "mt_device_bytes": ([_P], C.c_int64),
+    "mt_transport": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P], C.c_int),
+    "mt_transport_scaled": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P,
+                             C.c_int32, _P], C.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load_library():
+    """Load libmt.so; raises if it has not been built (call __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise ImportError(f"libmt.so not built at {path}: run `python -c 'import __graft_entry__ as g; "
+                                  f"g.build()'` first (there is no CPU fallback)")
+            L = C.CDLL(path)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def declared_symbols(header: Optional[str] = None):
+    """Names of the functions declared in include/mt.h."""
+    header = header or os.path.join(_build.INCLUDE, "mt.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mt_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int, where: str):
+    if status != MT_OK:
+        msg = load_library().mt_last_error().decode(errors="replace")
+        raise MtError(status, where, msg)
+
+
+def mt_abi_version() -> int:
+    return load_library().mt_abi_version()
+
+
+def mt_last_error() -> str:
+    return load_library().mt_last_error().decode(errors="replace")
+
+
+# --------------------------------------------------------------------------
+# descriptors from workload dicts
+# --------------------------------------------------------------------------
+class _Descs:
+    """C descriptors plus the numpy arrays they point into (kept alive here)."""
+
+    def __init__(self, geometry: dict, field: dict, hist: dict):
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a
+
+        g = mt_geometry_desc()
+        if geometry["kind"] == "boxes":
+            boxes = geometry["boxes"]
+            g.kind = MT_GEOM_BOXES
+            g.n_boxes = len(boxes)
+            arr_t = mt_box * max(1, len(boxes))
+            barr = arr_t()
+            for i, b in enumerate(boxes):
+                barr[i].lo[:] = list(map(float, b["lo"]))
+                barr[i].hi[:] = list(map(float, b["hi"]))
+                barr[i].material = int(b["material"])
+                barr[i].block_id = int(b.get("block_id", -1))
+                barr[i].B[:] = list(map(float, b.get("B", [0.0, 0.0, 0.0])))
+            keep.append(barr)
+            g.boxes = C.cast(barr, C.POINTER(mt_box))
+        elif geometry["kind"] == "voxels":
+            vox = arr(geometry["voxels"], np.uint8)
+            nz, ny, nx = vox.shape
+            g.kind = MT_GEOM_VOXELS
+            g.vox_dims[:] = [nx, ny, nz]
+            g.vox_origin[:] = list(map(float, geometry["origin"]))
+            g.vox_spacing[:] = list(map(float, geometry["spacing"]))
+            g.voxels = vox.ctypes.data
+        else:
+            raise ValueError(geometry["kind"])
+        g.world_material = int(geometry["world_material"])
+        g.x_max, g.y_max, g.z_max = (float(geometry[k]) for k in ("x_max", "y_max", "z_max"))
+        g.p_min = float(geometry["p_min"])
+
+        f = mt_field_desc()
+        kind = field["kind"]
+        f.kind = {"none": MT_FIELD_NONE, "box": MT_FIELD_BOX, "map": MT_FIELD_MAP}[kind]
+        if kind == "map":
+            B = arr(field["B"], np.float32)
+            f.dims[:] = list(map(int, field["dims"]))
+            f.origin[:] = list(map(float, field["origin"]))
+            f.spacing[:] = list(map(float, field["spacing"]))
+            f.B = B.ctypes.data
+
+        h = mt_hist_desc()
+        h.n_mat, h.n_pbin = int(hist["n_mat"]), int(hist["n_pbin"])
+        h.p_lo, h.p_hi = float(hist["p_lo"]), float(hist["p_hi"])
+        h.nf, h.ntheta = int(hist["nf"]), int(hist["ntheta"])
+        h.weights = arr(hist["weights"], np.float64).ctypes.data
+        h.f_max = arr(hist["f_max"], np.float64).ctypes.data
+        h.theta_max = arr(hist["theta_max"], np.float64).ctypes.data
+        self.g, self.f, self.h = g, f, h
+        self._keep = keep
+
+
+def mt_create(geometry: dict, field: dict, hist: dict) -> int:
+    """Build a device-resident world on the current CUDA device; returns the handle (int)."""
+    L = load_library()
+    d = _Descs(geometry, field, hist)
+    out = C.c_void_p()
+    _check(L.mt_create(C.byref(d.g), C.byref(d.f), C.byref(d.h), C.byref(out)), "mt_create")
+    return out.value
+
+
+def mt_destroy(handle: Optional[int]) -> None:
+    if handle:
+        load_library().mt_destroy(C.c_void_p(handle))
+
+
+def mt_device_bytes(handle: int) -> int:
+    return load_library().mt_device_bytes(C.c_void_p(handle))
+
+
+SOA_FIELDS = ("x", "y", "z", "px", "py", "pz", "q", "steps", "status")
+SOA_DTYPES = dict(x="float32", y="float32", z="float32", px="float32", py="float32", pz="float32", q="int8",
+                  steps="int32", status="uint8")
+
+
+def soa_struct(muons: Dict, id_offset: int = 0, instance: int = 0) -> mt_muon_soa:
+    """mt_muon_soa over torch CUDA tensors (contiguous, dtypes of mt.h)."""
+    s = mt_muon_soa()
+    for k in SOA_FIELDS:
+        t = muons[k]
+        if str(t.dtype).replace("torch.", "") != SOA_DTYPES[k]:
+            raise TypeError(f"muon field {k}: dtype {t.dtype}, want {SOA_DTYPES[k]}")
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"muon field {k} must be a contiguous CUDA tensor")
+        setattr(s, k, t.data_ptr())
+    s.id_offset = int(id_offset)
+    s.instance = int(instance)
+    return s
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def mt_transport(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, id_offset: int = 0,
+                 instance: int = 0, stream=None, n: Optional[int] = None) -> None:
+    """Transport the muons (dict of CUDA tensors, updated in place) on `stream`."""
+    s = soa_struct(muons, id_offset, instance)
+    n = int(muons["x"].numel()) if n is None else int(n)
+    _check(load_library().mt_transport(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(_stream_ptr(stream))),
+           "mt_transport")
+
+
+def mt_transport_scaled(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, alpha,
+                        id_offset: int = 0, instance: int = 0, stream=None) -> None:
+    """mt_transport with per-block field scales alpha (CUDA float32 tensor [n_block, 3] or None)."""
+    s = soa_struct(muons, id_offset, instance)
+    n = int(muons["x"].numel())
+    if alpha is not None:
+        if not alpha.is_cuda or str(alpha.dtype) != "torch.float32" or not alpha.is_contiguous():
+            raise TypeError("alpha must be a contiguous float32 CUDA tensor")
+        a_ptr, nb = alpha.data_ptr(), alpha.numel() // 3
+    else:
+        a_ptr, nb = None, 0
+    _check(load_library().mt_transport_scaled(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
+                                              int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr), int(nb),
+                                              C.c_void_p(_stream_ptr(stream))), "mt_transport_scaled")

@@ -1,0 +1,74 @@
+"""Owning wrappers around the binding: a World (one mt_handle) and SoA transfers."""
+from __future__ import annotations
+
+from typing import Dict, Optional
+
+import numpy as np
+
+from . import _binding as B
+
+
+class World:
+    """A device-resident world (geometry, field map, sampling tables) = one mt_handle."""
+
+    def __init__(self, geometry: dict, field: dict, hist: dict):
+        self.handle = B.mt_create(geometry, field, hist)
+
+    @classmethod
+    def from_workload(cls, wl) -> "World":
+        return cls(wl.geometry, wl.field, wl.hist)
+
+    @property
+    def device_bytes(self) -> int:
+        return B.mt_device_bytes(self.handle)
+
+    def transport(self, muons: Dict, step_len: float, max_steps: int, seed: int, id_offset: int = 0,
+                  instance: int = 0, alpha=None, stream=None) -> None:
+        if alpha is None:
+            B.mt_transport(self.handle, muons, step_len, max_steps, seed, id_offset, instance, stream)
+        else:
+            B.mt_transport_scaled(self.handle, muons, step_len, max_steps, seed, alpha, id_offset, instance,
+                                  stream)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            B.mt_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def muons_to_device(soa: Dict[str, np.ndarray], device="cuda", pin: bool = False) -> Dict:
+    """Copy a numpy SoA (fields of mt_muon_soa) to CUDA tensors."""
+    import torch
+    out = {}
+    for k in B.SOA_FIELDS:
+        t = torch.from_numpy(np.ascontiguousarray(soa[k], dtype=B.SOA_DTYPES[k]))
+        out[k] = t.to(device, non_blocking=pin)
+    return out
+
+
+def muons_to_host(dev: Dict) -> Dict[str, np.ndarray]:
+    return {k: dev[k].cpu().numpy() for k in B.SOA_FIELDS}
+
+
+def empty_like_soa(n: int, device="cuda", pinned: bool = False) -> Dict:
+    import torch
+    out = {}
+    for k in B.SOA_FIELDS:
+        dt = getattr(torch, B.SOA_DTYPES[k])
+        if device == "cpu":
+            out[k] = torch.empty(n, dtype=dt, pin_memory=pinned)
+        else:
+            out[k] = torch.empty(n, dtype=dt, device=device)
+    return out

@@ -1,0 +1,376 @@
+// api.cu -- host side of libmt: descriptor validation, sampling-table
+// construction and the device-resident world (mt_create / mt_destroy).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mt_internal.cuh"
+
+namespace mt {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+mt_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MT_ERR_OOM : MT_ERR_CUDA;
+}
+
+// Defined in transport.cu: repack a [nz][ny][nx][3] map into x-adjacent node pairs.
+cudaError_t launch_repack_field(const float *raw, float4 *pairs, int nx, int ny, int nz, cudaStream_t st);
+
+static void split(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+static bool finite3(const double v[3])
+{
+    return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+// Sampling tables of one histogram set (cells are encoded as (a << 16) | b with
+// a the f bin and b the theta bin).  T_j = floor(2^32 S_j / S_total) with S_j
+// the left-to-right FP64 prefix sum; the selectable cells (T_{c-1} < T_c) with
+// their upper thresholds U_k form the pair list; the guide table over the
+// 2^gbits equal slices of the draw space stores either the answer cell (when
+// no threshold falls inside the slice) or the pair range to search.
+static mt_status build_tables(const mt_hist_desc *h, int gbits, std::vector<HistRec> &rec,
+                              std::vector<uint32_t> &guide, std::vector<uint2> &pairs)
+{
+    const int ncell = h->nf * h->ntheta;
+    const int64_t n_hist = (int64_t)h->n_mat * h->n_pbin;
+    const int G = 1 << gbits;
+    const int shift = 32 - gbits;
+    std::vector<uint64_t> T(ncell);
+    std::vector<uint64_t> U;
+    std::vector<uint32_t> cells;
+    rec.resize(n_hist);
+    guide.resize((size_t)n_hist * G);
+    pairs.clear();
+    for (int64_t hi = 0; hi < n_hist; ++hi) {
+        const double *w = h->weights + hi * ncell;
+        double total = 0.0;
+        for (int j = 0; j < ncell; ++j) {
+            if (!(w[j] >= 0.0) || !std::isfinite(w[j])) {
+                set_error("histogram %lld cell %d: weight %g is negative or not finite", (long long)hi, j, w[j]);
+                return MT_ERR_TABLE;
+            }
+            total += w[j];
+        }
+        if (!(total > 0.0) || !std::isfinite(total)) {
+            set_error("histogram %lld has no positive finite mass", (long long)hi);
+            return MT_ERR_TABLE;
+        }
+        double S = 0.0;
+        for (int j = 0; j < ncell - 1; ++j) {
+            S += w[j];
+            T[j] = (uint64_t)std::floor(S / total * 4294967296.0);
+        }
+        T[ncell - 1] = 1ull << 32;
+        U.clear();
+        cells.clear();
+        uint64_t prev = 0;
+        for (int c = 0; c < ncell; ++c) {
+            if (T[c] > prev) {
+                U.push_back(T[c]);
+                cells.push_back(((uint32_t)(c / h->ntheta) << 16) | (uint32_t)(c % h->ntheta));
+            }
+            prev = T[c] > prev ? T[c] : prev;
+        }
+        const int m = (int)cells.size();
+        rec[hi].pair_off = (uint32_t)pairs.size();
+        rec[hi].guide_off = (uint32_t)(hi * G);
+        const double fm = h->f_max[hi], tm = h->theta_max[hi];
+        rec[hi].fscale = (float)(fm / h->nf);
+        rec[hi].tscale = (float)(tm / h->ntheta);
+        for (int k = 0; k < m; ++k)
+            pairs.push_back(make_uint2((uint32_t)(U[k] > 0xFFFFFFFFull ? 0xFFFFFFFFull : U[k]), cells[k]));
+        int lo = 0;
+        for (int g = 0; g < G; ++g) {
+            const uint64_t start = (uint64_t)g << shift;
+            const uint64_t last = (((uint64_t)g + 1) << shift) - 1;
+            while (lo < m - 1 && U[lo] < start) ++lo;
+            int hi2 = lo;
+            while (hi2 < m - 1 && U[hi2] <= last) ++hi2;
+            uint32_t e;
+            if (hi2 == lo)
+                e = cells[lo];
+            else
+                e = 0x80000000u | (uint32_t)lo | ((uint32_t)(hi2 - lo) << 15);
+            guide[(size_t)hi * G + g] = e;
+        }
+    }
+    return MT_OK;
+}
+
+static mt_status validate(const mt_geometry_desc *g, const mt_field_desc *f, const mt_hist_desc *h)
+{
+    if (!g || !f || !h) {
+        set_error("null descriptor");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h->n_mat < 1 || h->n_mat > MT_MAX_MATERIALS || h->n_pbin < 1 || h->n_pbin > MT_MAX_PBINS) {
+        set_error("hist: n_mat %d / n_pbin %d out of range", h->n_mat, h->n_pbin);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h->nf < 1 || h->ntheta < 1 || (int64_t)h->nf * h->ntheta < 2 || (int64_t)h->nf * h->ntheta > MT_MAX_CELLS) {
+        set_error("hist: nf*ntheta = %lld outside [2, %d]", (long long)h->nf * h->ntheta, MT_MAX_CELLS);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (!(h->p_lo > 0.0) || !(h->p_hi > h->p_lo) || !std::isfinite(h->p_hi)) {
+        set_error("hist: need 0 < p_lo < p_hi");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (!h->weights || !h->f_max || !h->theta_max) {
+        set_error("hist: null array");
+        return MT_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < (int64_t)h->n_mat * h->n_pbin; ++i)
+        if (!(h->f_max[i] > 0.0) || !(h->theta_max[i] > 0.0) || !std::isfinite(h->f_max[i]) ||
+            !std::isfinite(h->theta_max[i])) {
+            set_error("hist: f_max/theta_max[%lld] must be positive and finite", (long long)i);
+            return MT_ERR_INVALID_ARG;
+        }
+    if (!(g->x_max > 0.0) || !(g->y_max > 0.0) || std::isnan(g->z_max) || !(g->p_min >= 0.0) ||
+        !std::isfinite(g->p_min)) {
+        set_error("geometry: bad world bounds or p_min");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (g->world_material < 0 || g->world_material > h->n_mat) {
+        set_error("geometry: world material %d outside [0, %d]", g->world_material, h->n_mat);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (g->kind == MT_GEOM_BOXES) {
+        if (g->n_boxes < 0 || g->n_boxes > MT_MAX_BOXES || (g->n_boxes > 0 && !g->boxes)) {
+            set_error("geometry: n_boxes %d outside [0, %d] or null boxes", g->n_boxes, MT_MAX_BOXES);
+            return MT_ERR_INVALID_ARG;
+        }
+        for (int b = 0; b < g->n_boxes; ++b) {
+            const mt_box &bx = g->boxes[b];
+            if (!finite3(bx.lo) || !finite3(bx.hi) || !finite3(bx.B) || bx.material < 0 ||
+                bx.material > h->n_mat || bx.block_id < -1 || bx.block_id >= MT_MAX_BOXES) {
+                set_error("geometry: box %d invalid (material %d, block %d)", b, bx.material, bx.block_id);
+                return MT_ERR_INVALID_ARG;
+            }
+        }
+    } else if (g->kind == MT_GEOM_VOXELS) {
+        if (!g->voxels || g->vox_dims[0] < 1 || g->vox_dims[1] < 1 || g->vox_dims[2] < 1 ||
+            !finite3(g->vox_origin) || !(g->vox_spacing[0] > 0) || !(g->vox_spacing[1] > 0) ||
+            !(g->vox_spacing[2] > 0)) {
+            set_error("geometry: bad voxel grid");
+            return MT_ERR_INVALID_ARG;
+        }
+        const int64_t nv = (int64_t)g->vox_dims[0] * g->vox_dims[1] * g->vox_dims[2];
+        for (int64_t i = 0; i < nv; ++i)
+            if (g->voxels[i] > h->n_mat) {
+                set_error("geometry: voxel %lld material %d > n_mat", (long long)i, g->voxels[i]);
+                return MT_ERR_INVALID_ARG;
+            }
+    } else {
+        set_error("geometry: unknown kind %d", g->kind);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (f->kind == MT_FIELD_MAP) {
+        if (!f->B || f->dims[0] < 2 || f->dims[1] < 2 || f->dims[2] < 2 || !finite3(f->origin) ||
+            !(f->spacing[0] > 0) || !(f->spacing[1] > 0) || !(f->spacing[2] > 0)) {
+            set_error("field: bad map (dims >= 2, spacing > 0, B non-null)");
+            return MT_ERR_INVALID_ARG;
+        }
+        const int64_t nv = 3ll * f->dims[0] * f->dims[1] * f->dims[2];
+        for (int64_t i = 0; i < nv; ++i)
+            if (!std::isfinite(f->B[i])) {
+                set_error("field: non-finite value at %lld", (long long)i);
+                return MT_ERR_INVALID_ARG;
+            }
+    } else if (f->kind == MT_FIELD_BOX) {
+        if (g->kind != MT_GEOM_BOXES) {
+            set_error("field: per-box field needs box geometry");
+            return MT_ERR_INVALID_ARG;
+        }
+    } else if (f->kind != MT_FIELD_NONE) {
+        set_error("field: unknown kind %d", f->kind);
+        return MT_ERR_INVALID_ARG;
+    }
+    return MT_OK;
+}
+
+template <class T>
+static mt_status upload(void *&dst, const T *src, size_t count, int64_t &bytes, const char *what)
+{
+    size_t nb = count * sizeof(T);
+    if (nb == 0) nb = sizeof(T);
+    cudaError_t e = cudaMalloc(&dst, nb);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    bytes += (int64_t)nb;
+    if (count) {
+        e = cudaMemcpy(dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+    return MT_OK;
+}
+
+}  // namespace mt
+
+using namespace mt;
+
+extern "C" {
+
+int32_t mt_abi_version(void) { return MT_ABI_VERSION; }
+
+const char *mt_last_error(void) { return g_err; }
+
+void mt_destroy(mt_handle *h)
+{
+    if (!h) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    void *bufs[] = {h->d_boxes, h->d_hist, h->d_guide, h->d_pairs, h->d_e2, h->d_fmap, h->d_vox};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete h;
+}
+
+int64_t mt_device_bytes(const mt_handle *h) { return h ? h->bytes : 0; }
+
+mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_hist_desc *hd, mt_handle **out)
+{
+    g_err[0] = 0;
+    if (!out) {
+        set_error("null output pointer");
+        return MT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    mt_status st = validate(g, f, hd);
+    if (st != MT_OK) return st;
+
+    const int ncell = hd->nf * hd->ntheta;
+    int gbits = 12;
+    while ((1 << gbits) < ncell && gbits < 15) ++gbits;   // at least one guide slot per cell up to 32K
+    std::vector<HistRec> rec;
+    std::vector<uint32_t> guide;
+    std::vector<uint2> pairs;
+    st = build_tables(hd, gbits, rec, guide, pairs);
+    if (st != MT_OK) return st;
+
+    mt_handle *h = new mt_handle();
+    cudaGetDevice(&h->device);
+    WorldParams &w = h->w;
+    memset(&w, 0, sizeof(w));
+    w.geom_kind = g->kind;
+    w.world_mat = g->world_material;
+    w.n_mat = hd->n_mat;
+    split(g->x_max, w.xmax_hi, w.xmax_lo);
+    split(g->y_max, w.ymax_hi, w.ymax_lo);
+    split(g->z_max, w.zmax_hi, w.zmax_lo);
+    w.pmin2 = (float)(g->p_min * g->p_min);
+
+#define MT_TRY(expr)              \
+    do {                          \
+        mt_status s_ = (expr);    \
+        if (s_ != MT_OK) {        \
+            mt_destroy(h);        \
+            return s_;            \
+        }                         \
+    } while (0)
+
+    if (g->kind == MT_GEOM_BOXES) {
+        std::vector<DevBox> boxes(g->n_boxes);
+        for (int b = 0; b < g->n_boxes; ++b) {
+            const mt_box &s = g->boxes[b];
+            DevBox &d = boxes[b];
+            for (int a = 0; a < 3; ++a) {
+                split(s.lo[a], d.lo_hi[a], d.lo_lo[a]);
+                split(s.hi[a], d.hi_hi[a], d.hi_lo[a]);
+                d.B[a] = (float)s.B[a];
+            }
+            d.material = s.material;
+            d.block = s.block_id;
+            d.pad = 0;
+        }
+        w.n_box = g->n_boxes;
+        MT_TRY(upload(h->d_boxes, boxes.data(), boxes.size(), h->bytes, "boxes"));
+        w.boxes = (const DevBox *)h->d_boxes;
+    } else {
+        const size_t nv = (size_t)g->vox_dims[0] * g->vox_dims[1] * g->vox_dims[2];
+        MT_TRY(upload(h->d_vox, g->voxels, nv, h->bytes, "voxels"));
+        w.vox = (const uint8_t *)h->d_vox;
+        for (int a = 0; a < 3; ++a) {
+            w.vdims[a] = g->vox_dims[a];
+            split(g->vox_origin[a], w.vorigin[a], w.vorigin_lo[a]);
+            split(g->vox_spacing[a], w.vspacing[a], w.vspacing_lo[a]);
+            w.vinv[a] = (float)(1.0 / g->vox_spacing[a]);
+        }
+    }
+
+    w.field_kind = f->kind;
+    if (f->kind == MT_FIELD_MAP) {
+        const int nx = f->dims[0], ny = f->dims[1], nz = f->dims[2];
+        const size_t nraw = 3ull * nx * ny * nz;
+        const size_t npair = 2ull * (size_t)(nx - 1) * ny * nz;
+        void *raw = nullptr;
+        cudaError_t e = cudaMalloc(&raw, nraw * sizeof(float));
+        if (e != cudaSuccess) {
+            mt_destroy(h);
+            return cuda_fail(e, "field staging");
+        }
+        e = cudaMemcpy(raw, f->B, nraw * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_fmap, npair * sizeof(float4));
+        if (e == cudaSuccess) {
+            h->bytes += (int64_t)(npair * sizeof(float4));
+            e = launch_repack_field((const float *)raw, (float4 *)h->d_fmap, nx, ny, nz, 0);
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(raw);
+        if (e != cudaSuccess) {
+            mt_destroy(h);
+            return cuda_fail(e, "field map upload");
+        }
+        w.fmap = (const float4 *)h->d_fmap;
+        for (int a = 0; a < 3; ++a) {
+            w.fdims[a] = f->dims[a];
+            w.forigin[a] = (float)f->origin[a];
+            w.finv[a] = (float)(1.0 / f->spacing[a]);
+        }
+    }
+
+    MT_TRY(upload(h->d_hist, rec.data(), rec.size(), h->bytes, "histogram records"));
+    MT_TRY(upload(h->d_guide, guide.data(), guide.size(), h->bytes, "guide tables"));
+    MT_TRY(upload(h->d_pairs, pairs.data(), pairs.size(), h->bytes, "threshold pairs"));
+    std::vector<float2> e2(hd->n_pbin + 1);
+    for (int k = 0; k <= hd->n_pbin; ++k) {
+        const double E = hd->p_lo * std::pow(hd->p_hi / hd->p_lo, (double)k / hd->n_pbin);
+        float a, b;
+        split(E * E, a, b);
+        e2[k] = make_float2(a, b);
+    }
+    MT_TRY(upload(h->d_e2, e2.data(), e2.size(), h->bytes, "bin edges"));
+#undef MT_TRY
+    w.hist = (const HistRec *)h->d_hist;
+    w.guide = (const uint32_t *)h->d_guide;
+    w.pairs = (const uint2 *)h->d_pairs;
+    w.e2 = (const float2 *)h->d_e2;
+    w.n_pbin = hd->n_pbin;
+    w.nf = hd->nf;
+    w.ntheta = hd->ntheta;
+    w.gshift = 32 - gbits;
+    w.log2_plo = (float)std::log2(hd->p_lo);
+    w.pbin_scale = (float)(hd->n_pbin / std::log2(hd->p_hi / hd->p_lo));
+    *out = h;
+    return MT_OK;
+}
+
+}  // extern "C"

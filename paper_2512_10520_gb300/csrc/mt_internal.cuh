@@ -1,0 +1,104 @@
+// mt_internal.cuh -- device data layout and handle of libmt (CUDA path only).
+//
+// HBM layout of one world (all built once by mt_create):
+//   boxes   : DevBox[n_box]          float hi/lo pairs of every face, material, block, B
+//   hist    : HistRec[n_mat*n_pbin]  per histogram: guide/pair offsets and jitter scales
+//   guide   : u32[n_hist << gbits]   Chen-Asau guide table over the 32-bit draw space
+//   pairs   : uint2[sum m_h]         (upper threshold, cell) of the selectable cells
+//   e2      : float2[n_pbin+1]       squared log10 bin edges as (hi, lo) float pairs
+//   fmap    : float4[nz][ny][nx-1][2] x-adjacent node pairs (Bx,By,Bz,0 | Bx,By,Bz,0)
+//   vox     : u8[nz][ny][nx]         voxel materials
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mt.h"
+
+namespace mt {
+
+constexpr float kKappa = 0.299792458f;   // GeV / (T m)
+
+struct DevBox {
+    float lo_hi[3], lo_lo[3];
+    float hi_hi[3], hi_lo[3];
+    float B[3];
+    int32_t material;
+    int32_t block;
+    int32_t pad;
+};
+
+// Guide entry: bit 31 clear -> the answer cell; set -> binary search over
+// pairs[lo .. lo+span] with lo = bits 0..14 and span = bits 15..29.
+struct HistRec {
+    uint32_t guide_off;
+    uint32_t pair_off;
+    float fscale;     // f_max / nf
+    float tscale;     // theta_max / ntheta
+};
+
+struct WorldParams {
+    // geometry
+    int32_t geom_kind;
+    int32_t n_box;
+    int32_t world_mat;
+    int32_t n_mat;
+    const DevBox *boxes;
+    const uint8_t *vox;
+    int32_t vdims[3];
+    float vorigin[3];
+    float vinv[3];
+    float vorigin_lo[3];
+    float vspacing[3];
+    float vspacing_lo[3];
+    float xmax_hi, xmax_lo, ymax_hi, ymax_lo, zmax_hi, zmax_lo;
+    float pmin2;
+    // field
+    int32_t field_kind;
+    const float4 *fmap;
+    int32_t fdims[3];
+    float forigin[3];
+    float finv[3];
+    // histograms
+    const HistRec *hist;
+    const uint32_t *guide;
+    const uint2 *pairs;
+    const float2 *e2;
+    int32_t n_pbin;
+    int32_t nf;
+    int32_t ntheta;
+    int32_t gshift;
+    float log2_plo;
+    float pbin_scale;   // n_pbin / log2(p_hi / p_lo)
+};
+
+struct RunParams {
+    float d;
+    int32_t max_steps;
+    uint32_t key0, key1;
+    const float *alpha;   // device [n_block][3] or null
+    int32_t n_block;
+    int32_t instance;
+    int64_t id_offset;
+};
+
+}  // namespace mt
+
+struct mt_handle {
+    int device;
+    mt::WorldParams w;
+    // owned device allocations
+    void *d_boxes = nullptr;
+    void *d_hist = nullptr;
+    void *d_guide = nullptr;
+    void *d_pairs = nullptr;
+    void *d_e2 = nullptr;
+    void *d_fmap = nullptr;
+    void *d_vox = nullptr;
+    int64_t bytes = 0;
+};
+
+namespace mt {
+void set_error(const char *fmt, ...);
+mt_status cuda_fail(cudaError_t e, const char *what);
+}  // namespace mt

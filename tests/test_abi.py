@@ -1,0 +1,81 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads without a GPU,
+exports every function include/mt.h declares, and rejects bad arguments on the
+host before touching the device."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_2512_10520_gb300 as mt
+from paper_2512_10520_gb300 import _binding as B
+from paper_2512_10520_gb300 import _build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return mt.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = mt.declared_symbols()
+    assert {"mt_create", "mt_transport", "mt_destroy", "mt_last_error"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_abi_version(lib):
+    assert mt.mt_abi_version() == 1
+
+
+def _descs(weights=None):
+    from workloads import gen
+    h = gen.histogram_set(["iron"], n_pbin=2, nf=4, ntheta=4, n_samples=1000, cache=False)
+    if weights is not None:
+        h["weights"] = weights
+    geo = gen.geometry_config0()
+    geo["boxes"][0]["material"] = 1
+    geo["world_material"] = 0
+    return geo, dict(kind="box"), h
+
+
+def test_create_rejects_bad_tables_on_host(lib):
+    geo, fld, h = _descs()
+    w = h["weights"].copy()
+    w[0, 1, 2, 3] = -1.0
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_create(geo, fld, dict(h, weights=w))
+    assert e.value.status == B.MT_ERR_TABLE
+    w = h["weights"].copy()
+    w[0, 0] = 0.0
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_create(geo, fld, dict(h, weights=w))
+    assert e.value.status == B.MT_ERR_TABLE and "no positive" in mt.mt_last_error()
+
+
+def test_create_rejects_bad_descriptors_on_host(lib):
+    geo, fld, h = _descs()
+    bad = dict(geo, world_material=7)
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_create(bad, fld, h)
+    assert e.value.status == B.MT_ERR_INVALID_ARG
+    with pytest.raises(mt.MtError):
+        mt.mt_create(geo, fld, dict(h, p_lo=5.0, p_hi=1.0))
+    with pytest.raises(mt.MtError):
+        mt.mt_create(dict(geo, kind="boxes", boxes=geo["boxes"] * 40), fld, h)
+    out = C.c_void_p()
+    assert lib.mt_create(None, None, None, C.byref(out)) == B.MT_ERR_INVALID_ARG
+    assert out.value is None
+
+
+def test_transport_rejects_bad_arguments_on_host(lib):
+    s = B.mt_muon_soa()
+    assert lib.mt_transport(None, C.byref(s), 10, 0.02, 10, 1, None) == B.MT_ERR_INVALID_ARG
+    assert "null handle" in mt.mt_last_error()
+    mt.mt_destroy(None)
+
+
+def test_declared_symbols_parser_sees_comments_removed():
+    names = mt.declared_symbols()
+    assert all(n.startswith("mt_") for n in names)
+    assert "mt_status" not in names and "mt_box" not in names

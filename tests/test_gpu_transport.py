@@ -1,0 +1,193 @@
+"""GPU parity of the plain transport (mt_transport through the C ABI) against the
+FP64 oracle: per muon (position 1e-4 m, momentum 1e-5 relative, identical
+step count and status for >= 99.9 % of muons) and in distribution (two-sample
+KS on final x, y, |p|), plus closed forms, edge cases and launch invariance."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from helpers import PASS_FRAC, compare, describe, gpu_transport
+from workloads import gen
+
+pytestmark = pytest.mark.gpu
+
+KAPPA = 0.299792458
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_10520_gb300 as mt
+    mt.load_library()
+
+
+@pytest.fixture(scope="module")
+def wl0():
+    return gen.workload("config0")
+
+
+@pytest.fixture(scope="module")
+def wl1_small():
+    return gen.workload("config1", n=20000)
+
+
+def test_config0_full_parity(wl0):
+    ora = oracle.transport(oracle.world_of(wl0), wl0.muons, wl0.step_len, wl0.max_steps, wl0.seed)
+    gpu = gpu_transport(wl0)
+    ok, err = compare(gpu, ora)
+    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+
+
+def test_config1_subset_parity_and_ks(wl1_small):
+    ora = oracle.transport(oracle.world_of(wl1_small), wl1_small.muons, wl1_small.step_len,
+                           wl1_small.max_steps, wl1_small.seed)
+    gpu = gpu_transport(wl1_small)
+    ok, err = compare(gpu, ora)
+    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    for k in ("x", "y"):
+        assert stats.ks_2samp(gpu[k], ora[k]).pvalue > 0.01, k
+    pg = np.sqrt(gpu["px"].astype(np.float64) ** 2 + gpu["py"] ** 2 + gpu["pz"] ** 2)
+    po = np.sqrt(ora["px"] ** 2 + ora["py"] ** 2 + ora["pz"] ** 2)
+    assert stats.ks_2samp(pg, po).pvalue > 0.01
+
+
+def test_config1_full_size_sampled_parity():
+    """The full 1e6-muon workload in the benchmark's launch configuration; the
+    oracle recomputes a spread sample of muon ids one by one."""
+    wl = gen.workload("config1")
+    gpu = gpu_transport(wl)
+    idx = np.unique(np.linspace(0, wl.n - 1, 1500).astype(np.int64))
+    ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed, index=idx)
+    ok, err = compare(gpu, ora, idx)
+    assert ok.mean() >= 0.998, describe(ok, err)
+    # every muon ends in a valid terminal state
+    assert set(np.unique(gpu["status"])) <= {1, 2, 3, 4}
+    assert gpu["steps"].max() <= wl.max_steps
+
+
+def test_chunking_resume_and_offsets_are_bit_identical(wl0):
+    full = gpu_transport(wl0)
+    chunked = gpu_transport(wl0, chunks=7)
+    part = gpu_transport(wl0, max_steps=77)
+    rest = gpu_transport(wl0, muons=part)
+    for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+        np.testing.assert_array_equal(full[k], chunked[k])
+    # resuming re-enters from the FP32 state (the hi + lo split restarts), so the
+    # resumed run matches to rounding, with identical steps and statuses
+    ok, err = compare(rest, {k: np.asarray(full[k], np.float64) for k in full})
+    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+
+
+def _vacuum_workload(n, field, boxes=(), max_steps=400, z_max=1e5, xy=1e5, world_mat=0, seed=3):
+    h = gen.histogram_set(["iron"], n_pbin=8, nf=16, ntheta=8, n_samples=20000, cache=False)
+    geo = dict(kind="boxes", boxes=list(boxes), world_material=world_mat, x_max=xy, y_max=xy, z_max=z_max,
+               p_min=0.5)
+    mu = gen.muons_config0(n, seed=seed)
+    return gen.Workload("vac", geo, field, h, mu, 0.02, max_steps, 11)
+
+
+def test_straight_lines_in_vacuum():
+    wl = _vacuum_workload(1000, dict(kind="none"), max_steps=250)
+    gpu = gpu_transport(wl)
+    mu = wl.muons
+    p = np.stack([mu["px"], mu["py"], mu["pz"]], 1).astype(np.float64)
+    u = p / np.linalg.norm(p, axis=1, keepdims=True)
+    r0 = np.stack([mu["x"], mu["y"], mu["z"]], 1).astype(np.float64)
+    r = np.stack([gpu["x"], gpu["y"], gpu["z"]], 1)
+    np.testing.assert_allclose(r, r0 + 250 * 0.02 * u, atol=2e-6)
+    np.testing.assert_allclose(np.stack([gpu["px"], gpu["py"], gpu["pz"]], 1), p, rtol=1e-6, atol=1e-7)
+    assert (gpu["steps"] == 250).all() and (gpu["status"] == 4).all()
+
+
+def test_helix_in_uniform_field():
+    B = 1.3
+    box = dict(lo=[-1e4, -1e4, -1e4], hi=[1e4, 1e4, 1e4], material=0, block_id=-1, B=[0.0, 0.0, B])
+    wl = _vacuum_workload(2000, dict(kind="box"), boxes=[box], max_steps=1500)
+    gpu = gpu_transport(wl)
+    mu = wl.muons
+    for m in range(0, 2000, 97):
+        px, py, pz = (float(mu[k][m]) for k in ("px", "py", "pz"))
+        q = int(mu["q"][m])
+        P = math.sqrt(px * px + py * py + pz * pz)
+        s = 1500 * 0.02
+        w = KAPPA * q * B / P
+        c, sn = math.cos(w * s), math.sin(w * s)
+        # rotation of (px, py) by angle -w s about z
+        pxe, pye = px * c + py * sn, -px * sn + py * c
+        xe = float(mu["x"][m]) + (px * sn - py * (c - 1.0)) / (P * w)
+        ye = float(mu["y"][m]) + (py * sn + px * (c - 1.0)) / (P * w)
+        ze = float(mu["z"][m]) + s * pz / P
+        assert abs(gpu["x"][m] - xe) < 1e-4 and abs(gpu["y"][m] - ye) < 1e-4 and abs(gpu["z"][m] - ze) < 1e-4
+        assert abs(gpu["px"][m] - pxe) < 1e-5 * P and abs(gpu["py"][m] - pye) < 1e-5 * P
+        Pg = math.sqrt(float(gpu["px"][m]) ** 2 + float(gpu["py"][m]) ** 2 + float(gpu["pz"][m]) ** 2)
+        assert abs(Pg / P - 1.0) < 1e-6
+
+
+def test_edge_cases_empty_ragged_terminal_invalid(wl0):
+    import paper_2512_10520_gb300 as mt
+    import torch
+    with mt.World.from_workload(wl0) as world:
+        empty = mt.muons_to_device({k: v[:0] for k, v in wl0.muons.items()})
+        world.transport(empty, 0.02, 10, 1)
+        mu = {k: v[:257].copy() for k, v in wl0.muons.items()}
+        mu["status"][3] = 1
+        mu["status"][4] = 3
+        mu["steps"][5] = 500            # beyond max_steps: nothing runs
+        mu["y"][6] = np.nan
+        mu["status"][7] = 4             # MAX_STEPS is resumable
+        dev = mt.muons_to_device(mu)
+        world.transport(dev, wl0.step_len, wl0.max_steps, wl0.seed)
+        torch.cuda.synchronize()
+        out = mt.muons_to_host(dev)
+    ora = oracle.transport(oracle.world_of(wl0), mu, wl0.step_len, wl0.max_steps, wl0.seed)
+    ok, err = compare(out, ora)
+    assert ok.all(), describe(ok, err)
+    assert out["status"][3] == 1 and out["x"][3] == mu["x"][3]
+    assert out["status"][4] == 3 and out["steps"][4] == mu["steps"][4]
+    assert out["steps"][5] == 500 and out["status"][5] == 4
+    assert out["status"][6] == 5 and out["steps"][6] == 0
+
+
+def test_invalid_arguments_return_status():
+    import paper_2512_10520_gb300 as mt
+    wl = _vacuum_workload(4, dict(kind="none"))
+    with mt.World.from_workload(wl) as world:
+        dev = mt.muons_to_device(wl.muons)
+        with pytest.raises(mt.MtError):
+            mt.mt_transport(world.handle, dev, -0.02, 10, 1)
+        with pytest.raises(mt.MtError):
+            mt.mt_transport(world.handle, dev, 0.02, -1, 1)
+
+
+def test_voxel_geometry_with_map_parity():
+    h = gen.histogram_set(["iron", "air", "concrete"], n_pbin=16, nf=32, ntheta=16, n_samples=50000, cache=False)
+    vox = np.full((64, 16, 16), 2, np.uint8)          # [nz][ny][nx], air
+    vox[8:24, 4:12, 4:12] = 1                           # iron
+    vox[30:40, :, :] = 3                                # concrete wall
+    vox[45:50, 6:10, 6:10] = 0                          # a vacuum pocket
+    geo = dict(kind="voxels", voxels=vox, origin=[-0.8, -0.8, 0.0], spacing=[0.1, 0.1, 0.05],
+               world_material=2, x_max=1.0, y_max=1.0, z_max=3.3, p_min=0.5)
+    fld = gen.field_map_config1(nx=20, ny=20, nz=40, z_lo=-0.1, z_hi=3.3, half_xy=1.0,
+                                magnet_z0=[0.4], magnet_B=[1.5])
+    mu = gen.muons_config0(3000, seed=21)
+    wl = gen.Workload("vox", geo, fld, h, mu, 0.02, 200, 5)
+    ora = oracle.transport(oracle.world_of(wl), mu, wl.step_len, wl.max_steps, wl.seed)
+    gpu = gpu_transport(wl)
+    ok, err = compare(gpu, ora)
+    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+
+
+def test_field_scaled_transport_parity():
+    wl = gen.workload("config1", n=3000)
+    alpha = np.linspace(0.6, 1.4, 18).reshape(6, 3)
+    ora = oracle.transport(oracle.world_of(wl, alpha), wl.muons, wl.step_len, wl.max_steps, wl.seed)
+    gpu = gpu_transport(wl, alpha=alpha)
+    ok, err = compare(gpu, ora)
+    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    base = gpu_transport(wl)
+    assert not np.array_equal(base["x"], gpu["x"])
