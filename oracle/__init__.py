@@ -83,6 +83,14 @@ def lib():
             L.or_trace.restype = C.c_int32
             L.or_draw.argtypes = [P, P, P, C.c_int32, C.c_uint64, C.c_int32, C.c_uint64, P, P]
             L.or_draw.restype = C.c_int32
+            L.or_acceptance_loss.argtypes = [C.c_int64] + [P] * 7 + [C.c_double] * 3 + [P]
+            L.or_acceptance_loss.restype = C.c_double
+            L.or_adjoint.argtypes = [P, C.c_int64] + [P] * 9 + [C.c_int64, C.c_int32, C.c_double, C.c_int32,
+                                                             C.c_uint64, P, P, C.c_int32]
+            L.or_adjoint.restype = C.c_int
+            L.or_transport_tangent.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, C.c_double,
+                                               C.c_int32, C.c_uint64, P, P]
+            L.or_transport_tangent.restype = C.c_int32
             _lib = L
     return _lib
 
@@ -312,3 +320,51 @@ def trace(world: OracleWorld, r, p, q: int, max_steps: int, step_len: float, see
     return dict(n=s, mat=ib[:s, 0], box=ib[:s, 1], pbin=ib[:s, 2], cell=ib[:s, 3], f=fb[:s, 0],
                 theta=fb[:s, 1], phi=fb[:s, 2], r=db[:s, :3], p_scat=db[:s, 3:6], B=db[:s, 6:9],
                 r_final=rr, p_final=pp)
+
+
+# --------------------------------------------------------------------------
+# differentiable form
+# --------------------------------------------------------------------------
+N_TANGENT = 18
+
+
+def acceptance_loss(final: dict, z_plane: float = 30.0, half: float = 0.5, width: float = 0.01):
+    """Mean acceptance loss of a final state and dL/d(x, y, z, px, py, pz) as a [6, n] array."""
+    cols = [np.ascontiguousarray(final[k], dtype=np.float64) for k in ("x", "y", "z", "px", "py", "pz")]
+    st = np.ascontiguousarray(final["status"], dtype=np.uint8)
+    n = len(cols[0])
+    g = np.zeros((6, n))
+    L = lib().or_acceptance_loss(n, *(_p(c) for c in cols), _p(st), float(z_plane), float(half), float(width),
+                                 _p(g))
+    return L, g
+
+
+def adjoint(world: OracleWorld, muons: dict, step_len: float, max_steps: int, seed: int, g: np.ndarray,
+            id_offset: int = 0, instance: int = 0, n_threads: Optional[int] = None) -> np.ndarray:
+    """dL/dalpha [n_block, 3] from the INITIAL muons and dL/d(final state) g [6, n] (FP64 reverse mode)."""
+    if not world.w.alpha:
+        raise ValueError("the oracle world needs alpha for the adjoint")
+    cols = [np.ascontiguousarray(muons[k], dtype=np.float64) for k in ("x", "y", "z", "px", "py", "pz")]
+    q = np.ascontiguousarray(muons["q"], dtype=np.int8)
+    steps = np.ascontiguousarray(muons["steps"], dtype=np.int32)
+    status = np.ascontiguousarray(muons["status"], dtype=np.uint8)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(3 * world.w.n_block)
+    rc = lib().or_adjoint(world.ptr, len(cols[0]), *(_p(c) for c in cols), _p(q), _p(steps), _p(status),
+                          int(id_offset), int(instance), float(step_len), int(max_steps), int(seed), _p(gg),
+                          _p(out), int(n_threads or os.cpu_count() or 1))
+    if rc != 0:
+        raise RuntimeError("or_adjoint failed")
+    return out.reshape(-1, 3)
+
+
+def transport_tangent(world: OracleWorld, r, p, q: int, max_steps: int, step_len: float, seed: int, mid: int,
+                      instance: int = 0, steps0: int = 0):
+    """Final (x,y,z,px,py,pz) of one muon and d(final)/d(alpha) [6, 18] by forward-mode dual numbers."""
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.zeros(6)
+    tan = np.zeros((6, N_TANGENT))
+    ns = lib().or_transport_tangent(world.ptr, _p(rr), _p(pp), int(q), int(steps0), int(mid), int(instance),
+                                    float(step_len), int(max_steps), int(seed), _p(out), _p(tan))
+    return out, tan, ns

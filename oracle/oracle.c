@@ -449,3 +449,515 @@ int32_t or_draw(const or_world *w, const double r[3], const double p[3], int32_t
     dbuf[0] = dr.f; dbuf[1] = dr.theta; dbuf[2] = dr.phi;
     return in_matter;
 }
+
+/* ======================================================================== */
+/* Differentiable form (the paper's Discussion suggests gradients of the     */
+/* transport with respect to geometry and field parameters).  Parameters are */
+/* per-block field scales alpha[block][c]; the draws of every step (material,*/
+/* box, momentum bin, cell, f, theta, phi) and the number of steps are held  */
+/* fixed (common random numbers), which gives the pathwise derivative.       */
+/* ======================================================================== */
+
+static double or_sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+/* Acceptance loss: mean over all n muons of s((h - |x_e|)/w) s((h - |y_e|)/w),
+ * s the logistic function, (x_e, y_e) the straight-line extrapolation of the
+ * final state to the plane z = zL.  Muons that stopped or are invalid, or have
+ * pz <= 0, contribute 0 with zero gradient.  g (may be NULL) receives
+ * dL/d(x, y, z, px, py, pz) as six arrays of n. */
+double or_acceptance_loss(int64_t n, const double *x, const double *y, const double *z, const double *px,
+                          const double *py, const double *pz, const uint8_t *status, double zL, double h,
+                          double w, double *g)
+{
+    double L = 0.0;
+    for (int64_t m = 0; m < n; ++m) {
+        if (g)
+            for (int c = 0; c < 6; ++c) g[c * n + m] = 0.0;
+        if (status[m] == OR_STOPPED || status[m] == OR_INVALID || !(pz[m] > 0.0)) continue;
+        double lz = zL - z[m];
+        double xe = x[m] + lz * px[m] / pz[m];
+        double ye = y[m] + lz * py[m] / pz[m];
+        double a = (h - fabs(xe)) / w, b = (h - fabs(ye)) / w;
+        double sa = or_sigmoid(a), sb = or_sigmoid(b);
+        L += sa * sb;
+        if (g) {
+            double dxe = sa * (1.0 - sa) * sb * (xe >= 0.0 ? -1.0 : 1.0) / w / (double)n;
+            double dye = sb * (1.0 - sb) * sa * (ye >= 0.0 ? -1.0 : 1.0) / w / (double)n;
+            g[0 * n + m] = dxe;
+            g[1 * n + m] = dye;
+            g[2 * n + m] = -(dxe * px[m] + dye * py[m]) / pz[m];
+            g[3 * n + m] = dxe * lz / pz[m];
+            g[4 * n + m] = dye * lz / pz[m];
+            g[5 * n + m] = -(dxe * px[m] + dye * py[m]) * lz / (pz[m] * pz[m]);
+        }
+    }
+    return n > 0 ? L / (double)n : 0.0;
+}
+
+typedef struct or_tape {
+    double r[3], p[3];
+    int32_t scattered, box;
+    double f, theta, phi;
+} or_tape;
+
+/* Unscaled field at r (map / per-box / none) and, for maps, its Jacobian
+ * dBm_c/dr_a in J[c][a] (zero outside the node box). */
+static void or_field_unscaled(const or_world *w, const double r[3], int32_t box, double Bm[3], double J[3][3])
+{
+    for (int c = 0; c < 3; ++c) {
+        Bm[c] = 0.0;
+        for (int a = 0; a < 3; ++a) J[c][a] = 0.0;
+    }
+    if (w->field_kind == 1) {
+        if (box >= 0)
+            for (int c = 0; c < 3; ++c) Bm[c] = w->box_B[3 * box + c];
+        return;
+    }
+    if (w->field_kind != 2) return;
+    int64_t i0[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = (r[a] - w->forigin[a]) / w->fspacing[a];
+        if (!(u >= 0.0 && u <= (double)(w->fdims[a] - 1))) return;
+        double fl = floor(u);
+        if (fl > (double)(w->fdims[a] - 2)) fl = (double)(w->fdims[a] - 2);
+        i0[a] = (int64_t)fl;
+        t[a] = u - fl;
+    }
+    const int64_t nx = w->fdims[0], ny = w->fdims[1];
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                double fx = di ? t[0] : 1.0 - t[0], fy = dj ? t[1] : 1.0 - t[1], fz = dk ? t[2] : 1.0 - t[2];
+                double gx = (di ? 1.0 : -1.0) * fy * fz / w->fspacing[0];
+                double gy = (dj ? 1.0 : -1.0) * fx * fz / w->fspacing[1];
+                double gz = (dk ? 1.0 : -1.0) * fx * fy / w->fspacing[2];
+                const float *node = w->Bmap + 3 * (((i0[2] + dk) * ny + (i0[1] + dj)) * nx + (i0[0] + di));
+                for (int c = 0; c < 3; ++c) {
+                    Bm[c] += fx * fy * fz * (double)node[c];
+                    J[c][0] += gx * (double)node[c];
+                    J[c][1] += gy * (double)node[c];
+                    J[c][2] += gz * (double)node[c];
+                }
+            }
+}
+
+static int32_t or_block_of(const or_world *w, int32_t box)
+{
+    if (!w->alpha || box < 0 || !w->box_block) return -1;
+    int32_t blk = w->box_block[box];
+    return (blk >= 0 && blk < w->n_block) ? blk : -1;
+}
+
+/* Reverse of or_scatter with (f, theta, phi) fixed: pbar += (d out/d p)^T obar. */
+static void or_scatter_vjp(const double p[3], double f, double theta, double phi, const double obar[3], double pbar[3])
+{
+    double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    double ph[3] = {p[0] / P, p[1] / P, p[2] / P};
+    double sT = sin(theta), cT = cos(theta), cp = cos(phi), sp = sin(phi);
+    double dt = P * (1.0 - f) * sT, dz = P * ((1.0 - f) * cT - 1.0);
+    double dp[3] = {dt * cp, dt * sp, dz};
+    double s = sqrt(ph[0] * ph[0] + ph[1] * ph[1]);
+    double dpbar[3] = {0, 0, 0}, phbar[3] = {0, 0, 0}, Pbar = 0.0;
+    for (int c = 0; c < 3; ++c) pbar[c] += obar[c];            /* out = p + rot */
+    if (s < 1e-12) {
+        double sg = ph[2] > 0.0 ? 1.0 : -1.0;
+        dpbar[0] = obar[0];
+        dpbar[1] = sg * obar[1];
+        dpbar[2] = sg * obar[2];
+    } else {
+        double k[3] = {-ph[1] / s, ph[0] / s, 0.0};
+        double ca = ph[2], sa = s;
+        double kxv[3] = {k[1] * dp[2] - k[2] * dp[1], k[2] * dp[0] - k[0] * dp[2], k[0] * dp[1] - k[1] * dp[0]};
+        double kv = k[0] * dp[0] + k[1] * dp[1] + k[2] * dp[2];
+        double kbar[3] = {0, 0, 0}, kxvbar[3], cabar = 0.0, sabar = 0.0, kvbar = 0.0, sbar = 0.0;
+        double rk = obar[0] * k[0] + obar[1] * k[1] + obar[2] * k[2];
+        for (int c = 0; c < 3; ++c) {
+            dpbar[c] += obar[c] * ca;
+            cabar += obar[c] * dp[c];
+            kxvbar[c] = obar[c] * sa;
+            sabar += obar[c] * kxv[c];
+            kbar[c] += obar[c] * kv * (1.0 - ca);
+        }
+        kvbar = rk * (1.0 - ca);
+        cabar -= rk * kv;
+        for (int c = 0; c < 3; ++c) {                          /* kv = k . dp */
+            kbar[c] += kvbar * dp[c];
+            dpbar[c] += kvbar * k[c];
+        }
+        /* kxv = k x dp: kbar += dp x kxvbar, dpbar += kxvbar x k */
+        kbar[0] += dp[1] * kxvbar[2] - dp[2] * kxvbar[1];
+        kbar[1] += dp[2] * kxvbar[0] - dp[0] * kxvbar[2];
+        kbar[2] += dp[0] * kxvbar[1] - dp[1] * kxvbar[0];
+        dpbar[0] += kxvbar[1] * k[2] - kxvbar[2] * k[1];
+        dpbar[1] += kxvbar[2] * k[0] - kxvbar[0] * k[2];
+        dpbar[2] += kxvbar[0] * k[1] - kxvbar[1] * k[0];
+        sbar += sabar;
+        phbar[2] += cabar;
+        /* k = (-ph1/s, ph0/s, 0) */
+        phbar[1] += -kbar[0] / s;
+        phbar[0] += kbar[1] / s;
+        sbar += -(kbar[0] * k[0] + kbar[1] * k[1]) / s;
+        phbar[0] += sbar * ph[0] / s;                          /* s = |ph_xy| */
+        phbar[1] += sbar * ph[1] / s;
+    }
+    double dtbar = dpbar[0] * cp + dpbar[1] * sp, dzbar = dpbar[2];
+    Pbar += dtbar * (1.0 - f) * sT + dzbar * ((1.0 - f) * cT - 1.0);
+    double php = phbar[0] * p[0] + phbar[1] * p[1] + phbar[2] * p[2];
+    for (int c = 0; c < 3; ++c) pbar[c] += phbar[c] / P;       /* ph = p / P */
+    Pbar -= php / (P * P);
+    for (int c = 0; c < 3; ++c) pbar[c] += Pbar * p[c] / P;    /* P = |p| */
+}
+
+/* Reverse of F(x) = (x/P0, qk (x x B)/P0) given its cotangent (ar, ap). */
+static void or_deriv_vjp(const double x[3], const double B[3], double qk, double P0, const double ar[3],
+                         const double ap[3], double xbar[3], double Bbar[3], double *P0bar)
+{
+    double xB[3] = {x[1] * B[2] - x[2] * B[1], x[2] * B[0] - x[0] * B[2], x[0] * B[1] - x[1] * B[0]};
+    double Bxa[3] = {B[1] * ap[2] - B[2] * ap[1], B[2] * ap[0] - B[0] * ap[2], B[0] * ap[1] - B[1] * ap[0]};
+    double axx[3] = {ap[1] * x[2] - ap[2] * x[1], ap[2] * x[0] - ap[0] * x[2], ap[0] * x[1] - ap[1] * x[0]};
+    double dotr = 0.0, dotp = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        xbar[c] += ar[c] / P0 + qk * Bxa[c] / P0;
+        Bbar[c] += qk * axx[c] / P0;
+        dotr += ar[c] * x[c];
+        dotp += ap[c] * xB[c];
+    }
+    *P0bar -= (dotr + qk * dotp) / (P0 * P0);
+}
+
+/* Reverse of or_rk4: given (rbar, pbar) of the outputs, overwrite them with the
+ * cotangents of the inputs (r, p) and accumulate Bbar. */
+static void or_rk4_vjp(const double p[3], const double B[3], int32_t q, double d, double rbar[3], double pbar[3],
+                       double Bbar[3])
+{
+    double P0 = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    double qk = OR_KAPPA * (double)q;
+    double k1r[3], k1p[3], k2r[3], k2p[3], k3r[3], k3p[3], k4r[3], k4p[3];
+    double t1[3], t2[3], t3[3];
+    or_deriv(p, B, qk, P0, k1r, k1p);
+    for (int c = 0; c < 3; ++c) t1[c] = p[c] + 0.5 * d * k1p[c];
+    or_deriv(t1, B, qk, P0, k2r, k2p);
+    for (int c = 0; c < 3; ++c) t2[c] = p[c] + 0.5 * d * k2p[c];
+    or_deriv(t2, B, qk, P0, k3r, k3p);
+    for (int c = 0; c < 3; ++c) t3[c] = p[c] + d * k3p[c];
+    or_deriv(t3, B, qk, P0, k4r, k4p);
+    double ro[3], po[3], a1r[3], a1p[3], a2r[3], a2p[3], a3r[3], a3p[3], a4r[3], a4p[3];
+    for (int c = 0; c < 3; ++c) {
+        ro[c] = rbar[c];
+        po[c] = pbar[c];
+        a1r[c] = d / 6.0 * ro[c];
+        a2r[c] = d / 3.0 * ro[c];
+        a3r[c] = d / 3.0 * ro[c];
+        a4r[c] = d / 6.0 * ro[c];
+        a1p[c] = d / 6.0 * po[c];
+        a2p[c] = d / 3.0 * po[c];
+        a3p[c] = d / 3.0 * po[c];
+        a4p[c] = d / 6.0 * po[c];
+    }
+    double P0bar = 0.0, t3bar[3] = {0, 0, 0}, t2bar[3] = {0, 0, 0}, t1bar[3] = {0, 0, 0};
+    double pb[3] = {po[0], po[1], po[2]};
+    or_deriv_vjp(t3, B, qk, P0, a4r, a4p, t3bar, Bbar, &P0bar);
+    for (int c = 0; c < 3; ++c) {
+        pb[c] += t3bar[c];
+        a3p[c] += d * t3bar[c];
+    }
+    or_deriv_vjp(t2, B, qk, P0, a3r, a3p, t2bar, Bbar, &P0bar);
+    for (int c = 0; c < 3; ++c) {
+        pb[c] += t2bar[c];
+        a2p[c] += 0.5 * d * t2bar[c];
+    }
+    or_deriv_vjp(t1, B, qk, P0, a2r, a2p, t1bar, Bbar, &P0bar);
+    for (int c = 0; c < 3; ++c) {
+        pb[c] += t1bar[c];
+        a1p[c] += 0.5 * d * t1bar[c];
+    }
+    or_deriv_vjp(p, B, qk, P0, a1r, a1p, pb, Bbar, &P0bar);
+    for (int c = 0; c < 3; ++c) pb[c] += P0bar * p[c] / P0;
+    for (int c = 0; c < 3; ++c) {
+        pbar[c] = pb[c];
+        /* rbar passes through unchanged (r enters additively) */
+    }
+}
+
+/* Forward with a tape, then the reverse sweep, for one muon.  g6 holds
+ * dL/d(final x,y,z,px,py,pz); dalpha[3*block + c] accumulates dL/dalpha. */
+static void or_adjoint_one(const or_world *w, const double r0[3], const double p0[3], int32_t q, int32_t steps0,
+                           uint8_t status0, uint64_t id, int32_t inst, double d, int32_t max_steps, uint64_t seed,
+                           const double g6[6], double *dalpha, or_tape *tape)
+{
+    if (status0 != OR_ALIVE && status0 != OR_MAX_STEPS) return;
+    double r[3] = {r0[0], r0[1], r0[2]}, p[3] = {p0[0], p0[1], p0[2]};
+    for (int c = 0; c < 3; ++c)
+        if (!isfinite(r[c]) || !isfinite(p[c])) return;
+    int32_t ns = 0;
+    for (int32_t k = steps0; k < max_steps; ++k) {
+        if (or_check(w, r, p) != OR_ALIVE) break;
+        or_tape *t = &tape[ns++];
+        for (int c = 0; c < 3; ++c) {
+            t->r[c] = r[c];
+            t->p[c] = p[c];
+        }
+        or_step_draw dr;
+        t->scattered = or_draw_step(w, r, p, k, id, inst, seed, &dr);
+        t->box = dr.box;
+        t->f = dr.f;
+        t->theta = dr.theta;
+        t->phi = dr.phi;
+        if (t->scattered) or_scatter(p, dr.f, dr.theta, dr.phi, p);
+        double B[3];
+        or_field(w, r, dr.box, B);
+        or_rk4(r, p, B, q, d);
+    }
+    double rbar[3] = {g6[0], g6[1], g6[2]}, pbar[3] = {g6[3], g6[4], g6[5]};
+    for (int32_t s = ns - 1; s >= 0; --s) {
+        const or_tape *t = &tape[s];
+        double ps[3] = {t->p[0], t->p[1], t->p[2]};
+        if (t->scattered) or_scatter(t->p, t->f, t->theta, t->phi, ps);
+        double Bm[3], J[3][3], B[3];
+        or_field_unscaled(w, t->r, t->box, Bm, J);
+        int32_t blk = or_block_of(w, t->box);
+        for (int c = 0; c < 3; ++c) B[c] = blk >= 0 ? w->alpha[3 * blk + c] * Bm[c] : Bm[c];
+        double Bbar[3] = {0, 0, 0};
+        or_rk4_vjp(ps, B, q, d, rbar, pbar, Bbar);     /* rbar unchanged, pbar -> cotangent of ps */
+        for (int c = 0; c < 3; ++c) {
+            double Bmbar = blk >= 0 ? w->alpha[3 * blk + c] * Bbar[c] : Bbar[c];
+            if (blk >= 0) dalpha[3 * blk + c] += Bbar[c] * Bm[c];
+            for (int a = 0; a < 3; ++a) rbar[a] += J[c][a] * Bmbar;
+        }
+        if (t->scattered) {
+            double pb[3] = {0, 0, 0};
+            or_scatter_vjp(t->p, t->f, t->theta, t->phi, pbar, pb);
+            for (int c = 0; c < 3; ++c) pbar[c] = pb[c];
+        }
+    }
+}
+
+typedef struct or_adj_job {
+    const or_world *w;
+    int64_t begin, end, n;
+    const double *x, *y, *z, *px, *py, *pz;
+    const int8_t *q;
+    const int32_t *steps;
+    const uint8_t *status;
+    int64_t id_offset;
+    int32_t inst;
+    double d;
+    int32_t max_steps;
+    uint64_t seed;
+    const double *g;
+    double dalpha[3 * 64];
+} or_adj_job;
+
+static void *or_adj_worker(void *arg)
+{
+    or_adj_job *j = (or_adj_job *)arg;
+    or_tape *tape = (or_tape *)malloc(sizeof(or_tape) * (size_t)(j->max_steps > 0 ? j->max_steps : 1));
+    if (!tape) return NULL;
+    for (int64_t m = j->begin; m < j->end; ++m) {
+        double r[3] = {j->x[m], j->y[m], j->z[m]}, p[3] = {j->px[m], j->py[m], j->pz[m]};
+        double g6[6];
+        for (int c = 0; c < 6; ++c) g6[c] = j->g[c * j->n + m];
+        or_adjoint_one(j->w, r, p, j->q[m], j->steps[m], j->status[m], (uint64_t)(j->id_offset + m), j->inst, j->d,
+                       j->max_steps, j->seed, g6, j->dalpha, tape);
+    }
+    free(tape);
+    return NULL;
+}
+
+/* dL/dalpha for n muons given their INITIAL state and dL/d(final state) g
+ * ([6][n] SoA).  dalpha has n_block*3 entries (overwritten).  Returns 0, or -1
+ * for bad arguments (alpha must be set, n_block <= 64). */
+int or_adjoint(const or_world *w, int64_t n, const double *x, const double *y, const double *z, const double *px,
+               const double *py, const double *pz, const int8_t *q, const int32_t *steps, const uint8_t *status,
+               int64_t id_offset, int32_t inst, double d, int32_t max_steps, uint64_t seed, const double *g,
+               double *dalpha, int32_t n_threads)
+{
+    if (!w || !w->alpha || w->n_block < 1 || w->n_block > 64 || n < 0 || n_threads < 1) return -1;
+    for (int i = 0; i < 3 * w->n_block; ++i) dalpha[i] = 0.0;
+    if (n == 0) return 0;
+    if (n_threads > 256) n_threads = 256;
+    if ((int64_t)n_threads > n) n_threads = (int32_t)n;
+    or_adj_job *jobs = (or_adj_job *)calloc((size_t)n_threads, sizeof(or_adj_job));
+    pthread_t th[256];
+    if (!jobs) return -1;
+    for (int32_t t = 0; t < n_threads; ++t) {
+        or_adj_job *j = &jobs[t];
+        j->w = w;
+        j->begin = n * t / n_threads;
+        j->end = n * (t + 1) / n_threads;
+        j->n = n;
+        j->x = x; j->y = y; j->z = z; j->px = px; j->py = py; j->pz = pz;
+        j->q = q; j->steps = steps; j->status = status;
+        j->id_offset = id_offset; j->inst = inst; j->d = d; j->max_steps = max_steps; j->seed = seed; j->g = g;
+    }
+    for (int32_t t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, or_adj_worker, &jobs[t]);
+    or_adj_worker(&jobs[0]);
+    for (int32_t t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+    for (int32_t t = 0; t < n_threads; ++t)
+        for (int i = 0; i < 3 * w->n_block; ++i) dalpha[i] += jobs[t].dalpha[i];
+    free(jobs);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward-mode dual numbers: an independent check of the adjoint.  Every     */
+/* quantity carries its derivatives with respect to the OR_NT field scales.  */
+/* ------------------------------------------------------------------------ */
+#define OR_NT 18
+typedef struct { double v, d[OR_NT]; } or_dual;
+
+static or_dual dc(double v) { or_dual r; r.v = v; for (int i = 0; i < OR_NT; ++i) r.d[i] = 0.0; return r; }
+static or_dual dadd(or_dual a, or_dual b) { for (int i = 0; i < OR_NT; ++i) a.d[i] += b.d[i]; a.v += b.v; return a; }
+static or_dual dsub(or_dual a, or_dual b) { for (int i = 0; i < OR_NT; ++i) a.d[i] -= b.d[i]; a.v -= b.v; return a; }
+static or_dual dmul(or_dual a, or_dual b)
+{
+    or_dual r;
+    r.v = a.v * b.v;
+    for (int i = 0; i < OR_NT; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+static or_dual dscale(or_dual a, double s) { for (int i = 0; i < OR_NT; ++i) a.d[i] *= s; a.v *= s; return a; }
+static or_dual ddiv(or_dual a, or_dual b)
+{
+    or_dual r;
+    r.v = a.v / b.v;
+    for (int i = 0; i < OR_NT; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    return r;
+}
+static or_dual dsqrt(or_dual a)
+{
+    or_dual r;
+    r.v = sqrt(a.v);
+    for (int i = 0; i < OR_NT; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+    return r;
+}
+static or_dual dnorm3(const or_dual v[3]) { return dsqrt(dadd(dadd(dmul(v[0], v[0]), dmul(v[1], v[1])), dmul(v[2], v[2]))); }
+
+static void dscatter(or_dual p[3], double f, double theta, double phi)
+{
+    or_dual P = dnorm3(p);
+    or_dual ph[3] = {ddiv(p[0], P), ddiv(p[1], P), ddiv(p[2], P)};
+    or_dual dt = dscale(P, (1.0 - f) * sin(theta));
+    or_dual dz = dscale(P, (1.0 - f) * cos(theta) - 1.0);
+    or_dual dp[3] = {dscale(dt, cos(phi)), dscale(dt, sin(phi)), dz};
+    or_dual rot[3];
+    or_dual s = dsqrt(dadd(dmul(ph[0], ph[0]), dmul(ph[1], ph[1])));
+    if (s.v < 1e-12) {
+        double sg = ph[2].v > 0.0 ? 1.0 : -1.0;
+        rot[0] = dp[0];
+        rot[1] = dscale(dp[1], sg);
+        rot[2] = dscale(dp[2], sg);
+    } else {
+        or_dual k[3] = {dscale(ddiv(ph[1], s), -1.0), ddiv(ph[0], s), dc(0.0)};
+        or_dual ca = ph[2], sa = s, omc = dsub(dc(1.0), ph[2]);
+        or_dual kxv[3] = {dsub(dmul(k[1], dp[2]), dmul(k[2], dp[1])), dsub(dmul(k[2], dp[0]), dmul(k[0], dp[2])),
+                          dsub(dmul(k[0], dp[1]), dmul(k[1], dp[0]))};
+        or_dual kv = dadd(dadd(dmul(k[0], dp[0]), dmul(k[1], dp[1])), dmul(k[2], dp[2]));
+        for (int c = 0; c < 3; ++c) rot[c] = dadd(dadd(dmul(dp[c], ca), dmul(kxv[c], sa)), dmul(dmul(k[c], kv), omc));
+    }
+    for (int c = 0; c < 3; ++c) p[c] = dadd(p[c], rot[c]);
+}
+
+static void dderiv(const or_dual x[3], const or_dual B[3], double qk, or_dual P0, or_dual dr[3], or_dual dp[3])
+{
+    for (int c = 0; c < 3; ++c) dr[c] = ddiv(x[c], P0);
+    or_dual xB[3] = {dsub(dmul(x[1], B[2]), dmul(x[2], B[1])), dsub(dmul(x[2], B[0]), dmul(x[0], B[2])),
+                     dsub(dmul(x[0], B[1]), dmul(x[1], B[0]))};
+    for (int c = 0; c < 3; ++c) dp[c] = ddiv(dscale(xB[c], qk), P0);
+}
+
+static void drk4(or_dual r[3], or_dual p[3], const or_dual B[3], int32_t q, double d)
+{
+    or_dual P0 = dnorm3(p);
+    double qk = OR_KAPPA * (double)q;
+    or_dual k1r[3], k1p[3], k2r[3], k2p[3], k3r[3], k3p[3], k4r[3], k4p[3], t[3];
+    dderiv(p, B, qk, P0, k1r, k1p);
+    for (int c = 0; c < 3; ++c) t[c] = dadd(p[c], dscale(k1p[c], 0.5 * d));
+    dderiv(t, B, qk, P0, k2r, k2p);
+    for (int c = 0; c < 3; ++c) t[c] = dadd(p[c], dscale(k2p[c], 0.5 * d));
+    dderiv(t, B, qk, P0, k3r, k3p);
+    for (int c = 0; c < 3; ++c) t[c] = dadd(p[c], dscale(k3p[c], d));
+    dderiv(t, B, qk, P0, k4r, k4p);
+    for (int c = 0; c < 3; ++c) {
+        or_dual sr = dadd(dadd(k1r[c], dscale(k2r[c], 2.0)), dadd(dscale(k3r[c], 2.0), k4r[c]));
+        or_dual sp = dadd(dadd(k1p[c], dscale(k2p[c], 2.0)), dadd(dscale(k3p[c], 2.0), k4p[c]));
+        r[c] = dadd(r[c], dscale(sr, d / 6.0));
+        p[c] = dadd(p[c], dscale(sp, d / 6.0));
+    }
+}
+
+static void dfield(const or_world *w, const or_dual r[3], int32_t box, or_dual B[3])
+{
+    for (int c = 0; c < 3; ++c) B[c] = dc(0.0);
+    if (w->field_kind == 1) {
+        if (box >= 0)
+            for (int c = 0; c < 3; ++c) B[c] = dc(w->box_B[3 * box + c]);
+    } else if (w->field_kind == 2) {
+        int64_t i0[3];
+        or_dual t[3];
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+            double u = (r[a].v - w->forigin[a]) / w->fspacing[a];
+            if (!(u >= 0.0 && u <= (double)(w->fdims[a] - 1))) inside = 0;
+            double fl = floor(u);
+            if (fl > (double)(w->fdims[a] - 2)) fl = (double)(w->fdims[a] - 2);
+            i0[a] = (int64_t)fl;
+            t[a] = dsub(dscale(dsub(r[a], dc(w->forigin[a])), 1.0 / w->fspacing[a]), dc(fl));
+        }
+        if (inside) {
+            const int64_t nx = w->fdims[0], ny = w->fdims[1];
+            for (int dk = 0; dk < 2; ++dk)
+                for (int dj = 0; dj < 2; ++dj)
+                    for (int di = 0; di < 2; ++di) {
+                        or_dual fx = di ? t[0] : dsub(dc(1.0), t[0]);
+                        or_dual fy = dj ? t[1] : dsub(dc(1.0), t[1]);
+                        or_dual fz = dk ? t[2] : dsub(dc(1.0), t[2]);
+                        or_dual wgt = dmul(dmul(fx, fy), fz);
+                        const float *node = w->Bmap + 3 * (((i0[2] + dk) * ny + (i0[1] + dj)) * nx + (i0[0] + di));
+                        for (int c = 0; c < 3; ++c) B[c] = dadd(B[c], dscale(wgt, (double)node[c]));
+                    }
+        }
+    }
+    int32_t blk = or_block_of(w, box);
+    if (blk >= 0)
+        for (int c = 0; c < 3; ++c) {
+            or_dual a = dc(w->alpha[3 * blk + c]);
+            if (3 * blk + c < OR_NT) a.d[3 * blk + c] = 1.0;
+            B[c] = dmul(a, B[c]);
+        }
+}
+
+/* Final state of one muon and its derivatives with respect to the field scales
+ * (tangent directions 3*block + c, at most OR_NT of them):
+ * out6 = final (x,y,z,px,py,pz), tan[6][OR_NT].  Returns the number of steps. */
+int32_t or_transport_tangent(const or_world *w, const double r0[3], const double p0[3], int32_t q, int32_t steps0,
+                             uint64_t id, int32_t inst, double d, int32_t max_steps, uint64_t seed, double out6[6],
+                             double *tan)
+{
+    or_dual r[3], p[3];
+    for (int c = 0; c < 3; ++c) {
+        r[c] = dc(r0[c]);
+        p[c] = dc(p0[c]);
+    }
+    int32_t ns = 0;
+    for (int32_t k = steps0; k < max_steps; ++k) {
+        double rv[3] = {r[0].v, r[1].v, r[2].v}, pv[3] = {p[0].v, p[1].v, p[2].v};
+        if (or_check(w, rv, pv) != OR_ALIVE) break;
+        or_step_draw dr;
+        if (or_draw_step(w, rv, pv, k, id, inst, seed, &dr)) dscatter(p, dr.f, dr.theta, dr.phi);
+        or_dual B[3];
+        dfield(w, r, dr.box, B);
+        drk4(r, p, B, q, d);
+        ++ns;
+    }
+    for (int c = 0; c < 3; ++c) {
+        out6[c] = r[c].v;
+        out6[3 + c] = p[c].v;
+        for (int i = 0; i < OR_NT; ++i) {
+            tan[c * OR_NT + i] = r[c].d[i];
+            tan[(3 + c) * OR_NT + i] = p[c].d[i];
+        }
+    }
+    return ns;
+}

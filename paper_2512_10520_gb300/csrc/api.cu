@@ -342,7 +342,8 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
         w.fmap = (const float4 *)h->d_fmap;
         for (int a = 0; a < 3; ++a) {
             w.fdims[a] = f->dims[a];
-            w.forigin[a] = (float)f->origin[a];
+            split(f->origin[a], w.forigin[a], w.forigin_lo[a]);
+            split(f->spacing[a], w.fspacing[a], w.fspacing_lo[a]);
             w.finv[a] = (float)(1.0 / f->spacing[a]);
         }
     }

@@ -17,7 +17,6 @@
 
 namespace mt {
 
-constexpr float kKappa = 0.299792458f;   // GeV / (T m)
 
 struct DevBox {
     float lo_hi[3], lo_lo[3];
@@ -58,6 +57,9 @@ struct WorldParams {
     const float4 *fmap;
     int32_t fdims[3];
     float forigin[3];
+    float forigin_lo[3];
+    float fspacing[3];
+    float fspacing_lo[3];
     float finv[3];
     // histograms
     const HistRec *hist;
@@ -74,6 +76,7 @@ struct WorldParams {
 
 struct RunParams {
     float d;
+    float kd;            // kappa * d
     int32_t max_steps;
     uint32_t key0, key1;
     const float *alpha;   // device [n_block][3] or null

@@ -143,6 +143,13 @@ __device__ __forceinline__ int voxel_material(const WorldParams &w, const State 
     return __ldg(w.vox + ((int64_t)idx[2] * w.vdims[1] + idx[1]) * w.vdims[0] + idx[0]);
 }
 
+// |p|^2 of the hi + lo momentum to first order in lo.
+__device__ __forceinline__ float p2_of(const State &s)
+{
+    float P2 = s.px * s.px + s.py * s.py + s.pz * s.pz;
+    return fmaf(2.0f * s.px, s.pxl, fmaf(2.0f * s.py, s.pyl, fmaf(2.0f * s.pz, s.pzl, P2)));
+}
+
 // (h + l)^2 as an unnormalised pair.
 __device__ __forceinline__ void sq2(float h, float l, float &sh, float &sl)
 {
@@ -205,7 +212,7 @@ __device__ __forceinline__ uint32_t sample_cell(const uint32_t *guide, const uin
 // increment is small, so it is accumulated into the hi + lo momentum.
 __device__ __forceinline__ void scatter(State &s, float f, float theta, float cphi, float sphi)
 {
-    const float P2 = s.px * s.px + s.py * s.py + s.pz * s.pz;
+    const float P2 = p2_of(s);
     float rP = rsqrtf(P2);
     rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
     const float P = P2 * rP;
@@ -233,18 +240,40 @@ __device__ __forceinline__ void scatter(State &s, float f, float theta, float cp
     acc(s.pz, s.pzl, fmaf(sm1, s.pz, kick * tz));
 }
 
+// a + t (b - a)
+__device__ __forceinline__ float lerp(float t, float a, float b) { return fmaf(t, b - a, a); }
+
+// Cell index and in-cell fraction of one axis of the node map.  The offset from
+// the cell's lower node, (x - origin) - i * spacing, is formed from hi + lo
+// pairs, so the fraction carries ~1e-7 relative error however far the cell is
+// from the origin (the plain FP32 coordinate would lose ~2e-7 m, which matters
+// where the field changes by tens of T/m at a magnet edge).
+__device__ __forceinline__ bool map_axis(float xh, float xl, float oh, float ol, float sh, float sl, float inv, int n,
+                                         int &i, float &t)
+{
+    float dh, de;
+    two_sum(xh, -oh, dh, de);
+    const float dl = de + (xl - ol);
+    const float u = (dh + dl) * inv;
+    if (!(u >= 0.0f && u <= (float)(n - 1))) return false;
+    i = min((int)u, n - 2);
+    const float fi = (float)i;
+    const float ph = fi * sh;
+    const float pl = fmaf(fi, sh, -ph) + fi * sl;
+    t = ((dh - ph) + (dl - pl)) * inv;
+    return true;
+}
+
 // Trilinear field from the pair layout; zero outside the node box.
 __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s)
 {
-    const float u = (s.x - w.forigin[0]) * w.finv[0];
-    const float v = (s.y - w.forigin[1]) * w.finv[1];
-    const float t = (s.z - w.forigin[2]) * w.finv[2];
     const int nx = w.fdims[0], ny = w.fdims[1], nz = w.fdims[2];
-    if (!(u >= 0.0f && u <= (float)(nx - 1) && v >= 0.0f && v <= (float)(ny - 1) && t >= 0.0f &&
-          t <= (float)(nz - 1)))
+    int i, j, k;
+    float tx, ty, tz;
+    if (!map_axis(s.x, s.xl, w.forigin[0], w.forigin_lo[0], w.fspacing[0], w.fspacing_lo[0], w.finv[0], nx, i, tx) ||
+        !map_axis(s.y, s.yl, w.forigin[1], w.forigin_lo[1], w.fspacing[1], w.fspacing_lo[1], w.finv[1], ny, j, ty) ||
+        !map_axis(s.z, s.zl, w.forigin[2], w.forigin_lo[2], w.fspacing[2], w.fspacing_lo[2], w.finv[2], nz, k, tz))
         return make_float3(0.0f, 0.0f, 0.0f);
-    const int i = min((int)u, nx - 2), j = min((int)v, ny - 2), k = min((int)t, nz - 2);
-    const float tx = u - (float)i, ty = v - (float)j, tz = t - (float)k;
     const int64_t row = nx - 1;
     const float4 *p00 = w.fmap + 2 * (((int64_t)k * ny + j) * row + i);
     const float4 *p10 = p00 + 2 * row;                 // j + 1
@@ -254,38 +283,40 @@ __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s
     const float4 b0 = __ldg(p10), b1 = __ldg(p10 + 1);
     const float4 c0 = __ldg(p01), c1 = __ldg(p01 + 1);
     const float4 d0 = __ldg(p11), d1 = __ldg(p11 + 1);
-#define MT_LX(A, B, C) fmaf(tx, (B).C - (A).C, (A).C)
-    const float ax = MT_LX(a0, a1, x), ay = MT_LX(a0, a1, y), az = MT_LX(a0, a1, z);
-    const float bx = MT_LX(b0, b1, x), by = MT_LX(b0, b1, y), bz = MT_LX(b0, b1, z);
-    const float cx = MT_LX(c0, c1, x), cy = MT_LX(c0, c1, y), cz = MT_LX(c0, c1, z);
-    const float dx = MT_LX(d0, d1, x), dy = MT_LX(d0, d1, y), dz = MT_LX(d0, d1, z);
-#undef MT_LX
-    const float ex = fmaf(ty, bx - ax, ax), ey = fmaf(ty, by - ay, ay), ez = fmaf(ty, bz - az, az);
-    const float gx = fmaf(ty, dx - cx, cx), gy = fmaf(ty, dy - cy, cy), gz = fmaf(ty, dz - cz, cz);
-    return make_float3(fmaf(tz, gx - ex, ex), fmaf(tz, gy - ey, ey), fmaf(tz, gz - ez, ez));
+    const float ax = lerp(tx, a0.x, a1.x), ay = lerp(tx, a0.y, a1.y), az = lerp(tx, a0.z, a1.z);
+    const float bx = lerp(tx, b0.x, b1.x), by = lerp(tx, b0.y, b1.y), bz = lerp(tx, b0.z, b1.z);
+    const float cx = lerp(tx, c0.x, c1.x), cy = lerp(tx, c0.y, c1.y), cz = lerp(tx, c0.z, c1.z);
+    const float dx = lerp(tx, d0.x, d1.x), dy = lerp(tx, d0.y, d1.y), dz = lerp(tx, d0.z, d1.z);
+    const float ex = lerp(ty, ax, bx), ey = lerp(ty, ay, by), ez = lerp(ty, az, bz);
+    const float gx = lerp(ty, cx, dx), gy = lerp(ty, cy, dy), gz = lerp(ty, cz, dz);
+    return make_float3(lerp(tz, ex, gx), lerp(tz, ey, gy), lerp(tz, ez, gz));
+}
+
+// o = a x h
+__device__ __forceinline__ void cross_h(float ax, float ay, float az, float hx, float hy, float hz, float &ox,
+                                        float &oy, float &oz)
+{
+    ox = ay * hz - az * hy;
+    oy = az * hx - ax * hz;
+    oz = ax * hy - ay * hx;
 }
 
 // RK4 over path length d with B fixed: dr/ds = p/P0, dp/ds = kappa q (p x B)/P0.
-// With h = kappa q d B / P0 the stage increments are k_i = p_i x h, and the
+// kd = kappa d, rounded once on the host.  With h = kappa q d B / P0 the stage increments are k_i = p_i x h, and the
 // position increment reduces to (d/P0) (p + (k1 + k2 + k3)/6).
-__device__ __forceinline__ void rk4(State &s, float3 B, float q, float d)
+__device__ __forceinline__ void rk4(State &s, float3 B, float q, float d, float kd)
 {
     const float px = s.px, py = s.py, pz = s.pz;
-    const float P2 = px * px + py * py + pz * pz;
+    const float P2 = p2_of(s);
     float rP = rsqrtf(P2);
     rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
-    const float c = kKappa * q * d * rP;
+    const float c = (kd * q) * rP;
     const float hx = c * B.x, hy = c * B.y, hz = c * B.z;
-#define MT_CROSS(ax, ay, az, ox, oy, oz) \
-    ox = ay * hz - az * hy;              \
-    oy = az * hx - ax * hz;              \
-    oz = ax * hy - ay * hx;
-    float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
-    MT_CROSS(px, py, pz, k1x, k1y, k1z);
-    MT_CROSS(fmaf(0.5f, k1x, px), fmaf(0.5f, k1y, py), fmaf(0.5f, k1z, pz), k2x, k2y, k2z);
-    MT_CROSS(fmaf(0.5f, k2x, px), fmaf(0.5f, k2y, py), fmaf(0.5f, k2z, pz), k3x, k3y, k3z);
-    MT_CROSS(px + k3x, py + k3y, pz + k3z, k4x, k4y, k4z);
-#undef MT_CROSS
+float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+    cross_h(px, py, pz, hx, hy, hz, k1x, k1y, k1z);
+    cross_h(fmaf(0.5f, k1x, px), fmaf(0.5f, k1y, py), fmaf(0.5f, k1z, pz), hx, hy, hz, k2x, k2y, k2z);
+    cross_h(fmaf(0.5f, k2x, px), fmaf(0.5f, k2y, py), fmaf(0.5f, k2z, pz), hx, hy, hz, k3x, k3y, k3z);
+    cross_h(px + k3x, py + k3y, pz + k3z, hx, hy, hz, k4x, k4y, k4z);
     const float sixth = 1.0f / 6.0f;
     const float a = d * rP;
     acc(s.x, s.xl, a * fmaf(sixth, k1x + k2x + k3x, px));
@@ -349,7 +380,7 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
             B.z *= sw.alpha[2][blk];
         }
     }
-    rk4(s, B, q, rp.d);
+    rk4(s, B, q, rp.d, rp.kd);
     return MT_ALIVE;
 }
 
@@ -494,6 +525,7 @@ extern "C" mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int
     if (n == 0) return MT_OK;
     RunParams rp;
     rp.d = step_len;
+    rp.kd = (float)(0.299792458 * (double)step_len);
     rp.max_steps = max_steps;
     rp.key0 = (uint32_t)seed;
     rp.key1 = (uint32_t)(seed >> 32);
