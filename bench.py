@@ -218,17 +218,22 @@ def run_mine(args):
             work[k].copy_(init[k], non_blocking=True)
 
     ev_k = []
+    launch = {}
+    if args.mode != "auto" or args.blocks_per_sm or args.steps_per_pass:
+        launch = dict(mode={"auto": mt.MT_LAUNCH_AUTO, "static": mt.MT_LAUNCH_STATIC,
+                            "persistent": mt.MT_LAUNCH_PERSISTENT, "compact": mt.MT_LAUNCH_COMPACT}[args.mode],
+                      blocks_per_sm=args.blocks_per_sm, steps_per_pass=args.steps_per_pass)
 
     def one_step(timed: bool):
         reset()
         if timed:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream, **launch)
             b.record(stream)
             ev_k.append((a, b))
         else:
-            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream, **launch)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -266,7 +271,7 @@ def run_mine(args):
         for _ in range(e2e_steps):
             for k in work:
                 work[k].copy_(host_in[k], non_blocking=True)
-            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream, **launch)
             for k in work:
                 host_out[k].copy_(work[k], non_blocking=True)
         b.record(stream)
@@ -294,7 +299,8 @@ def run_mine(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "plain", "muons_per_gpu": n, "max_steps": wl.max_steps,
+            "config": {"workload": WORKLOAD, "form": "plain", "launch": args.mode,
+                       "blocks_per_sm": args.blocks_per_sm, "muons_per_gpu": n, "max_steps": wl.max_steps,
                        "muon_steps_per_batch_per_gpu": steps_per_batch, "muons_per_s": n * ws * args.steps / elapsed,
                        "l2": "inputs larger than L2 (field map 764 MB in HBM vs 129 MB L2); no flush",
                        "parallelism": f"replicas x{ws}"},
@@ -320,6 +326,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--muons", type=int, default=None, help="muons per GPU (default: the workload's 1e6)")
+    ap.add_argument("--mode", default="auto", choices=["auto", "static", "persistent", "compact"])
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--steps-per-pass", type=int, default=0)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -140,9 +140,8 @@ int32_t mt_abi_version(void);
 const char *mt_last_error(void);
 
 /* Build the device-resident static data of one world: geometry, field map and
- * sampling tables (the paper pre-loads "geometry definitions, magnetic field
- * maps, and pre-computed physics histograms" into GPU global memory, Sec.
- * Simulation).  For each histogram the library normalises the weights into a
+ * sampling tables (the paper keeps all of its static inputs resident in GPU
+ * global memory for the whole run, Sec. Simulation).  For each histogram the library normalises the weights into a
  * discrete CDF and quantises it to uint32 thresholds
  * T_j = floor(2^32 S_j / S_total) (S_j the left-to-right FP64 prefix sum), so the
  * cell of a 32-bit draw w is #{j < ncell-1 : T_j <= w}.
@@ -161,13 +160,16 @@ void mt_destroy(mt_handle *h);
 int64_t mt_device_bytes(const mt_handle *h);
 
 /* Transport n muons in place (Algorithm 1), asynchronously on `stream`
- * (a cudaStream_t; NULL = legacy default stream).  For each muon whose status
+ * (a cudaStream_t; NULL = legacy default stream).  Runs the MT_LAUNCH_AUTO
+ * launch shape of mt_transport_cfg, whose scratch list comes from the
+ * stream-ordered allocator (cudaMallocAsync / cudaFreeAsync on `stream`).  For each muon whose status
  * is MT_ALIVE or MT_MAX_STEPS it runs steps k = steps .. max_steps-1 and stops
  * at the first break condition; terminal statuses are left untouched.
  * step_len is d [m].  seed is the 64-bit Philox key.
  * Errors (returned before anything is enqueued): MT_ERR_INVALID_ARG for a null
  * handle/soa, null arrays with n > 0, n < 0, non-finite or non-positive
- * step_len, max_steps < 0; MT_ERR_CUDA if the launch fails. */
+ * step_len, max_steps < 0; MT_ERR_OOM if the scratch allocation fails;
+ * MT_ERR_CUDA if a launch fails. */
 mt_status mt_transport(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len,
                        int32_t max_steps, uint64_t seed, void *stream);
 
@@ -178,6 +180,41 @@ mt_status mt_transport(mt_handle *h, const mt_muon_soa *s, int64_t n, float step
 mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len,
                               int32_t max_steps, uint64_t seed, const float *alpha, int32_t n_block,
                               void *stream);
+
+/* Launch shape of the transport kernels (performance only: results do not
+ * depend on it).
+ *  MT_LAUNCH_STATIC     one thread per muon over a grid covering all n muons;
+ *  MT_LAUNCH_PERSISTENT a resident grid of (SM count x blocks_per_sm) blocks
+ *                       whose lanes pick up the next muon of their block's range
+ *                       as soon as the current one stops;
+ *  MT_LAUNCH_COMPACT    lockstep passes: every live muon advances steps_per_pass
+ *                       steps, then the survivors are compacted into a scratch
+ *                       list (two 64-byte entries per muon plus 256 bytes, see
+ *                       mt_transport_workspace_bytes) for the next pass; n must
+ *                       be below 2^31;
+ *  MT_LAUNCH_AUTO       the fastest measured form: MT_LAUNCH_COMPACT with 64 steps
+ *                       per pass (the static grid for n >= 2^31). */
+enum { MT_LAUNCH_AUTO = 0, MT_LAUNCH_STATIC = 1, MT_LAUNCH_PERSISTENT = 2, MT_LAUNCH_COMPACT = 3 };
+typedef struct mt_launch_cfg {
+    int32_t mode;             /* MT_LAUNCH_*                                              */
+    int32_t blocks_per_sm;    /* 0 = as many as fit (occupancy calculator)                */
+    int32_t steps_per_pass;   /* MT_LAUNCH_COMPACT: steps between compactions, 0 = 64     */
+    int32_t reserved;
+    void *workspace;          /* MT_LAUNCH_COMPACT: device scratch (256-byte aligned), or */
+    int64_t workspace_bytes;  /*   NULL = taken from the stream-ordered allocator         */
+} mt_launch_cfg;
+
+/* Scratch bytes MT_LAUNCH_COMPACT needs for n muons. */
+int64_t mt_transport_workspace_bytes(int64_t n);
+
+/* mt_transport_scaled with an explicit launch shape (cfg may be NULL = auto).
+ * Errors as mt_transport, plus MT_ERR_INVALID_ARG for an unknown mode, a
+ * negative blocks_per_sm or steps_per_pass, a workspace that is too small or
+ * not 256-byte aligned, or n >= 2^31 in compact mode; MT_ERR_OOM if the
+ * stream-ordered allocation fails. */
+mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
+                           uint64_t seed, const float *alpha, int32_t n_block, const mt_launch_cfg *cfg,
+                           void *stream);
 
 #ifdef __cplusplus
 }

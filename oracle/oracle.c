@@ -120,7 +120,7 @@ double or_uniform(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
 
 /* ------------------------------------------------------------------------ */
 /* Histogram -> normalised discrete CDF -> uint32 thresholds (Sec. Building  */
-/* histograms: "normalized to obtain a discrete probability distribution").  */
+/* histograms: each histogram, once normalised, is a joint discrete PDF).    */
 /* T_j = floor(2^32 * S_j / S_tot), j = 0..ncell-2; stored in 64 bits, since */
 /* a trailing run of empty cells gives T_j = 2^32 (never <= any 32-bit draw). */
 /* Returns 0, or -1 (negative / non-finite weight), -2 (empty histogram).    */

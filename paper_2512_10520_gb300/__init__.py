@@ -8,6 +8,7 @@ from ._binding import (  # noqa: F401
     MT_ALIVE, MT_STOPPED, MT_EXIT_Z, MT_EXIT_XY, MT_MAX_STEPS, MT_INVALID,
     MtError, declared_symbols, library_path, load_library,
     mt_abi_version, mt_last_error, mt_create, mt_destroy, mt_device_bytes,
-    mt_transport, mt_transport_scaled,
+    mt_transport, mt_transport_scaled, mt_transport_cfg, mt_transport_workspace_bytes,
+    MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT,
 )
 from .api import World, muons_to_device, muons_to_host  # noqa: F401

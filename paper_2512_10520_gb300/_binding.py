@@ -54,6 +54,14 @@ class mt_hist_desc(C.Structure):
                 ("theta_max", C.c_void_p)]
 
 
+class mt_launch_cfg(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("blocks_per_sm", C.c_int32), ("steps_per_pass", C.c_int32),
+                ("reserved", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64)]
+
+
+MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT = 0, 1, 2, 3
+
+
 class mt_muon_soa(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("px", C.c_void_p),
                 ("py", C.c_void_p), ("pz", C.c_void_p), ("q", C.c_void_p), ("steps", C.c_void_p),
@@ -75,6 +83,9 @@ _SIGNATURES = {
     "mt_transport": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P], C.c_int),
     "mt_transport_scaled": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P,
                              C.c_int32, _P], C.c_int),
+    "mt_transport_cfg": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P,
+                          C.c_int32, C.POINTER(mt_launch_cfg), _P], C.c_int),
+    "mt_transport_workspace_bytes": ([C.c_int64], C.c_int64),
 }
 
 
@@ -255,3 +266,27 @@ def mt_transport_scaled(handle: int, muons: Dict, step_len: float, max_steps: in
     _check(load_library().mt_transport_scaled(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
                                               int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr), int(nb),
                                               C.c_void_p(_stream_ptr(stream))), "mt_transport_scaled")
+
+
+def mt_transport_workspace_bytes(n: int) -> int:
+    return load_library().mt_transport_workspace_bytes(int(n))
+
+
+def mt_transport_cfg(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, alpha=None,
+                     mode: int = MT_LAUNCH_AUTO, blocks_per_sm: int = 0, id_offset: int = 0, instance: int = 0,
+                     stream=None, steps_per_pass: int = 0, workspace=None) -> None:
+    """mt_transport with field scales (or None) and an explicit launch shape."""
+    s = soa_struct(muons, id_offset, instance)
+    n = int(muons["x"].numel())
+    if alpha is not None:
+        if not alpha.is_cuda or str(alpha.dtype) != "torch.float32" or not alpha.is_contiguous():
+            raise TypeError("alpha must be a contiguous float32 CUDA tensor")
+        a_ptr, nb = alpha.data_ptr(), alpha.numel() // 3
+    else:
+        a_ptr, nb = None, 0
+    ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(),
+                                                           workspace.numel() * workspace.element_size())
+    cfg = mt_launch_cfg(int(mode), int(blocks_per_sm), int(steps_per_pass), 0, ws_ptr, int(ws_bytes))
+    _check(load_library().mt_transport_cfg(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
+                                           int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr), int(nb), C.byref(cfg),
+                                           C.c_void_p(_stream_ptr(stream))), "mt_transport_cfg")

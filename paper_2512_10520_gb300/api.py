@@ -23,8 +23,12 @@ class World:
         return B.mt_device_bytes(self.handle)
 
     def transport(self, muons: Dict, step_len: float, max_steps: int, seed: int, id_offset: int = 0,
-                  instance: int = 0, alpha=None, stream=None) -> None:
-        if alpha is None:
+                  instance: int = 0, alpha=None, stream=None, mode: Optional[int] = None,
+                  blocks_per_sm: int = 0, steps_per_pass: int = 0, workspace=None) -> None:
+        if mode is not None or blocks_per_sm or steps_per_pass or workspace is not None:
+            B.mt_transport_cfg(self.handle, muons, step_len, max_steps, seed, alpha, mode or 0, blocks_per_sm,
+                               id_offset, instance, stream, steps_per_pass, workspace)
+        elif alpha is None:
             B.mt_transport(self.handle, muons, step_len, max_steps, seed, id_offset, instance, stream)
         else:
             B.mt_transport_scaled(self.handle, muons, step_len, max_steps, seed, alpha, id_offset, instance,

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -237,7 +238,7 @@ void mt_destroy(mt_handle *h)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
-    void *bufs[] = {h->d_boxes, h->d_hist, h->d_guide, h->d_pairs, h->d_e2, h->d_fmap, h->d_vox};
+    void *bufs[] = {h->d_boxes, h->d_hist, h->d_guide, h->d_pairs, h->d_e2, h->d_fmap, h->d_vox, h->d_zmask};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);
@@ -304,6 +305,33 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
         w.n_box = g->n_boxes;
         MT_TRY(upload(h->d_boxes, boxes.data(), boxes.size(), h->bytes, "boxes"));
         w.boxes = (const DevBox *)h->d_boxes;
+        // z-slab candidate index: slab s holds every box whose z range meets the
+        // slab or its two neighbours (the slab of a point is computed in FP32 and
+        // may be off by one near a slab face; the exact box test decides).
+        std::vector<uint32_t> zmask(kZSlabs, 0u);
+        double zlo = 0.0, zhi = 1.0;
+        if (g->n_boxes > 0) {
+            zlo = g->boxes[0].lo[2];
+            zhi = g->boxes[0].hi[2];
+            for (int b = 1; b < g->n_boxes; ++b) {
+                zlo = std::min(zlo, g->boxes[b].lo[2]);
+                zhi = std::max(zhi, g->boxes[b].hi[2]);
+            }
+            if (!(zhi > zlo)) zhi = zlo + 1.0;
+        }
+        const double dz = (zhi - zlo) / kZSlabs;
+        for (int b = 0; b < g->n_boxes; ++b) {
+            if (!(g->boxes[b].hi[2] > g->boxes[b].lo[2])) continue;   // empty box: never contains a point
+            int s0 = (int)std::floor((g->boxes[b].lo[2] - zlo) / dz) - 1;
+            int s1 = (int)std::floor((g->boxes[b].hi[2] - zlo) / dz) + 1;
+            s0 = std::max(s0, 0);
+            s1 = std::min(s1, kZSlabs - 1);
+            for (int sl = s0; sl <= s1; ++sl) zmask[sl] |= 1u << b;
+        }
+        MT_TRY(upload(h->d_zmask, zmask.data(), zmask.size(), h->bytes, "z-slab index"));
+        w.zmask = (const uint32_t *)h->d_zmask;
+        w.zslab_lo = (float)zlo;
+        w.zslab_inv = (float)(1.0 / dz);
     } else {
         const size_t nv = (size_t)g->vox_dims[0] * g->vox_dims[1] * g->vox_dims[2];
         MT_TRY(upload(h->d_vox, g->voxels, nv, h->bytes, "voxels"));

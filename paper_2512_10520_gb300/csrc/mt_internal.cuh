@@ -36,10 +36,14 @@ struct HistRec {
     float tscale;     // theta_max / ntheta
 };
 
+constexpr int kZSlabs = 256;   // z slabs of the box-candidate index
+
 struct WorldParams {
     // geometry
     int32_t geom_kind;
     int32_t n_box;
+    const uint32_t *zmask;         // [kZSlabs] candidate boxes per z slab (bit b = box b)
+    float zslab_lo, zslab_inv;     // slab = floor((z - zslab_lo) * zslab_inv), clamped
     int32_t world_mat;
     int32_t n_mat;
     const DevBox *boxes;
@@ -98,6 +102,7 @@ struct mt_handle {
     void *d_e2 = nullptr;
     void *d_fmap = nullptr;
     void *d_vox = nullptr;
+    void *d_zmask = nullptr;
     int64_t bytes = 0;
 };
 
