@@ -216,6 +216,29 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
                            uint64_t seed, const float *alpha, int32_t n_block, const mt_launch_cfg *cfg,
                            void *stream);
 
+/* Largest n that mt_transport_noalloc accepts. */
+#define MT_NOALLOC_MAX_MUONS 65536
+
+/* mt_transport for callers that must not allocate device memory: a process
+ * whose framework has already reserved the GPU's memory in its own pool, a
+ * latency-critical path that cannot afford an allocation's synchronisation, or
+ * a deployment whose memory use must be fixed when the library is loaded.  (The
+ * paper has no counterpart: it describes no allocation policy.)
+ * It runs the compacting transport (MT_LAUNCH_COMPACT, 64 steps per pass) with
+ * its scratch list in an 8 MiB array that the library reserves in device
+ * memory on every GPU that loads it, held until the process exits; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *  - n may be at most MT_NOALLOC_MAX_MUONS; larger n returns MT_ERR_INVALID_ARG
+ *    before anything is enqueued.  Other arguments and errors as mt_transport.
+ *  - All calls on one device share that array and leave their contents in it;
+ *    each call clears the counters it needs.  Calls that can overlap on the GPU
+ *    (different streams, or different host threads without ordering) race on the
+ *    array: order them, e.g. on one stream.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, thread-safe); make that first call before any stream capture. */
+mt_status mt_transport_noalloc(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
+                               uint64_t seed, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

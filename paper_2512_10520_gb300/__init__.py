@@ -10,5 +10,6 @@ from ._binding import (  # noqa: F401
     mt_abi_version, mt_last_error, mt_create, mt_destroy, mt_device_bytes,
     mt_transport, mt_transport_scaled, mt_transport_cfg, mt_transport_workspace_bytes,
     MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT,
+    mt_transport_noalloc, MT_NOALLOC_MAX_MUONS,
 )
 from .api import World, muons_to_device, muons_to_host  # noqa: F401

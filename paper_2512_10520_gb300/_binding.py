@@ -86,7 +86,11 @@ _SIGNATURES = {
     "mt_transport_cfg": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P,
                           C.c_int32, C.POINTER(mt_launch_cfg), _P], C.c_int),
     "mt_transport_workspace_bytes": ([C.c_int64], C.c_int64),
+    "mt_transport_noalloc": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P],
+                             C.c_int),
 }
+
+MT_NOALLOC_MAX_MUONS = 65536
 
 
 def library_path() -> str:
@@ -290,3 +294,14 @@ def mt_transport_cfg(handle: int, muons: Dict, step_len: float, max_steps: int, 
     _check(load_library().mt_transport_cfg(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
                                            int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr), int(nb), C.byref(cfg),
                                            C.c_void_p(_stream_ptr(stream))), "mt_transport_cfg")
+
+
+def mt_transport_noalloc(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, id_offset: int = 0,
+                         instance: int = 0, stream=None) -> None:
+    """mt_transport without any device allocation (scratch in the library's fixed device array;
+    at most MT_NOALLOC_MAX_MUONS muons per call; calls on one device must not overlap)."""
+    s = soa_struct(muons, id_offset, instance)
+    n = int(muons["x"].numel())
+    _check(load_library().mt_transport_noalloc(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
+                                               int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(_stream_ptr(stream))),
+           "mt_transport_noalloc")
