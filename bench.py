@@ -255,6 +255,13 @@ def run_mine(args):
     elapsed = start.elapsed_time(stop) / 1e3
     elapsed = _barrier_max(elapsed, ws, dev)
     kernel_s = float(np.mean([a.elapsed_time(b) for a, b in ev_k])) / 1e3
+    # kernels of this library per transport call: the compacting form launches
+    # compact_init plus ceil(max_steps / steps_per_pass) compact_pass kernels
+    if args.mode in ("auto", "compact"):
+        spp = args.steps_per_pass or 64
+        launches_per_call = 1 + (wl.max_steps + spp - 1) // spp
+    else:
+        launches_per_call = 1
     total_steps = _barrier_sum(steps_per_batch * args.steps, ws, dev)
     value = total_steps / elapsed
 
@@ -283,9 +290,11 @@ def run_mine(args):
     peaks, peak_kind = _peaks()
     achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": _traffic("transport_kernel"),
+            "frac": achieved_gbs / peaks["hbm_gbs"],
+            "traffic": _traffic("transport") if args.mode == "auto" and not args.steps_per_pass else None,
             "peak_kind": peak_kind, "bytes_per_step": BYTES_PER_STEP,
-            "kernel_ms": kernel_s * 1e3}
+            "kernel_ms": kernel_s * 1e3,
+            "timed_unit": "one mt_transport call (all of its kernels), CUDA events on the launching stream"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
@@ -307,7 +316,7 @@ def run_mine(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_call,
             "clocks": clocks,
         }
         print(json.dumps(line))
