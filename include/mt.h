@@ -216,6 +216,61 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
                            uint64_t seed, const float *alpha, int32_t n_block, const mt_launch_cfg *cfg,
                            void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiable form.  The paper's Discussion proposes turning the histogram
+ * transport into a differentiable layer so that magnet fields can be optimised
+ * by gradient descent.  Parameters: per-magnet field scales alpha (device,
+ * n_block x 3 floats, B inside block b scaled component-wise by alpha[3b+c]).
+ * Gradients are pathwise: every draw of every step (material, box, momentum
+ * bin, cell, f, theta, phi) and every muon's step count are held fixed (common
+ * random numbers); the scattering rotation (Eq. 3), the trilinear field (with
+ * its gradient in r) and the RK4 step (Eq. 4) are differentiated by
+ * hand-written adjoints.  Checkpoints every ckpt_every = K steps (1..64) bound
+ * the memory: the backward recomputes each K-step segment from its checkpoint.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of checkpoint storage for n muons (n < 2^31). */
+int64_t mt_ckpt_bytes(int64_t n, int32_t max_steps, int32_t ckpt_every);
+
+/* Checkpointing forward: exactly mt_transport_scaled (same results), keeping
+ * the state of every muon alive at steps 0, K, 2K, ... in `ckpt` (device,
+ * 256-byte aligned, at least mt_ckpt_bytes bytes, caller-owned and reused by
+ * mt_adjoint_ckpt).  Errors as mt_transport_scaled, plus MT_ERR_INVALID_ARG for
+ * K outside [1, 64], n >= 2^31 or a checkpoint buffer too small / unaligned. */
+mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
+                            uint64_t seed, const float *alpha, int32_t n_block, int32_t ckpt_every, void *ckpt,
+                            int64_t ckpt_bytes, void *stream);
+
+/* Backward from the checkpoints of one mt_transport_ckpt call, which must be
+ * given the same n, step_len, max_steps, seed, alpha (values), ckpt_every,
+ * id_offset and instance.  dL_dfinal: device [6][n] floats, dL/d(x, y, z, px,
+ * py, pz) of the final state (SoA rows).  dL_dalpha: device [n_block][3],
+ * overwritten.  dL_dinitial (may be NULL): device [6][n], receives dL/d(initial
+ * state) in the same layout.  The checkpoint buffer's header is used as the
+ * gradient accumulator.  Scratch (6n floats when dL_dinitial is NULL) comes
+ * from the stream-ordered allocator.  Errors: MT_ERR_INVALID_ARG for null or
+ * inconsistent arguments, MT_ERR_OOM, MT_ERR_CUDA. */
+mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, int32_t max_steps, uint64_t seed,
+                          const float *alpha, int32_t n_block, int32_t ckpt_every, void *ckpt, int64_t ckpt_bytes,
+                          int64_t id_offset, int32_t instance, const float *dL_dfinal, float *dL_dinitial,
+                          float *dL_dalpha, void *stream);
+
+/* dL/dalpha in one call from the INITIAL muon state s0 (left unchanged): a
+ * checkpointing forward on a private copy, then mt_adjoint_ckpt.  All scratch
+ * (checkpoints and the state copy) comes from the stream-ordered allocator. */
+mt_status mt_transport_adjoint(mt_handle *h, const mt_muon_soa *s0, int64_t n, float step_len, int32_t max_steps,
+                               uint64_t seed, const float *alpha, int32_t n_block, const float *dL_dfinal,
+                               float *dL_dalpha, int32_t ckpt_every, void *stream);
+
+/* Acceptance loss of final states: L = (1/n) sum over muons of
+ * s((h - |x_e|)/e) s((h - |y_e|)/e), s the logistic function and (x_e, y_e)
+ * the straight-line extrapolation of (x, y) to the plane z = z_plane; muons
+ * that stopped or are invalid, or have pz <= 0, contribute 0.  *loss (device
+ * double) is overwritten; dL_dfinal (device [6][n] floats, may be NULL)
+ * receives dL/d(x, y, z, px, py, pz).  Reads x..pz and status of s only. */
+mt_status mt_acceptance_loss(const mt_muon_soa *s, int64_t n, double z_plane, double half_width, double edge,
+                             double *loss, float *dL_dfinal, void *stream);
+
 /* Largest n that mt_transport_noalloc accepts. */
 #define MT_NOALLOC_MAX_MUONS 65536
 

@@ -11,5 +11,7 @@ from ._binding import (  # noqa: F401
     mt_transport, mt_transport_scaled, mt_transport_cfg, mt_transport_workspace_bytes,
     MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT,
     mt_transport_noalloc, MT_NOALLOC_MAX_MUONS,
+    mt_ckpt_bytes, mt_transport_ckpt, mt_adjoint_ckpt, mt_transport_adjoint, mt_acceptance_loss,
 )
 from .api import World, muons_to_device, muons_to_host  # noqa: F401
+from .autograd import MuonTransportFn, AcceptanceLossFn, transport_differentiable, acceptance_loss  # noqa: F401,E402

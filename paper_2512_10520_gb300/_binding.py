@@ -88,6 +88,15 @@ _SIGNATURES = {
     "mt_transport_workspace_bytes": ([C.c_int64], C.c_int64),
     "mt_transport_noalloc": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P],
                              C.c_int),
+    "mt_ckpt_bytes": ([C.c_int64, C.c_int32, C.c_int32], C.c_int64),
+    "mt_transport_ckpt": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P, C.c_int32,
+                           C.c_int32, _P, C.c_int64, _P], C.c_int),
+    "mt_adjoint_ckpt": ([_P, C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P, C.c_int32, C.c_int32, _P, C.c_int64,
+                         C.c_int64, C.c_int32, _P, _P, _P, _P], C.c_int),
+    "mt_transport_adjoint": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P,
+                              C.c_int32, _P, _P, C.c_int32, _P], C.c_int),
+    "mt_acceptance_loss": ([C.POINTER(mt_muon_soa), C.c_int64, C.c_double, C.c_double, C.c_double, _P, _P, _P],
+                           C.c_int),
 }
 
 MT_NOALLOC_MAX_MUONS = 65536
@@ -305,3 +314,79 @@ def mt_transport_noalloc(handle: int, muons: Dict, step_len: float, max_steps: i
     _check(load_library().mt_transport_noalloc(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
                                                int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(_stream_ptr(stream))),
            "mt_transport_noalloc")
+
+
+# --------------------------------------------------------------------------
+# differentiable form
+# --------------------------------------------------------------------------
+def _alpha_ptr(alpha):
+    if alpha is None:
+        return None, 0
+    if not alpha.is_cuda or str(alpha.dtype) != "torch.float32" or not alpha.is_contiguous():
+        raise TypeError("alpha must be a contiguous float32 CUDA tensor [n_block, 3]")
+    return alpha.data_ptr(), alpha.numel() // 3
+
+
+def _f32_dev(t, what):
+    if t is None:
+        return None
+    if not t.is_cuda or str(t.dtype) != "torch.float32" or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def mt_ckpt_bytes(n: int, max_steps: int, ckpt_every: int) -> int:
+    return load_library().mt_ckpt_bytes(int(n), int(max_steps), int(ckpt_every))
+
+
+def mt_transport_ckpt(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, alpha, ckpt_every: int,
+                      ckpt, id_offset: int = 0, instance: int = 0, stream=None) -> None:
+    """Checkpointing forward: transport in place, keeping every K-step live list in `ckpt` (uint8 CUDA tensor)."""
+    s = soa_struct(muons, id_offset, instance)
+    a_ptr, nb = _alpha_ptr(alpha)
+    _check(load_library().mt_transport_ckpt(C.c_void_p(handle), C.byref(s), int(muons["x"].numel()), float(step_len),
+                                            int(max_steps), int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr),
+                                            int(nb), int(ckpt_every), C.c_void_p(ckpt.data_ptr()),
+                                            int(ckpt.numel() * ckpt.element_size()),
+                                            C.c_void_p(_stream_ptr(stream))), "mt_transport_ckpt")
+
+
+def mt_adjoint_ckpt(handle: int, n: int, step_len: float, max_steps: int, seed: int, alpha, ckpt_every: int, ckpt,
+                    dL_dfinal, dL_dalpha, dL_dinitial=None, id_offset: int = 0, instance: int = 0,
+                    stream=None) -> None:
+    """Backward from the checkpoints: dL/dalpha (and optionally dL/d initial state) from dL/d final state [6, n]."""
+    a_ptr, nb = _alpha_ptr(alpha)
+    _check(load_library().mt_adjoint_ckpt(C.c_void_p(handle), int(n), float(step_len), int(max_steps),
+                                          int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr), int(nb),
+                                          int(ckpt_every), C.c_void_p(ckpt.data_ptr()),
+                                          int(ckpt.numel() * ckpt.element_size()), int(id_offset), int(instance),
+                                          C.c_void_p(_f32_dev(dL_dfinal, "dL_dfinal")),
+                                          C.c_void_p(_f32_dev(dL_dinitial, "dL_dinitial")),
+                                          C.c_void_p(_f32_dev(dL_dalpha, "dL_dalpha")),
+                                          C.c_void_p(_stream_ptr(stream))), "mt_adjoint_ckpt")
+
+
+def mt_transport_adjoint(handle: int, muons0: Dict, step_len: float, max_steps: int, seed: int, alpha, dL_dfinal,
+                         dL_dalpha, ckpt_every: int = 32, id_offset: int = 0, instance: int = 0, stream=None) -> None:
+    """dL/dalpha from the INITIAL muons (left unchanged) and dL/d final state, in one call."""
+    s = soa_struct(muons0, id_offset, instance)
+    a_ptr, nb = _alpha_ptr(alpha)
+    _check(load_library().mt_transport_adjoint(C.c_void_p(handle), C.byref(s), int(muons0["x"].numel()),
+                                               float(step_len), int(max_steps), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                               C.c_void_p(a_ptr), int(nb), C.c_void_p(_f32_dev(dL_dfinal, "dL_dfinal")),
+                                               C.c_void_p(_f32_dev(dL_dalpha, "dL_dalpha")), int(ckpt_every),
+                                               C.c_void_p(_stream_ptr(stream))), "mt_transport_adjoint")
+
+
+def mt_acceptance_loss(muons: Dict, loss, dL_dfinal=None, z_plane: float = 30.0, half_width: float = 0.5,
+                       edge: float = 0.01, stream=None) -> None:
+    """Acceptance loss of final states into `loss` (float64 CUDA tensor [1]); dL/d final state into dL_dfinal."""
+    s = mt_muon_soa()
+    for k in ("x", "y", "z", "px", "py", "pz", "status"):
+        setattr(s, k, muons[k].data_ptr())
+    if not loss.is_cuda or str(loss.dtype) != "torch.float64":
+        raise TypeError("loss must be a float64 CUDA tensor")
+    _check(load_library().mt_acceptance_loss(C.byref(s), int(muons["x"].numel()), float(z_plane), float(half_width),
+                                             float(edge), C.c_void_p(loss.data_ptr()),
+                                             C.c_void_p(_f32_dev(dL_dfinal, "dL_dfinal")),
+                                             C.c_void_p(_stream_ptr(stream))), "mt_acceptance_loss")

@@ -1,0 +1,721 @@
+// adjoint.cu -- the differentiable form: pathwise gradients of a loss of the
+// final muon states with respect to per-magnet field scales alpha[block][c].
+//
+// The paper's Discussion proposes making the histogram transport a
+// differentiable layer.  Here every random choice of a step (material, box,
+// momentum bin, cell, f, theta, phi) and every muon's step count are held
+// fixed (common random numbers), and the derivative of the remaining smooth
+// map -- scattering rotation (Eq. 3), trilinear field (with dB/dr) and the RK4
+// step of Eq. 4 -- is propagated backwards by hand-written adjoints.
+//
+// Forward (mt_transport_ckpt): the compacting transport with a pass length of
+// K = ckpt_every steps whose live lists are all kept: the list that enters
+// pass p is the checkpoint of every muon alive at step p K.
+// Backward (mt_adjoint_ckpt): passes in reverse order; each live muon of pass
+// p recomputes its (at most K) steps from the checkpoint with the forward's own
+// step function, recording a tape in local memory, then walks the tape
+// backwards, carrying (dL/dr, dL/dp) in a per-muon buffer from pass to pass and
+// accumulating dL/dalpha.
+//
+// Checkpoint buffer: [ counts | dL/dalpha | list 0 | list 1 | ... | list P ]:
+// P + 1 live counts (uint64), the dL/dalpha accumulator (double
+// [MT_MAX_BOXES][3]), then P + 1 live lists of four float4 arrays of n entries
+// (step.cuh), each section 256-byte aligned, P = ceil(max_steps / K).
+#include <cstdio>
+
+#include "compact.cuh"
+
+namespace mt {
+
+constexpr int kTapeMax = 64;
+
+struct CkptLayout {
+    int passes;
+    int64_t alpha_off, lists_off, list_bytes, total;
+};
+
+static CkptLayout ckpt_layout(int64_t n, int32_t max_steps, int32_t K)
+{
+    CkptLayout L;
+    const int64_t cap = n > 0 ? n : 1;
+    L.passes = max_steps > 0 ? (max_steps + K - 1) / K : 1;
+    L.alpha_off = ((int64_t)(L.passes + 1) * 8 + 255) & ~(int64_t)255;
+    L.lists_off = (L.alpha_off + 3 * MT_MAX_BOXES * 8 + 255) & ~(int64_t)255;
+    L.list_bytes = 4 * cap * (int64_t)sizeof(float4);
+    L.total = L.lists_off + (L.passes + 1) * L.list_bytes;
+    return L;
+}
+
+struct TapeEntry {
+    float r[3];   // position at the step's start
+    float p[3];   // momentum at the step's start (before scattering)
+    float f, th, cphi, sphi;
+    int meta;     // bit 0: scattered; bits 8..15: box + 1 (0: no box)
+};
+
+struct TapeWriter {
+    TapeEntry *t;
+    __device__ __forceinline__ void begin(const State &s, int box)
+    {
+        t->r[0] = s.x + s.xl;
+        t->r[1] = s.y + s.yl;
+        t->r[2] = s.z + s.zl;
+        t->p[0] = s.px + s.pxl;
+        t->p[1] = s.py + s.pyl;
+        t->p[2] = s.pz + s.pzl;
+        t->meta = (box + 1) << 8;
+    }
+    __device__ __forceinline__ void draw(float f, float th, float c, float sn)
+    {
+        t->f = f;
+        t->th = th;
+        t->cphi = c;
+        t->sphi = sn;
+        t->meta |= 1;
+    }
+};
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ float dot3(const float a[3], const float b[3])
+{
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+// Unscaled trilinear field at r and its Jacobian J[c][a] = dB_c/dr_a (zero
+// outside the node box).
+__device__ __forceinline__ void field_map_grad(const WorldParams &w, const float r[3], float B[3], float J[3][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        B[c] = 0.0f;
+        J[c][0] = J[c][1] = J[c][2] = 0.0f;
+    }
+    const int nx = w.fdims[0], ny = w.fdims[1], nz = w.fdims[2];
+    int i, j, k;
+    float tx, ty, tz;
+    if (!map_axis(r[0], 0.0f, w.forigin[0], w.forigin_lo[0], w.fspacing[0], w.fspacing_lo[0], w.finv[0], nx, i, tx) ||
+        !map_axis(r[1], 0.0f, w.forigin[1], w.forigin_lo[1], w.fspacing[1], w.fspacing_lo[1], w.finv[1], ny, j, ty) ||
+        !map_axis(r[2], 0.0f, w.forigin[2], w.forigin_lo[2], w.fspacing[2], w.fspacing_lo[2], w.finv[2], nz, k, tz))
+        return;
+    const int64_t row = nx - 1;
+    const float4 *p00 = w.fmap + 2 * (((int64_t)k * ny + j) * row + i);
+    const float4 *p10 = p00 + 2 * row;
+    const float4 *p01 = p00 + 2 * row * ny;
+    const float4 *p11 = p01 + 2 * row;
+    const float4 c4[8] = {__ldg(p00), __ldg(p00 + 1), __ldg(p10), __ldg(p10 + 1),
+                          __ldg(p01), __ldg(p01 + 1), __ldg(p11), __ldg(p11 + 1)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = c == 0 ? c4[q].x : (c == 1 ? c4[q].y : c4[q].z);
+        // v: (i,j,k) (i+1,j,k) (i,j+1,k) (i+1,j+1,k) (i,j,k+1) (i+1,j,k+1) (i,j+1,k+1) (i+1,j+1,k+1)
+        const float a = lerp(tx, v[0], v[1]), b = lerp(tx, v[2], v[3]);
+        const float cc = lerp(tx, v[4], v[5]), d = lerp(tx, v[6], v[7]);
+        const float e = lerp(ty, a, b), g = lerp(ty, cc, d);
+        B[c] = lerp(tz, e, g);
+        J[c][0] = lerp(tz, lerp(ty, v[1] - v[0], v[3] - v[2]), lerp(ty, v[5] - v[4], v[7] - v[6])) * w.finv[0];
+        J[c][1] = lerp(tz, b - a, d - cc) * w.finv[1];
+        J[c][2] = (g - e) * w.finv[2];
+    }
+}
+
+// dL/dalpha of the current magnet block, flushed to shared memory when the
+// muon changes block (rare: it stays in a block for hundreds of steps).
+struct AlphaAcc {
+    int blk = -1;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    __device__ __forceinline__ void flush(float (*sacc)[MT_MAX_BOXES])
+    {
+        if (blk >= 0) {
+            atomicAdd(&sacc[0][blk], a0);
+            atomicAdd(&sacc[1][blk], a1);
+            atomicAdd(&sacc[2][blk], a2);
+        }
+        a0 = a1 = a2 = 0.0f;
+    }
+    __device__ __forceinline__ void add(int b, float x, float y, float z, float (*sacc)[MT_MAX_BOXES])
+    {
+        if (b != blk) {
+            flush(sacc);
+            blk = b;
+        }
+        a0 += x;
+        a1 += y;
+        a2 += z;
+    }
+};
+
+// Reverse of one forward step recorded in t: (rb, pb) enter as dL/d(r, p) after
+// the step and leave as dL/d(r, p) before it.
+template <int GEOM, int FIELD>
+__device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWorld &sw, const TapeEntry &t, float q,
+                                             float d, float kd, float rb[3], float pb[3], AlphaAcc &acc,
+                                             float (*sacc)[MT_MAX_BOXES])
+{
+    const float p[3] = {t.p[0], t.p[1], t.p[2]};
+    const bool scat = t.meta & 1;
+    const int box = (t.meta >> 8) - 1;
+    // -- recompute the scattered momentum ps = p + sm1 p + P kf tv(u)
+    float ps[3] = {p[0], p[1], p[2]};
+    float u[3] = {0.0f, 0.0f, 0.0f}, tv[3] = {0.0f, 0.0f, 0.0f};
+    float P = 0.0f, rPs = 0.0f, sm1 = 0.0f, kf = 0.0f, g = 0.0f, wv = 0.0f;
+    bool degen = false;
+    if (scat) {
+        const float P2 = dot3(p, p);
+        rPs = rsqrtf(P2);
+        rPs = rPs * fmaf(-0.5f * P2 * rPs, rPs, 1.5f);
+        P = P2 * rPs;
+        u[0] = p[0] * rPs;
+        u[1] = p[1] * rPs;
+        u[2] = p[2] * rPs;
+        float st, omc;
+        sin_omc(t.th, st, omc);
+        sm1 = -fmaf(t.f, 1.0f - omc, omc);
+        kf = (1.0f - t.f) * st;
+        const float s2 = fmaf(u[0], u[0], u[1] * u[1]);
+        if (u[2] < 0.0f && s2 < 1e-24f) {
+            degen = true;
+            tv[0] = t.cphi;
+            tv[1] = -t.sphi;
+        } else {
+            g = u[2] >= 0.0f ? 1.0f / (1.0f + u[2]) : (1.0f - u[2]) / s2;
+            wv = fmaf(t.cphi, u[0], t.sphi * u[1]);
+            tv[0] = t.cphi - u[0] * wv * g;
+            tv[1] = t.sphi - u[1] * wv * g;
+            tv[2] = -wv;
+        }
+        const float kick = P * kf;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ps[c] = fmaf(sm1, p[c], fmaf(kick, tv[c], p[c]));
+    }
+    // -- field: B = sc (.) Bm(r)
+    float Bm[3] = {0.0f, 0.0f, 0.0f}, J[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    if (FIELD == MT_FIELD_BOX) {
+        if (box >= 0) {
+            Bm[0] = sw.B[0][box];
+            Bm[1] = sw.B[1][box];
+            Bm[2] = sw.B[2][box];
+        }
+    } else if (FIELD == MT_FIELD_MAP) {
+        field_map_grad(w, t.r, Bm, J);
+    }
+    int blk = -1;
+    float sc[3] = {1.0f, 1.0f, 1.0f};
+    if (GEOM == MT_GEOM_BOXES && FIELD != MT_FIELD_NONE && box >= 0) {
+        blk = sw.block[box];
+        if (blk >= 0) {
+            sc[0] = sw.alpha[0][blk];
+            sc[1] = sw.alpha[1][blk];
+            sc[2] = sw.alpha[2][blk];
+        }
+    }
+    const float B[3] = {sc[0] * Bm[0], sc[1] * Bm[1], sc[2] * Bm[2]};
+    // -- recompute the RK4 stages (k_i = p_i x h, h = kappa q d B / P0)
+    const float P02 = dot3(ps, ps);
+    float rP0 = rsqrtf(P02);
+    rP0 = rP0 * fmaf(-0.5f * P02 * rP0, rP0, 1.5f);
+    const float cc = (kd * q) * rP0;
+    const float a = d * rP0;
+    const float h[3] = {cc * B[0], cc * B[1], cc * B[2]};
+    float k1[3], k2[3], k3[3], k4[3], p2[3], p3[3], p4[3];
+    cross3(ps, h, k1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p2[c] = fmaf(0.5f, k1[c], ps[c]);
+    cross3(p2, h, k2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p3[c] = fmaf(0.5f, k2[c], ps[c]);
+    cross3(p3, h, k3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p4[c] = ps[c] + k3[c];
+    cross3(p4, h, k4);
+    // -- reverse of r' = r + a (ps + (k1+k2+k3)/6), p' = ps + (k1 + 2k2 + 2k3 + k4)/6
+    const float sixth = 1.0f / 6.0f;
+    float rsum[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rsum[c] = fmaf(sixth, k1[c] + k2[c] + k3[c], ps[c]);
+    const float abar = dot3(rb, rsum);
+    float psb[3], k1b[3], k2b[3], k3b[3], k4b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        psb[c] = fmaf(a, rb[c], pb[c]);
+        const float ra = a * sixth * rb[c];
+        k1b[c] = fmaf(sixth, pb[c], ra);
+        k2b[c] = fmaf(2.0f * sixth, pb[c], ra);
+        k3b[c] = k2b[c];
+        k4b[c] = sixth * pb[c];
+    }
+    float hb[3] = {0.0f, 0.0f, 0.0f}, tmp[3];
+    // k4 = p4 x h, p4 = ps + k3
+    cross3(h, k4b, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        psb[c] += tmp[c];
+        k3b[c] += tmp[c];
+    }
+    cross3(k4b, p4, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
+    // k3 = p3 x h, p3 = ps + k2 / 2
+    cross3(h, k3b, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        psb[c] += tmp[c];
+        k2b[c] = fmaf(0.5f, tmp[c], k2b[c]);
+    }
+    cross3(k3b, p3, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
+    // k2 = p2 x h, p2 = ps + k1 / 2
+    cross3(h, k2b, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        psb[c] += tmp[c];
+        k1b[c] = fmaf(0.5f, tmp[c], k1b[c]);
+    }
+    cross3(k2b, p2, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
+    // k1 = ps x h
+    cross3(h, k1b, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) psb[c] += tmp[c];
+    cross3(k1b, ps, tmp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
+    // h = cc B, cc = kappa q d / P0, a = d / P0, P0 = |ps|
+    const float ccb = dot3(hb, B);
+    const float P0b = -(ccb * cc + abar * a) * rP0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) psb[c] = fmaf(P0b * rP0, ps[c], psb[c]);
+    // -- field: B = sc (.) Bm(r)
+    const float Bb[3] = {cc * hb[0], cc * hb[1], cc * hb[2]};
+    if (blk >= 0) acc.add(blk, Bb[0] * Bm[0], Bb[1] * Bm[1], Bb[2] * Bm[2], sacc);
+    if (FIELD == MT_FIELD_MAP) {
+        const float Bmb[3] = {sc[0] * Bb[0], sc[1] * Bb[1], sc[2] * Bb[2]};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) rb[ax] += Bmb[0] * J[0][ax] + Bmb[1] * J[1][ax] + Bmb[2] * J[2][ax];
+    }
+    // -- scattering: ps = (1 + sm1) p + P kf tv(u), u = p / P
+    if (!scat) {
+        pb[0] = psb[0];
+        pb[1] = psb[1];
+        pb[2] = psb[2];
+        return;
+    }
+    const float Pb = kf * dot3(tv, psb);
+    float ub[3] = {0.0f, 0.0f, 0.0f};
+    if (!degen) {
+        const float kick = P * kf;
+        const float tb[3] = {kick * psb[0], kick * psb[1], kick * psb[2]};
+        const float s = tb[0] * u[0] + tb[1] * u[1];
+        const float wb = -s * g - tb[2];
+        const float gb = -s * wv;
+        ub[0] = fmaf(wb, t.cphi, -tb[0] * wv * g);
+        ub[1] = fmaf(wb, t.sphi, -tb[1] * wv * g);
+        ub[2] = -gb * g * g;
+    }
+    const float uu = dot3(u, ub);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pb[c] = fmaf(1.0f + sm1, psb[c], fmaf(Pb, u[c], (ub[c] - u[c] * uu) * rPs));
+}
+
+template <int GEOM, int FIELD>
+__global__ void __launch_bounds__(kBlock) adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck,
+                                                       const unsigned long long *count_p, int S, float *adj,
+                                                       int64_t n, double *dalpha)
+{
+    __shared__ SmemWorld sw;
+    __shared__ float sacc[3][MT_MAX_BOXES];
+    const int64_t count = (int64_t)*count_p;
+    if (count == 0) return;
+    stage_world(sw, w, rp);
+    for (int t = threadIdx.x; t < 3 * MT_MAX_BOXES; t += blockDim.x) (&sacc[0][0])[t] = 0.0f;
+    __syncthreads();
+    AlphaAcc acc;
+    TapeEntry tape[kTapeMax];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        State s;
+        float q;
+        int k;
+        int64_t idx;
+        get_live(ck, i, s, q, k, idx);
+        const uint64_t id = (uint64_t)(rp.id_offset + idx);
+        const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+        const int kend = min(k + S, rp.max_steps);
+        int ns = 0;
+#pragma unroll 1
+        for (; k < kend; ++k) {
+            const int r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp, TapeWriter{&tape[ns]});
+            if (r != MT_ALIVE) break;
+            ++ns;
+        }
+        float rb[3] = {adj[idx], adj[n + idx], adj[2 * n + idx]};
+        float pb[3] = {adj[3 * n + idx], adj[4 * n + idx], adj[5 * n + idx]};
+#pragma unroll 1
+        for (int j = ns - 1; j >= 0; --j) reverse_step<GEOM, FIELD>(w, sw, tape[j], q, rp.d, rp.kd, rb, pb, acc, sacc);
+        adj[idx] = rb[0];
+        adj[n + idx] = rb[1];
+        adj[2 * n + idx] = rb[2];
+        adj[3 * n + idx] = pb[0];
+        adj[4 * n + idx] = pb[1];
+        adj[5 * n + idx] = pb[2];
+    }
+    acc.flush(sacc);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * MT_MAX_BOXES; t += blockDim.x) {
+        const float v = sacc[t % 3][t / 3];
+        if (v != 0.0f) atomicAdd(&dalpha[t], (double)v);
+    }
+}
+
+__global__ void alpha_to_float(const double *src, float *dst, int m)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) dst[t] = (float)src[t];
+}
+
+// Acceptance loss of the differentiable form: mean over all n muons of
+// s((h - |x_e|)/w) s((h - |y_e|)/w), (x_e, y_e) the straight-line extrapolation
+// of the final state to z = zL; STOPPED / INVALID muons and pz <= 0 give 0.
+__global__ void __launch_bounds__(kBlock) acceptance_loss_kernel(const mt_muon_soa s, int64_t n, float zL, float half,
+                                                                 float width, double *loss, float *g)
+{
+    __shared__ double part[kBlock / 32];
+    double local = 0.0;
+    const float inv_n = 1.0f / (float)n;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t st = s.status[m];
+        const float pz = s.pz[m];
+        float gx = 0.0f, gy = 0.0f, gz = 0.0f, gpx = 0.0f, gpy = 0.0f, gpz = 0.0f;
+        if (st != MT_STOPPED && st != MT_INVALID && pz > 0.0f) {
+            const float x = s.x[m], y = s.y[m], z = s.z[m], px = s.px[m], py = s.py[m];
+            const float lz = zL - z;
+            const float xe = fmaf(lz, px / pz, x), ye = fmaf(lz, py / pz, y);
+            const float sa = 1.0f / (1.0f + expf(-(half - fabsf(xe)) / width));
+            const float sb = 1.0f / (1.0f + expf(-(half - fabsf(ye)) / width));
+            local += (double)(sa * sb);
+            const float dxe = sa * (1.0f - sa) * sb * (xe >= 0.0f ? -1.0f : 1.0f) / width * inv_n;
+            const float dye = sb * (1.0f - sb) * sa * (ye >= 0.0f ? -1.0f : 1.0f) / width * inv_n;
+            gx = dxe;
+            gy = dye;
+            gz = -(dxe * px + dye * py) / pz;
+            gpx = dxe * lz / pz;
+            gpy = dye * lz / pz;
+            gpz = -(dxe * px + dye * py) * lz / (pz * pz);
+        }
+        if (g) {
+            g[m] = gx;
+            g[n + m] = gy;
+            g[2 * n + m] = gz;
+            g[3 * n + m] = gpx;
+            g[4 * n + m] = gpy;
+            g[5 * n + m] = gpz;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
+        atomicAdd(loss, t / (double)n);
+    }
+}
+
+static int resident_grid(const void *kernel, int64_t work)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t need = (work + kBlock - 1) / kBlock;
+    if (grid > need) grid = need;
+    return (int)(grid < 1 ? 1 : grid);
+}
+
+int64_t ckpt_bytes(int64_t n, int32_t max_steps, int32_t K) { return ckpt_layout(n, max_steps, K).total; }
+
+template <int GEOM, int FIELD>
+static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
+                                cudaStream_t st, int K, char *ck)
+{
+    const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
+    cudaError_t e = cudaMemsetAsync(ck, 0, (size_t)L.lists_off, st);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (n + kBlock - 1) / kBlock;
+    compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
+        soa, n, rp, live_buf_at(ck + L.lists_off, n), ctr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int grid = resident_grid((const void *)compact_pass<GEOM, FIELD>, n);
+    for (int p = 0; p < L.passes; ++p) {
+        compact_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(
+            w, soa, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
+            live_buf_at(ck + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, nullptr, K);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <int GEOM, int FIELD>
+static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
+                                 char *ck, float *adj)
+{
+    const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
+    const unsigned long long *ctr = reinterpret_cast<const unsigned long long *>(ck);
+    double *dalpha = reinterpret_cast<double *>(ck + L.alpha_off);
+    cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int grid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+    for (int p = L.passes - 1; p >= 0; --p) {
+        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
+                                                           ctr + p, K, adj, n, dalpha);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+#define MT_DISPATCH(FN, ...)                                                           \
+    (w.geom_kind == MT_GEOM_BOXES                                                      \
+         ? (w.field_kind == MT_FIELD_MAP   ? FN<MT_GEOM_BOXES, MT_FIELD_MAP>(__VA_ARGS__) \
+            : w.field_kind == MT_FIELD_BOX ? FN<MT_GEOM_BOXES, MT_FIELD_BOX>(__VA_ARGS__) \
+                                           : FN<MT_GEOM_BOXES, MT_FIELD_NONE>(__VA_ARGS__)) \
+         : (w.field_kind == MT_FIELD_MAP ? FN<MT_GEOM_VOXELS, MT_FIELD_MAP>(__VA_ARGS__)   \
+                                         : FN<MT_GEOM_VOXELS, MT_FIELD_NONE>(__VA_ARGS__)))
+
+}  // namespace mt
+
+using namespace mt;
+
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+mt_status fill_run(RunParams &rp, float step_len, int32_t max_steps, uint64_t seed, const float *alpha,
+                   int32_t n_block, int64_t id_offset, int32_t instance)
+{
+    if (!(step_len > 0.0f) || !isfinite(step_len) || max_steps < 0) {
+        set_error("step_len must be positive and finite, max_steps >= 0");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (alpha && (n_block < 0 || n_block > MT_MAX_BOXES)) {
+        set_error("n_block %d outside [0, %d]", n_block, MT_MAX_BOXES);
+        return MT_ERR_INVALID_ARG;
+    }
+    rp.d = step_len;
+    rp.kd = (float)(0.299792458 * (double)step_len);
+    rp.max_steps = max_steps;
+    rp.key0 = (uint32_t)seed;
+    rp.key1 = (uint32_t)(seed >> 32);
+    rp.alpha = alpha;
+    rp.n_block = alpha ? n_block : 0;
+    rp.instance = instance;
+    rp.id_offset = id_offset;
+    return MT_OK;
+}
+
+mt_status check_ckpt(int64_t n, int32_t max_steps, int32_t K, const void *ck, int64_t bytes)
+{
+    if (K < 1 || K > kTapeMax) {
+        set_error("ckpt_every %d outside [1, %d]", K, kTapeMax);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (n < 0 || n >= ((int64_t)1 << 31)) {
+        set_error("n = %lld outside [0, 2^31)", (long long)n);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (!ck || (reinterpret_cast<uintptr_t>(ck) & 255u) || bytes < ckpt_bytes(n, max_steps, K)) {
+        set_error("checkpoint buffer %p of %lld bytes: need %lld bytes, 256-byte aligned", ck, (long long)bytes,
+                  (long long)ckpt_bytes(n, max_steps, K));
+        return MT_ERR_INVALID_ARG;
+    }
+    return MT_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t mt_ckpt_bytes(int64_t n, int32_t max_steps, int32_t ckpt_every)
+{
+    if (ckpt_every < 1) return -1;
+    return ckpt_bytes(n, max_steps, ckpt_every);
+}
+
+extern "C" mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
+                                       uint64_t seed, const float *alpha, int32_t n_block, int32_t ckpt_every,
+                                       void *ckpt, int64_t ckpt_bytes_, void *stream)
+{
+    if (!h || !s) {
+        set_error("null handle or muon SoA");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!s->x || !s->y || !s->z || !s->px || !s->py || !s->pz || !s->q || !s->steps || !s->status)) {
+        set_error("null muon array with n > 0");
+        return MT_ERR_INVALID_ARG;
+    }
+    RunParams rp;
+    mt_status stt = fill_run(rp, step_len, max_steps, seed, alpha, n_block, s->id_offset, s->instance);
+    if (stt != MT_OK) return stt;
+    stt = check_ckpt(n, max_steps, ckpt_every, ckpt, ckpt_bytes_);
+    if (stt != MT_OK) return stt;
+    if (n == 0) return MT_OK;
+    DevGuard g(h->device);
+    const WorldParams &w = h->w;
+    const cudaError_t e = MT_DISPATCH(ckpt_forward, w, *s, n, rp, (cudaStream_t)stream, ckpt_every, (char *)ckpt);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpointing transport");
+    return MT_OK;
+}
+
+extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, int32_t max_steps, uint64_t seed,
+                                     const float *alpha, int32_t n_block, int32_t ckpt_every, void *ckpt,
+                                     int64_t ckpt_bytes_, int64_t id_offset, int32_t instance, const float *dL_dfinal,
+                                     float *dL_dinitial, float *dL_dalpha, void *stream)
+{
+    if (!h) {
+        set_error("null handle");
+        return MT_ERR_INVALID_ARG;
+    }
+    RunParams rp;
+    mt_status stt = fill_run(rp, step_len, max_steps, seed, alpha, n_block, id_offset, instance);
+    if (stt != MT_OK) return stt;
+    if (n != 0) {
+        stt = check_ckpt(n, max_steps, ckpt_every, ckpt, ckpt_bytes_);
+        if (stt != MT_OK) return stt;
+    }
+    if (id_offset < 0 || n < 0 || (n > 0 && !dL_dfinal) || (alpha && n_block > 0 && !dL_dalpha)) {
+        set_error("negative id_offset or n, or null dL_dfinal / dL_dalpha");
+        return MT_ERR_INVALID_ARG;
+    }
+    DevGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const WorldParams &w = h->w;
+    if (n == 0) {
+        if (alpha && n_block > 0) {
+            const cudaError_t e = cudaMemsetAsync(dL_dalpha, 0, 3 * n_block * sizeof(float), st);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+        }
+        return MT_OK;
+    }
+    float *adj = dL_dinitial;
+    bool own = false;
+    cudaError_t e = cudaSuccess;
+    if (!adj) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&adj), 6 * n * sizeof(float), st);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
+        own = true;
+    }
+    e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj);
+    if (e == cudaSuccess && alpha && n_block > 0) {
+        const CkptLayout L = ckpt_layout(n, max_steps, ckpt_every);
+        alpha_to_float<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L.alpha_off), dL_dalpha,
+                                           3 * n_block);
+        e = cudaGetLastError();
+    }
+    if (own) {
+        const cudaError_t f = cudaFreeAsync(adj, st);
+        if (e == cudaSuccess) e = f;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+    return MT_OK;
+}
+
+extern "C" mt_status mt_transport_adjoint(mt_handle *h, const mt_muon_soa *s0, int64_t n, float step_len,
+                                          int32_t max_steps, uint64_t seed, const float *alpha, int32_t n_block,
+                                          const float *dL_dfinal, float *dL_dalpha, int32_t ckpt_every, void *stream)
+{
+    if (!h || !s0) {
+        set_error("null handle or muon SoA");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (ckpt_every < 1 || ckpt_every > kTapeMax || n < 0 || n >= ((int64_t)1 << 31)) {
+        set_error("ckpt_every %d outside [1, %d] or n out of range", ckpt_every, kTapeMax);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (n == 0) return mt_adjoint_ckpt(h, 0, step_len, max_steps, seed, alpha, n_block, ckpt_every, nullptr, 0,
+                                       s0->id_offset, s0->instance, dL_dfinal, nullptr, dL_dalpha, stream);
+    DevGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t cb = ckpt_bytes(n, max_steps, ckpt_every);
+    const int64_t soa_bytes = 30 * n + 9 * 256;
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), (size_t)(cb + soa_bytes), st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
+    // private copy of the initial state (the forward updates its SoA in place)
+    mt_muon_soa c = *s0;
+    char *q = buf + cb;
+    auto take = [&](void *src, size_t bytes) {
+        void *dst = q;
+        q += (bytes + 255) & ~(size_t)255;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+        return dst;
+    };
+    c.x = (float *)take(s0->x, 4 * n);
+    c.y = (float *)take(s0->y, 4 * n);
+    c.z = (float *)take(s0->z, 4 * n);
+    c.px = (float *)take(s0->px, 4 * n);
+    c.py = (float *)take(s0->py, 4 * n);
+    c.pz = (float *)take(s0->pz, 4 * n);
+    c.q = (int8_t *)take(s0->q, n);
+    c.steps = (int32_t *)take(s0->steps, 4 * n);
+    c.status = (uint8_t *)take(s0->status, n);
+    mt_status stt = MT_OK;
+    if (e == cudaSuccess)
+        stt = mt_transport_ckpt(h, &c, n, step_len, max_steps, seed, alpha, n_block, ckpt_every, buf, cb, stream);
+    if (e == cudaSuccess && stt == MT_OK)
+        stt = mt_adjoint_ckpt(h, n, step_len, max_steps, seed, alpha, n_block, ckpt_every, buf, cb, s0->id_offset,
+                              s0->instance, dL_dfinal, nullptr, dL_dalpha, stream);
+    const cudaError_t f = cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint state copy");
+    if (stt != MT_OK) return stt;
+    if (f != cudaSuccess) return cuda_fail(f, "adjoint scratch release");
+    return MT_OK;
+}
+
+extern "C" mt_status mt_acceptance_loss(const mt_muon_soa *s, int64_t n, double z_plane, double half_width,
+                                        double edge, double *loss, float *dL_dfinal, void *stream)
+{
+    if (!s || !loss || n < 0 || !(edge > 0.0) || !(half_width > 0.0)) {
+        set_error("acceptance loss: null pointer, n < 0 or non-positive width");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!s->x || !s->y || !s->z || !s->px || !s->py || !s->pz || !s->status)) {
+        set_error("null muon array with n > 0");
+        return MT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), st);
+    if (e == cudaSuccess && n > 0) {
+        const int64_t blocks = (n + kBlock - 1) / kBlock;
+        acceptance_loss_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), kBlock, 0, st>>>(
+            *s, n, (float)z_plane, (float)half_width, (float)edge, loss, dL_dfinal);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "acceptance loss");
+    return MT_OK;
+}

@@ -1,0 +1,71 @@
+// compact.cuh -- kernels of the lockstep compacting transport, shared by the
+// plain transport (compact.cu) and the checkpointing forward of the adjoint
+// (adjoint.cu).
+#pragma once
+
+#include "step.cuh"
+
+namespace mt {
+
+// Pack the live muons (status ALIVE or MAX_STEPS, finite state) of the
+// caller's arrays into a live list; non-finite states are marked MT_INVALID.
+static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa soa, int64_t n, const RunParams rp,
+                                                       LiveBuf out, unsigned long long *ctr)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t m = base + threadIdx.x;
+        State s;
+        float q = 0.0f;
+        int k = 0;
+        uint32_t id_lo, id_hi;
+        const bool live = m < n && load_muon(soa, m, rp, s, q, k, id_lo, id_hi);
+        const int64_t slot = warp_append(&ctr[0], live);
+        if (live) put_live(out, slot, s, q, k, m);
+    }
+}
+
+// One pass: live count from *cin, survivors appended at *cout; *czero (if not
+// null) is cleared for the pass after this one.
+template <int GEOM, int FIELD>
+__global__ void __launch_bounds__(kBlock) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
+                                                       LiveBuf in, LiveBuf out, const unsigned long long *cin,
+                                                       unsigned long long *cout, unsigned long long *czero, int S)
+{
+    __shared__ SmemWorld sw;
+    const int64_t count = (int64_t)*cin;
+    if (czero && blockIdx.x == 0 && threadIdx.x == 0) *czero = 0ull;
+    if (count == 0) return;
+    stage_world(sw, w, rp);
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool keep = false;
+        State s;
+        float q = 0.0f;
+        int k = 0;
+        int64_t idx = 0;
+        if (i < count) {
+            get_live(in, i, s, q, k, idx);
+            const uint64_t id = (uint64_t)(rp.id_offset + idx);
+            const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+            const int kend = min(k + S, rp.max_steps);
+            int r = MT_ALIVE;
+#pragma unroll 1
+            for (; k < kend; ++k) {
+                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp);
+                if (r != MT_ALIVE) break;
+            }
+            if (r == MT_ALIVE && k >= rp.max_steps) r = MT_MAX_STEPS;
+            if (r != MT_ALIVE)
+                store_muon(soa, idx, s, k, r);
+            else
+                keep = true;
+        }
+        const int64_t slot = warp_append(cout, keep);
+        if (keep) put_live(out, slot, s, q, k, idx);
+    }
+}
+
+}  // namespace mt

@@ -363,10 +363,18 @@ __device__ __forceinline__ int check_stop(const WorldParams &w, const State &s, 
     return MT_ALIVE;
 }
 
+// Recorder hooks of step(): the plain kernels pass NoRecord (every hook
+// compiles away); the adjoint's recompute passes a tape writer, so the tape
+// comes from exactly the arithmetic of the forward pass.
+struct NoRecord {
+    __device__ __forceinline__ void begin(const State &, int) {}
+    __device__ __forceinline__ void draw(float, float, float, float) {}
+};
+
 // One full step k of Algorithm 1.  Returns MT_ALIVE or the break status.
-template <int GEOM, int FIELD>
+template <int GEOM, int FIELD, class Rec = NoRecord>
 __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, State &s, float q, int k,
-                                    uint32_t id_lo, uint32_t id_hi, const RunParams &rp)
+                                    uint32_t id_lo, uint32_t id_hi, const RunParams &rp, Rec &&rec = Rec())
 {
     const float P2 = s.px * s.px + s.py * s.py + s.pz * s.pz;
     const int stop = check_stop(w, s, P2);
@@ -379,6 +387,7 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         const int vm = voxel_material(w, s);
         mat = vm >= 0 ? vm : w.world_mat;
     }
+    rec.begin(s, box);
     if (mat != 0) {
         const int ib = momentum_bin(w, sw, s, P2);
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, id_lo, id_hi, (uint32_t)rp.instance), rp.key0, rp.key1);
@@ -389,6 +398,7 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         const float th = ((float)(ab & 0xFFFFu) + u01(rnd.z)) * hr.tscale;
         float sp, cp;
         __sincosf(fmaf(6.283185307179586f, u01(rnd.w), -3.14159265358979f), &sp, &cp);   // phi - pi
+        rec.draw(f, th, -cp, -sp);
         scatter(s, f, th, -cp, -sp);
     }
     float3 B = make_float3(0.0f, 0.0f, 0.0f);
@@ -446,6 +456,49 @@ __device__ __forceinline__ void store_muon(const mt_muon_soa &soa, int64_t m, co
     soa.pz[m] = s.pz + s.pzl;
     soa.steps[m] = k;
     soa.status[m] = (uint8_t)status;
+}
+
+// Live-list entries of the compacting kernels (64 B per muon, four 16-byte
+// words in structure-of-arrays order): w0 = (x, y, z, q), w1 = (px, py, pz, k),
+// w2 = (xl, yl, zl, idx), w3 = (pxl, pyl, pzl, 0).
+struct LiveBuf {
+    float4 *w0, *w1, *w2, *w3;
+};
+
+__host__ __device__ inline LiveBuf live_buf_at(void *base, int64_t cap)
+{
+    float4 *p = reinterpret_cast<float4 *>(base);
+    return LiveBuf{p, p + cap, p + 2 * cap, p + 3 * cap};
+}
+
+// Warp-aggregated append: returns this lane's slot (valid when keep).
+__device__ __forceinline__ int64_t warp_append(unsigned long long *ctr, bool keep)
+{
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+    if (!mask) return -1;
+    const unsigned lane = threadIdx.x & 31u;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    return (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void put_live(const LiveBuf &b, int64_t i, const State &s, float q, int k, int64_t idx)
+{
+    b.w0[i] = make_float4(s.x, s.y, s.z, q);
+    b.w1[i] = make_float4(s.px, s.py, s.pz, __int_as_float(k));
+    b.w2[i] = make_float4(s.xl, s.yl, s.zl, __int_as_float((int)idx));
+    b.w3[i] = make_float4(s.pxl, s.pyl, s.pzl, 0.0f);
+}
+
+__device__ __forceinline__ void get_live(const LiveBuf &b, int64_t i, State &s, float &q, int &k, int64_t &idx)
+{
+    const float4 a = b.w0[i], c = b.w1[i], e = b.w2[i], g = b.w3[i];
+    s.x = a.x; s.y = a.y; s.z = a.z; q = a.w;
+    s.px = c.x; s.py = c.y; s.pz = c.z; k = __float_as_int(c.w);
+    s.xl = e.x; s.yl = e.y; s.zl = e.z; idx = __float_as_int(e.w);
+    s.pxl = g.x; s.pyl = g.y; s.pzl = g.z;
 }
 
 }  // namespace mt

@@ -1,0 +1,215 @@
+"""GPU parity of the differentiable form: the checkpointing forward, the
+acceptance-loss kernel and the hand-written adjoint (dL/dalpha of per-magnet
+field scales) against the FP64 oracle adjoint and central finite differences
+with common random numbers."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import compare, describe, gpu_transport
+from workloads import gen
+
+pytestmark = pytest.mark.gpu
+
+ALPHA_SEED = 5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_10520_gb300 as mt
+    mt.load_library()
+
+
+def _alpha(seed=ALPHA_SEED):
+    rng = np.random.default_rng(seed)
+    return (1.0 + 0.2 * rng.standard_normal((6, 3))).astype(np.float32)
+
+
+def _gpu_grad(wl, alpha, K=32, want_initial=False):
+    """(loss, dL/dalpha, final state, dL/dinitial) from the GPU: ckpt forward, loss kernel, adjoint."""
+    import torch
+    import paper_2512_10520_gb300 as mt
+    with mt.World.from_workload(wl) as world:
+        dev = mt.muons_to_device(wl.muons)
+        a = torch.as_tensor(alpha, dtype=torch.float32).cuda().contiguous()
+        n = wl.n
+        ckpt = torch.empty(mt.mt_ckpt_bytes(n, wl.max_steps, K), dtype=torch.uint8, device="cuda")
+        mt.mt_transport_ckpt(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, K, ckpt)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.empty((6, n), dtype=torch.float32, device="cuda")
+        mt.mt_acceptance_loss(dev, loss, g)
+        da = torch.empty_like(a)
+        gi = torch.empty((6, n), dtype=torch.float32, device="cuda") if want_initial else None
+        mt.mt_adjoint_ckpt(world.handle, n, wl.step_len, wl.max_steps, wl.seed, a, K, ckpt, g, da, gi)
+        torch.cuda.synchronize()
+        return (float(loss.item()), da.cpu().numpy().astype(np.float64), mt.muons_to_host(dev),
+                None if gi is None else gi.cpu().numpy())
+
+
+def test_checkpointing_forward_equals_transport():
+    wl = gen.workload("config1", n=5000)
+    alpha = _alpha()
+    ref = gpu_transport(wl, alpha=alpha)
+    _, _, fin, _ = _gpu_grad(wl, alpha)
+    for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+        np.testing.assert_array_equal(ref[k], fin[k])
+
+
+def test_loss_kernel_matches_oracle_loss():
+    wl = gen.workload("config1", n=20000)
+    alpha = _alpha()
+    L, _, fin, _ = _gpu_grad(wl, alpha)
+    Lo, go = oracle.acceptance_loss({k: np.asarray(v, np.float64) for k, v in fin.items()})
+    assert abs(L - Lo) <= 1e-6 * max(abs(Lo), 1e-12), (L, Lo)
+    import torch
+    import paper_2512_10520_gb300 as mt
+    dev = mt.muons_to_device(fin)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.empty((6, wl.n), dtype=torch.float32, device="cuda")
+    mt.mt_acceptance_loss(dev, loss, g)
+    g = g.cpu().numpy()
+    scale = np.abs(go).max()
+    assert scale > 0
+    np.testing.assert_allclose(g, go, rtol=1e-3, atol=1e-4 * scale)
+
+
+@pytest.mark.parametrize("field", ["map", "box"])
+def test_adjoint_matches_fp64_oracle_adjoint(field):
+    wl = gen.workload("config1", n=10000, field="box" if field == "box" else None)
+    alpha = _alpha()
+    _, g_gpu, _, _ = _gpu_grad(wl, alpha)
+    world = oracle.world_of(wl, alpha.astype(np.float64))
+    fin = oracle.transport(world, wl.muons, wl.step_len, wl.max_steps, wl.seed)
+    _, go = oracle.acceptance_loss(fin)
+    g_ora = oracle.adjoint(world, wl.muons, wl.step_len, wl.max_steps, wl.seed, go)
+    rel = np.linalg.norm(g_gpu - g_ora) / np.linalg.norm(g_ora)
+    assert rel <= 1e-3, (rel, g_gpu.ravel().tolist(), g_ora.ravel().tolist())
+
+
+def _per_muon_loss(f, z_plane=30.0, half=0.5, edge=0.01):
+    """Per-muon acceptance term (used only to sort muons into smooth and jumping)."""
+    x, y, z, px, py, pz = (np.asarray(f[k], np.float64) for k in ("x", "y", "z", "px", "py", "pz"))
+    ok = (f["status"] != 1) & (f["status"] != 5) & (pz > 0)
+    safe = np.where(ok, pz, 1.0)
+    xe = x + (z_plane - z) * px / safe
+    ye = y + (z_plane - z) * py / safe
+    sig = lambda t: 0.5 * (1.0 + np.tanh(0.5 * t))
+    return np.where(ok, sig((half - np.abs(xe)) / edge) * sig((half - np.abs(ye)) / edge), 0.0)
+
+
+def test_adjoint_against_central_differences():
+    """Central differences with common random numbers on 1e4 muons, h = 2e-4
+    relative (at h = 1e-3 the 1 cm sigmoid edge of the loss already gives the
+    central difference a ~1 % truncation error).  A step of h moves tracks by
+    up to a millimetre; some muons then change a discrete
+    choice (a box face, a momentum bin, a stop or exit step) and their term jumps
+    (muon 3633 of this set goes from 1.0 to 0.0 across +-h and alone outweighs
+    the whole sum).  The pathwise gradient holds those choices fixed by
+    construction, so the two are compared on the muons that kept every discrete
+    choice: the field never changes |p| and, with the same materials and bins,
+    the common random numbers give the same losses, so such a muon keeps its step
+    count, status and final |p| (to rounding) for every alpha +- h.  The adjoint
+    is run with dL/dfinal of the other muons set to zero."""
+    import torch
+    import paper_2512_10520_gb300 as mt
+    wl = gen.workload("config1", n=10000)
+    alpha = _alpha().astype(np.float32)
+    h = 2e-4
+    n = wl.n
+    with mt.World.from_workload(wl) as world:
+        def run(a):
+            dev = mt.muons_to_device(wl.muons)
+            world.transport(dev, wl.step_len, wl.max_steps, wl.seed,
+                            alpha=torch.as_tensor(a, dtype=torch.float32).cuda().contiguous())
+            torch.cuda.synchronize()
+            return mt.muons_to_host(dev)
+
+        f0 = run(alpha)
+        P = lambda f: np.sqrt(f["px"].astype(np.float64) ** 2 + f["py"] ** 2 + f["pz"] ** 2)
+        P0 = P(f0)
+        d = np.zeros((18, n))
+        smooth = np.ones(n, bool)
+        for j in range(18):
+            ap, am = alpha.ravel().copy(), alpha.ravel().copy()
+            ap[j] = np.float32(ap[j] * (1 + h))
+            am[j] = np.float32(am[j] * (1 - h))
+            fp, fm = run(ap.reshape(6, 3)), run(am.reshape(6, 3))
+            for f in (fp, fm):
+                smooth &= (f["steps"] == f0["steps"]) & (f["status"] == f0["status"])
+                smooth &= np.abs(P(f) - P0) <= 1e-5 * P0
+            d[j] = (_per_muon_loss(fp) - _per_muon_loss(fm)) / (float(ap[j]) - float(am[j])) / n
+        fd = d[:, smooth].sum(1)
+        # adjoint restricted to the smooth muons
+        dev = mt.muons_to_device(wl.muons)
+        a = torch.as_tensor(alpha).cuda().contiguous()
+        ckpt = torch.empty(mt.mt_ckpt_bytes(n, wl.max_steps, 32), dtype=torch.uint8, device="cuda")
+        mt.mt_transport_ckpt(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, 32, ckpt)
+        g = torch.empty((6, n), dtype=torch.float32, device="cuda")
+        mt.mt_acceptance_loss(dev, torch.zeros(1, dtype=torch.float64, device="cuda"), g)
+        g *= torch.as_tensor(smooth, device="cuda").to(torch.float32)
+        da = torch.empty_like(a)
+        mt.mt_adjoint_ckpt(world.handle, n, wl.step_len, wl.max_steps, wl.seed, a, 32, ckpt, g, da)
+        torch.cuda.synchronize()
+    adj = da.cpu().numpy().astype(np.float64).ravel()
+    rel = np.linalg.norm(adj - fd) / np.linalg.norm(fd)
+    print("smooth muons", smooth.sum(), "of", n, "FD rel", rel, "full-population FD",
+          d.sum(1).tolist(), "smooth FD", fd.tolist(), "adjoint", adj.tolist())
+    assert smooth.mean() > 0.5
+    assert rel < 1e-2, (rel, adj.tolist(), fd.tolist())
+
+
+def test_autograd_function_and_one_call_adjoint():
+    import torch
+    import paper_2512_10520_gb300 as mt
+    wl = gen.workload("config1", n=4000)
+    alpha = _alpha()
+    _, g_ref, _, _ = _gpu_grad(wl, alpha)
+    with mt.World.from_workload(wl) as world:
+        a = torch.as_tensor(alpha).cuda().requires_grad_(True)
+        fin = mt.transport_differentiable(world, mt.muons_to_device(wl.muons), a, wl.step_len, wl.max_steps, wl.seed)
+        L = mt.acceptance_loss(fin)
+        L.backward()
+        np.testing.assert_allclose(a.grad.cpu().numpy(), g_ref, rtol=1e-5, atol=1e-7 * np.abs(g_ref).max())
+        # the one-call form from the initial state
+        dev0 = mt.muons_to_device(wl.muons)
+        g6 = torch.empty((6, wl.n), dtype=torch.float32, device="cuda")
+        dev = mt.muons_to_device(wl.muons)
+        world.transport(dev, wl.step_len, wl.max_steps, wl.seed, alpha=a.detach().contiguous())
+        mt.mt_acceptance_loss(dev, torch.zeros(1, dtype=torch.float64, device="cuda"), g6)
+        da = torch.empty_like(a.detach())
+        mt.mt_transport_adjoint(world.handle, dev0, wl.step_len, wl.max_steps, wl.seed, a.detach().contiguous(), g6,
+                                da, 32)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(da.cpu().numpy(), g_ref, rtol=1e-5, atol=1e-7 * np.abs(g_ref).max())
+        # the initial state is left unchanged
+        np.testing.assert_array_equal(dev0["x"].cpu().numpy(), wl.muons["x"])
+
+
+def test_initial_state_gradient_matches_finite_differences():
+    """dL/d(initial px) of single muons against central differences on the GPU."""
+    import torch
+    import paper_2512_10520_gb300 as mt
+    wl = gen.workload("config1", n=4000)
+    alpha = _alpha()
+    _, _, fin, gi = _gpu_grad(wl, alpha, want_initial=True)
+    # muons with a sizeable gradient, i.e. ending near the acceptance edge
+    mag = np.abs(gi[3])
+    cand = np.argsort(-mag)[:6]
+    with mt.World.from_workload(wl) as world:
+        a = torch.as_tensor(alpha).cuda().contiguous()
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for m in cand:
+            vals = []
+            for sgn in (+1, -1):
+                mu = {k: v.copy() for k, v in wl.muons.items()}
+                mu["px"][m] = np.float32(mu["px"][m] + sgn * 1e-3)
+                dev = mt.muons_to_device(mu)
+                world.transport(dev, wl.step_len, wl.max_steps, wl.seed, alpha=a)
+                mt.mt_acceptance_loss(dev, loss)
+                vals.append(float(loss.item()))
+            dpx = float(np.float32(wl.muons["px"][m] + 1e-3)) - float(np.float32(wl.muons["px"][m] - 1e-3))
+            fd = (vals[0] - vals[1]) / dpx
+            assert abs(fd - gi[3][m]) <= 0.05 * abs(gi[3][m]) + 1e-9, (m, fd, gi[3][m])
