@@ -159,6 +159,42 @@ def cpu_oracle_run(wl, n_sample: int, threads: int):
     return float(out["steps"].sum()), dt
 
 
+def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32):
+    """fwd+adjoint form (config3: config1 geometry, 18 field scales, checkpoints every K
+    steps): checkpointing forward + acceptance loss + adjoint, each timed with CUDA events."""
+    import torch
+    n = wl.n
+    alpha = torch.ones((6, 3), dtype=torch.float32, device=init["x"].device)
+    ckpt = torch.empty(mt.mt_ckpt_bytes(n, wl.max_steps, K), dtype=torch.uint8, device=init["x"].device)
+    loss = torch.zeros(1, dtype=torch.float64, device=init["x"].device)
+    g = torch.empty((6, n), dtype=torch.float32, device=init["x"].device)
+    da = torch.empty_like(alpha)
+    times = []
+    with torch.cuda.stream(stream):
+        for r in range(reps + 1):
+            for k in work:
+                work[k].copy_(init[k], non_blocking=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            mt.mt_transport_ckpt(world.handle, work, wl.step_len, wl.max_steps, wl.seed, alpha, K, ckpt,
+                                 id_offset=id_offset, stream=stream)
+            ev[1].record(stream)
+            mt.mt_acceptance_loss(work, loss, g, stream=stream)
+            ev[2].record(stream)
+            mt.mt_adjoint_ckpt(world.handle, n, wl.step_len, wl.max_steps, wl.seed, alpha, K, ckpt, g, da,
+                               id_offset=id_offset, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            if r:
+                times.append([ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3)])
+    t = np.mean(np.array(times), axis=0)
+    steps = float(work["steps"].sum().item())
+    del ckpt
+    return dict(t_forward_ckpt_ms=1e3 * t[0], t_loss_ms=1e3 * t[1], t_adjoint_ms=1e3 * t[2], muon_steps=steps,
+                loss=float(loss.item()), ckpt_every=K, dL_dalpha_norm=float(da.norm().item()),
+                passes=int((wl.max_steps + K - 1) // K))
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -287,6 +323,17 @@ def run_mine(args):
     e2e_value = (_barrier_sum(float(host_out["steps"].sum().item()) * e2e_steps, ws, dev) / e2e_t
                  if e2e_steps else None)
 
+    forms = {}
+    if not args.no_forms:
+        adj = time_adjoint_form(mt, world, wl, init, work, stream, id_offset, K=args.ckpt_every)
+        t_all = (adj["t_forward_ckpt_ms"] + adj["t_loss_ms"] + adj["t_adjoint_ms"]) / 1e3
+        forms["fwd_adjoint"] = dict(
+            value=_barrier_sum(adj["muon_steps"], ws, dev) / _barrier_max(t_all, ws, dev), unit=UNIT,
+            workload="config3: config1 geometry and map, 18 field scales alpha = 1, 1e6 muons, 1500 steps, "
+                     "checkpoints every 32 steps, acceptance loss at z = 30 m",
+            adjoint_over_forward=adj["t_adjoint_ms"] / (kernel_s * 1e3),
+            total_over_forward=t_all / kernel_s, **adj)
+        forms["plain"] = dict(value=value, unit=UNIT, kernel_ms=kernel_s * 1e3)
     peaks, peak_kind = _peaks()
     achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -318,6 +365,7 @@ def run_mine(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * launches_per_call,
             "clocks": clocks,
+            "forms": forms,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -334,6 +382,8 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the fwd+adjoint and batched forms")
+    ap.add_argument("--ckpt-every", type=int, default=32, help="checkpoint interval of the fwd+adjoint form")
     ap.add_argument("--muons", type=int, default=None, help="muons per GPU (default: the workload's 1e6)")
     ap.add_argument("--mode", default="auto", choices=["auto", "static", "persistent", "compact"])
     ap.add_argument("--blocks-per-sm", type=int, default=0)

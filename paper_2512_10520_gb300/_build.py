@@ -33,9 +33,15 @@ def _stale(target: str, deps: List[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: Optional[List[str]] = None) -> str:
-    """Compile every CUDA translation unit (in parallel) and link libmt.so; returns its path."""
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: Optional[List[str]] = None,
+          out_path: Optional[str] = None, obj_dir: Optional[str] = None) -> str:
+    """Compile every CUDA translation unit (in parallel) and link libmt.so; returns its path.
+
+    ``out_path`` / ``obj_dir`` / ``extra_flags`` (e.g. ``-DMT_PASS_MIN_BLOCKS=5``) build a
+    tuning variant of the library elsewhere without touching the default one."""
+    lib_path = out_path or LIB_PATH
+    odir = obj_dir or OBJ_DIR
+    os.makedirs(odir, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
@@ -47,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: Optional[List
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(odir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc] + flags + ["-c", s, "-o", o])
@@ -62,12 +68,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags: Optional[List
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         for out in ex.map(run, jobs):
             logs.append(out)
-    if force or jobs or _stale(LIB_PATH, objs):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         libdir = _cuda_lib_dir()
         logs.append(run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs +
                         ["-cudart", "shared", "-Xlinker", f"-rpath,{libdir}"]))
-        os.replace(tmp, LIB_PATH)
+        os.replace(tmp, lib_path)
     if verbose:
         print("\n".join(l for l in logs if l.strip()))
-    return LIB_PATH
+    return lib_path

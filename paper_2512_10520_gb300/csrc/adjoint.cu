@@ -29,6 +29,18 @@ namespace mt {
 
 constexpr int kTapeMax = 64;
 
+// Reverse sweep: load the next step's tape words while reversing this one
+// (measured slower on config3, so off by default).
+#ifndef MT_ADJ_PIPELINE
+#define MT_ADJ_PIPELINE 0
+#endif
+
+// Resident blocks per SM of the adjoint pass (4 blocks of 256 = 64 registers;
+// on config3 5 blocks spill and 3 blocks hide too little latency).
+#ifndef MT_ADJ_MIN_BLOCKS
+#define MT_ADJ_MIN_BLOCKS 4
+#endif
+
 struct CkptLayout {
     int passes;
     int64_t alpha_off, lists_off, list_bytes, total;
@@ -46,33 +58,52 @@ static CkptLayout ckpt_layout(int64_t n, int32_t max_steps, int32_t K)
     return L;
 }
 
-struct TapeEntry {
-    float r[3];   // position at the step's start
-    float p[3];   // momentum at the step's start (before scattering)
-    float f, th, cphi, sphi;
-    int meta;     // bit 0: scattered; bits 8..15: box + 1 (0: no box)
+// The tape of the reverse sweep lives in a global scratch array, four 16-byte
+// words per recorded step, word q of step j of thread t at [(4 j + q) T + t]
+// (T = threads of the grid, so a warp's stores are contiguous):
+//   a = (rx, ry, rz, meta)  b = (px, py, pz, f)  c = (Bmx, Bmy, Bmz, theta)  d = (phi - pi, -, -, -)
+// with r and p at the step's start, Bm the field there before the block scale,
+// meta bit 0 = scattered and bits 8..15 = box + 1.  It is written and read once
+// with streaming (evict-first) hints, so it passes through L2 without pushing
+// out the field map.
+struct TapeRef {
+    float4 *base;
+    int64_t T;     // threads of the grid
+    int64_t tid;   // this thread
+    __device__ __forceinline__ float4 *at(int j, int q) const { return base + (4 * (int64_t)j + q) * T + tid; }
 };
 
 struct TapeWriter {
-    TapeEntry *t;
-    __device__ __forceinline__ void begin(const State &s, int box)
+    const TapeRef *tr;
+    int j;
+    float f = 0.0f, th = 0.0f, phs = 0.0f;
+    bool scat = false;
+    __device__ __forceinline__ void begin(const State &s, int box, bool scattered)
     {
-        t->r[0] = s.x + s.xl;
-        t->r[1] = s.y + s.yl;
-        t->r[2] = s.z + s.zl;
-        t->p[0] = s.px + s.pxl;
-        t->p[1] = s.py + s.pyl;
-        t->p[2] = s.pz + s.pzl;
-        t->meta = (box + 1) << 8;
+        scat = scattered;
+        const int meta = ((box + 1) << 8) | (scattered ? 1 : 0);
+        __stcs(tr->at(j, 0), make_float4(s.x + s.xl, s.y + s.yl, s.z + s.zl, __int_as_float(meta)));
+        pxs = s.px + s.pxl;
+        pys = s.py + s.pyl;
+        pzs = s.pz + s.pzl;
     }
-    __device__ __forceinline__ void draw(float f, float th, float c, float sn)
+    float pxs = 0.0f, pys = 0.0f, pzs = 0.0f;
+    __device__ __forceinline__ void draw(float f_, float th_, float phs_)
     {
-        t->f = f;
-        t->th = th;
-        t->cphi = c;
-        t->sphi = sn;
-        t->meta |= 1;
+        f = f_;
+        th = th_;
+        phs = phs_;
     }
+    __device__ __forceinline__ void field(float3 B)
+    {
+        __stcs(tr->at(j, 1), make_float4(pxs, pys, pzs, f));
+        __stcs(tr->at(j, 2), make_float4(B.x, B.y, B.z, th));
+        if (scat) __stcs(tr->at(j, 3), make_float4(phs, 0.0f, 0.0f, 0.0f));
+    }
+};
+
+struct TapeEntry {
+    float4 a, b, c, d;
 };
 
 __device__ __forceinline__ void cross3(const float a[3], const float b[3], float o[3])
@@ -87,15 +118,10 @@ __device__ __forceinline__ float dot3(const float a[3], const float b[3])
     return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
 }
 
-// Unscaled trilinear field at r and its Jacobian J[c][a] = dB_c/dr_a (zero
+// rb += J(r)^T Bb with J[c][a] = dB_c/dr_a of the unscaled trilinear map (zero
 // outside the node box).
-__device__ __forceinline__ void field_map_grad(const WorldParams &w, const float r[3], float B[3], float J[3][3])
+__device__ __forceinline__ void field_map_jt(const WorldParams &w, const float r[3], const float Bb[3], float rb[3])
 {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        B[c] = 0.0f;
-        J[c][0] = J[c][1] = J[c][2] = 0.0f;
-    }
     const int nx = w.fdims[0], ny = w.fdims[1], nz = w.fdims[2];
     int i, j, k;
     float tx, ty, tz;
@@ -108,22 +134,50 @@ __device__ __forceinline__ void field_map_grad(const WorldParams &w, const float
     const float4 *p10 = p00 + 2 * row;
     const float4 *p01 = p00 + 2 * row * ny;
     const float4 *p11 = p01 + 2 * row;
-    const float4 c4[8] = {__ldg(p00), __ldg(p00 + 1), __ldg(p10), __ldg(p10 + 1),
-                          __ldg(p01), __ldg(p01 + 1), __ldg(p11), __ldg(p11 + 1)};
+    // project the corners on Bb first: v_q = Bb . B(corner q)
+    float v[8];
+    const float4 *src[8] = {p00, p00 + 1, p10, p10 + 1, p01, p01 + 1, p11, p11 + 1};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = c == 0 ? c4[q].x : (c == 1 ? c4[q].y : c4[q].z);
-        // v: (i,j,k) (i+1,j,k) (i,j+1,k) (i+1,j+1,k) (i,j,k+1) (i+1,j,k+1) (i,j+1,k+1) (i+1,j+1,k+1)
-        const float a = lerp(tx, v[0], v[1]), b = lerp(tx, v[2], v[3]);
-        const float cc = lerp(tx, v[4], v[5]), d = lerp(tx, v[6], v[7]);
-        const float e = lerp(ty, a, b), g = lerp(ty, cc, d);
-        B[c] = lerp(tz, e, g);
-        J[c][0] = lerp(tz, lerp(ty, v[1] - v[0], v[3] - v[2]), lerp(ty, v[5] - v[4], v[7] - v[6])) * w.finv[0];
-        J[c][1] = lerp(tz, b - a, d - cc) * w.finv[1];
-        J[c][2] = (g - e) * w.finv[2];
+    for (int q = 0; q < 8; ++q) {
+        const float4 c = __ldg(src[q]);
+        v[q] = fmaf(Bb[0], c.x, fmaf(Bb[1], c.y, Bb[2] * c.z));
     }
+    // v: (i,j,k) (i+1,j,k) (i,j+1,k) (i+1,j+1,k) (i,j,k+1) (i+1,j,k+1) (i,j+1,k+1) (i+1,j+1,k+1)
+    const float a = lerp(tx, v[0], v[1]), b = lerp(tx, v[2], v[3]);
+    const float cc = lerp(tx, v[4], v[5]), d = lerp(tx, v[6], v[7]);
+    rb[0] += lerp(tz, lerp(ty, v[1] - v[0], v[3] - v[2]), lerp(ty, v[5] - v[4], v[7] - v[6])) * w.finv[0];
+    rb[1] += lerp(tz, b - a, d - cc) * w.finv[1];
+    rb[2] += (lerp(ty, cc, d) - lerp(ty, a, b)) * w.finv[2];
+}
+
+// The forward's scattering update in plain FP32 on a recorded momentum.
+__device__ __forceinline__ void scatter_fp32(const float p[3], float f, float th, float cphi, float sphi, float ps[3])
+{
+    const float P2 = dot3(p, p);
+    float rP = rsqrtf(P2);
+    rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
+    const float P = P2 * rP;
+    const float ux = p[0] * rP, uy = p[1] * rP, uz = p[2] * rP;
+    float st, omc;
+    sin_omc(th, st, omc);
+    const float sm1 = -fmaf(f, 1.0f - omc, omc);
+    const float kick = P * (1.0f - f) * st;
+    const float s2 = fmaf(ux, ux, uy * uy);
+    float tx, ty, tz;
+    if (uz < 0.0f && s2 < 1e-24f) {
+        tx = cphi;
+        ty = -sphi;
+        tz = 0.0f;
+    } else {
+        const float g = uz >= 0.0f ? 1.0f / (1.0f + uz) : (1.0f - uz) / s2;
+        const float wv = fmaf(cphi, ux, sphi * uy);
+        tx = cphi - ux * wv * g;
+        ty = sphi - uy * wv * g;
+        tz = -wv;
+    }
+    ps[0] = fmaf(sm1, p[0], fmaf(kick, tx, p[0]));
+    ps[1] = fmaf(sm1, p[1], fmaf(kick, ty, p[1]));
+    ps[2] = fmaf(sm1, p[2], fmaf(kick, tz, p[2]));
 }
 
 // dL/dalpha of the current magnet block, flushed to shared memory when the
@@ -154,58 +208,35 @@ struct AlphaAcc {
 
 // Reverse of one forward step recorded in t: (rb, pb) enter as dL/d(r, p) after
 // the step and leave as dL/d(r, p) before it.
+//
+// RK4 for dp/ds = p x w with w fixed (B held over the step) is, exactly, the
+// degree-4 Taylor polynomial of the rotation: with h = kappa q d B / P0 and
+// v1 = ps x h, v2 = v1 x h, v3 = v2 x h, v4 = v3 x h,
+//   p' = ps + v1 + v2/2 + v3/6 + v4/24,  r' = r + (d/P0)(ps + v1/2 + v2/6 + v3/24)
+// (the stage form k1..k4 of the forward expands to the same polynomials), so
+// its adjoint is taken in that form, which keeps fewer values live.
 template <int GEOM, int FIELD>
 __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWorld &sw, const TapeEntry &t, float q,
                                              float d, float kd, float rb[3], float pb[3], AlphaAcc &acc,
                                              float (*sacc)[MT_MAX_BOXES])
 {
-    const float p[3] = {t.p[0], t.p[1], t.p[2]};
-    const bool scat = t.meta & 1;
-    const int box = (t.meta >> 8) - 1;
-    // -- recompute the scattered momentum ps = p + sm1 p + P kf tv(u)
-    float ps[3] = {p[0], p[1], p[2]};
-    float u[3] = {0.0f, 0.0f, 0.0f}, tv[3] = {0.0f, 0.0f, 0.0f};
-    float P = 0.0f, rPs = 0.0f, sm1 = 0.0f, kf = 0.0f, g = 0.0f, wv = 0.0f;
-    bool degen = false;
+    const int meta = __float_as_int(t.a.w);
+    const int box = (meta >> 8) - 1;
+    const bool scat = meta & 1;
+    const float r[3] = {t.a.x, t.a.y, t.a.z};
+    const float p[3] = {t.b.x, t.b.y, t.b.z};
+    const float f = t.b.w, th = t.c.w;
+    float sphi = 0.0f, cphi = 0.0f;
     if (scat) {
-        const float P2 = dot3(p, p);
-        rPs = rsqrtf(P2);
-        rPs = rPs * fmaf(-0.5f * P2 * rPs, rPs, 1.5f);
-        P = P2 * rPs;
-        u[0] = p[0] * rPs;
-        u[1] = p[1] * rPs;
-        u[2] = p[2] * rPs;
-        float st, omc;
-        sin_omc(t.th, st, omc);
-        sm1 = -fmaf(t.f, 1.0f - omc, omc);
-        kf = (1.0f - t.f) * st;
-        const float s2 = fmaf(u[0], u[0], u[1] * u[1]);
-        if (u[2] < 0.0f && s2 < 1e-24f) {
-            degen = true;
-            tv[0] = t.cphi;
-            tv[1] = -t.sphi;
-        } else {
-            g = u[2] >= 0.0f ? 1.0f / (1.0f + u[2]) : (1.0f - u[2]) / s2;
-            wv = fmaf(t.cphi, u[0], t.sphi * u[1]);
-            tv[0] = t.cphi - u[0] * wv * g;
-            tv[1] = t.sphi - u[1] * wv * g;
-            tv[2] = -wv;
-        }
-        const float kick = P * kf;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) ps[c] = fmaf(sm1, p[c], fmaf(kick, tv[c], p[c]));
+        __sincosf(t.d.x, &sphi, &cphi);
+        sphi = -sphi;
+        cphi = -cphi;
     }
-    // -- field: B = sc (.) Bm(r)
-    float Bm[3] = {0.0f, 0.0f, 0.0f}, J[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-    if (FIELD == MT_FIELD_BOX) {
-        if (box >= 0) {
-            Bm[0] = sw.B[0][box];
-            Bm[1] = sw.B[1][box];
-            Bm[2] = sw.B[2][box];
-        }
-    } else if (FIELD == MT_FIELD_MAP) {
-        field_map_grad(w, t.r, Bm, J);
-    }
+    // -- scattered momentum ps = p + sm1 p + P kf tv(u) (recomputed in FP32)
+    float ps[3] = {p[0], p[1], p[2]};
+    if (scat) scatter_fp32(p, f, th, cphi, sphi, ps);
+    // -- field before the block scale (recorded)
+    const float Bm[3] = {t.c.x, t.c.y, t.c.z};
     int blk = -1;
     float sc[3] = {1.0f, 1.0f, 1.0f};
     if (GEOM == MT_GEOM_BOXES && FIELD != MT_FIELD_NONE && box >= 0) {
@@ -217,79 +248,54 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
         }
     }
     const float B[3] = {sc[0] * Bm[0], sc[1] * Bm[1], sc[2] * Bm[2]};
-    // -- recompute the RK4 stages (k_i = p_i x h, h = kappa q d B / P0)
+    // -- RK4 (Taylor form)
     const float P02 = dot3(ps, ps);
     float rP0 = rsqrtf(P02);
     rP0 = rP0 * fmaf(-0.5f * P02 * rP0, rP0, 1.5f);
     const float cc = (kd * q) * rP0;
     const float a = d * rP0;
     const float h[3] = {cc * B[0], cc * B[1], cc * B[2]};
-    float k1[3], k2[3], k3[3], k4[3], p2[3], p3[3], p4[3];
-    cross3(ps, h, k1);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) p2[c] = fmaf(0.5f, k1[c], ps[c]);
-    cross3(p2, h, k2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) p3[c] = fmaf(0.5f, k2[c], ps[c]);
-    cross3(p3, h, k3);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) p4[c] = ps[c] + k3[c];
-    cross3(p4, h, k4);
-    // -- reverse of r' = r + a (ps + (k1+k2+k3)/6), p' = ps + (k1 + 2k2 + 2k3 + k4)/6
-    const float sixth = 1.0f / 6.0f;
+    float v1[3], v2[3], v3[3];
+    cross3(ps, h, v1);
+    cross3(v1, h, v2);
+    cross3(v2, h, v3);
     float rsum[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rsum[c] = fmaf(sixth, k1[c] + k2[c] + k3[c], ps[c]);
+    for (int c = 0; c < 3; ++c) rsum[c] = ps[c] + 0.5f * v1[c] + (1.0f / 6.0f) * v2[c] + (1.0f / 24.0f) * v3[c];
     const float abar = dot3(rb, rsum);
-    float psb[3], k1b[3], k2b[3], k3b[3], k4b[3];
+    float vb[3], hb[3] = {0.0f, 0.0f, 0.0f}, tmp[3];
+    // v4 = v3 x h: v3b += h x v4b, hb += v4b x v3, with v4b = pb / 24
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        psb[c] = fmaf(a, rb[c], pb[c]);
-        const float ra = a * sixth * rb[c];
-        k1b[c] = fmaf(sixth, pb[c], ra);
-        k2b[c] = fmaf(2.0f * sixth, pb[c], ra);
-        k3b[c] = k2b[c];
-        k4b[c] = sixth * pb[c];
-    }
-    float hb[3] = {0.0f, 0.0f, 0.0f}, tmp[3];
-    // k4 = p4 x h, p4 = ps + k3
-    cross3(h, k4b, tmp);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        psb[c] += tmp[c];
-        k3b[c] += tmp[c];
-    }
-    cross3(k4b, p4, tmp);
+    for (int c = 0; c < 3; ++c) vb[c] = (1.0f / 24.0f) * pb[c];
+    cross3(vb, v3, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
-    // k3 = p3 x h, p3 = ps + k2 / 2
-    cross3(h, k3b, tmp);
+    cross3(h, vb, tmp);
+    // v3b = pb/6 + a rb/24 + h x v4b;  v3 = v2 x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        psb[c] += tmp[c];
-        k2b[c] = fmaf(0.5f, tmp[c], k2b[c]);
-    }
-    cross3(k3b, p3, tmp);
+    for (int c = 0; c < 3; ++c) vb[c] = (1.0f / 6.0f) * pb[c] + (a / 24.0f) * rb[c] + tmp[c];
+    cross3(vb, v2, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
-    // k2 = p2 x h, p2 = ps + k1 / 2
-    cross3(h, k2b, tmp);
+    cross3(h, vb, tmp);
+    // v2b = pb/2 + a rb/6 + h x v3b;  v2 = v1 x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        psb[c] += tmp[c];
-        k1b[c] = fmaf(0.5f, tmp[c], k1b[c]);
-    }
-    cross3(k2b, p2, tmp);
+    for (int c = 0; c < 3; ++c) vb[c] = 0.5f * pb[c] + (a / 6.0f) * rb[c] + tmp[c];
+    cross3(vb, v1, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
-    // k1 = ps x h
-    cross3(h, k1b, tmp);
+    cross3(h, vb, tmp);
+    // v1b = pb + a rb/2 + h x v2b;  v1 = ps x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) psb[c] += tmp[c];
-    cross3(k1b, ps, tmp);
+    for (int c = 0; c < 3; ++c) vb[c] = pb[c] + 0.5f * a * rb[c] + tmp[c];
+    cross3(vb, ps, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
-    // h = cc B, cc = kappa q d / P0, a = d / P0, P0 = |ps|
+    cross3(h, vb, tmp);
+    float psb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) psb[c] = pb[c] + a * rb[c] + tmp[c];
+    // h = cc B with cc = kappa q d / P0, a = d / P0, P0 = |ps|
     const float ccb = dot3(hb, B);
     const float P0b = -(ccb * cc + abar * a) * rP0;
 #pragma unroll
@@ -299,37 +305,55 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     if (blk >= 0) acc.add(blk, Bb[0] * Bm[0], Bb[1] * Bm[1], Bb[2] * Bm[2], sacc);
     if (FIELD == MT_FIELD_MAP) {
         const float Bmb[3] = {sc[0] * Bb[0], sc[1] * Bb[1], sc[2] * Bb[2]};
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) rb[ax] += Bmb[0] * J[0][ax] + Bmb[1] * J[1][ax] + Bmb[2] * J[2][ax];
+        field_map_jt(w, r, Bmb, rb);
     }
-    // -- scattering: ps = (1 + sm1) p + P kf tv(u), u = p / P
+    // -- scattering: ps = (1 + sm1) p + P kf tv(u), u = p / P, held draws (f, theta, phi)
     if (!scat) {
         pb[0] = psb[0];
         pb[1] = psb[1];
         pb[2] = psb[2];
         return;
     }
-    const float Pb = kf * dot3(tv, psb);
-    float ub[3] = {0.0f, 0.0f, 0.0f};
-    if (!degen) {
+    const float P2 = dot3(p, p);
+    float rPs = rsqrtf(P2);
+    rPs = rPs * fmaf(-0.5f * P2 * rPs, rPs, 1.5f);
+    const float P = P2 * rPs;
+    const float u[3] = {p[0] * rPs, p[1] * rPs, p[2] * rPs};
+    float st, omc;
+    sin_omc(th, st, omc);
+    const float sm1 = -fmaf(f, 1.0f - omc, omc);
+    const float kf = (1.0f - f) * st;
+    const float s2 = fmaf(u[0], u[0], u[1] * u[1]);
+    float tv[3], ub[3] = {0.0f, 0.0f, 0.0f};
+    if (u[2] < 0.0f && s2 < 1e-24f) {
+        tv[0] = cphi;
+        tv[1] = -sphi;
+        tv[2] = 0.0f;
+    } else {
+        const float g = u[2] >= 0.0f ? 1.0f / (1.0f + u[2]) : (1.0f - u[2]) / s2;
+        const float wv = fmaf(cphi, u[0], sphi * u[1]);
+        tv[0] = cphi - u[0] * wv * g;
+        tv[1] = sphi - u[1] * wv * g;
+        tv[2] = -wv;
         const float kick = P * kf;
         const float tb[3] = {kick * psb[0], kick * psb[1], kick * psb[2]};
-        const float s = tb[0] * u[0] + tb[1] * u[1];
-        const float wb = -s * g - tb[2];
-        const float gb = -s * wv;
-        ub[0] = fmaf(wb, t.cphi, -tb[0] * wv * g);
-        ub[1] = fmaf(wb, t.sphi, -tb[1] * wv * g);
+        const float sx = tb[0] * u[0] + tb[1] * u[1];
+        const float wb = -sx * g - tb[2];
+        const float gb = -sx * wv;
+        ub[0] = fmaf(wb, cphi, -tb[0] * wv * g);
+        ub[1] = fmaf(wb, sphi, -tb[1] * wv * g);
         ub[2] = -gb * g * g;
     }
+    const float Pb = kf * dot3(tv, psb);
     const float uu = dot3(u, ub);
 #pragma unroll
     for (int c = 0; c < 3; ++c) pb[c] = fmaf(1.0f + sm1, psb[c], fmaf(Pb, u[c], (ub[c] - u[c] * uu) * rPs));
 }
 
 template <int GEOM, int FIELD>
-__global__ void __launch_bounds__(kBlock) adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck,
+__global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS) adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck,
                                                        const unsigned long long *count_p, int S, float *adj,
-                                                       int64_t n, double *dalpha)
+                                                       int64_t n, double *dalpha, float4 *tape_base)
 {
     __shared__ SmemWorld sw;
     __shared__ float sacc[3][MT_MAX_BOXES];
@@ -339,8 +363,8 @@ __global__ void __launch_bounds__(kBlock) adjoint_pass(const WorldParams w, cons
     for (int t = threadIdx.x; t < 3 * MT_MAX_BOXES; t += blockDim.x) (&sacc[0][0])[t] = 0.0f;
     __syncthreads();
     AlphaAcc acc;
-    TapeEntry tape[kTapeMax];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const TapeRef tr{tape_base, stride, (int64_t)blockIdx.x * blockDim.x + threadIdx.x};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         State s;
         float q;
@@ -353,14 +377,43 @@ __global__ void __launch_bounds__(kBlock) adjoint_pass(const WorldParams w, cons
         int ns = 0;
 #pragma unroll 1
         for (; k < kend; ++k) {
-            const int r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp, TapeWriter{&tape[ns]});
+            const int r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp, TapeWriter{&tr, ns});
             if (r != MT_ALIVE) break;
             ++ns;
         }
         float rb[3] = {adj[idx], adj[n + idx], adj[2 * n + idx]};
         float pb[3] = {adj[3 * n + idx], adj[4 * n + idx], adj[5 * n + idx]};
+#if MT_ADJ_PIPELINE
+        // the words of step j - 1 are in flight while step j is reversed
+        TapeEntry nxt;
+        if (ns > 0) {
+            nxt.a = __ldcs(tr.at(ns - 1, 0));
+            nxt.b = __ldcs(tr.at(ns - 1, 1));
+            nxt.c = __ldcs(tr.at(ns - 1, 2));
+            nxt.d = __ldcs(tr.at(ns - 1, 3));
+        }
 #pragma unroll 1
-        for (int j = ns - 1; j >= 0; --j) reverse_step<GEOM, FIELD>(w, sw, tape[j], q, rp.d, rp.kd, rb, pb, acc, sacc);
+        for (int j = ns - 1; j >= 0; --j) {
+            const TapeEntry t = nxt;
+            if (j > 0) {
+                nxt.a = __ldcs(tr.at(j - 1, 0));
+                nxt.b = __ldcs(tr.at(j - 1, 1));
+                nxt.c = __ldcs(tr.at(j - 1, 2));
+                nxt.d = __ldcs(tr.at(j - 1, 3));
+            }
+            reverse_step<GEOM, FIELD>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
+        }
+#else
+#pragma unroll 1
+        for (int j = ns - 1; j >= 0; --j) {
+            TapeEntry t;
+            t.a = __ldcs(tr.at(j, 0));
+            t.b = __ldcs(tr.at(j, 1));
+            t.c = __ldcs(tr.at(j, 2));
+            t.d = (__float_as_int(t.a.w) & 1) ? __ldcs(tr.at(j, 3)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            reverse_step<GEOM, FIELD>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
+        }
+#endif
         adj[idx] = rb[0];
         adj[n + idx] = rb[1];
         adj[2 * n + idx] = rb[2];
@@ -446,6 +499,26 @@ static int resident_grid(const void *kernel, int64_t work)
 int64_t ckpt_bytes(int64_t n, int32_t max_steps, int32_t K) { return ckpt_layout(n, max_steps, K).total; }
 
 template <int GEOM, int FIELD>
+static int adjoint_grid(int64_t n)
+{
+    return resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+}
+
+// Tape scratch of the reverse sweep: 3 words x K steps x every thread of the grid.
+static int64_t tape_bytes(const WorldParams &w, int64_t n, int K)
+{
+    int grid;
+    if (w.geom_kind == MT_GEOM_BOXES)
+        grid = w.field_kind == MT_FIELD_MAP   ? adjoint_grid<MT_GEOM_BOXES, MT_FIELD_MAP>(n)
+               : w.field_kind == MT_FIELD_BOX ? adjoint_grid<MT_GEOM_BOXES, MT_FIELD_BOX>(n)
+                                              : adjoint_grid<MT_GEOM_BOXES, MT_FIELD_NONE>(n);
+    else
+        grid = w.field_kind == MT_FIELD_MAP ? adjoint_grid<MT_GEOM_VOXELS, MT_FIELD_MAP>(n)
+                                            : adjoint_grid<MT_GEOM_VOXELS, MT_FIELD_NONE>(n);
+    return 4 * (int64_t)K * grid * kBlock * (int64_t)sizeof(float4);
+}
+
+template <int GEOM, int FIELD>
 static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
                                 cudaStream_t st, int K, char *ck)
 {
@@ -471,17 +544,17 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
 
 template <int GEOM, int FIELD>
 static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
-                                 char *ck, float *adj)
+                                 char *ck, float *adj, float4 *tape)
 {
     const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
     const unsigned long long *ctr = reinterpret_cast<const unsigned long long *>(ck);
     double *dalpha = reinterpret_cast<double *>(ck + L.alpha_off);
     cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    const int grid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+    const int grid = adjoint_grid<GEOM, FIELD>(n);
     for (int p = L.passes - 1; p >= 0; --p) {
         adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
-                                                           ctr + p, K, adj, n, dalpha);
+                                                           ctr + p, K, adj, n, dalpha, tape);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -621,26 +694,25 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
         }
         return MT_OK;
     }
-    float *adj = dL_dinitial;
-    bool own = false;
-    cudaError_t e = cudaSuccess;
-    if (!adj) {
-        e = cudaMallocAsync(reinterpret_cast<void **>(&adj), 6 * n * sizeof(float), st);
-        if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
-        own = true;
-    }
+    // scratch: the tape of the reverse sweep, and the adjoint state unless the
+    // caller asked for dL/d(initial state) in place
+    const int64_t tbytes = tape_bytes(w, n, ckpt_every);
+    const int64_t abytes = dL_dinitial ? 0 : ((6 * n * (int64_t)sizeof(float) + 255) & ~(int64_t)255);
+    char *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)(tbytes + abytes), st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
+    float4 *tape = reinterpret_cast<float4 *>(scratch);
+    float *adj = dL_dinitial ? dL_dinitial : reinterpret_cast<float *>(scratch + tbytes);
     e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj);
+    if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj, tape);
     if (e == cudaSuccess && alpha && n_block > 0) {
         const CkptLayout L = ckpt_layout(n, max_steps, ckpt_every);
         alpha_to_float<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L.alpha_off), dL_dalpha,
                                            3 * n_block);
         e = cudaGetLastError();
     }
-    if (own) {
-        const cudaError_t f = cudaFreeAsync(adj, st);
-        if (e == cudaSuccess) e = f;
-    }
+    const cudaError_t f = cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = f;
     if (e != cudaSuccess) return cuda_fail(e, "adjoint");
     return MT_OK;
 }

@@ -5,6 +5,13 @@
 
 #include "step.cuh"
 
+// Resident blocks per SM the compiler must allow for (register budget of the
+// pass kernels): 5 blocks of 256 threads = 48 registers per thread (measured
+// fastest on config1: 40 registers spill and run 8 % slower).
+#ifndef MT_PASS_MIN_BLOCKS
+#define MT_PASS_MIN_BLOCKS 5
+#endif
+
 namespace mt {
 
 // Pack the live muons (status ALIVE or MAX_STEPS, finite state) of the
@@ -28,7 +35,7 @@ static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa 
 // One pass: live count from *cin, survivors appended at *cout; *czero (if not
 // null) is cleared for the pass after this one.
 template <int GEOM, int FIELD>
-__global__ void __launch_bounds__(kBlock) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
+__global__ void __launch_bounds__(kBlock, MT_PASS_MIN_BLOCKS) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
                                                        LiveBuf in, LiveBuf out, const unsigned long long *cin,
                                                        unsigned long long *cout, unsigned long long *czero, int S)
 {

@@ -367,8 +367,9 @@ __device__ __forceinline__ int check_stop(const WorldParams &w, const State &s, 
 // compiles away); the adjoint's recompute passes a tape writer, so the tape
 // comes from exactly the arithmetic of the forward pass.
 struct NoRecord {
-    __device__ __forceinline__ void begin(const State &, int) {}
-    __device__ __forceinline__ void draw(float, float, float, float) {}
+    __device__ __forceinline__ void begin(const State &, int, bool) {}
+    __device__ __forceinline__ void draw(float, float, float) {}
+    __device__ __forceinline__ void field(float3) {}
 };
 
 // One full step k of Algorithm 1.  Returns MT_ALIVE or the break status.
@@ -387,7 +388,7 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         const int vm = voxel_material(w, s);
         mat = vm >= 0 ? vm : w.world_mat;
     }
-    rec.begin(s, box);
+    rec.begin(s, box, mat != 0);
     if (mat != 0) {
         const int ib = momentum_bin(w, sw, s, P2);
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, id_lo, id_hi, (uint32_t)rp.instance), rp.key0, rp.key1);
@@ -396,9 +397,10 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         const uint32_t ab = sample_cell(w.guide + hr.guide_off, w.pairs + hr.pair_off, w.gshift, rnd.x);
         const float f = ((float)(ab >> 16) + u01(rnd.y)) * hr.fscale;
         const float th = ((float)(ab & 0xFFFFu) + u01(rnd.z)) * hr.tscale;
+        const float phs = fmaf(6.283185307179586f, u01(rnd.w), -3.14159265358979f);   // phi - pi
         float sp, cp;
-        __sincosf(fmaf(6.283185307179586f, u01(rnd.w), -3.14159265358979f), &sp, &cp);   // phi - pi
-        rec.draw(f, th, -cp, -sp);
+        __sincosf(phs, &sp, &cp);
+        rec.draw(f, th, phs);
         scatter(s, f, th, -cp, -sp);
     }
     float3 B = make_float3(0.0f, 0.0f, 0.0f);
@@ -407,6 +409,7 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
     } else if (FIELD == MT_FIELD_MAP) {
         B = field_map(w, s);
     }
+    rec.field(B);   // before the block scale
     if (GEOM == MT_GEOM_BOXES && FIELD != MT_FIELD_NONE && box >= 0) {
         const int blk = sw.block[box];
         if (blk >= 0) {
