@@ -195,6 +195,74 @@ def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32
                 passes=int((wl.max_steps + K - 1) // K))
 
 
+def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True):
+    """Batched form (config2): n_inst worlds, each its own 64x64x512 voxel geometry
+    and 100x100x300 field map, one shared histogram set, instance sizes log-uniform
+    in [1e3, 1e6].  One mt_transport_batched call (autotuned launch shape, CUDA
+    graph) is timed with CUDA events; the same instances as one mt_transport call
+    each, in n_inst separate worlds, are timed beside it."""
+    import torch
+    from paper_2512_10520_gb300.api import empty_like_soa
+    from workloads import gen
+    hist = gen.batched_hist()
+    b = mt.Batch(hist, n_inst)
+    inits, insts = [], []
+    for i, inst in enumerate(gen.batched_instances(n_inst)):
+        b.set_instance(i, inst["geometry"], inst["field"])
+        inits.append(mt.muons_to_device(inst["muons"], device=dev))
+        insts.append(inst if separate else None)
+    counts = [int(t["x"].numel()) for t in inits]
+    ids = list(np.cumsum([0] + counts[:-1]) + rank * sum(counts))
+    works = [empty_like_soa(c, device=dev) for c in counts]
+
+    def reset():
+        for w, s0 in zip(works, inits):
+            for k in w:
+                w[k].copy_(s0[k], non_blocking=True)
+
+    args = (gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
+    out = dict(instances=n_inst, muons=sum(counts), min_instance=min(counts), max_instance=max(counts))
+    with torch.cuda.stream(stream):
+        reset()
+        blk, S = b.autotune(works, *args, sample_per_instance=4096, id_offsets=ids, stream=stream)
+        times = []
+        for r in range(reps + 1):
+            reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.transport(works, *args, use_graph=True, id_offsets=ids, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+        steps = float(sum(int(w["steps"].sum().item()) for w in works))
+        ref_status = [w["status"].clone() for w in works[:8]]
+        t = float(np.mean(times)) / 1e3
+        out.update(value=steps / t, unit=UNIT, batched_ms=1e3 * t, muon_steps=steps, block=blk, steps_per_pass=S,
+                   graph=True, device_bytes=b.device_bytes)
+        if separate:
+            worlds = [mt.World(inst["geometry"], inst["field"], hist) for inst in insts]
+            times = []
+            for r in range(2):
+                reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for i, w in enumerate(worlds):
+                    w.transport(works[i], *args, id_offset=int(ids[i]), instance=i, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            same = all(torch.equal(a, w["status"]) for a, w in zip(ref_status, works[:8]))
+            for w in worlds:
+                w.close()
+            ts = float(np.mean(times)) / 1e3
+            out.update(separate_calls_ms=1e3 * ts, separate_value=steps / ts, speedup_vs_separate=ts / t,
+                       separate_equal_status_first8=bool(same))
+    b.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -241,6 +309,13 @@ def run_mine(args):
     from paper_2512_10520_gb300.api import empty_like_soa
     from workloads import gen
 
+    if args.batch_only:
+        with ClockSampler(local) as clk:
+            res = time_batched_form(mt, torch.cuda.Stream(device=dev), dev, n_inst=args.batch_instances,
+                                    rank=rank, separate=not args.no_separate)
+        if rank == 0:
+            print(json.dumps({"form": "batched", "clocks": clk.summary(), **res}))
+        return 0
     wl = gen.workload("config1", n=args.muons)
     n = wl.n
     id_offset = rank * n
@@ -334,6 +409,12 @@ def run_mine(args):
             adjoint_over_forward=adj["t_adjoint_ms"] / (kernel_s * 1e3),
             total_over_forward=t_all / kernel_s, **adj)
         forms["plain"] = dict(value=value, unit=UNIT, kernel_ms=kernel_s * 1e3)
+        bt = time_batched_form(mt, stream, dev, n_inst=args.batch_instances, rank=rank,
+                               separate=not args.no_separate)
+        bt["value"] = _barrier_sum(bt["muon_steps"], ws, dev) / _barrier_max(bt["batched_ms"] / 1e3, ws, dev)
+        bt["workload"] = (f"config2: {bt['instances']} worlds (64x64x512 voxels, 100x100x300 map each), shared "
+                          f"iron/air/concrete tables, {bt['muons']} muons, log-uniform sizes, 2000 steps")
+        forms["batched"] = bt
     peaks, peak_kind = _peaks()
     achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -388,6 +469,10 @@ def main(argv=None):
     ap.add_argument("--mode", default="auto", choices=["auto", "static", "persistent", "compact"])
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--steps-per-pass", type=int, default=0)
+    ap.add_argument("--batch-instances", type=int, default=256, help="worlds in the batched form")
+    ap.add_argument("--batch-only", action="store_true", help="run only the batched form (one JSON line)")
+    ap.add_argument("--no-separate", action="store_true",
+                    help="batched form: skip timing one mt_transport call per instance")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -217,6 +217,67 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
                            void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched form: many independent worlds (each its own geometry and field map,
+ * all sharing one histogram set) transported in one sequence of launches.
+ * The live muons of every instance advance in lockstep passes of
+ * steps_per_pass steps; a device work queue hands (instance, chunk) items to a
+ * resident grid whose blocks stage one instance's world at a time in shared
+ * memory; survivors are compacted per instance between passes.  The paper
+ * runs one geometry per launch; scanning many magnet configurations is the
+ * design-optimisation use it motivates (Sec. Introduction).
+ * ------------------------------------------------------------------------- */
+typedef struct mt_batch mt_batch;
+
+typedef struct mt_batch_cfg {
+    int32_t block;            /* threads per block: 128 or 256; 0 = tuned / 256      */
+    int32_t steps_per_pass;   /* steps between compactions; 0 = tuned / 64           */
+    int32_t use_graph;        /* 1 = capture the launch sequence in a CUDA graph once */
+    int32_t reserved;         /*     per (workspace, sizes, arguments) and replay it  */
+    void *workspace;          /* device scratch (256-byte aligned) of at least        */
+    int64_t workspace_bytes;  /*   mt_batch_workspace_bytes, or NULL = stream-ordered  */
+} mt_batch_cfg;
+
+/* A batch of n_inst worlds sharing the histogram set `hist` (copied, as in
+ * mt_create).  Every instance must then be given a world with
+ * mt_batch_set_instance before the batch is transported.  Synchronous. */
+mt_status mt_batch_create(const mt_hist_desc *hist, int32_t n_inst, mt_batch **out);
+
+/* Geometry and field of instance i (copied to the device, synchronously; the
+ * caller may free its arrays on return).  All instances need the same geometry
+ * kind and field kind.  Errors: MT_ERR_INVALID_ARG for a bad descriptor, an
+ * index out of range or a different kind, MT_ERR_OOM, MT_ERR_CUDA. */
+mt_status mt_batch_set_instance(mt_batch *b, int32_t i, const mt_geometry_desc *geometry,
+                                const mt_field_desc *field);
+
+/* Release a batch and its device memory (NULL is a no-op). */
+void mt_batch_destroy(mt_batch *b);
+
+/* Device bytes held by the batch (tables, every instance's geometry and map). */
+int64_t mt_batch_device_bytes(const mt_batch *b);
+
+/* Scratch bytes mt_transport_batched needs for the counts n[0..n_inst-1]. */
+int64_t mt_batch_workspace_bytes(const mt_batch *b, const int64_t *n);
+
+/* Transport the muons of every instance in place (Algorithm 1 in each world).
+ * soas, n: host arrays of n_inst entries; soas[i] describes instance i's muons
+ * (device arrays, ids id_offset + m, Philox counter word 3 = soas[i].instance).
+ * Results equal n_inst separate mt_transport calls.  Asynchronous on `stream`;
+ * calls on one batch must not overlap (the batch holds the cached graph).
+ * Errors: MT_ERR_INVALID_ARG (null arrays, unset instance, bad cfg or counts),
+ * MT_ERR_OOM, MT_ERR_CUDA. */
+mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64_t *n, float step_len,
+                               int32_t max_steps, uint64_t seed, const mt_batch_cfg *cfg, void *stream);
+
+/* Pick the block size (128, 256) and pass length (32, 64, 128) that transport
+ * a sample (the first sample_per_instance muons of every instance, copied to
+ * scratch; the caller's muons are not modified) fastest; the choice is kept
+ * in the batch for calls whose cfg leaves them 0 and returned in *best (may be
+ * NULL).  Synchronises `stream`. */
+mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t *n, float step_len,
+                            int32_t max_steps, uint64_t seed, int64_t sample_per_instance, mt_batch_cfg *best,
+                            void *stream);
+
+/* ---------------------------------------------------------------------------
  * Differentiable form.  The paper's Discussion proposes turning the histogram
  * transport into a differentiable layer so that magnet fields can be optimised
  * by gradient descent.  Parameters: per-magnet field scales alpha (device,

@@ -62,6 +62,11 @@ class mt_launch_cfg(C.Structure):
 MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT = 0, 1, 2, 3
 
 
+class mt_batch_cfg(C.Structure):
+    _fields_ = [("block", C.c_int32), ("steps_per_pass", C.c_int32), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64)]
+
+
 class mt_muon_soa(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("px", C.c_void_p),
                 ("py", C.c_void_p), ("pz", C.c_void_p), ("q", C.c_void_p), ("steps", C.c_void_p),
@@ -97,6 +102,15 @@ _SIGNATURES = {
                               C.c_int32, _P, _P, C.c_int32, _P], C.c_int),
     "mt_acceptance_loss": ([C.POINTER(mt_muon_soa), C.c_int64, C.c_double, C.c_double, C.c_double, _P, _P, _P],
                            C.c_int),
+    "mt_batch_create": ([C.POINTER(mt_hist_desc), C.c_int32, C.POINTER(_P)], C.c_int),
+    "mt_batch_set_instance": ([_P, C.c_int32, C.POINTER(mt_geometry_desc), C.POINTER(mt_field_desc)], C.c_int),
+    "mt_batch_destroy": ([_P], None),
+    "mt_batch_device_bytes": ([_P], C.c_int64),
+    "mt_batch_workspace_bytes": ([_P, C.POINTER(C.c_int64)], C.c_int64),
+    "mt_transport_batched": ([_P, C.POINTER(mt_muon_soa), C.POINTER(C.c_int64), C.c_float, C.c_int32, C.c_uint64,
+                              C.POINTER(mt_batch_cfg), _P], C.c_int),
+    "mt_batch_autotune": ([_P, C.POINTER(mt_muon_soa), C.POINTER(C.c_int64), C.c_float, C.c_int32, C.c_uint64,
+                           C.c_int64, C.POINTER(mt_batch_cfg), _P], C.c_int),
 }
 
 MT_NOALLOC_MAX_MUONS = 65536
@@ -152,14 +166,25 @@ def mt_last_error() -> str:
 class _Descs:
     """C descriptors plus the numpy arrays they point into (kept alive here)."""
 
-    def __init__(self, geometry: dict, field: dict, hist: dict):
+    def __init__(self, geometry: Optional[dict], field: Optional[dict], hist: Optional[dict]):
         keep = []
+        self.g = self.f = self.h = None
 
         def arr(a, dt):
             a = np.ascontiguousarray(a, dtype=dt)
             keep.append(a)
             return a
 
+        if geometry is not None:
+            self.g = self._geometry(geometry, arr, keep)
+        if field is not None:
+            self.f = self._field(field, arr)
+        if hist is not None:
+            self.h = self._hist(hist, arr)
+        self._keep = keep
+
+    @staticmethod
+    def _geometry(geometry, arr, keep):
         g = mt_geometry_desc()
         if geometry["kind"] == "boxes":
             boxes = geometry["boxes"]
@@ -188,7 +213,10 @@ class _Descs:
         g.world_material = int(geometry["world_material"])
         g.x_max, g.y_max, g.z_max = (float(geometry[k]) for k in ("x_max", "y_max", "z_max"))
         g.p_min = float(geometry["p_min"])
+        return g
 
+    @staticmethod
+    def _field(field, arr):
         f = mt_field_desc()
         kind = field["kind"]
         f.kind = {"none": MT_FIELD_NONE, "box": MT_FIELD_BOX, "map": MT_FIELD_MAP}[kind]
@@ -198,7 +226,10 @@ class _Descs:
             f.origin[:] = list(map(float, field["origin"]))
             f.spacing[:] = list(map(float, field["spacing"]))
             f.B = B.ctypes.data
+        return f
 
+    @staticmethod
+    def _hist(hist, arr):
         h = mt_hist_desc()
         h.n_mat, h.n_pbin = int(hist["n_mat"]), int(hist["n_pbin"])
         h.p_lo, h.p_hi = float(hist["p_lo"]), float(hist["p_hi"])
@@ -206,8 +237,7 @@ class _Descs:
         h.weights = arr(hist["weights"], np.float64).ctypes.data
         h.f_max = arr(hist["f_max"], np.float64).ctypes.data
         h.theta_max = arr(hist["theta_max"], np.float64).ctypes.data
-        self.g, self.f, self.h = g, f, h
-        self._keep = keep
+        return h
 
 
 def mt_create(geometry: dict, field: dict, hist: dict) -> int:
@@ -390,3 +420,75 @@ def mt_acceptance_loss(muons: Dict, loss, dL_dfinal=None, z_plane: float = 30.0,
                                              float(edge), C.c_void_p(loss.data_ptr()),
                                              C.c_void_p(_f32_dev(dL_dfinal, "dL_dfinal")),
                                              C.c_void_p(_stream_ptr(stream))), "mt_acceptance_loss")
+
+
+# --------------------------------------------------------------------------
+# batched form
+# --------------------------------------------------------------------------
+def mt_batch_create(hist: dict, n_inst: int) -> int:
+    """A batch of n_inst worlds sharing the histogram set `hist`; returns the batch pointer (int)."""
+    L = load_library()
+    d = _Descs(None, None, hist)
+    out = C.c_void_p()
+    _check(L.mt_batch_create(C.byref(d.h), int(n_inst), C.byref(out)), "mt_batch_create")
+    return out.value
+
+
+def mt_batch_set_instance(batch: int, i: int, geometry: dict, field: dict) -> None:
+    d = _Descs(geometry, field, None)
+    _check(load_library().mt_batch_set_instance(C.c_void_p(batch), int(i), C.byref(d.g), C.byref(d.f)),
+           "mt_batch_set_instance")
+
+
+def mt_batch_destroy(batch: Optional[int]) -> None:
+    if batch:
+        load_library().mt_batch_destroy(C.c_void_p(batch))
+
+
+def mt_batch_device_bytes(batch: int) -> int:
+    return load_library().mt_batch_device_bytes(C.c_void_p(batch))
+
+
+def _counts(counts):
+    a = (C.c_int64 * max(1, len(counts)))()
+    for i, c in enumerate(counts):
+        a[i] = int(c)
+    return a
+
+
+def mt_batch_workspace_bytes(batch: int, counts) -> int:
+    return load_library().mt_batch_workspace_bytes(C.c_void_p(batch), _counts(counts))
+
+
+def _soas(muons_list, id_offsets, instances):
+    arr = (mt_muon_soa * max(1, len(muons_list)))()
+    n = []
+    for i, m in enumerate(muons_list):
+        arr[i] = soa_struct(m, 0 if id_offsets is None else id_offsets[i], i if instances is None else instances[i])
+        n.append(int(m["x"].numel()))
+    return arr, _counts(n)
+
+
+def mt_transport_batched(batch: int, muons_list, step_len: float, max_steps: int, seed: int, block: int = 0,
+                         steps_per_pass: int = 0, use_graph: bool = False, workspace=None, id_offsets=None,
+                         instances=None, stream=None) -> None:
+    """Transport instance i's muons (dict of CUDA tensors, in place) in world i, for every i.
+    Muon ids are id_offsets[i] + m (default 0) and the Philox instance word is instances[i] (default i)."""
+    soas, n = _soas(muons_list, id_offsets, instances)
+    ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(),
+                                                           workspace.numel() * workspace.element_size())
+    cfg = mt_batch_cfg(int(block), int(steps_per_pass), int(bool(use_graph)), 0, ws_ptr, int(ws_bytes))
+    _check(load_library().mt_transport_batched(C.c_void_p(batch), soas, n, float(step_len), int(max_steps),
+                                               int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(cfg),
+                                               C.c_void_p(_stream_ptr(stream))), "mt_transport_batched")
+
+
+def mt_batch_autotune(batch: int, muons_list, step_len: float, max_steps: int, seed: int,
+                      sample_per_instance: int = 4096, id_offsets=None, instances=None, stream=None):
+    """Time the launch shapes on a sample of every instance's muons (left unchanged); returns (block, S)."""
+    soas, n = _soas(muons_list, id_offsets, instances)
+    best = mt_batch_cfg()
+    _check(load_library().mt_batch_autotune(C.c_void_p(batch), soas, n, float(step_len), int(max_steps),
+                                            int(seed) & 0xFFFFFFFFFFFFFFFF, int(sample_per_instance),
+                                            C.byref(best), C.c_void_p(_stream_ptr(stream))), "mt_batch_autotune")
+    return int(best.block), int(best.steps_per_pass)

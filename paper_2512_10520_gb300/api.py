@@ -52,6 +52,48 @@ class World:
             pass
 
 
+class Batch:
+    """Many worlds sharing one histogram set (one mt_batch), transported together."""
+
+    def __init__(self, hist: dict, n_inst: int):
+        self.handle = B.mt_batch_create(hist, n_inst)
+        self.n_inst = int(n_inst)
+
+    def set_instance(self, i: int, geometry: dict, field: dict) -> None:
+        B.mt_batch_set_instance(self.handle, i, geometry, field)
+
+    @property
+    def device_bytes(self) -> int:
+        return B.mt_batch_device_bytes(self.handle)
+
+    def workspace_bytes(self, counts) -> int:
+        return B.mt_batch_workspace_bytes(self.handle, counts)
+
+    def transport(self, muons_list, step_len: float, max_steps: int, seed: int, **kw) -> None:
+        B.mt_transport_batched(self.handle, muons_list, step_len, max_steps, seed, **kw)
+
+    def autotune(self, muons_list, step_len: float, max_steps: int, seed: int, sample_per_instance: int = 4096,
+                 **kw):
+        return B.mt_batch_autotune(self.handle, muons_list, step_len, max_steps, seed, sample_per_instance, **kw)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            B.mt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def muons_to_device(soa: Dict[str, np.ndarray], device="cuda", pin: bool = False) -> Dict:
     """Copy a numpy SoA (fields of mt_muon_soa) to CUDA tensors."""
     import torch

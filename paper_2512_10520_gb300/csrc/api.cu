@@ -116,10 +116,10 @@ static mt_status build_tables(const mt_hist_desc *h, int gbits, std::vector<Hist
     return MT_OK;
 }
 
-static mt_status validate(const mt_geometry_desc *g, const mt_field_desc *f, const mt_hist_desc *h)
+mt_status validate_hist(const mt_hist_desc *h)
 {
-    if (!g || !f || !h) {
-        set_error("null descriptor");
+    if (!h) {
+        set_error("null histogram descriptor");
         return MT_ERR_INVALID_ARG;
     }
     if (h->n_mat < 1 || h->n_mat > MT_MAX_MATERIALS || h->n_pbin < 1 || h->n_pbin > MT_MAX_PBINS) {
@@ -144,13 +144,22 @@ static mt_status validate(const mt_geometry_desc *g, const mt_field_desc *f, con
             set_error("hist: f_max/theta_max[%lld] must be positive and finite", (long long)i);
             return MT_ERR_INVALID_ARG;
         }
+    return MT_OK;
+}
+
+mt_status validate_geometry(const mt_geometry_desc *g, int n_mat)
+{
+    if (!g) {
+        set_error("null geometry descriptor");
+        return MT_ERR_INVALID_ARG;
+    }
     if (!(g->x_max > 0.0) || !(g->y_max > 0.0) || std::isnan(g->z_max) || !(g->p_min >= 0.0) ||
         !std::isfinite(g->p_min)) {
         set_error("geometry: bad world bounds or p_min");
         return MT_ERR_INVALID_ARG;
     }
-    if (g->world_material < 0 || g->world_material > h->n_mat) {
-        set_error("geometry: world material %d outside [0, %d]", g->world_material, h->n_mat);
+    if (g->world_material < 0 || g->world_material > n_mat) {
+        set_error("geometry: world material %d outside [0, %d]", g->world_material, n_mat);
         return MT_ERR_INVALID_ARG;
     }
     if (g->kind == MT_GEOM_BOXES) {
@@ -161,7 +170,7 @@ static mt_status validate(const mt_geometry_desc *g, const mt_field_desc *f, con
         for (int b = 0; b < g->n_boxes; ++b) {
             const mt_box &bx = g->boxes[b];
             if (!finite3(bx.lo) || !finite3(bx.hi) || !finite3(bx.B) || bx.material < 0 ||
-                bx.material > h->n_mat || bx.block_id < -1 || bx.block_id >= MT_MAX_BOXES) {
+                bx.material > n_mat || bx.block_id < -1 || bx.block_id >= MT_MAX_BOXES) {
                 set_error("geometry: box %d invalid (material %d, block %d)", b, bx.material, bx.block_id);
                 return MT_ERR_INVALID_ARG;
             }
@@ -175,12 +184,21 @@ static mt_status validate(const mt_geometry_desc *g, const mt_field_desc *f, con
         }
         const int64_t nv = (int64_t)g->vox_dims[0] * g->vox_dims[1] * g->vox_dims[2];
         for (int64_t i = 0; i < nv; ++i)
-            if (g->voxels[i] > h->n_mat) {
+            if (g->voxels[i] > n_mat) {
                 set_error("geometry: voxel %lld material %d > n_mat", (long long)i, g->voxels[i]);
                 return MT_ERR_INVALID_ARG;
             }
     } else {
         set_error("geometry: unknown kind %d", g->kind);
+        return MT_ERR_INVALID_ARG;
+    }
+    return MT_OK;
+}
+
+mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g)
+{
+    if (!f) {
+        set_error("null field descriptor");
         return MT_ERR_INVALID_ARG;
     }
     if (f->kind == MT_FIELD_MAP) {
@@ -208,86 +226,73 @@ static mt_status validate(const mt_geometry_desc *g, const mt_field_desc *f, con
 }
 
 template <class T>
-static mt_status upload(void *&dst, const T *src, size_t count, int64_t &bytes, const char *what)
+static mt_status upload(DevOwner &own, const T *src, size_t count, const char *what, const T **dst)
 {
     size_t nb = count * sizeof(T);
     if (nb == 0) nb = sizeof(T);
-    cudaError_t e = cudaMalloc(&dst, nb);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, nb);
     if (e != cudaSuccess) return cuda_fail(e, what);
-    bytes += (int64_t)nb;
+    own.bufs.push_back(p);
+    own.bytes += (int64_t)nb;
     if (count) {
-        e = cudaMemcpy(dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, what);
     }
+    *dst = (const T *)p;
     return MT_OK;
 }
 
-}  // namespace mt
-
-using namespace mt;
-
-extern "C" {
-
-int32_t mt_abi_version(void) { return MT_ABI_VERSION; }
-
-const char *mt_last_error(void) { return g_err; }
-
-void mt_destroy(mt_handle *h)
+void DevOwner::release()
 {
-    if (!h) return;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(h->device);
-    void *bufs[] = {h->d_boxes, h->d_hist, h->d_guide, h->d_pairs, h->d_e2, h->d_fmap, h->d_vox, h->d_zmask};
     for (void *p : bufs)
         if (p) cudaFree(p);
-    if (prev >= 0) cudaSetDevice(prev);
-    delete h;
+    bufs.clear();
+    bytes = 0;
 }
 
-int64_t mt_device_bytes(const mt_handle *h) { return h ? h->bytes : 0; }
-
-mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_hist_desc *hd, mt_handle **out)
+// Sampling tables and bin edges of a histogram set (validated) into w.
+mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
 {
-    g_err[0] = 0;
-    if (!out) {
-        set_error("null output pointer");
-        return MT_ERR_INVALID_ARG;
-    }
-    *out = nullptr;
-    mt_status st = validate(g, f, hd);
-    if (st != MT_OK) return st;
-
     const int ncell = hd->nf * hd->ntheta;
     int gbits = 12;
     while ((1 << gbits) < ncell && gbits < 15) ++gbits;   // at least one guide slot per cell up to 32K
     std::vector<HistRec> rec;
     std::vector<uint32_t> guide;
     std::vector<uint2> pairs;
-    st = build_tables(hd, gbits, rec, guide, pairs);
+    mt_status st = build_tables(hd, gbits, rec, guide, pairs);
     if (st != MT_OK) return st;
+    std::vector<float2> e2(hd->n_pbin + 1);
+    for (int k = 0; k <= hd->n_pbin; ++k) {
+        const double E = hd->p_lo * std::pow(hd->p_hi / hd->p_lo, (double)k / hd->n_pbin);
+        float a, b;
+        split(E * E, a, b);
+        e2[k] = make_float2(a, b);
+    }
+    if ((st = upload(own, rec.data(), rec.size(), "histogram records", &w.hist)) != MT_OK) return st;
+    if ((st = upload(own, guide.data(), guide.size(), "guide tables", &w.guide)) != MT_OK) return st;
+    if ((st = upload(own, pairs.data(), pairs.size(), "threshold pairs", &w.pairs)) != MT_OK) return st;
+    if ((st = upload(own, e2.data(), e2.size(), "bin edges", &w.e2)) != MT_OK) return st;
+    w.n_mat = hd->n_mat;
+    w.n_pbin = hd->n_pbin;
+    w.nf = hd->nf;
+    w.ntheta = hd->ntheta;
+    w.gshift = 32 - gbits;
+    w.log2_plo = (float)std::log2(hd->p_lo);
+    w.pbin_scale = (float)(hd->n_pbin / std::log2(hd->p_hi / hd->p_lo));
+    return MT_OK;
+}
 
-    mt_handle *h = new mt_handle();
-    cudaGetDevice(&h->device);
-    WorldParams &w = h->w;
-    memset(&w, 0, sizeof(w));
+// Geometry and world bounds (validated) into w.
+mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &own)
+{
+    mt_status st;
     w.geom_kind = g->kind;
     w.world_mat = g->world_material;
-    w.n_mat = hd->n_mat;
     split(g->x_max, w.xmax_hi, w.xmax_lo);
     split(g->y_max, w.ymax_hi, w.ymax_lo);
     split(g->z_max, w.zmax_hi, w.zmax_lo);
     w.pmin2 = (float)(g->p_min * g->p_min);
-
-#define MT_TRY(expr)              \
-    do {                          \
-        mt_status s_ = (expr);    \
-        if (s_ != MT_OK) {        \
-            mt_destroy(h);        \
-            return s_;            \
-        }                         \
-    } while (0)
-
     if (g->kind == MT_GEOM_BOXES) {
         std::vector<DevBox> boxes(g->n_boxes);
         for (int b = 0; b < g->n_boxes; ++b) {
@@ -303,8 +308,7 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
             d.pad = 0;
         }
         w.n_box = g->n_boxes;
-        MT_TRY(upload(h->d_boxes, boxes.data(), boxes.size(), h->bytes, "boxes"));
-        w.boxes = (const DevBox *)h->d_boxes;
+        if ((st = upload(own, boxes.data(), boxes.size(), "boxes", &w.boxes)) != MT_OK) return st;
         // z-slab candidate index: slab s holds every box whose z range meets the
         // slab or its two neighbours (the slab of a point is computed in FP32 and
         // may be off by one near a slab face; the exact box test decides).
@@ -328,14 +332,13 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
             s1 = std::min(s1, kZSlabs - 1);
             for (int sl = s0; sl <= s1; ++sl) zmask[sl] |= 1u << b;
         }
-        MT_TRY(upload(h->d_zmask, zmask.data(), zmask.size(), h->bytes, "z-slab index"));
-        w.zmask = (const uint32_t *)h->d_zmask;
+        if ((st = upload(own, zmask.data(), zmask.size(), "z-slab index", &w.zmask)) != MT_OK) return st;
         w.zslab_lo = (float)zlo;
         w.zslab_inv = (float)(1.0 / dz);
     } else {
         const size_t nv = (size_t)g->vox_dims[0] * g->vox_dims[1] * g->vox_dims[2];
-        MT_TRY(upload(h->d_vox, g->voxels, nv, h->bytes, "voxels"));
-        w.vox = (const uint8_t *)h->d_vox;
+        if ((st = upload(own, g->voxels, nv, "voxels", &w.vox)) != MT_OK) return st;
+        w.n_box = 0;
         for (int a = 0; a < 3; ++a) {
             w.vdims[a] = g->vox_dims[a];
             split(g->vox_origin[a], w.vorigin[a], w.vorigin_lo[a]);
@@ -343,61 +346,86 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
             w.vinv[a] = (float)(1.0 / g->vox_spacing[a]);
         }
     }
+    return MT_OK;
+}
 
+// Field (validated) into w; a map is uploaded and repacked into x-adjacent node pairs.
+mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
+{
     w.field_kind = f->kind;
-    if (f->kind == MT_FIELD_MAP) {
-        const int nx = f->dims[0], ny = f->dims[1], nz = f->dims[2];
-        const size_t nraw = 3ull * nx * ny * nz;
-        const size_t npair = 2ull * (size_t)(nx - 1) * ny * nz;
-        void *raw = nullptr;
-        cudaError_t e = cudaMalloc(&raw, nraw * sizeof(float));
-        if (e != cudaSuccess) {
-            mt_destroy(h);
-            return cuda_fail(e, "field staging");
-        }
-        e = cudaMemcpy(raw, f->B, nraw * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_fmap, npair * sizeof(float4));
-        if (e == cudaSuccess) {
-            h->bytes += (int64_t)(npair * sizeof(float4));
-            e = launch_repack_field((const float *)raw, (float4 *)h->d_fmap, nx, ny, nz, 0);
-        }
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        cudaFree(raw);
-        if (e != cudaSuccess) {
-            mt_destroy(h);
-            return cuda_fail(e, "field map upload");
-        }
-        w.fmap = (const float4 *)h->d_fmap;
-        for (int a = 0; a < 3; ++a) {
-            w.fdims[a] = f->dims[a];
-            split(f->origin[a], w.forigin[a], w.forigin_lo[a]);
-            split(f->spacing[a], w.fspacing[a], w.fspacing_lo[a]);
-            w.finv[a] = (float)(1.0 / f->spacing[a]);
-        }
+    if (f->kind != MT_FIELD_MAP) return MT_OK;
+    const int nx = f->dims[0], ny = f->dims[1], nz = f->dims[2];
+    const size_t nraw = 3ull * nx * ny * nz;
+    const size_t npair = 2ull * (size_t)(nx - 1) * ny * nz;
+    void *raw = nullptr, *pairs = nullptr;
+    cudaError_t e = cudaMalloc(&raw, nraw * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "field staging");
+    e = cudaMemcpy(raw, f->B, nraw * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&pairs, npair * sizeof(float4));
+    if (e == cudaSuccess) {
+        own.bufs.push_back(pairs);
+        own.bytes += (int64_t)(npair * sizeof(float4));
+        e = launch_repack_field((const float *)raw, (float4 *)pairs, nx, ny, nz, 0);
     }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(raw);
+    if (e != cudaSuccess) return cuda_fail(e, "field map upload");
+    w.fmap = (const float4 *)pairs;
+    for (int a = 0; a < 3; ++a) {
+        w.fdims[a] = f->dims[a];
+        split(f->origin[a], w.forigin[a], w.forigin_lo[a]);
+        split(f->spacing[a], w.fspacing[a], w.fspacing_lo[a]);
+        w.finv[a] = (float)(1.0 / f->spacing[a]);
+    }
+    return MT_OK;
+}
 
-    MT_TRY(upload(h->d_hist, rec.data(), rec.size(), h->bytes, "histogram records"));
-    MT_TRY(upload(h->d_guide, guide.data(), guide.size(), h->bytes, "guide tables"));
-    MT_TRY(upload(h->d_pairs, pairs.data(), pairs.size(), h->bytes, "threshold pairs"));
-    std::vector<float2> e2(hd->n_pbin + 1);
-    for (int k = 0; k <= hd->n_pbin; ++k) {
-        const double E = hd->p_lo * std::pow(hd->p_hi / hd->p_lo, (double)k / hd->n_pbin);
-        float a, b;
-        split(E * E, a, b);
-        e2[k] = make_float2(a, b);
+}  // namespace mt
+
+using namespace mt;
+
+extern "C" {
+
+int32_t mt_abi_version(void) { return MT_ABI_VERSION; }
+
+const char *mt_last_error(void) { return g_err; }
+
+void mt_destroy(mt_handle *h)
+{
+    if (!h) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    h->own.release();
+    if (prev >= 0) cudaSetDevice(prev);
+    delete h;
+}
+
+int64_t mt_device_bytes(const mt_handle *h) { return h ? h->own.bytes : 0; }
+
+mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_hist_desc *hd, mt_handle **out)
+{
+    g_err[0] = 0;
+    if (!out) {
+        set_error("null output pointer");
+        return MT_ERR_INVALID_ARG;
     }
-    MT_TRY(upload(h->d_e2, e2.data(), e2.size(), h->bytes, "bin edges"));
-#undef MT_TRY
-    w.hist = (const HistRec *)h->d_hist;
-    w.guide = (const uint32_t *)h->d_guide;
-    w.pairs = (const uint2 *)h->d_pairs;
-    w.e2 = (const float2 *)h->d_e2;
-    w.n_pbin = hd->n_pbin;
-    w.nf = hd->nf;
-    w.ntheta = hd->ntheta;
-    w.gshift = 32 - gbits;
-    w.log2_plo = (float)std::log2(hd->p_lo);
-    w.pbin_scale = (float)(hd->n_pbin / std::log2(hd->p_hi / hd->p_lo));
+    *out = nullptr;
+    mt_status st = validate_hist(hd);
+    if (st == MT_OK) st = validate_geometry(g, hd->n_mat);
+    if (st == MT_OK) st = validate_field(f, g);
+    if (st != MT_OK) return st;
+    // table construction first: it checks the weights before any device work
+    mt_handle *h = new mt_handle();
+    memset(&h->w, 0, sizeof(h->w));
+    cudaGetDevice(&h->device);
+    st = build_hist(hd, h->w, h->own);
+    if (st == MT_OK) st = build_geometry(g, h->w, h->own);
+    if (st == MT_OK) st = build_field(f, h->w, h->own);
+    if (st != MT_OK) {
+        mt_destroy(h);
+        return st;
+    }
     *out = h;
     return MT_OK;
 }

@@ -1,0 +1,683 @@
+// batched.cu -- many independent worlds (geometry + field map) sharing one
+// histogram set, transported together: lockstep passes over every live muon of
+// every instance, fed to a resident grid by a device work queue of
+// (instance, chunk) items, with per-instance compaction between passes.
+//
+// Live list: the live muons of instance i occupy region [off_i, off_i + n_i) of
+// each of the two live buffers (entries as in step.cuh).  Per pass p:
+//   plan  : one block turns the live count of every instance into work items of
+//           up to BLOCK muons, an exclusive scan cof (cof[n_inst] = items), and
+//           clears the queue and the counters of the pass after next;
+//   pass  : each block pops items from the queue; all of its lanes take the
+//           same instance, whose world it stages in shared memory once per
+//           instance change; each lane advances its muon S steps, finished
+//           muons go back to the instance's arrays, survivors are appended to
+//           the instance's region of the other buffer.
+// All loops are bounded: the queue is finite and each muon runs at most
+// max_steps steps.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "step.cuh"
+
+struct mt_batch {
+    int device = 0;
+    int n_inst = 0;
+    int geom_kind = -1, field_kind = -1;
+    int hist_n_mat = 0;
+    mt::WorldParams tables;                 // histogram part shared by every instance
+    mt::DevOwner own_tables;
+    std::vector<mt::WorldParams> inst;      // host copies, tables filled in
+    std::vector<mt::DevOwner> inst_own;
+    std::vector<char> is_set;
+    mt::WorldParams *d_inst = nullptr;      // device copy of inst
+    bool dirty = true;
+    // launch shape chosen by mt_batch_autotune (0 = defaults)
+    int tuned_block = 0, tuned_S = 0;
+    // CUDA graph of the last launch sequence and the arguments it was made for
+    cudaGraphExec_t graph = nullptr;
+    std::vector<char> graph_key;
+};
+
+namespace mt {
+
+struct BatchWs {
+    unsigned int *cnt;          // [3][n_inst] live counts (rotating)
+    unsigned int *cof;          // [n_inst + 1] item offsets of the current pass
+    unsigned int *queue;        // [1] next item
+    unsigned long long *off;    // [n_inst + 1] region offsets
+    mt_muon_soa *soa;           // [n_inst] caller arrays
+    char *live0, *live1;        // two live buffers of N entries
+    int64_t N;
+};
+
+static int64_t round256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+static int64_t batch_ws_layout(int n_inst, int64_t N, BatchWs *ws, char *base)
+{
+    int64_t o = 0;
+    const int64_t c_cnt = o;
+    o = round256(o + 3 * (int64_t)n_inst * 4);
+    const int64_t c_cof = o;
+    o = round256(o + ((int64_t)n_inst + 1) * 4);
+    const int64_t c_q = o;
+    o = round256(o + 4);
+    const int64_t c_off = o;
+    o = round256(o + ((int64_t)n_inst + 1) * 8);
+    const int64_t c_soa = o;
+    o = round256(o + (int64_t)n_inst * (int64_t)sizeof(mt_muon_soa));
+    const int64_t cap = N > 0 ? N : 1;
+    const int64_t c_l0 = o;
+    o += 4 * cap * (int64_t)sizeof(float4);
+    const int64_t c_l1 = o;
+    o += 4 * cap * (int64_t)sizeof(float4);
+    if (ws && base) {
+        ws->cnt = reinterpret_cast<unsigned int *>(base + c_cnt);
+        ws->cof = reinterpret_cast<unsigned int *>(base + c_cof);
+        ws->queue = reinterpret_cast<unsigned int *>(base + c_q);
+        ws->off = reinterpret_cast<unsigned long long *>(base + c_off);
+        ws->soa = reinterpret_cast<mt_muon_soa *>(base + c_soa);
+        ws->live0 = base + c_l0;
+        ws->live1 = base + c_l1;
+        ws->N = cap;
+    }
+    return o;
+}
+
+__device__ __forceinline__ int find_region(const unsigned long long *off, int n_inst, unsigned long long g)
+{
+    int lo = 0, hi = n_inst;   // off[lo] <= g < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= g)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Warp-aggregated append to a 32-bit counter shared by the whole warp.
+__device__ __forceinline__ int64_t warp_append_u32(unsigned int *ctr, bool keep)
+{
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+    if (!mask) return -1;
+    const unsigned lane = threadIdx.x & 31u;
+    const int leader = __ffs(mask) - 1;
+    unsigned int base = 0;
+    if ((int)lane == leader) base = atomicAdd(ctr, (unsigned)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    return (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// Pack the live muons of every instance into its region of live buffer 0.
+__global__ void __launch_bounds__(256) batch_init(const unsigned long long *off, int n_inst, const mt_muon_soa *soa,
+                                                  RunParams rp, LiveBuf out, unsigned int *cnt)
+{
+    const unsigned long long N = off[n_inst];
+    const unsigned lane = threadIdx.x & 31u;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < N;
+         base += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long g = base + threadIdx.x;
+        int i = -1;
+        bool live = false;
+        State s;
+        float q = 0.0f;
+        int k = 0;
+        int64_t m = 0;
+        if (g < N) {
+            i = find_region(off, n_inst, g);
+            m = (int64_t)(g - off[i]);
+            RunParams r = rp;
+            r.id_offset = soa[i].id_offset;
+            r.instance = soa[i].instance;
+            uint32_t a, b;
+            live = load_muon(soa[i], m, r, s, q, k, a, b);
+        }
+        // lanes of one warp may straddle two instances: aggregate per instance
+        const unsigned act = __ballot_sync(0xFFFFFFFFu, live);
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, live ? i : -1) & act;
+        if (live) {
+            const int leader = __ffs(peers) - 1;
+            unsigned int b0 = 0;
+            if ((int)lane == leader) b0 = atomicAdd(&cnt[i], (unsigned)__popc(peers));
+            b0 = __shfl_sync(peers, b0, leader);
+            const int64_t slot = (int64_t)off[i] + b0 + __popc(peers & ((1u << lane) - 1u));
+            put_live(out, slot, s, q, k, m);
+        }
+    }
+}
+
+// Items of pass p: ceil(live_i / block) per instance, exclusive scan in cof.
+__global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, unsigned int *cnt_zero, int n_inst,
+                                                   int block, unsigned int *cof, unsigned int *queue)
+{
+    __shared__ unsigned int carry;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        *queue = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < n_inst; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const unsigned int items = i < n_inst ? (cnt_in[i] + block - 1) / block : 0u;
+        if (i < n_inst) cnt_zero[i] = 0;
+        // block-wide exclusive scan of items
+        __shared__ unsigned int warp_sums[32];
+        unsigned int v = items;
+        const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if ((int)lane >= o) v += t;
+        }
+        if (lane == 31) warp_sums[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned int ws = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, ws, o);
+                if ((int)lane >= o) ws += t;
+            }
+            warp_sums[lane] = ws;
+        }
+        __syncthreads();
+        const unsigned int incl = v + (wid ? warp_sums[wid - 1] : 0u);
+        if (i < n_inst) cof[i] = carry + incl - items;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cof[n_inst] = carry;
+}
+
+template <int GEOM, int FIELD, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
+                                                   const unsigned long long *off, int n_inst, RunParams rp,
+                                                   LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
+                                                   unsigned int *cnt_out, const unsigned int *cof,
+                                                   unsigned int *queue, int S)
+{
+    __shared__ SmemWorld sw;
+    __shared__ WorldParams wi;
+    __shared__ int s_item, s_inst;
+    __shared__ mt_muon_soa s_soa;
+    int cur = -1;
+    const unsigned int total = cof[n_inst];
+#pragma unroll 1
+    while (true) {
+        if (threadIdx.x == 0) {
+            const unsigned int item = atomicAdd(queue, 1u);
+            s_item = (int)item;
+            s_inst = -1;
+            if (item < total) {
+                int lo = 0, hi = n_inst;   // cof[lo] <= item < cof[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cof[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                // lo is the last instance with cof[lo] <= item, so instances without
+                // items (cof[j] == cof[j + 1]) are never chosen
+                s_inst = lo;
+            }
+        }
+        __syncthreads();
+        const unsigned int item = (unsigned int)s_item;
+        const int i = s_inst;
+        if (item >= total) break;
+        if (i != cur) {
+            const int words = (int)(sizeof(WorldParams) / 4);
+            const int *src = reinterpret_cast<const int *>(&inst[i]);
+            int *dst = reinterpret_cast<int *>(&wi);
+            for (int t = threadIdx.x; t < words; t += BLOCK) dst[t] = src[t];
+            if (threadIdx.x == 0) s_soa = soa[i];
+            __syncthreads();
+            RunParams r0 = rp;
+            stage_world(sw, wi, r0);
+            __syncthreads();
+            cur = i;
+        }
+        RunParams r = rp;
+        r.id_offset = s_soa.id_offset;
+        r.instance = s_soa.instance;
+        const int64_t e = (int64_t)(item - cof[i]) * BLOCK + threadIdx.x;
+        bool keep = false;
+        State s;
+        float q = 0.0f;
+        int k = 0;
+        int64_t idx = 0;
+        if (e < (int64_t)cnt_in[i]) {
+            get_live(in, (int64_t)off[i] + e, s, q, k, idx);
+            const uint64_t id = (uint64_t)(r.id_offset + idx);
+            const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+            const int kend = min(k + S, r.max_steps);
+            int st = MT_ALIVE;
+#pragma unroll 1
+            for (; k < kend; ++k) {
+                st = step<GEOM, FIELD>(wi, sw, s, q, k, id_lo, id_hi, r);
+                if (st != MT_ALIVE) break;
+            }
+            if (st == MT_ALIVE && k >= r.max_steps) st = MT_MAX_STEPS;
+            if (st != MT_ALIVE)
+                store_muon(s_soa, idx, s, k, st);
+            else
+                keep = true;
+        }
+        const int64_t slot = warp_append_u32(&cnt_out[i], keep);
+        if (keep) put_live(out, (int64_t)off[i] + slot, s, q, k, idx);
+        __syncthreads();
+    }
+}
+
+template <int GEOM, int FIELD, int BLOCK>
+static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
+                             cudaStream_t st)
+{
+    const LiveBuf L[2] = {live_buf_at(ws.live0, ws.N), live_buf_at(ws.live1, ws.N)};
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_pass<GEOM, FIELD, BLOCK>, BLOCK, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t need = (ws.N + BLOCK - 1) / BLOCK;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    const int64_t ig = std::min<int64_t>(need < 1 ? 1 : need, 65535 * 8);
+    batch_init<<<(unsigned)ig, 256, 0, st>>>(ws.off, n_inst, ws.soa, rp, L[0], ws.cnt);
+    cudaError_t e = cudaGetLastError();
+    const int passes = rp.max_steps > 0 ? (rp.max_steps + S - 1) / S : 1;
+    for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+        unsigned int *c_in = ws.cnt + (p % 3) * n_inst;
+        unsigned int *c_out = ws.cnt + ((p + 1) % 3) * n_inst;
+        unsigned int *c_zero = ws.cnt + ((p + 2) % 3) * n_inst;
+        batch_plan<<<1, 1024, 0, st>>>(c_in, c_zero, n_inst, BLOCK, ws.cof, ws.queue);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        batch_pass<GEOM, FIELD, BLOCK><<<(unsigned)grid, BLOCK, 0, st>>>(b->d_inst, ws.soa, ws.off, n_inst, rp,
+                                                                        L[p & 1], L[(p + 1) & 1], c_in, c_out,
+                                                                        ws.cof, ws.queue, S);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <int BLOCK>
+static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
+                                  cudaStream_t st)
+{
+    if (b->geom_kind == MT_GEOM_BOXES) {
+        if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_BOXES, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
+        if (b->field_kind == MT_FIELD_BOX) return run_batch<MT_GEOM_BOXES, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st);
+        return run_batch<MT_GEOM_BOXES, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
+    }
+    if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
+    return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
+}
+
+}  // namespace mt
+
+using namespace mt;
+
+namespace {
+
+struct DevGuardB {
+    int prev = -1;
+    explicit DevGuardB(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuardB()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+mt_status sync_instances(mt_batch *b)
+{
+    if (!b->dirty) return MT_OK;
+    for (int i = 0; i < b->n_inst; ++i)
+        if (!b->is_set[i]) {
+            set_error("batch instance %d has no world (mt_batch_set_instance)", i);
+            return MT_ERR_INVALID_ARG;
+        }
+    cudaError_t e = cudaSuccess;
+    if (!b->d_inst) {
+        e = cudaMalloc(&b->d_inst, sizeof(WorldParams) * (size_t)b->n_inst);
+        if (e != cudaSuccess) return cuda_fail(e, "batch instance table");
+    }
+    e = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(WorldParams) * (size_t)b->n_inst, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch instance table");
+    b->dirty = false;
+    return MT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mt_status mt_batch_create(const mt_hist_desc *hist, int32_t n_inst, mt_batch **out)
+{
+    if (!out) {
+        set_error("null output pointer");
+        return MT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (n_inst < 1 || n_inst > (1 << 20)) {
+        set_error("n_inst %d outside [1, 2^20]", n_inst);
+        return MT_ERR_INVALID_ARG;
+    }
+    mt_status st = validate_hist(hist);
+    if (st != MT_OK) return st;
+    mt_batch *b = new mt_batch();
+    memset(&b->tables, 0, sizeof(b->tables));
+    cudaGetDevice(&b->device);
+    st = build_hist(hist, b->tables, b->own_tables);
+    if (st != MT_OK) {
+        b->own_tables.release();
+        delete b;
+        return st;
+    }
+    b->n_inst = n_inst;
+    b->hist_n_mat = hist->n_mat;
+    b->inst.assign(n_inst, b->tables);
+    b->inst_own.resize(n_inst);
+    b->is_set.assign(n_inst, 0);
+    *out = b;
+    return MT_OK;
+}
+
+mt_status mt_batch_set_instance(mt_batch *b, int32_t i, const mt_geometry_desc *g, const mt_field_desc *f)
+{
+    if (!b || i < 0 || i >= b->n_inst) {
+        set_error("null batch or instance %d out of range", i);
+        return MT_ERR_INVALID_ARG;
+    }
+    mt_status st = validate_geometry(g, b->hist_n_mat);
+    if (st == MT_OK) st = validate_field(f, g);
+    if (st != MT_OK) return st;
+    if ((b->geom_kind >= 0 && g->kind != b->geom_kind) || (b->field_kind >= 0 && f->kind != b->field_kind)) {
+        set_error("every instance of a batch needs the same geometry kind and field kind");
+        return MT_ERR_INVALID_ARG;
+    }
+    DevGuardB guard(b->device);
+    b->inst_own[i].release();
+    WorldParams w = b->tables;
+    st = build_geometry(g, w, b->inst_own[i]);
+    if (st == MT_OK) st = build_field(f, w, b->inst_own[i]);
+    if (st != MT_OK) {
+        b->inst_own[i].release();
+        b->is_set[i] = 0;
+        return st;
+    }
+    b->inst[i] = w;
+    b->is_set[i] = 1;
+    b->geom_kind = g->kind;
+    b->field_kind = f->kind;
+    b->dirty = true;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return MT_OK;
+}
+
+void mt_batch_destroy(mt_batch *b)
+{
+    if (!b) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto &o : b->inst_own) o.release();
+    b->own_tables.release();
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete b;
+}
+
+int64_t mt_batch_device_bytes(const mt_batch *b)
+{
+    if (!b) return 0;
+    int64_t t = b->own_tables.bytes;
+    for (const auto &o : b->inst_own) t += o.bytes;
+    return t;
+}
+
+int64_t mt_batch_workspace_bytes(const mt_batch *b, const int64_t *n)
+{
+    if (!b || !n) return -1;
+    int64_t N = 0;
+    for (int i = 0; i < b->n_inst; ++i) N += n[i] > 0 ? n[i] : 0;
+    return batch_ws_layout(b->n_inst, N, nullptr, nullptr);
+}
+
+mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64_t *n, float step_len,
+                               int32_t max_steps, uint64_t seed, const mt_batch_cfg *cfg, void *stream)
+{
+    if (!b || !soas || !n) {
+        set_error("null batch, muon arrays or counts");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (!(step_len > 0.0f) || !isfinite(step_len) || max_steps < 0) {
+        set_error("step_len must be positive and finite, max_steps >= 0");
+        return MT_ERR_INVALID_ARG;
+    }
+    mt_batch_cfg c = {0, 0, 0, 0, nullptr, 0};
+    if (cfg) c = *cfg;
+    int block = c.block ? c.block : (b->tuned_block ? b->tuned_block : 256);
+    int S = c.steps_per_pass ? c.steps_per_pass : (b->tuned_S ? b->tuned_S : 64);
+    if ((block != 128 && block != 256) || S < 1) {
+        set_error("batch launch: block must be 128 or 256 and steps_per_pass >= 1 (got %d, %d)", block, S);
+        return MT_ERR_INVALID_ARG;
+    }
+    std::vector<unsigned long long> off(b->n_inst + 1, 0);
+    for (int i = 0; i < b->n_inst; ++i) {
+        if (n[i] < 0 || n[i] >= ((int64_t)1 << 31)) {
+            set_error("instance %d: n = %lld outside [0, 2^31)", i, (long long)n[i]);
+            return MT_ERR_INVALID_ARG;
+        }
+        if (n[i] > 0 && (!soas[i].x || !soas[i].y || !soas[i].z || !soas[i].px || !soas[i].py || !soas[i].pz ||
+                         !soas[i].q || !soas[i].steps || !soas[i].status || soas[i].id_offset < 0)) {
+            set_error("instance %d: null muon array or negative id_offset", i);
+            return MT_ERR_INVALID_ARG;
+        }
+        off[i + 1] = off[i] + (unsigned long long)n[i];
+    }
+    const int64_t N = (int64_t)off[b->n_inst];
+    const int64_t need = batch_ws_layout(b->n_inst, N, nullptr, nullptr);
+    if (c.workspace && (c.workspace_bytes < need || (reinterpret_cast<uintptr_t>(c.workspace) & 255u))) {
+        set_error("batch workspace of %lld bytes too small or not 256-byte aligned (need %lld)",
+                  (long long)c.workspace_bytes, (long long)need);
+        return MT_ERR_INVALID_ARG;
+    }
+    DevGuardB guard(b->device);
+    mt_status st = sync_instances(b);
+    if (st != MT_OK) return st;
+    if (N == 0) return MT_OK;
+    cudaStream_t cs = (cudaStream_t)stream;
+    char *base = reinterpret_cast<char *>(c.workspace);
+    bool own = false;
+    cudaError_t e = cudaSuccess;
+    if (!base) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&base), (size_t)need, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
+        own = true;
+    }
+    BatchWs ws{};
+    batch_ws_layout(b->n_inst, N, &ws, base);
+    RunParams rp;
+    rp.d = step_len;
+    rp.kd = (float)(0.299792458 * (double)step_len);
+    rp.max_steps = max_steps;
+    rp.key0 = (uint32_t)seed;
+    rp.key1 = (uint32_t)(seed >> 32);
+    rp.alpha = nullptr;
+    rp.n_block = 0;
+    rp.instance = 0;
+    rp.id_offset = 0;
+    // per-call inputs: region offsets, the instances' arrays, cleared counters
+    e = cudaMemcpyAsync(ws.off, off.data(), off.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.soa, soas, sizeof(mt_muon_soa) * (size_t)b->n_inst, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.cnt, 0, 3 * (size_t)b->n_inst * sizeof(unsigned int), cs);
+    if (e == cudaSuccess) {
+        if (c.use_graph) {
+            // capture the launch sequence once per (arguments) and replay it
+            std::vector<char> key(sizeof(void *) + 3 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 8);
+            char *kp = key.data();
+            memcpy(kp, &base, sizeof(void *));
+            kp += sizeof(void *);
+            const int ints[3] = {block, S, max_steps};
+            memcpy(kp, ints, sizeof(ints));
+            kp += sizeof(ints);
+            memcpy(kp, &step_len, sizeof(float));
+            kp += sizeof(float);
+            memcpy(kp, &seed, sizeof(uint64_t));
+            kp += sizeof(uint64_t);
+            memcpy(kp, &N, sizeof(int64_t));
+            if (!b->graph || b->graph_key != key) {
+                if (b->graph) {
+                    cudaGraphExecDestroy(b->graph);
+                    b->graph = nullptr;
+                }
+                cudaStream_t cap = nullptr;
+                e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+                cudaGraph_t gr = nullptr;
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t le = block == 128 ? dispatch_batch<128>(b, ws, b->n_inst, rp, S, cap)
+                                                  : dispatch_batch<256>(b, ws, b->n_inst, rp, S, cap);
+                    e = cudaStreamEndCapture(cap, &gr);
+                    if (le != cudaSuccess) e = le;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+                if (gr) cudaGraphDestroy(gr);
+                if (cap) cudaStreamDestroy(cap);
+                if (e == cudaSuccess) b->graph_key = key;
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, cs);
+        } else {
+            e = block == 128 ? dispatch_batch<128>(b, ws, b->n_inst, rp, S, cs)
+                             : dispatch_batch<256>(b, ws, b->n_inst, rp, S, cs);
+        }
+    }
+    if (own) {
+        const cudaError_t f = cudaFreeAsync(base, cs);
+        if (e == cudaSuccess) e = f;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batched transport");
+    return MT_OK;
+}
+
+mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t *n, float step_len, int32_t max_steps,
+                            uint64_t seed, int64_t sample_per_instance, mt_batch_cfg *best, void *stream)
+{
+    if (!b || !soas || !n || sample_per_instance < 1) {
+        set_error("null batch, muon arrays or counts, or sample_per_instance < 1");
+        return MT_ERR_INVALID_ARG;
+    }
+    DevGuardB guard(b->device);
+    cudaStream_t cs = (cudaStream_t)stream;
+    // scratch copies of the first min(n_i, sample) muons of every instance
+    std::vector<int64_t> m(b->n_inst);
+    int64_t M = 0;
+    for (int i = 0; i < b->n_inst; ++i) {
+        if (n[i] < 0) {
+            set_error("instance %d: n < 0", i);
+            return MT_ERR_INVALID_ARG;
+        }
+        m[i] = std::min<int64_t>(n[i], sample_per_instance);
+        M += m[i];
+    }
+    if (M == 0) {
+        if (best) *best = mt_batch_cfg{256, 64, 0, 0, nullptr, 0};
+        return MT_OK;
+    }
+    const size_t per = 4 * 6 + 1 + 4 + 1;   // bytes per muon over the nine arrays
+    char *init = nullptr, *work = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&init), (size_t)M * per + 9 * 256, cs);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&work), (size_t)M * per + 9 * 256, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune scratch");
+    auto carve = [&](char *base, std::vector<mt_muon_soa> &out) {
+        const size_t sizes[9] = {4, 4, 4, 4, 4, 4, 1, 4, 1};
+        char *q = base;
+        void *arr[9];
+        for (int a = 0; a < 9; ++a) {
+            arr[a] = q;
+            q += ((size_t)M * sizes[a] + 255) & ~(size_t)255;
+        }
+        out.resize(b->n_inst);
+        int64_t o = 0;
+        for (int i = 0; i < b->n_inst; ++i) {
+            mt_muon_soa s = soas[i];
+            s.x = (float *)arr[0] + o;
+            s.y = (float *)arr[1] + o;
+            s.z = (float *)arr[2] + o;
+            s.px = (float *)arr[3] + o;
+            s.py = (float *)arr[4] + o;
+            s.pz = (float *)arr[5] + o;
+            s.q = (int8_t *)arr[6] + o;
+            s.steps = (int32_t *)arr[7] + o;
+            s.status = (uint8_t *)arr[8] + o;
+            out[i] = s;
+            o += m[i];
+        }
+    };
+    std::vector<mt_muon_soa> si, sw;
+    carve(init, si);
+    carve(work, sw);
+    for (int i = 0; i < b->n_inst && e == cudaSuccess; ++i) {
+        if (!m[i]) continue;
+        const size_t sz4 = (size_t)m[i] * 4, sz1 = (size_t)m[i];
+        const void *src[9] = {soas[i].x, soas[i].y, soas[i].z, soas[i].px, soas[i].py, soas[i].pz, soas[i].q,
+                              soas[i].steps, soas[i].status};
+        void *dst[9] = {si[i].x, si[i].y, si[i].z, si[i].px, si[i].py, si[i].pz, si[i].q, si[i].steps, si[i].status};
+        const size_t sz[9] = {sz4, sz4, sz4, sz4, sz4, sz4, sz1, sz4, sz1};
+        for (int a = 0; a < 9 && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(dst[a], src[a], sz[a], cudaMemcpyDeviceToDevice, cs);
+    }
+    const int blocks[2] = {128, 256};
+    const int Ss[3] = {32, 64, 128};
+    float best_ms = 1e30f;
+    mt_batch_cfg bc = {256, 64, 0, 0, nullptr, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    mt_status st = MT_OK;
+    for (int bi = 0; bi < 2 && e == cudaSuccess && st == MT_OK; ++bi)
+        for (int si_ = 0; si_ < 3 && e == cudaSuccess && st == MT_OK; ++si_) {
+            mt_batch_cfg c = {blocks[bi], Ss[si_], 0, 0, nullptr, 0};
+            for (int rep = 0; rep < 2 && e == cudaSuccess && st == MT_OK; ++rep) {   // warm-up, then timed
+                e = cudaMemcpyAsync(work, init, (size_t)M * per + 9 * 256, cudaMemcpyDeviceToDevice, cs);
+                if (e != cudaSuccess) break;
+                e = cudaEventRecord(e0, cs);
+                if (e == cudaSuccess) st = mt_transport_batched(b, sw.data(), m.data(), step_len, max_steps, seed, &c, cs);
+                if (e == cudaSuccess && st == MT_OK) e = cudaEventRecord(e1, cs);
+                if (e == cudaSuccess && st == MT_OK) e = cudaEventSynchronize(e1);
+            }
+            float ms = 0.0f;
+            if (e == cudaSuccess && st == MT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                bc = c;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(init, cs);
+    cudaFreeAsync(work, cs);
+    if (st != MT_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    b->tuned_block = bc.block;
+    b->tuned_S = bc.steps_per_pass;
+    if (best) *best = bc;
+    return MT_OK;
+}
+
+}  // extern "C"

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/mt.h"
@@ -91,22 +92,28 @@ struct RunParams {
 
 }  // namespace mt
 
+namespace mt {
+// Device allocations owned by a handle or a batch.
+struct DevOwner {
+    std::vector<void *> bufs;
+    int64_t bytes = 0;
+    void release();
+};
+}  // namespace mt
+
 struct mt_handle {
     int device;
     mt::WorldParams w;
-    // owned device allocations
-    void *d_boxes = nullptr;
-    void *d_hist = nullptr;
-    void *d_guide = nullptr;
-    void *d_pairs = nullptr;
-    void *d_e2 = nullptr;
-    void *d_fmap = nullptr;
-    void *d_vox = nullptr;
-    void *d_zmask = nullptr;
-    int64_t bytes = 0;
+    mt::DevOwner own;
 };
 
 namespace mt {
 void set_error(const char *fmt, ...);
 mt_status cuda_fail(cudaError_t e, const char *what);
+mt_status validate_hist(const mt_hist_desc *h);
+mt_status validate_geometry(const mt_geometry_desc *g, int n_mat);
+mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g);
+mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own);
+mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &own);
+mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own);
 }  // namespace mt

@@ -79,3 +79,24 @@ def test_declared_symbols_parser_sees_comments_removed():
     names = mt.declared_symbols()
     assert all(n.startswith("mt_") for n in names)
     assert "mt_status" not in names and "mt_box" not in names
+
+
+def test_batch_host_errors(lib):
+    """The batch entry points reject bad arguments on the host, before any device work."""
+    _, _, h = _descs()
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_batch_create(h, 0)
+    assert e.value.status == B.MT_ERR_INVALID_ARG
+    w = h["weights"].copy()
+    w[0, 1, 2, 3] = -1.0
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_batch_create(dict(h, weights=w), 4)
+    assert e.value.status == B.MT_ERR_TABLE
+    assert lib.mt_batch_workspace_bytes(None, None) == -1
+    assert lib.mt_batch_device_bytes(None) == 0
+    lib.mt_batch_destroy(None)
+    n = (C.c_int64 * 1)(5)
+    st = lib.mt_transport_batched(None, None, n, 0.02, 10, 1, None, None)
+    assert st == B.MT_ERR_INVALID_ARG and "null batch" in mt.mt_last_error()
+    st = lib.mt_batch_autotune(None, None, n, 0.02, 10, 1, 0, None, None)
+    assert st == B.MT_ERR_INVALID_ARG

@@ -1,0 +1,172 @@
+"""GPU checks of the batched form (mt_transport_batched): many worlds with their
+own voxel geometry and field map, sharing one histogram set, transported in one
+launch sequence.  Each instance must give exactly what a separate mt_transport
+call in its own world gives (same muon ids and Philox instance word), and agree
+with the FP64 oracle per muon."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import compare, describe
+from workloads import gen
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("x", "y", "z", "px", "py", "pz", "steps", "status")
+# instance sizes: empty instances, a single muon, ragged sizes around the block sizes
+SIZES = [0, 1, 37, 128, 129, 0, 1000, 2500, 255, 4096, 3, 777]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_10520_gb300 as mt
+    mt.load_library()
+
+
+@pytest.fixture(scope="module")
+def hist():
+    return gen.batched_hist(hist_samples=200_000)
+
+
+@pytest.fixture(scope="module")
+def instances():
+    return [gen.batched_instance(i, n=n) for i, n in enumerate(SIZES)]
+
+
+@pytest.fixture(scope="module")
+def batch(hist, instances):
+    import paper_2512_10520_gb300 as mt
+    b = mt.Batch(hist, len(instances))
+    for i, inst in enumerate(instances):
+        b.set_instance(i, inst["geometry"], inst["field"])
+    yield b
+    b.close()
+
+
+def _dev(instances, id_offsets=None):
+    import paper_2512_10520_gb300 as mt
+    return [mt.muons_to_device(inst["muons"]) for inst in instances]
+
+
+def _host(devs):
+    import torch
+    import paper_2512_10520_gb300 as mt
+    torch.cuda.synchronize()
+    return [mt.muons_to_host(d) for d in devs]
+
+
+def _separate(hist, instances, id_offsets, instances_word):
+    """Each instance through mt_transport in its own World."""
+    import paper_2512_10520_gb300 as mt
+    out = []
+    for i, inst in enumerate(instances):
+        with mt.World(inst["geometry"], inst["field"], hist) as w:
+            d = mt.muons_to_device(inst["muons"])
+            if inst["n"]:
+                w.transport(d, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED,
+                            id_offset=id_offsets[i], instance=instances_word[i])
+            out.append(_host([d])[0])
+    return out
+
+
+def _assert_same(a, b):
+    for i, (x, y) in enumerate(zip(a, b)):
+        for k in FIELDS:
+            np.testing.assert_array_equal(x[k], y[k], err_msg=f"instance {i} field {k}")
+
+
+@pytest.mark.parametrize("block,S", [(256, 64), (128, 32), (256, 7)])
+def test_batched_equals_separate_transports(hist, instances, batch, block, S):
+    ids = [1000 * i for i in range(len(instances))]
+    words = [i + 3 for i in range(len(instances))]
+    ref = _separate(hist, instances, ids, words)
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=block,
+                    steps_per_pass=S, id_offsets=ids, instances=words)
+    _assert_same(_host(devs), ref)
+
+
+def test_batched_matches_fp64_oracle(hist, instances, batch):
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
+    got = _host(devs)
+    oks = []
+    for i, inst in enumerate(instances):
+        if not inst["n"]:
+            continue
+        w = oracle.OracleWorld(inst["geometry"], inst["field"], hist)
+        ora = oracle.transport(w, inst["muons"], gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED,
+                               id_offset=0, instance=i)
+        ok, err = compare(got[i], ora)
+        oks.append(ok)
+        assert ok.mean() >= 0.995 or (~ok).sum() <= 2, (i, describe(ok, err))
+    allok = np.concatenate(oks)
+    assert allok.mean() >= 0.998, allok.mean()
+
+
+def test_graph_replay_equals_plain_launches(instances, batch):
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
+    ref = _host(devs)
+    for _ in range(2):   # capture, then replay of the cached graph
+        devs = _dev(instances)
+        batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, use_graph=True)
+        _assert_same(_host(devs), ref)
+
+
+def test_explicit_workspace_and_errors(instances, batch):
+    import torch
+    import paper_2512_10520_gb300 as mt
+    counts = [inst["n"] for inst in instances]
+    need = batch.workspace_bytes(counts)
+    assert need > 0
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
+    ref = _host(devs)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, workspace=ws)
+    _assert_same(_host(devs), ref)
+    small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(mt.MtError):
+        batch.transport(_dev(instances), gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, workspace=small)
+    with pytest.raises(mt.MtError):
+        batch.transport(_dev(instances), gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=64)
+
+
+def test_unset_instance_and_mixed_kinds_are_rejected(hist, instances):
+    import paper_2512_10520_gb300 as mt
+    with mt.Batch(hist, 2) as b:
+        b.set_instance(0, instances[1]["geometry"], instances[1]["field"])
+        with pytest.raises(mt.MtError) as e:
+            b.transport(_dev(instances[:2]), gen.BATCH_STEP_LEN, 10, 1)
+        assert "no world" in str(e.value)
+        boxes = gen.geometry_config1()
+        with pytest.raises(mt.MtError):
+            b.set_instance(1, boxes, instances[1]["field"])
+
+
+def test_autotune_leaves_muons_and_results_unchanged(instances, batch):
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=256, steps_per_pass=64)
+    ref = _host(devs)
+    devs = _dev(instances)
+    before = _host(devs)
+    blk, S = batch.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, sample_per_instance=300)
+    assert blk in (128, 256) and S in (32, 64, 128)
+    _assert_same(_host(devs), before)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)   # tuned shape
+    _assert_same(_host(devs), ref)
+
+
+def test_all_instances_empty(hist, instances):
+    import paper_2512_10520_gb300 as mt
+    with mt.Batch(hist, 2) as b:
+        for i in range(2):
+            b.set_instance(i, instances[0]["geometry"], instances[0]["field"])
+        devs = _dev([instances[0], instances[5]])
+        b.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
+        assert all(d["x"].numel() == 0 for d in devs)

@@ -17,4 +17,11 @@ from .gen import (  # noqa: F401
     field_map_config1,
     workload,
     batched_instances,
+    batched_instance,
+    batched_counts,
+    magnet_field_map,
+    batched_hist,
+    BATCH_STEP_LEN,
+    BATCH_MAX_STEPS,
+    BATCH_SEED,
 )

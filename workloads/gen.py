@@ -198,37 +198,47 @@ def _smooth_box_edge(u: np.ndarray, a: float, b: float, w: float) -> np.ndarray:
     return 0.5 * (np.tanh((u - b) / w) ** 2 - np.tanh((u - a) / w) ** 2)
 
 
-def field_map_config1(nx: int = 200, ny: int = 200, nz: int = 600, z_lo: float = -0.5,
-                      z_hi: float = 27.5, half_xy: float = 3.0, magnet_z0=None,
-                      magnet_B=None, edge_w: float = 0.03) -> dict:
+def magnet_field_map(nx: int, ny: int, nz: int, half_xy: float, z_lo: float, z_hi: float, magnet_z0,
+                     magnet_B, magnet_len: float = MAGNET_LEN, edge_w: float = 0.03) -> dict:
     """Node-based synthetic magnet field, float32 [nz][ny][nx][3].
 
-    Nodes sit at origin + (i,j,k)*spacing over x,y in [-3,3] m and z in [z_lo, z_hi]
-    (the map extends 0.5 m past the magnets at both ends, so the field is ~0 at the
-    map boundary).  Inside each block B_y ~ +-1.7 T with tanh edges of width 3 cm, plus
-    a small quadrupole-like B_x and a fringe B_z at the block ends.
+    Nodes sit at origin + (i,j,k)*spacing over x,y in [-half_xy, half_xy] and z in
+    [z_lo, z_hi].  Inside each block B_y ~ magnet_B[k] with tanh edges of width 3 cm,
+    plus a small quadrupole-like B_x and a fringe B_z at the block ends.  Every
+    component is a sum over blocks of (z profile) x (x-y profile), built as outer
+    products.
     """
-    magnet_z0 = MAGNET_Z0 if magnet_z0 is None else magnet_z0
-    if magnet_B is None:
-        magnet_B = [1.7 if k % 2 == 0 else -1.7 for k in range(len(magnet_z0))]
     x = np.linspace(-half_xy, half_xy, nx)
     y = np.linspace(-half_xy, half_xy, ny)
     z = np.linspace(z_lo, z_hi, nz)
     Sx = _smooth_box(x, -MAGNET_HALF, MAGNET_HALF, edge_w)
     Sy = _smooth_box(y, -MAGNET_HALF, MAGNET_HALF, edge_w)
-    B = np.zeros((nz, ny, nx, 3), dtype=np.float32)
-    SxSy = (Sy[:, None] * Sx[None, :]).astype(np.float32)
-    quad = ((y[:, None] * x[None, :]) / (MAGNET_HALF * MAGNET_HALF) * SxSy).astype(np.float32)
-    ylin = ((y[:, None] / MAGNET_HALF) * SxSy).astype(np.float32)
+    SxSy = Sy[:, None] * Sx[None, :]
+    quad = (y[:, None] * x[None, :]) / (MAGNET_HALF * MAGNET_HALF) * SxSy
+    ylin = (y[:, None] / MAGNET_HALF) * SxSy
+    zy = np.zeros(nz)
+    ze = np.zeros(nz)
     for z0, b in zip(magnet_z0, magnet_B):
-        Sz = _smooth_box(z, z0, z0 + MAGNET_LEN, edge_w).astype(np.float32)
-        Ez = _smooth_box_edge(z, z0, z0 + MAGNET_LEN, edge_w).astype(np.float32)
-        B[..., 1] += np.float32(b) * Sz[:, None, None] * SxSy[None]
-        B[..., 0] += np.float32(0.1 * b) * Sz[:, None, None] * quad[None]
-        B[..., 2] += np.float32(0.3 * b) * Ez[:, None, None] * ylin[None]
+        zy += b * _smooth_box(z, z0, z0 + magnet_len, edge_w)
+        ze += b * _smooth_box_edge(z, z0, z0 + magnet_len, edge_w)
+    B = np.empty((nz, ny, nx, 3), dtype=np.float32)
+    B[..., 0] = (0.1 * zy)[:, None, None] * quad[None]
+    B[..., 1] = zy[:, None, None] * SxSy[None]
+    B[..., 2] = (0.3 * ze)[:, None, None] * ylin[None]
     spacing = [(2 * half_xy) / (nx - 1), (2 * half_xy) / (ny - 1), (z_hi - z_lo) / (nz - 1)]
-    return dict(kind="map", dims=[nx, ny, nz], origin=[-half_xy, -half_xy, z_lo],
-                spacing=spacing, B=B)
+    return dict(kind="map", dims=[nx, ny, nz], origin=[-half_xy, -half_xy, z_lo], spacing=spacing, B=B)
+
+
+def field_map_config1(nx: int = 200, ny: int = 200, nz: int = 600, z_lo: float = -0.5,
+                      z_hi: float = 27.5, half_xy: float = 3.0, magnet_z0=None,
+                      magnet_B=None, edge_w: float = 0.03) -> dict:
+    """Field map of the six-magnet shield: 200x200x600 nodes over x,y in [-3,3] m and
+    z in [-0.5, 27.5] m (0.5 m past the magnets at both ends, so the field is ~0 at
+    the map boundary), B_y = +-1.7 T alternating."""
+    magnet_z0 = MAGNET_Z0 if magnet_z0 is None else magnet_z0
+    if magnet_B is None:
+        magnet_B = [1.7 if k % 2 == 0 else -1.7 for k in range(len(magnet_z0))]
+    return magnet_field_map(nx, ny, nz, half_xy, z_lo, z_hi, magnet_z0, magnet_B, edge_w=edge_w)
 
 
 # --------------------------------------------------------------------------
@@ -338,5 +348,66 @@ def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = N
     raise KeyError(name)
 
 
-def batched_instances(*args, **kwargs):  # pragma: no cover - filled in with the batched form
-    raise NotImplementedError("batched instance generator not built yet")
+def batched_instance(i: int, seed: int = 2024, vox_dims=(64, 64, 512), map_dims=(100, 100, 300),
+                     half_xy: float = 1.6, n_range=(1000, 1_000_000), n: Optional[int] = None) -> dict:
+    """Instance i of the batched workload: six iron blocks 1.2x1.2x4 m with field
+    magnitudes U(1.0, 1.9) T (alternating sign) and five gaps U(0.1, 1.0) m, 0.5 m of
+    air and a 2 m concrete wall, voxelised to uint8 [nz][ny][nx] over x,y in
+    [-1.6, 1.6] m and z in [0, L]; its own node field map over the same x,y and
+    z in [-0.5, L]; n muons (log-uniform in n_range) of the p^-2.7 spectrum.
+    Materials: 1 iron, 2 air (world), 3 concrete.  World |x|,|y| < 1.6 m, z < L."""
+    rng = np.random.default_rng([seed, i])
+    Bmag = rng.uniform(1.0, 1.9, 6) * np.array([1.0 if k % 2 == 0 else -1.0 for k in range(6)])
+    gaps = rng.uniform(0.1, 1.0, 5)
+    z0 = [0.0]
+    for g in gaps:
+        z0.append(z0[-1] + MAGNET_LEN + g)
+    end = z0[-1] + MAGNET_LEN
+    wall = (end + 0.5, end + 2.5)
+    L = wall[1]
+    nxv, nyv, nzv = vox_dims
+    sx, sy, sz = 2 * half_xy / nxv, 2 * half_xy / nyv, L / nzv
+    xc = -half_xy + (np.arange(nxv) + 0.5) * sx
+    yc = -half_xy + (np.arange(nyv) + 0.5) * sy
+    zc = (np.arange(nzv) + 0.5) * sz
+    in_xy = (np.abs(yc)[:, None] < MAGNET_HALF) & (np.abs(xc)[None, :] < MAGNET_HALF)
+    in_block = np.zeros(nzv, bool)
+    for a in z0:
+        in_block |= (zc >= a) & (zc < a + MAGNET_LEN)
+    vox = np.full((nzv, nyv, nxv), 2, np.uint8)
+    vox[in_block[:, None, None] & in_xy[None]] = 1
+    vox[(zc >= wall[0]) & (zc < wall[1])] = 3
+    geo = dict(kind="voxels", voxels=vox, origin=[-half_xy, -half_xy, 0.0], spacing=[sx, sy, sz],
+               world_material=2, x_max=half_xy, y_max=half_xy, z_max=L, p_min=0.5)
+    fld = magnet_field_map(map_dims[0], map_dims[1], map_dims[2], half_xy, -0.5, L, z0, list(Bmag))
+    if n is None:
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+    mu = muons_config1(n, seed=seed * 7919 + i)
+    return dict(geometry=geo, field=fld, muons=mu, n=n, length=L, B=Bmag, gaps=gaps)
+
+
+def batched_counts(n_inst: int = 256, seed: int = 2024, n_range=(1000, 1_000_000)):
+    """Muon counts of the batched workload's instances (same draws as batched_instance)."""
+    out = []
+    for i in range(n_inst):
+        rng = np.random.default_rng([seed, i])
+        rng.uniform(1.0, 1.9, 6)
+        rng.uniform(0.1, 1.0, 5)
+        out.append(int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]))))))
+    return out
+
+
+def batched_instances(n_inst: int = 256, seed: int = 2024, **kw):
+    """Generator over the instances of the batched workload (one in host memory at a time)."""
+    for i in range(n_inst):
+        yield batched_instance(i, seed=seed, **kw)
+
+
+BATCH_STEP_LEN = 0.02
+BATCH_MAX_STEPS = 2000
+BATCH_SEED = 11
+
+
+def batched_hist(hist_samples: Optional[int] = None) -> dict:
+    """Histogram set of the batched workload (iron, air, concrete, as config1)."""
+    return histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
