@@ -108,9 +108,9 @@ struct TapeEntry {
 
 __device__ __forceinline__ void cross3(const float a[3], const float b[3], float o[3])
 {
-    o[0] = a[1] * b[2] - a[2] * b[1];
-    o[1] = a[2] * b[0] - a[0] * b[2];
-    o[2] = a[0] * b[1] - a[1] * b[0];
+    o[0] = fmaf(a[1], b[2], -(a[2] * b[1]));
+    o[1] = fmaf(a[2], b[0], -(a[0] * b[2]));
+    o[2] = fmaf(a[0], b[1], -(a[1] * b[0]));
 }
 
 __device__ __forceinline__ float dot3(const float a[3], const float b[3])
@@ -145,9 +145,9 @@ __device__ __forceinline__ void field_map_jt(const WorldParams &w, const float r
     // v: (i,j,k) (i+1,j,k) (i,j+1,k) (i+1,j+1,k) (i,j,k+1) (i+1,j,k+1) (i,j+1,k+1) (i+1,j+1,k+1)
     const float a = lerp(tx, v[0], v[1]), b = lerp(tx, v[2], v[3]);
     const float cc = lerp(tx, v[4], v[5]), d = lerp(tx, v[6], v[7]);
-    rb[0] += lerp(tz, lerp(ty, v[1] - v[0], v[3] - v[2]), lerp(ty, v[5] - v[4], v[7] - v[6])) * w.finv[0];
-    rb[1] += lerp(tz, b - a, d - cc) * w.finv[1];
-    rb[2] += (lerp(ty, cc, d) - lerp(ty, a, b)) * w.finv[2];
+    rb[0] = fmaf(lerp(tz, lerp(ty, v[1] - v[0], v[3] - v[2]), lerp(ty, v[5] - v[4], v[7] - v[6])), w.finv[0], rb[0]);
+    rb[1] = fmaf(lerp(tz, b - a, d - cc), w.finv[1], rb[1]);
+    rb[2] = fmaf(lerp(ty, cc, d) - lerp(ty, a, b), w.finv[2], rb[2]);
 }
 
 // The forward's scattering update in plain FP32 on a recorded momentum.
@@ -171,8 +171,8 @@ __device__ __forceinline__ void scatter_fp32(const float p[3], float f, float th
     } else {
         const float g = uz >= 0.0f ? 1.0f / (1.0f + uz) : (1.0f - uz) / s2;
         const float wv = fmaf(cphi, ux, sphi * uy);
-        tx = cphi - ux * wv * g;
-        ty = sphi - uy * wv * g;
+        tx = fmaf(-(ux * wv), g, cphi);
+        ty = fmaf(-(uy * wv), g, sphi);
         tz = -wv;
     }
     ps[0] = fmaf(sm1, p[0], fmaf(kick, tx, p[0]));
@@ -261,7 +261,8 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     cross3(v2, h, v3);
     float rsum[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rsum[c] = ps[c] + 0.5f * v1[c] + (1.0f / 6.0f) * v2[c] + (1.0f / 24.0f) * v3[c];
+    for (int c = 0; c < 3; ++c)
+        rsum[c] = fmaf(1.0f / 24.0f, v3[c], fmaf(1.0f / 6.0f, v2[c], fmaf(0.5f, v1[c], ps[c])));
     const float abar = dot3(rb, rsum);
     float vb[3], hb[3] = {0.0f, 0.0f, 0.0f}, tmp[3];
     // v4 = v3 x h: v3b += h x v4b, hb += v4b x v3, with v4b = pb / 24
@@ -273,31 +274,31 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     cross3(h, vb, tmp);
     // v3b = pb/6 + a rb/24 + h x v4b;  v3 = v2 x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vb[c] = (1.0f / 6.0f) * pb[c] + (a / 24.0f) * rb[c] + tmp[c];
+    for (int c = 0; c < 3; ++c) vb[c] = fmaf(1.0f / 6.0f, pb[c], fmaf(a / 24.0f, rb[c], tmp[c]));
     cross3(vb, v2, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
     cross3(h, vb, tmp);
     // v2b = pb/2 + a rb/6 + h x v3b;  v2 = v1 x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vb[c] = 0.5f * pb[c] + (a / 6.0f) * rb[c] + tmp[c];
+    for (int c = 0; c < 3; ++c) vb[c] = fmaf(0.5f, pb[c], fmaf(a / 6.0f, rb[c], tmp[c]));
     cross3(vb, v1, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
     cross3(h, vb, tmp);
     // v1b = pb + a rb/2 + h x v2b;  v1 = ps x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vb[c] = pb[c] + 0.5f * a * rb[c] + tmp[c];
+    for (int c = 0; c < 3; ++c) vb[c] = fmaf(0.5f * a, rb[c], pb[c] + tmp[c]);
     cross3(vb, ps, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
     cross3(h, vb, tmp);
     float psb[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) psb[c] = pb[c] + a * rb[c] + tmp[c];
+    for (int c = 0; c < 3; ++c) psb[c] = fmaf(a, rb[c], pb[c] + tmp[c]);
     // h = cc B with cc = kappa q d / P0, a = d / P0, P0 = |ps|
     const float ccb = dot3(hb, B);
-    const float P0b = -(ccb * cc + abar * a) * rP0;
+    const float P0b = -fmaf(ccb, cc, abar * a) * rP0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) psb[c] = fmaf(P0b * rP0, ps[c], psb[c]);
     // -- field: B = sc (.) Bm(r)
@@ -332,13 +333,13 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     } else {
         const float g = u[2] >= 0.0f ? 1.0f / (1.0f + u[2]) : (1.0f - u[2]) / s2;
         const float wv = fmaf(cphi, u[0], sphi * u[1]);
-        tv[0] = cphi - u[0] * wv * g;
-        tv[1] = sphi - u[1] * wv * g;
+        tv[0] = fmaf(-(u[0] * wv), g, cphi);
+        tv[1] = fmaf(-(u[1] * wv), g, sphi);
         tv[2] = -wv;
         const float kick = P * kf;
         const float tb[3] = {kick * psb[0], kick * psb[1], kick * psb[2]};
-        const float sx = tb[0] * u[0] + tb[1] * u[1];
-        const float wb = -sx * g - tb[2];
+        const float sx = fmaf(tb[0], u[0], tb[1] * u[1]);
+        const float wb = fmaf(-sx, g, -tb[2]);
         const float gb = -sx * wv;
         ub[0] = fmaf(wb, cphi, -tb[0] * wv * g);
         ub[1] = fmaf(wb, sphi, -tb[1] * wv * g);
@@ -347,7 +348,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     const float Pb = kf * dot3(tv, psb);
     const float uu = dot3(u, ub);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) pb[c] = fmaf(1.0f + sm1, psb[c], fmaf(Pb, u[c], (ub[c] - u[c] * uu) * rPs));
+    for (int c = 0; c < 3; ++c) pb[c] = fmaf(1.0f + sm1, psb[c], fmaf(Pb, u[c], fmaf(-u[c], uu, ub[c]) * rPs));
 }
 
 template <int GEOM, int FIELD>

@@ -19,7 +19,7 @@
 #include <cstring>
 #include <vector>
 
-#include "step.cuh"
+#include "compact.cuh"
 
 struct mt_batch {
     int device = 0;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, u
 }
 
 template <int GEOM, int FIELD, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
+__global__ void __launch_bounds__(BLOCK, MT_PASS_MIN_BLOCKS * 256 / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
                                                    const unsigned long long *off, int n_inst, RunParams rp,
                                                    LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
                                                    unsigned int *cnt_out, const unsigned int *cof,

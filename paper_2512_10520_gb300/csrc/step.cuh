@@ -140,7 +140,7 @@ __device__ __forceinline__ int voxel_material(const WorldParams &w, const State 
             const int ic = __float2int_rn(u);
             const float fic = (float)ic;
             const float fh = fic * w.vspacing[a];
-            const float fl = fmaf(fic, w.vspacing[a], -fh) + fic * w.vspacing_lo[a];
+            const float fl = fmaf(fic, w.vspacing_lo[a], fmaf(fic, w.vspacing[a], -fh));
             i = ((dh - fh) + (dl - fl)) >= 0.0f ? ic : ic - 1;
         }
         if (i < 0 || i >= w.vdims[a]) return -1;
@@ -152,7 +152,7 @@ __device__ __forceinline__ int voxel_material(const WorldParams &w, const State 
 // |p|^2 of the hi + lo momentum to first order in lo.
 __device__ __forceinline__ float p2_of(const State &s)
 {
-    float P2 = s.px * s.px + s.py * s.py + s.pz * s.pz;
+    const float P2 = fmaf(s.px, s.px, fmaf(s.py, s.py, s.pz * s.pz));
     return fmaf(2.0f * s.px, s.pxl, fmaf(2.0f * s.py, s.pyl, fmaf(2.0f * s.pz, s.pzl, P2)));
 }
 
@@ -160,7 +160,7 @@ __device__ __forceinline__ float p2_of(const State &s)
 __device__ __forceinline__ void sq2(float h, float l, float &sh, float &sl)
 {
     sh = h * h;
-    sl = fmaf(h, h, -sh) + 2.0f * h * l;
+    sl = fmaf(2.0f * h, l, fmaf(h, h, -sh));
 }
 
 
@@ -168,7 +168,7 @@ __device__ __forceinline__ void sq2(float h, float l, float &sh, float &sl)
 // squared edges held as hi + lo pairs whenever |p|^2 lies within 4e-6 of one.
 __device__ __forceinline__ int momentum_bin(const WorldParams &w, const SmemWorld &sw, const State &s, float P2)
 {
-    int i = __float2int_rd((0.5f * __log2f(P2) - w.log2_plo) * w.pbin_scale);
+    int i = __float2int_rd(fmaf(0.5f, __log2f(P2), -w.log2_plo) * w.pbin_scale);
     i = min(max(i, 0), w.n_pbin - 1);
     const float elo = sw.e2[i].x, ehi = sw.e2[i + 1].x;
     const bool near_lo = i > 0 && P2 < elo * 1.000004f;
@@ -256,8 +256,8 @@ __device__ __forceinline__ void scatter(State &s, float f, float theta, float cp
     } else {
         const float g = uz >= 0.0f ? 1.0f / (1.0f + uz) : (1.0f - uz) / s2;   // 1/(1+uz)
         const float wv = fmaf(cphi, ux, sphi * uy);
-        tx = cphi - ux * wv * g;
-        ty = sphi - uy * wv * g;
+        tx = fmaf(-(ux * wv), g, cphi);
+        ty = fmaf(-(uy * wv), g, sphi);
         tz = -wv;
     }
     acc(s.px, s.pxl, fmaf(sm1, s.px, kick * tx));
@@ -284,7 +284,7 @@ __device__ __forceinline__ bool map_axis(float xh, float xl, float oh, float ol,
     i = min((int)u, n - 2);
     const float fi = (float)i;
     const float ph = fi * sh;
-    const float pl = fmaf(fi, sh, -ph) + fi * sl;
+    const float pl = fmaf(fi, sl, fmaf(fi, sh, -ph));
     t = ((dh - ph) + (dl - pl)) * inv;
     return true;
 }
@@ -321,9 +321,9 @@ __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s
 __device__ __forceinline__ void cross_h(float ax, float ay, float az, float hx, float hy, float hz, float &ox,
                                         float &oy, float &oz)
 {
-    ox = ay * hz - az * hy;
-    oy = az * hx - ax * hz;
-    oz = ax * hy - ay * hx;
+    ox = fmaf(ay, hz, -(az * hy));
+    oy = fmaf(az, hx, -(ax * hz));
+    oz = fmaf(ax, hy, -(ay * hx));
 }
 
 // RK4 over path length d with B fixed: dr/ds = p/P0, dp/ds = kappa q (p x B)/P0.
@@ -377,7 +377,7 @@ template <int GEOM, int FIELD, class Rec = NoRecord>
 __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, State &s, float q, int k,
                                     uint32_t id_lo, uint32_t id_hi, const RunParams &rp, Rec &&rec = Rec())
 {
-    const float P2 = s.px * s.px + s.py * s.py + s.pz * s.pz;
+    const float P2 = fmaf(s.px, s.px, fmaf(s.py, s.py, s.pz * s.pz));
     const int stop = check_stop(w, s, P2);
     if (stop != MT_ALIVE) return stop;
     int box = -1, mat;
