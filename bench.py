@@ -159,7 +159,7 @@ def cpu_oracle_run(wl, n_sample: int, threads: int):
     return float(out["steps"].sum()), dt
 
 
-def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32):
+def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32, tape=True):
     """fwd+adjoint form (config3: config1 geometry, 18 field scales, checkpoints every K
     steps): checkpointing forward + acceptance loss + adjoint, each timed with CUDA events."""
     import torch
@@ -189,10 +189,40 @@ def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32
                 times.append([ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3)])
     t = np.mean(np.array(times), axis=0)
     steps = float(work["steps"].sum().item())
+    da_ck = da.clone()
     del ckpt
-    return dict(t_forward_ckpt_ms=1e3 * t[0], t_loss_ms=1e3 * t[1], t_adjoint_ms=1e3 * t[2], muon_steps=steps,
-                loss=float(loss.item()), ckpt_every=K, dL_dalpha_norm=float(da.norm().item()),
-                passes=int((wl.max_steps + K - 1) // K))
+    out = dict(t_forward_ckpt_ms=1e3 * t[0], t_loss_ms=1e3 * t[1], t_adjoint_ms=1e3 * t[2], muon_steps=steps,
+               loss=float(loss.item()), ckpt_every=K, dL_dalpha_norm=float(da.norm().item()),
+               passes=int((wl.max_steps + K - 1) // K))
+    # full-tape variant: the forward records every step, the backward does not recompute
+    free, _ = torch.cuda.mem_get_info(init["x"].device)
+    tb = mt.mt_tape_bytes(n, wl.max_steps, K)
+    if tape and tb <= free - (8 << 30):
+        buf = torch.empty(tb, dtype=torch.uint8, device=init["x"].device)
+        times = []
+        with torch.cuda.stream(stream):
+            for r in range(reps + 1):
+                for k in work:
+                    work[k].copy_(init[k], non_blocking=True)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev[0].record(stream)
+                mt.mt_transport_tape(world.handle, work, wl.step_len, wl.max_steps, wl.seed, alpha, K, buf,
+                                     id_offset=id_offset, stream=stream)
+                ev[1].record(stream)
+                mt.mt_acceptance_loss(work, loss, g, stream=stream)
+                ev[2].record(stream)
+                mt.mt_adjoint_tape(world.handle, n, wl.step_len, wl.max_steps, alpha, K, buf, g, da, stream=stream)
+                ev[3].record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    times.append([ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3)])
+        t = np.mean(np.array(times), axis=0)
+        out["tape"] = dict(t_forward_tape_ms=1e3 * t[0], t_loss_ms=1e3 * t[1], t_adjoint_ms=1e3 * t[2],
+                           tape_bytes=tb, tape_bytes_used=int(56 * steps),
+                           dL_dalpha_rel_diff_vs_ckpt=float((da - da_ck).norm().item() / max(da_ck.norm().item(),
+                                                                                              1e-30)))
+        del buf
+    return out
 
 
 def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True):
@@ -263,6 +293,120 @@ def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True
     return out
 
 
+def time_c4_form(mt, dev, n_total=None, chunk=None, rank=0, cpu_sample=2000):
+    """Throughput at scale (config4): 1e8 muons of config1's spectrum in 16M-muon chunks
+    through the config1 geometry with a 400x400x1200 map and 4 materials x 128 bins x
+    256x128 tables.  Three timings, CUDA events:
+      plain     -- all chunks resident in HBM, one mt_transport call per chunk, one stream;
+      batched   -- the same muons as one instance of a batch: one mt_transport_batched call
+                   (persistent work-queue kernel, CUDA graph);
+      streamed  -- pinned host chunks, double-buffered on two streams: H2D copy,
+                   mt_transport and D2H copy of chunk c overlap those of chunk c +- 1.
+    The FP64 oracle is timed on the first cpu_sample muons on the host cores."""
+    import torch
+    from paper_2512_10520_gb300.api import empty_like_soa
+    from workloads import gen
+    n_total = n_total or gen.C4_MUONS
+    chunk = min(chunk or gen.C4_CHUNK, n_total)
+    wl = gen.workload("config4", n=1)
+    bounds = list(range(0, n_total, chunk)) + [n_total]
+    spans = list(zip(bounds[:-1], bounds[1:]))
+    base_id = rank * n_total
+    host_in = empty_like_soa(n_total, device="cpu", pinned=True)
+    for c, (lo, hi) in enumerate(spans):
+        mu = gen.muons_config4_chunk(c, hi - lo)
+        for k in host_in:
+            host_in[k][lo:hi].copy_(torch.from_numpy(np.ascontiguousarray(mu[k], dtype=mt._binding.SOA_DTYPES[k])))
+    host_out = empty_like_soa(n_total, device="cpu", pinned=True)
+    init = {k: v.to(dev) for k, v in host_in.items()}
+    work = empty_like_soa(n_total, device=dev)
+    args = (wl.step_len, wl.max_steps, wl.seed)
+    st0 = torch.cuda.Stream(device=dev)
+    out = dict(muons=n_total, chunk=chunk, chunks=len(spans), max_steps=wl.max_steps)
+
+    def reset():
+        for k in work:
+            work[k].copy_(init[k], non_blocking=True)
+
+    with mt.World.from_workload(wl) as world, torch.cuda.stream(st0):
+        out["world_device_bytes"] = world.device_bytes
+        # warm-up on the first chunk
+        reset()
+        sub = {k: v[spans[0][0]:spans[0][1]] for k, v in work.items()}
+        world.transport(sub, *args, id_offset=base_id, stream=st0)
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st0)
+        for lo, hi in spans:
+            sub = {k: v[lo:hi] for k, v in work.items()}
+            world.transport(sub, *args, id_offset=base_id + lo, stream=st0)
+        e1.record(st0)
+        torch.cuda.synchronize()
+        t_plain = e0.elapsed_time(e1) / 1e3
+        steps = float(work["steps"].sum().item())
+        ref_steps = work["steps"].clone()
+        out.update(muon_steps=steps, plain_value=steps / t_plain, plain_ms=1e3 * t_plain,
+                   muons_per_s=n_total / t_plain)
+        # streamed: pinned host -> device -> host, two streams
+        streams = [st0, torch.cuda.Stream(device=dev)]
+        bufs = [empty_like_soa(chunk, device=dev) for _ in range(2)]
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(st0)
+        streams[1].wait_event(s0)
+        for c, (lo, hi) in enumerate(spans):
+            s = streams[c % 2]
+            b = {k: v[:hi - lo] for k, v in bufs[c % 2].items()}
+            with torch.cuda.stream(s):
+                for k in b:
+                    b[k].copy_(host_in[k][lo:hi], non_blocking=True)
+                world.transport(b, *args, id_offset=base_id + lo, stream=s)
+                for k in b:
+                    host_out[k][lo:hi].copy_(b[k], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(streams[1])
+        st0.wait_event(ev)
+        s1.record(st0)
+        torch.cuda.synchronize()
+        t_stream = s0.elapsed_time(s1) / 1e3
+        out.update(streamed_value=steps / t_stream, streamed_ms=1e3 * t_stream,
+                   streamed_h2d_bytes=sum(t.numel() * t.element_size() for t in host_in.values()),
+                   streamed_d2h_bytes=sum(t.numel() * t.element_size() for t in host_out.values()),
+                   streamed_equal_steps=bool(torch.equal(host_out["steps"], ref_steps.cpu())))
+        del bufs
+    # batched-persistent: one instance holding all n_total muons
+    b = mt.Batch(wl.hist, 1)
+    b.set_instance(0, wl.geometry, wl.field)
+    with torch.cuda.stream(st0):
+        reset()
+        b.transport([{k: v[:chunk] for k, v in work.items()}], *args, id_offsets=[base_id], instances=[0],
+                    use_graph=False, stream=st0)   # warm-up
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st0)
+        b.transport([work], *args, id_offsets=[base_id], instances=[0], use_graph=True, stream=st0)
+        e1.record(st0)
+        torch.cuda.synchronize()
+        t_b = e0.elapsed_time(e1) / 1e3
+        out.update(batched_value=steps / t_b, batched_ms=1e3 * t_b,
+                   batched_equal_steps=bool(torch.equal(work["steps"], ref_steps)))
+    b.close()
+    if cpu_sample and rank == 0:
+        import oracle
+        mu = {k: host_in[k][:cpu_sample].numpy() for k in host_in}
+        ow = oracle.world_of(wl)
+        t0 = time.perf_counter()
+        o = oracle.transport(ow, mu, *args, id_offset=base_id, n_threads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"value": float(o["steps"].sum()) / dt, "unit": UNIT, "cores": os.cpu_count(),
+                             "sample": f"first {cpu_sample} muons of config4"}
+    out["value"] = out["plain_value"]
+    out["unit"] = UNIT
+    return out
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -309,6 +453,12 @@ def run_mine(args):
     from paper_2512_10520_gb300.api import empty_like_soa
     from workloads import gen
 
+    if args.c4_only:
+        with ClockSampler(local) as clk:
+            res = time_c4_form(mt, dev, n_total=args.c4_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
+        if rank == 0:
+            print(json.dumps({"form": "c4", "clocks": clk.summary(), **res}))
+        return 0
     if args.batch_only:
         with ClockSampler(local) as clk:
             res = time_batched_form(mt, torch.cuda.Stream(device=dev), dev, n_inst=args.batch_instances,
@@ -408,6 +558,12 @@ def run_mine(args):
                      "checkpoints every 32 steps, acceptance loss at z = 30 m",
             adjoint_over_forward=adj["t_adjoint_ms"] / (kernel_s * 1e3),
             total_over_forward=t_all / kernel_s, **adj)
+        if "tape" in adj:
+            tp = adj["tape"]
+            t_tape = (tp["t_forward_tape_ms"] + tp["t_loss_ms"] + tp["t_adjoint_ms"]) / 1e3
+            tp.update(value=_barrier_sum(adj["muon_steps"], ws, dev) / _barrier_max(t_tape, ws, dev), unit=UNIT,
+                      adjoint_over_forward=tp["t_adjoint_ms"] / (kernel_s * 1e3),
+                      total_over_forward=t_tape / kernel_s)
         forms["plain"] = dict(value=value, unit=UNIT, kernel_ms=kernel_s * 1e3)
         bt = time_batched_form(mt, stream, dev, n_inst=args.batch_instances, rank=rank,
                                separate=not args.no_separate)
@@ -415,6 +571,17 @@ def run_mine(args):
         bt["workload"] = (f"config2: {bt['instances']} worlds (64x64x512 voxels, 100x100x300 map each), shared "
                           f"iron/air/concrete tables, {bt['muons']} muons, log-uniform sizes, 2000 steps")
         forms["batched"] = bt
+        if not args.no_c4:
+            c4 = time_c4_form(mt, dev, n_total=args.c4_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
+            peaks_, _ = _peaks()
+            for key in ("plain", "batched", "streamed"):
+                c4[key + "_value"] = (_barrier_sum(c4["muon_steps"], ws, dev)
+                                      / _barrier_max(c4[key + "_ms"] / 1e3, ws, dev))
+            c4["value"] = c4["plain_value"]
+            c4["roofline_frac_plain"] = BYTES_PER_STEP * c4["plain_value"] / ws / 1e9 / peaks_["hbm_gbs"]
+            c4["workload"] = ("config4: 1e8 muons of config1's spectrum in 16M chunks, config1 geometry, "
+                              "400x400x1200 map, 4 materials x 128 bins x 256x128 tables")
+            forms["c4"] = c4
     peaks, peak_kind = _peaks()
     achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -471,6 +638,9 @@ def main(argv=None):
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--batch-instances", type=int, default=256, help="worlds in the batched form")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched form (one JSON line)")
+    ap.add_argument("--no-c4", action="store_true", help="skip the config4 (1e8 muons) form")
+    ap.add_argument("--c4-only", action="store_true", help="run only the config4 form (one JSON line)")
+    ap.add_argument("--c4-muons", type=int, default=None, help="muons of the config4 form (default 1e8)")
     ap.add_argument("--no-separate", action="store_true",
                     help="batched form: skip timing one mt_transport call per instance")
     args = ap.parse_args(argv)

@@ -308,8 +308,10 @@ mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64_t n, float
  * py, pz) of the final state (SoA rows).  dL_dalpha: device [n_block][3],
  * overwritten.  dL_dinitial (may be NULL): device [6][n], receives dL/d(initial
  * state) in the same layout.  The checkpoint buffer's header is used as the
- * gradient accumulator.  Scratch (6n floats when dL_dinitial is NULL) comes
- * from the stream-ordered allocator.  Errors: MT_ERR_INVALID_ARG for null or
+ * gradient accumulator, and each checkpoint's list entries record the step
+ * counts of their segment.  Scratch (the tape of one K-step segment, 56 K n
+ * bytes, plus 6n floats when dL_dinitial is NULL) comes from the stream-ordered
+ * allocator.  Errors: MT_ERR_INVALID_ARG for null or
  * inconsistent arguments, MT_ERR_OOM, MT_ERR_CUDA. */
 mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, int32_t max_steps, uint64_t seed,
                           const float *alpha, int32_t n_block, int32_t ckpt_every, void *ckpt, int64_t ckpt_bytes,
@@ -322,6 +324,38 @@ mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, int32_t max_s
 mt_status mt_transport_adjoint(mt_handle *h, const mt_muon_soa *s0, int64_t n, float step_len, int32_t max_steps,
                                uint64_t seed, const float *alpha, int32_t n_block, const float *dL_dfinal,
                                float *dL_dalpha, int32_t ckpt_every, void *stream);
+
+/* Full-tape form (no recompute).  The checkpointing forward above keeps a
+ * state every K steps and the backward recomputes each K-step segment; with
+ * the GPU's high-bandwidth memory large enough to hold every recorded step
+ * (56 bytes per muon-step, e.g. 60 GB for 1e6 muons x ~1080 steps), the
+ * forward can instead record the whole trajectory once and the backward only
+ * walks it backwards.  Same gradients as mt_adjoint_ckpt (the same recorded
+ * quantities, the same reverse arithmetic).  steps_per_pass (1..64) sets the
+ * compaction interval of the forward. */
+
+/* Bytes of a tape buffer for n muons (n < 2^31): enough for every muon to run
+ * all max_steps steps (the tape actually used is 56 bytes x muon-steps taken).
+ * -1 for bad arguments. */
+int64_t mt_tape_bytes(int64_t n, int32_t max_steps, int32_t steps_per_pass);
+
+/* Forward that records the tape: exactly mt_transport_scaled (same results),
+ * with every step written into `tape` (device, 256-byte aligned, at least
+ * mt_tape_bytes bytes, caller-owned, read by mt_adjoint_tape).  Errors as
+ * mt_transport_ckpt.  A region that would overrun the buffer (only possible
+ * with a buffer smaller than mt_tape_bytes, which is rejected) is not written
+ * and makes mt_adjoint_tape return NaN gradients. */
+mt_status mt_transport_tape(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
+                            uint64_t seed, const float *alpha, int32_t n_block, int32_t steps_per_pass, void *tape,
+                            int64_t tape_bytes, void *stream);
+
+/* Backward from the tape of one mt_transport_tape call (same n, step_len,
+ * max_steps, alpha values, steps_per_pass).  dL_dfinal, dL_dinitial and
+ * dL_dalpha as in mt_adjoint_ckpt.  Scratch (6n floats when dL_dinitial is
+ * NULL) comes from the stream-ordered allocator. */
+mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, int32_t max_steps, const float *alpha,
+                          int32_t n_block, int32_t steps_per_pass, void *tape, int64_t tape_bytes,
+                          const float *dL_dfinal, float *dL_dinitial, float *dL_dalpha, void *stream);
 
 /* Acceptance loss of final states: L = (1/n) sum over muons of
  * s((h - |x_e|)/e) s((h - |y_e|)/e), s the logistic function and (x_e, y_e)

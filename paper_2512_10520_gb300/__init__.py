@@ -12,6 +12,7 @@ from ._binding import (  # noqa: F401
     MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT,
     mt_transport_noalloc, MT_NOALLOC_MAX_MUONS,
     mt_ckpt_bytes, mt_transport_ckpt, mt_adjoint_ckpt, mt_transport_adjoint, mt_acceptance_loss,
+    mt_tape_bytes, mt_transport_tape, mt_adjoint_tape,
     mt_batch_create, mt_batch_set_instance, mt_batch_destroy, mt_batch_device_bytes, mt_batch_workspace_bytes,
     mt_transport_batched, mt_batch_autotune,
 )

@@ -102,6 +102,11 @@ _SIGNATURES = {
                               C.c_int32, _P, _P, C.c_int32, _P], C.c_int),
     "mt_acceptance_loss": ([C.POINTER(mt_muon_soa), C.c_int64, C.c_double, C.c_double, C.c_double, _P, _P, _P],
                            C.c_int),
+    "mt_tape_bytes": ([C.c_int64, C.c_int32, C.c_int32], C.c_int64),
+    "mt_transport_tape": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P, C.c_int32,
+                           C.c_int32, _P, C.c_int64, _P], C.c_int),
+    "mt_adjoint_tape": ([_P, C.c_int64, C.c_float, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int64, _P, _P, _P,
+                         _P], C.c_int),
     "mt_batch_create": ([C.POINTER(mt_hist_desc), C.c_int32, C.POINTER(_P)], C.c_int),
     "mt_batch_set_instance": ([_P, C.c_int32, C.POINTER(mt_geometry_desc), C.POINTER(mt_field_desc)], C.c_int),
     "mt_batch_destroy": ([_P], None),
@@ -406,6 +411,35 @@ def mt_transport_adjoint(handle: int, muons0: Dict, step_len: float, max_steps: 
                                                C.c_void_p(a_ptr), int(nb), C.c_void_p(_f32_dev(dL_dfinal, "dL_dfinal")),
                                                C.c_void_p(_f32_dev(dL_dalpha, "dL_dalpha")), int(ckpt_every),
                                                C.c_void_p(_stream_ptr(stream))), "mt_transport_adjoint")
+
+
+def mt_tape_bytes(n: int, max_steps: int, steps_per_pass: int) -> int:
+    return load_library().mt_tape_bytes(int(n), int(max_steps), int(steps_per_pass))
+
+
+def mt_transport_tape(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, alpha,
+                      steps_per_pass: int, tape, id_offset: int = 0, instance: int = 0, stream=None) -> None:
+    """Forward recording every step into `tape` (uint8 CUDA tensor of mt_tape_bytes bytes)."""
+    s = soa_struct(muons, id_offset, instance)
+    a_ptr, nb = _alpha_ptr(alpha)
+    _check(load_library().mt_transport_tape(C.c_void_p(handle), C.byref(s), int(muons["x"].numel()), float(step_len),
+                                            int(max_steps), int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr),
+                                            int(nb), int(steps_per_pass), C.c_void_p(tape.data_ptr()),
+                                            int(tape.numel() * tape.element_size()),
+                                            C.c_void_p(_stream_ptr(stream))), "mt_transport_tape")
+
+
+def mt_adjoint_tape(handle: int, n: int, step_len: float, max_steps: int, alpha, steps_per_pass: int, tape,
+                    dL_dfinal, dL_dalpha, dL_dinitial=None, stream=None) -> None:
+    """Backward from the tape of one mt_transport_tape call."""
+    a_ptr, nb = _alpha_ptr(alpha)
+    _check(load_library().mt_adjoint_tape(C.c_void_p(handle), int(n), float(step_len), int(max_steps),
+                                          C.c_void_p(a_ptr), int(nb), int(steps_per_pass), C.c_void_p(tape.data_ptr()),
+                                          int(tape.numel() * tape.element_size()),
+                                          C.c_void_p(_f32_dev(dL_dfinal, "dL_dfinal")),
+                                          C.c_void_p(_f32_dev(dL_dinitial, "dL_dinitial")),
+                                          C.c_void_p(_f32_dev(dL_dalpha, "dL_dalpha")),
+                                          C.c_void_p(_stream_ptr(stream))), "mt_adjoint_tape")
 
 
 def mt_acceptance_loss(muons: Dict, loss, dL_dfinal=None, z_plane: float = 30.0, half_width: float = 0.5,

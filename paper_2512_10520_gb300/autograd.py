@@ -21,16 +21,26 @@ class MuonTransportFn:
 
         class _Fn(torch.autograd.Function):
             @staticmethod
-            def forward(ctx, alpha, world, muons, step_len, max_steps, seed, ckpt_every, id_offset, instance):
+            def forward(ctx, alpha, world, muons, step_len, max_steps, seed, ckpt_every, id_offset, instance, tape):
                 n = int(muons["x"].numel())
                 work = {k: v.clone() for k, v in muons.items()}
                 a = alpha.detach().contiguous()
-                ckpt = torch.empty(max(1, B.mt_ckpt_bytes(n, max_steps, ckpt_every)), dtype=torch.uint8,
-                                   device=alpha.device)
-                B.mt_transport_ckpt(world.handle, work, step_len, max_steps, seed, a, ckpt_every, ckpt, id_offset,
-                                    instance)
+                if tape == "auto":
+                    free, _ = torch.cuda.mem_get_info(alpha.device)
+                    tape = B.mt_tape_bytes(n, max_steps, ckpt_every) <= free // 2
+                if tape:
+                    buf = torch.empty(max(1, B.mt_tape_bytes(n, max_steps, ckpt_every)), dtype=torch.uint8,
+                                      device=alpha.device)
+                    B.mt_transport_tape(world.handle, work, step_len, max_steps, seed, a, ckpt_every, buf, id_offset,
+                                        instance)
+                else:
+                    buf = torch.empty(max(1, B.mt_ckpt_bytes(n, max_steps, ckpt_every)), dtype=torch.uint8,
+                                      device=alpha.device)
+                    B.mt_transport_ckpt(world.handle, work, step_len, max_steps, seed, a, ckpt_every, buf, id_offset,
+                                        instance)
                 ctx.save_for_backward(a)
-                ctx.ckpt = ckpt
+                ctx.ckpt = buf
+                ctx.tape = bool(tape)
                 ctx.world = world
                 ctx.args = (n, step_len, max_steps, seed, ckpt_every, id_offset, instance)
                 ctx.mark_non_differentiable(work["steps"], work["status"])
@@ -44,9 +54,12 @@ class MuonTransportFn:
                          for g in (gx, gy, gz, gpx, gpy, gpz)]
                 g6 = torch.stack([g.float() for g in grads]).contiguous()
                 dalpha = torch.empty_like(a)
-                B.mt_adjoint_ckpt(ctx.world.handle, n, step_len, max_steps, seed, a, ckpt_every, ctx.ckpt, g6, dalpha,
-                                  id_offset=id_offset, instance=instance)
-                return dalpha, None, None, None, None, None, None, None, None
+                if ctx.tape:
+                    B.mt_adjoint_tape(ctx.world.handle, n, step_len, max_steps, a, ckpt_every, ctx.ckpt, g6, dalpha)
+                else:
+                    B.mt_adjoint_ckpt(ctx.world.handle, n, step_len, max_steps, seed, a, ckpt_every, ctx.ckpt, g6,
+                                      dalpha, id_offset=id_offset, instance=instance)
+                return dalpha, None, None, None, None, None, None, None, None, None
 
         return _Fn
 
@@ -96,9 +109,15 @@ class AcceptanceLossFn:
 
 
 def transport_differentiable(world, muons: Dict, alpha, step_len: float, max_steps: int, seed: int,
-                             ckpt_every: int = 32, id_offset: int = 0, instance: int = 0) -> Dict:
-    """Differentiable transport: returns the final state dict; x..pz carry grad to alpha."""
-    out = MuonTransportFn.apply(alpha, world, muons, step_len, max_steps, seed, ckpt_every, id_offset, instance)
+                             ckpt_every: int = 32, id_offset: int = 0, instance: int = 0, tape="auto") -> Dict:
+    """Differentiable transport: returns the final state dict; x..pz carry grad to alpha.
+
+    tape: True records every step in the forward and the backward only walks the
+    record (56 B per muon-step of device memory); False keeps a checkpoint every
+    ckpt_every steps and recomputes each segment in the backward; "auto" takes
+    the tape when it needs at most half of the free device memory."""
+    out = MuonTransportFn.apply(alpha, world, muons, step_len, max_steps, seed, ckpt_every, id_offset, instance,
+                                tape)
     return dict(zip(_FIELDS + ("steps", "status"), out))
 
 

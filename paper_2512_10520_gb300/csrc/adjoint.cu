@@ -11,16 +11,20 @@
 // Forward (mt_transport_ckpt): the compacting transport with a pass length of
 // K = ckpt_every steps whose live lists are all kept: the list that enters
 // pass p is the checkpoint of every muon alive at step p K.
-// Backward (mt_adjoint_ckpt): passes in reverse order; each live muon of pass
-// p recomputes its (at most K) steps from the checkpoint with the forward's own
-// step function, recording a tape in local memory, then walks the tape
-// backwards, carrying (dL/dr, dL/dp) in a per-muon buffer from pass to pass and
-// accumulating dL/dalpha.
+// Backward (mt_adjoint_ckpt): passes in reverse order; for pass p, a recorded
+// pass recomputes each live muon's (at most K) steps from the checkpoint with
+// the forward's own step function, writing a tape of the pass, and a reverse
+// pass walks the tape backwards, carrying (dL/dr, dL/dp) in a per-muon buffer
+// from pass to pass and accumulating dL/dalpha.
+// Full-tape form (mt_transport_tape / mt_adjoint_tape): the forward's passes
+// record their tapes directly (every pass kept), so the backward only runs
+// the reverse passes.
 //
 // Checkpoint buffer: [ counts | dL/dalpha | list 0 | list 1 | ... | list P ]:
 // P + 1 live counts (uint64), the dL/dalpha accumulator (double
 // [MT_MAX_BOXES][3]), then P + 1 live lists of four float4 arrays of n entries
-// (step.cuh), each section 256-byte aligned, P = ceil(max_steps / K).
+// (step.cuh), each section 256-byte aligned, P = ceil(max_steps / K).  The
+// tape buffer appends the tape region offsets, a flag and the tape region.
 #include <cstdio>
 
 #include "compact.cuh"
@@ -29,17 +33,13 @@ namespace mt {
 
 constexpr int kTapeMax = 64;
 
-// Reverse sweep: load the next step's tape words while reversing this one
-// (measured slower on config3, so off by default).
-#ifndef MT_ADJ_PIPELINE
-#define MT_ADJ_PIPELINE 0
+// Resident blocks per SM of the reverse pass (3 blocks of 256 = 85 registers;
+// measured on config3: 34.5 ms against 38.2 ms with 4 blocks, which spill).
+#ifndef MT_ADJ_MIN_BLOCKS
+#define MT_ADJ_MIN_BLOCKS 3
 #endif
 
-// Resident blocks per SM of the adjoint pass (4 blocks of 256 = 64 registers;
-// on config3 5 blocks spill and 3 blocks hide too little latency).
-#ifndef MT_ADJ_MIN_BLOCKS
-#define MT_ADJ_MIN_BLOCKS 4
-#endif
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct CkptLayout {
     int passes;
@@ -51,43 +51,85 @@ static CkptLayout ckpt_layout(int64_t n, int32_t max_steps, int32_t K)
     CkptLayout L;
     const int64_t cap = n > 0 ? n : 1;
     L.passes = max_steps > 0 ? (max_steps + K - 1) / K : 1;
-    L.alpha_off = ((int64_t)(L.passes + 1) * 8 + 255) & ~(int64_t)255;
-    L.lists_off = (L.alpha_off + 3 * MT_MAX_BOXES * 8 + 255) & ~(int64_t)255;
+    L.alpha_off = round_up((int64_t)(L.passes + 1) * 8, 256);
+    L.lists_off = round_up(L.alpha_off + 3 * MT_MAX_BOXES * 8, 256);
     L.list_bytes = 4 * cap * (int64_t)sizeof(float4);
     L.total = L.lists_off + (L.passes + 1) * L.list_bytes;
     return L;
 }
 
-// The tape of the reverse sweep lives in a global scratch array, four 16-byte
-// words per recorded step, word q of step j of thread t at [(4 j + q) T + t]
-// (T = threads of the grid, so a warp's stores are contiguous):
-//   a = (rx, ry, rz, meta)  b = (px, py, pz, f)  c = (Bmx, Bmy, Bmz, theta)  d = (phi - pi, -, -, -)
-// with r and p at the step's start, Bm the field there before the block scale,
-// meta bit 0 = scattered and bits 8..15 = box + 1.  It is written and read once
-// with streaming (evict-first) hints, so it passes through L2 without pushing
-// out the field map.
-struct TapeRef {
-    float4 *base;
-    int64_t T;     // threads of the grid
-    int64_t tid;   // this thread
-    __device__ __forceinline__ float4 *at(int j, int q) const { return base + (4 * (int64_t)j + q) * T + tid; }
+// Tape buffer of the full-tape form: a checkpoint buffer (above) followed by
+// the region offsets of every pass (uint64 [P + 1]), an overflow flag and the
+// tape region, sized for n muons alive through every pass.
+struct TapeLayout {
+    CkptLayout ck;
+    int64_t off_off, flag_off, region_off, region_cap, total;
 };
 
+// Whether the tape holds the field at each step (16 more bytes per step) or
+// the reverse sweep evaluates it again at the recorded r (measured on config3:
+// recording is faster, 38 against 54 ms for the backward).
+#ifndef MT_TAPE_RECORD_B
+#define MT_TAPE_RECORD_B 1
+#endif
+
+// bytes of one recorded step
+__host__ __device__ constexpr int64_t tape_step_bytes(bool rb) { return rb ? 56 : 40; }
+
+__host__ __device__ inline int64_t tape_pass_bytes(int64_t count, int K)
+{
+    return round_up(tape_step_bytes(MT_TAPE_RECORD_B) * K * round_up(count, 32), 256);
+}
+
+static TapeLayout tape_layout(int64_t n, int32_t max_steps, int32_t K)
+{
+    TapeLayout T;
+    T.ck = ckpt_layout(n, max_steps, K);
+    T.off_off = T.ck.total;
+    T.flag_off = round_up(T.off_off + (int64_t)(T.ck.passes + 1) * 8, 256);
+    T.region_off = T.flag_off + 256;
+    T.region_cap = (int64_t)T.ck.passes * tape_pass_bytes(n > 0 ? n : 1, K);
+    T.total = T.region_off + T.region_cap;
+    return T;
+}
+
+// One recorded step takes 40 (or 56) bytes in three (four) planes, so that a
+// warp's stores and loads are contiguous: plane a = (rx, ry, rz, meta), plane
+// b = (px, py, pz, f), plane c = (theta, phi - pi), plane d = (Bx, By, Bz, -)
+// when the field is recorded, with r and p at the step's start, B there before
+// the block scale, and meta bit 0 = scattered, bits 8..15 = box + 1.  Step j of
+// entry t sits at base + step_bytes j T (T entries per plane, a multiple of
+// 32).  Written and read once with streaming (evict-first) hints, so it passes
+// through L2 without pushing out the field map.
+template <bool RB>
+struct TapeRef {
+    char *base;
+    int64_t T;
+    int64_t tid;
+    __device__ __forceinline__ char *row(int j) const { return base + tape_step_bytes(RB) * (int64_t)j * T; }
+    __device__ __forceinline__ float4 *a(int j) const { return reinterpret_cast<float4 *>(row(j)) + tid; }
+    __device__ __forceinline__ float4 *b(int j) const { return reinterpret_cast<float4 *>(row(j) + 16 * T) + tid; }
+    __device__ __forceinline__ float2 *c(int j) const { return reinterpret_cast<float2 *>(row(j) + 32 * T) + tid; }
+    __device__ __forceinline__ float4 *d(int j) const { return reinterpret_cast<float4 *>(row(j) + 40 * T) + tid; }
+};
+
+template <bool RB>
 struct TapeWriter {
-    const TapeRef *tr;
+    const TapeRef<RB> *tr;
     int j;
+    bool on = true;
     float f = 0.0f, th = 0.0f, phs = 0.0f;
+    float pxs = 0.0f, pys = 0.0f, pzs = 0.0f;
     bool scat = false;
     __device__ __forceinline__ void begin(const State &s, int box, bool scattered)
     {
         scat = scattered;
         const int meta = ((box + 1) << 8) | (scattered ? 1 : 0);
-        __stcs(tr->at(j, 0), make_float4(s.x + s.xl, s.y + s.yl, s.z + s.zl, __int_as_float(meta)));
+        if (on) __stcs(tr->a(j), make_float4(s.x + s.xl, s.y + s.yl, s.z + s.zl, __int_as_float(meta)));
         pxs = s.px + s.pxl;
         pys = s.py + s.pyl;
         pzs = s.pz + s.pzl;
     }
-    float pxs = 0.0f, pys = 0.0f, pzs = 0.0f;
     __device__ __forceinline__ void draw(float f_, float th_, float phs_)
     {
         f = f_;
@@ -96,15 +138,28 @@ struct TapeWriter {
     }
     __device__ __forceinline__ void field(float3 B)
     {
-        __stcs(tr->at(j, 1), make_float4(pxs, pys, pzs, f));
-        __stcs(tr->at(j, 2), make_float4(B.x, B.y, B.z, th));
-        if (scat) __stcs(tr->at(j, 3), make_float4(phs, 0.0f, 0.0f, 0.0f));
+        if (!on) return;
+        __stcs(tr->b(j), make_float4(pxs, pys, pzs, f));
+        if (scat) __stcs(tr->c(j), make_float2(th, phs));
+        if (RB) __stcs(tr->d(j), make_float4(B.x, B.y, B.z, 0.0f));
     }
 };
 
 struct TapeEntry {
-    float4 a, b, c, d;
+    float4 a, b, d;
+    float2 c;
 };
+
+template <bool RB>
+__device__ __forceinline__ TapeEntry load_tape(const TapeRef<RB> &tr, int j)
+{
+    TapeEntry t;
+    t.a = __ldcs(tr.a(j));
+    t.b = __ldcs(tr.b(j));
+    t.c = (__float_as_int(t.a.w) & 1) ? __ldcs(tr.c(j)) : make_float2(0.0f, 0.0f);
+    t.d = RB ? __ldcs(tr.d(j)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    return t;
+}
 
 __device__ __forceinline__ void cross3(const float a[3], const float b[3], float o[3])
 {
@@ -215,7 +270,7 @@ struct AlphaAcc {
 //   p' = ps + v1 + v2/2 + v3/6 + v4/24,  r' = r + (d/P0)(ps + v1/2 + v2/6 + v3/24)
 // (the stage form k1..k4 of the forward expands to the same polynomials), so
 // its adjoint is taken in that form, which keeps fewer values live.
-template <int GEOM, int FIELD>
+template <int GEOM, int FIELD, bool RB>
 __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWorld &sw, const TapeEntry &t, float q,
                                              float d, float kd, float rb[3], float pb[3], AlphaAcc &acc,
                                              float (*sacc)[MT_MAX_BOXES])
@@ -225,18 +280,39 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     const bool scat = meta & 1;
     const float r[3] = {t.a.x, t.a.y, t.a.z};
     const float p[3] = {t.b.x, t.b.y, t.b.z};
-    const float f = t.b.w, th = t.c.w;
+    const float f = t.b.w, th = t.c.x;
+    // -- field before the block scale, evaluated again at the recorded r
+    float Bm[3] = {0.0f, 0.0f, 0.0f};
+    if (RB) {
+        Bm[0] = t.d.x;
+        Bm[1] = t.d.y;
+        Bm[2] = t.d.z;
+    } else if (FIELD == MT_FIELD_BOX) {
+        if (box >= 0) {
+            Bm[0] = sw.B[0][box];
+            Bm[1] = sw.B[1][box];
+            Bm[2] = sw.B[2][box];
+        }
+    } else if (FIELD == MT_FIELD_MAP) {
+        State at;
+        at.x = r[0];
+        at.y = r[1];
+        at.z = r[2];
+        at.xl = at.yl = at.zl = 0.0f;
+        const float3 b = field_map(w, at);
+        Bm[0] = b.x;
+        Bm[1] = b.y;
+        Bm[2] = b.z;
+    }
     float sphi = 0.0f, cphi = 0.0f;
     if (scat) {
-        __sincosf(t.d.x, &sphi, &cphi);
+        __sincosf(t.c.y, &sphi, &cphi);
         sphi = -sphi;
         cphi = -cphi;
     }
     // -- scattered momentum ps = p + sm1 p + P kf tv(u) (recomputed in FP32)
     float ps[3] = {p[0], p[1], p[2]};
     if (scat) scatter_fp32(p, f, th, cphi, sphi, ps);
-    // -- field before the block scale (recorded)
-    const float Bm[3] = {t.c.x, t.c.y, t.c.z};
     int blk = -1;
     float sc[3] = {1.0f, 1.0f, 1.0f};
     if (GEOM == MT_GEOM_BOXES && FIELD != MT_FIELD_NONE && box >= 0) {
@@ -351,70 +427,103 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     for (int c = 0; c < 3; ++c) pb[c] = fmaf(1.0f + sm1, psb[c], fmaf(Pb, u[c], fmaf(-u[c], uu, ub[c]) * rPs));
 }
 
+// Recorded pass: every live muon of list `in` advances its (at most S) steps
+// with the forward's own step function, recording each step into the pass
+// tape at column = list entry (T = entries rounded up to 32); the number of
+// steps each entry took goes into the spare word of its list entry.  The tape
+// region's offset is read from tape_off[0] and its end written to tape_off[1];
+// a region that would run past region_cap is not written and sets *flag.
+// FWD: the full-tape forward (finished muons stored, survivors appended to
+// `out`, as in compact_pass); otherwise the recomputation of one checkpointed
+// pass in the backward (nothing but the tape and the step counts is written).
+template <int GEOM, int FIELD, bool FWD>
+__global__ void __launch_bounds__(kBlock, MT_PASS_MIN_BLOCKS)
+    tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
+              const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
+              unsigned long long *tape_off, int64_t region_cap, unsigned int *flag)
+{
+    __shared__ SmemWorld sw;
+    const int64_t count = (int64_t)*cin;
+    const unsigned long long off = tape_off[0];
+    const int64_t bytes = tape_pass_bytes(count, S);
+    if (blockIdx.x == 0 && threadIdx.x == 0) tape_off[1] = off + (count ? bytes : 0);
+    if (count == 0) return;
+    const bool room = (int64_t)off + bytes <= region_cap;
+    if (!room && blockIdx.x == 0 && threadIdx.x == 0) *flag = 1u;
+    stage_world(sw, w, rp);
+    __syncthreads();
+    TapeRef<MT_TAPE_RECORD_B> tr{tape_base + off, round_up(count, 32), 0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool keep = false;
+        State s;
+        float q = 0.0f;
+        int k = 0;
+        int64_t idx = 0;
+        if (i < count) {
+            get_live(in, i, s, q, k, idx);
+            tr.tid = i;
+            const uint64_t id = (uint64_t)(rp.id_offset + idx);
+            const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+            const int kend = min(k + S, rp.max_steps);
+            int r = MT_ALIVE, ns = 0;
+#pragma unroll 1
+            for (; k < kend; ++k) {
+                TapeWriter<MT_TAPE_RECORD_B> wr{&tr, ns};
+                wr.on = room;
+                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp, wr);
+                if (r != MT_ALIVE) break;
+                ++ns;
+            }
+            reinterpret_cast<float *>(in.w3 + i)[3] = __int_as_float(ns);
+            if (FWD) {
+                if (r == MT_ALIVE && k >= rp.max_steps) r = MT_MAX_STEPS;
+                if (r != MT_ALIVE)
+                    store_muon(soa, idx, s, k, r);
+                else
+                    keep = true;
+            }
+        }
+        if (FWD) {
+            const int64_t slot = warp_append(cout, keep);
+            if (keep) put_live(out, slot, s, q, k, idx);
+        }
+    }
+}
+
+// Reverse of one recorded pass: each entry of list `ck` walks its recorded
+// steps backwards (tape of the pass at tape_base + tape_off[0], column = list
+// entry), carrying (dL/dr, dL/dp) of muon idx in adj[6][n] and accumulating
+// dL/dalpha.  Nothing is done when *flag is set (the tape was not written).
 template <int GEOM, int FIELD>
-__global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS) adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck,
-                                                       const unsigned long long *count_p, int S, float *adj,
-                                                       int64_t n, double *dalpha, float4 *tape_base)
+__global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
+    adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck, const unsigned long long *count_p, float *adj,
+                 int64_t n, double *dalpha, const char *tape_base, const unsigned long long *tape_off,
+                 const unsigned int *flag)
 {
     __shared__ SmemWorld sw;
     __shared__ float sacc[3][MT_MAX_BOXES];
     const int64_t count = (int64_t)*count_p;
-    if (count == 0) return;
+    if (count == 0 || *flag) return;
     stage_world(sw, w, rp);
     for (int t = threadIdx.x; t < 3 * MT_MAX_BOXES; t += blockDim.x) (&sacc[0][0])[t] = 0.0f;
     __syncthreads();
     AlphaAcc acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const TapeRef tr{tape_base, stride, (int64_t)blockIdx.x * blockDim.x + threadIdx.x};
+    TapeRef<MT_TAPE_RECORD_B> tr{const_cast<char *>(tape_base) + *tape_off, round_up(count, 32), 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        State s;
-        float q;
-        int k;
-        int64_t idx;
-        get_live(ck, i, s, q, k, idx);
-        const uint64_t id = (uint64_t)(rp.id_offset + idx);
-        const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
-        const int kend = min(k + S, rp.max_steps);
-        int ns = 0;
-#pragma unroll 1
-        for (; k < kend; ++k) {
-            const int r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp, TapeWriter{&tr, ns});
-            if (r != MT_ALIVE) break;
-            ++ns;
-        }
+        tr.tid = i;
+        const float q = ck.w0[i].w;
+        const int64_t idx = __float_as_int(ck.w2[i].w);
+        const int ns = __float_as_int(ck.w3[i].w);
         float rb[3] = {adj[idx], adj[n + idx], adj[2 * n + idx]};
         float pb[3] = {adj[3 * n + idx], adj[4 * n + idx], adj[5 * n + idx]};
-#if MT_ADJ_PIPELINE
-        // the words of step j - 1 are in flight while step j is reversed
-        TapeEntry nxt;
-        if (ns > 0) {
-            nxt.a = __ldcs(tr.at(ns - 1, 0));
-            nxt.b = __ldcs(tr.at(ns - 1, 1));
-            nxt.c = __ldcs(tr.at(ns - 1, 2));
-            nxt.d = __ldcs(tr.at(ns - 1, 3));
-        }
 #pragma unroll 1
         for (int j = ns - 1; j >= 0; --j) {
-            const TapeEntry t = nxt;
-            if (j > 0) {
-                nxt.a = __ldcs(tr.at(j - 1, 0));
-                nxt.b = __ldcs(tr.at(j - 1, 1));
-                nxt.c = __ldcs(tr.at(j - 1, 2));
-                nxt.d = __ldcs(tr.at(j - 1, 3));
-            }
-            reverse_step<GEOM, FIELD>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
+            const TapeEntry t = load_tape(tr, j);
+            reverse_step<GEOM, FIELD, MT_TAPE_RECORD_B>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
         }
-#else
-#pragma unroll 1
-        for (int j = ns - 1; j >= 0; --j) {
-            TapeEntry t;
-            t.a = __ldcs(tr.at(j, 0));
-            t.b = __ldcs(tr.at(j, 1));
-            t.c = __ldcs(tr.at(j, 2));
-            t.d = (__float_as_int(t.a.w) & 1) ? __ldcs(tr.at(j, 3)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            reverse_step<GEOM, FIELD>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
-        }
-#endif
         adj[idx] = rb[0];
         adj[n + idx] = rb[1];
         adj[2 * n + idx] = rb[2];
@@ -428,12 +537,6 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS) adjoint_pass(const 
         const float v = sacc[t % 3][t / 3];
         if (v != 0.0f) atomicAdd(&dalpha[t], (double)v);
     }
-}
-
-__global__ void alpha_to_float(const double *src, float *dst, int m)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < m) dst[t] = (float)src[t];
 }
 
 // Acceptance loss of the differentiable form: mean over all n muons of
@@ -500,26 +603,6 @@ static int resident_grid(const void *kernel, int64_t work)
 int64_t ckpt_bytes(int64_t n, int32_t max_steps, int32_t K) { return ckpt_layout(n, max_steps, K).total; }
 
 template <int GEOM, int FIELD>
-static int adjoint_grid(int64_t n)
-{
-    return resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
-}
-
-// Tape scratch of the reverse sweep: 3 words x K steps x every thread of the grid.
-static int64_t tape_bytes(const WorldParams &w, int64_t n, int K)
-{
-    int grid;
-    if (w.geom_kind == MT_GEOM_BOXES)
-        grid = w.field_kind == MT_FIELD_MAP   ? adjoint_grid<MT_GEOM_BOXES, MT_FIELD_MAP>(n)
-               : w.field_kind == MT_FIELD_BOX ? adjoint_grid<MT_GEOM_BOXES, MT_FIELD_BOX>(n)
-                                              : adjoint_grid<MT_GEOM_BOXES, MT_FIELD_NONE>(n);
-    else
-        grid = w.field_kind == MT_FIELD_MAP ? adjoint_grid<MT_GEOM_VOXELS, MT_FIELD_MAP>(n)
-                                            : adjoint_grid<MT_GEOM_VOXELS, MT_FIELD_NONE>(n);
-    return 4 * (int64_t)K * grid * kBlock * (int64_t)sizeof(float4);
-}
-
-template <int GEOM, int FIELD>
 static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
                                 cudaStream_t st, int K, char *ck)
 {
@@ -544,22 +627,94 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
 }
 
 template <int GEOM, int FIELD>
-static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
-                                 char *ck, float *adj, float4 *tape)
+static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
+                                cudaStream_t st, int K, char *buf)
 {
-    const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
-    const unsigned long long *ctr = reinterpret_cast<const unsigned long long *>(ck);
-    double *dalpha = reinterpret_cast<double *>(ck + L.alpha_off);
-    cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
+    const TapeLayout T = tape_layout(n, rp.max_steps, K);
+    const CkptLayout &L = T.ck;
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(buf);
+    unsigned long long *toff = reinterpret_cast<unsigned long long *>(buf + T.off_off);
+    unsigned int *flag = reinterpret_cast<unsigned int *>(buf + T.flag_off);
+    cudaError_t e = cudaMemsetAsync(buf, 0, (size_t)L.lists_off, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf + T.off_off, 0, (size_t)(T.region_off - T.off_off), st);
     if (e != cudaSuccess) return e;
-    const int grid = adjoint_grid<GEOM, FIELD>(n);
-    for (int p = L.passes - 1; p >= 0; --p) {
-        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
-                                                           ctr + p, K, adj, n, dalpha, tape);
+    const int64_t need = (n + kBlock - 1) / kBlock;
+    compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
+        soa, n, rp, live_buf_at(buf + L.lists_off, n), ctr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int grid = resident_grid((const void *)tape_pass<GEOM, FIELD, true>, n);
+    for (int p = 0; p < L.passes; ++p) {
+        tape_pass<GEOM, FIELD, true><<<grid, kBlock, 0, st>>>(
+            w, soa, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
+            live_buf_at(buf + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, K,
+            buf + T.region_off, toff + p, T.region_cap, flag);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Scratch of the recompute form's backward: the tape of one pass of up to n
+// entries, after a 256-byte header holding the region offsets and the flag.
+static int64_t ckpt_scratch_bytes(int64_t n, int K) { return 256 + tape_pass_bytes(n > 0 ? n : 1, K); }
+
+template <int GEOM, int FIELD>
+static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
+                                 char *ck, float *adj, char *scratch)
+{
+    const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
+    double *dalpha = reinterpret_cast<double *>(ck + L.alpha_off);
+    unsigned long long *toff = reinterpret_cast<unsigned long long *>(scratch);
+    unsigned int *flag = reinterpret_cast<unsigned int *>(scratch + 64);
+    cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 256, st);
+    if (e != cudaSuccess) return e;
+    const int rgrid = resident_grid((const void *)tape_pass<GEOM, FIELD, false>, n);
+    const int agrid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+    const int64_t cap = tape_pass_bytes(n > 0 ? n : 1, K);
+    for (int p = L.passes - 1; p >= 0; --p) {
+        const LiveBuf lp = live_buf_at(ck + L.lists_off + p * L.list_bytes, n);
+        tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, st>>>(w, mt_muon_soa{}, rp, lp, lp, ctr + p, nullptr, K,
+                                                                scratch + 256, toff, cap, flag);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, scratch + 256, toff,
+                                                           flag);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <int GEOM, int FIELD>
+static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
+                                 char *buf, float *adj, char *)
+{
+    const TapeLayout T = tape_layout(n, rp.max_steps, K);
+    const CkptLayout &L = T.ck;
+    const unsigned long long *ctr = reinterpret_cast<const unsigned long long *>(buf);
+    const unsigned long long *toff = reinterpret_cast<const unsigned long long *>(buf + T.off_off);
+    const unsigned int *flag = reinterpret_cast<const unsigned int *>(buf + T.flag_off);
+    double *dalpha = reinterpret_cast<double *>(buf + L.alpha_off);
+    cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int grid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+    for (int p = L.passes - 1; p >= 0; --p) {
+        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
+                                                          ctr + p, adj, n, dalpha, buf + T.region_off, toff + p, flag);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// dL/dalpha as float; NaN when the forward ran out of tape (flag set).
+__global__ void alpha_out(const double *src, float *dst, int m, const unsigned int *flag)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) dst[t] = (flag && *flag) ? __int_as_float(0x7FC00000) : (float)src[t];
 }
 
 #define MT_DISPATCH(FN, ...)                                                           \
@@ -697,24 +852,131 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
     }
     // scratch: the tape of the reverse sweep, and the adjoint state unless the
     // caller asked for dL/d(initial state) in place
-    const int64_t tbytes = tape_bytes(w, n, ckpt_every);
+    const int64_t tbytes = ckpt_scratch_bytes(n, ckpt_every);
     const int64_t abytes = dL_dinitial ? 0 : ((6 * n * (int64_t)sizeof(float) + 255) & ~(int64_t)255);
     char *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)(tbytes + abytes), st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
-    float4 *tape = reinterpret_cast<float4 *>(scratch);
+    char *tape = scratch;
     float *adj = dL_dinitial ? dL_dinitial : reinterpret_cast<float *>(scratch + tbytes);
     e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj, tape);
     if (e == cudaSuccess && alpha && n_block > 0) {
         const CkptLayout L = ckpt_layout(n, max_steps, ckpt_every);
-        alpha_to_float<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L.alpha_off), dL_dalpha,
-                                           3 * n_block);
+        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L.alpha_off), dL_dalpha,
+                                     3 * n_block, nullptr);
         e = cudaGetLastError();
     }
     const cudaError_t f = cudaFreeAsync(scratch, st);
     if (e == cudaSuccess) e = f;
     if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+    return MT_OK;
+}
+
+extern "C" int64_t mt_tape_bytes(int64_t n, int32_t max_steps, int32_t steps_per_pass)
+{
+    if (steps_per_pass < 1 || steps_per_pass > kTapeMax || n < 0 || max_steps < 0) return -1;
+    return tape_layout(n, max_steps, steps_per_pass).total;
+}
+
+namespace {
+
+mt_status check_tape(int64_t n, int32_t max_steps, int32_t K, const void *buf, int64_t bytes)
+{
+    if (K < 1 || K > kTapeMax) {
+        set_error("steps_per_pass %d outside [1, %d]", K, kTapeMax);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (n < 0 || n >= ((int64_t)1 << 31)) {
+        set_error("n = %lld outside [0, 2^31)", (long long)n);
+        return MT_ERR_INVALID_ARG;
+    }
+    const int64_t need = tape_layout(n, max_steps, K).total;
+    if (!buf || (reinterpret_cast<uintptr_t>(buf) & 255u) || bytes < need) {
+        set_error("tape buffer %p of %lld bytes: need %lld bytes, 256-byte aligned", buf, (long long)bytes,
+                  (long long)need);
+        return MT_ERR_INVALID_ARG;
+    }
+    return MT_OK;
+}
+
+}  // namespace
+
+extern "C" mt_status mt_transport_tape(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
+                                       uint64_t seed, const float *alpha, int32_t n_block, int32_t steps_per_pass,
+                                       void *tape, int64_t tape_bytes_, void *stream)
+{
+    if (!h || !s) {
+        set_error("null handle or muon SoA");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!s->x || !s->y || !s->z || !s->px || !s->py || !s->pz || !s->q || !s->steps || !s->status)) {
+        set_error("null muon array with n > 0");
+        return MT_ERR_INVALID_ARG;
+    }
+    RunParams rp;
+    mt_status stt = fill_run(rp, step_len, max_steps, seed, alpha, n_block, s->id_offset, s->instance);
+    if (stt != MT_OK) return stt;
+    stt = check_tape(n, max_steps, steps_per_pass, tape, tape_bytes_);
+    if (stt != MT_OK) return stt;
+    if (n == 0) return MT_OK;
+    DevGuard g(h->device);
+    const WorldParams &w = h->w;
+    const cudaError_t e = MT_DISPATCH(tape_forward, w, *s, n, rp, (cudaStream_t)stream, steps_per_pass, (char *)tape);
+    if (e != cudaSuccess) return cuda_fail(e, "taped transport");
+    return MT_OK;
+}
+
+extern "C" mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, int32_t max_steps, const float *alpha,
+                                     int32_t n_block, int32_t steps_per_pass, void *tape, int64_t tape_bytes_,
+                                     const float *dL_dfinal, float *dL_dinitial, float *dL_dalpha, void *stream)
+{
+    if (!h) {
+        set_error("null handle");
+        return MT_ERR_INVALID_ARG;
+    }
+    RunParams rp;
+    mt_status stt = fill_run(rp, step_len, max_steps, 0, alpha, n_block, 0, 0);
+    if (stt != MT_OK) return stt;
+    if (n != 0) {
+        stt = check_tape(n, max_steps, steps_per_pass, tape, tape_bytes_);
+        if (stt != MT_OK) return stt;
+    }
+    if (n < 0 || (n > 0 && !dL_dfinal) || (alpha && n_block > 0 && !dL_dalpha)) {
+        set_error("negative n, or null dL_dfinal / dL_dalpha");
+        return MT_ERR_INVALID_ARG;
+    }
+    DevGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const WorldParams &w = h->w;
+    if (n == 0) {
+        if (alpha && n_block > 0) {
+            const cudaError_t e = cudaMemsetAsync(dL_dalpha, 0, 3 * n_block * sizeof(float), st);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+        }
+        return MT_OK;
+    }
+    float *adj = dL_dinitial;
+    char *scratch = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!adj) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)(6 * n * sizeof(float)), st);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
+        adj = reinterpret_cast<float *>(scratch);
+    }
+    e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = MT_DISPATCH(tape_backward, w, n, rp, st, steps_per_pass, (char *)tape, adj, nullptr);
+    if (e == cudaSuccess && alpha && n_block > 0) {
+        const TapeLayout T = tape_layout(n, max_steps, steps_per_pass);
+        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)tape + T.ck.alpha_off), dL_dalpha,
+                                     3 * n_block, reinterpret_cast<const unsigned int *>((char *)tape + T.flag_off));
+        e = cudaGetLastError();
+    }
+    if (scratch) {
+        const cudaError_t f = cudaFreeAsync(scratch, st);
+        if (e == cudaSuccess) e = f;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint (tape)");
     return MT_OK;
 }
 

@@ -213,3 +213,78 @@ def test_initial_state_gradient_matches_finite_differences():
             dpx = float(np.float32(wl.muons["px"][m] + 1e-3)) - float(np.float32(wl.muons["px"][m] - 1e-3))
             fd = (vals[0] - vals[1]) / dpx
             assert abs(fd - gi[3][m]) <= 0.05 * abs(gi[3][m]) + 1e-9, (m, fd, gi[3][m])
+
+
+def _gpu_grad_tape(wl, alpha, K=32, want_initial=False):
+    """(loss, dL/dalpha, final state, dL/dinitial) with the full-tape forward and backward."""
+    import torch
+    import paper_2512_10520_gb300 as mt
+    with mt.World.from_workload(wl) as world:
+        dev = mt.muons_to_device(wl.muons)
+        a = torch.as_tensor(alpha, dtype=torch.float32).cuda().contiguous()
+        n = wl.n
+        tape = torch.empty(mt.mt_tape_bytes(n, wl.max_steps, K), dtype=torch.uint8, device="cuda")
+        mt.mt_transport_tape(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, K, tape)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.empty((6, n), dtype=torch.float32, device="cuda")
+        mt.mt_acceptance_loss(dev, loss, g)
+        da = torch.empty_like(a)
+        gi = torch.empty((6, n), dtype=torch.float32, device="cuda") if want_initial else None
+        mt.mt_adjoint_tape(world.handle, n, wl.step_len, wl.max_steps, a, K, tape, g, da, gi)
+        torch.cuda.synchronize()
+        return (float(loss.item()), da.cpu().numpy().astype(np.float64), mt.muons_to_host(dev),
+                None if gi is None else gi.cpu().numpy())
+
+
+@pytest.mark.parametrize("field,K", [("map", 32), ("box", 32), ("map", 7), ("map", 64)])
+def test_tape_form_equals_checkpoint_form(field, K):
+    """The full-tape forward gives the plain transport's results bit for bit, and
+    its backward the checkpoint form's gradients (the same recorded quantities
+    and reverse arithmetic; only the order of the dL/dalpha atomics differs)."""
+    wl = gen.workload("config1", n=6000, field="box" if field == "box" else None)
+    alpha = _alpha()
+    ref = gpu_transport(wl, alpha=alpha)
+    _, g_ck, _, gi_ck = _gpu_grad(wl, alpha, K=K, want_initial=True)
+    _, g_tp, fin, gi_tp = _gpu_grad_tape(wl, alpha, K=K, want_initial=True)
+    for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+        np.testing.assert_array_equal(ref[k], fin[k])
+    np.testing.assert_allclose(g_tp, g_ck, rtol=1e-5, atol=1e-6 * np.abs(g_ck).max())
+    np.testing.assert_allclose(gi_tp, gi_ck, rtol=1e-5, atol=1e-6 * np.abs(gi_ck).max())
+
+
+def test_tape_adjoint_matches_fp64_oracle_adjoint():
+    wl = gen.workload("config1", n=10000)
+    alpha = _alpha()
+    _, g_gpu, _, _ = _gpu_grad_tape(wl, alpha)
+    world = oracle.world_of(wl, alpha.astype(np.float64))
+    fin = oracle.transport(world, wl.muons, wl.step_len, wl.max_steps, wl.seed)
+    _, go = oracle.acceptance_loss(fin)
+    g_ora = oracle.adjoint(world, wl.muons, wl.step_len, wl.max_steps, wl.seed, go)
+    rel = np.linalg.norm(g_gpu - g_ora) / np.linalg.norm(g_ora)
+    assert rel <= 1e-3, (rel, g_gpu.ravel().tolist(), g_ora.ravel().tolist())
+
+
+def test_tape_buffer_checks_and_autograd_mode():
+    import torch
+    import paper_2512_10520_gb300 as mt
+    wl = gen.workload("config1", n=3000)
+    alpha = _alpha()
+    with mt.World.from_workload(wl) as world:
+        dev = mt.muons_to_device(wl.muons)
+        a = torch.as_tensor(alpha).cuda().contiguous()
+        need = mt.mt_tape_bytes(wl.n, wl.max_steps, 32)
+        assert need >= 40 * wl.n * wl.max_steps
+        small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+        with pytest.raises(mt.MtError):
+            mt.mt_transport_tape(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, 32, small)
+        with pytest.raises(mt.MtError):
+            mt.mt_transport_tape(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, 65,
+                                 torch.empty(need, dtype=torch.uint8, device="cuda"))
+        grads = []
+        for tape in (True, False):
+            x = torch.as_tensor(alpha).cuda().requires_grad_(True)
+            fin = mt.transport_differentiable(world, mt.muons_to_device(wl.muons), x, wl.step_len, wl.max_steps,
+                                              wl.seed, tape=tape)
+            mt.acceptance_loss(fin).backward()
+            grads.append(x.grad.cpu().numpy())
+        np.testing.assert_allclose(grads[0], grads[1], rtol=1e-5, atol=1e-7 * np.abs(grads[1]).max())

@@ -24,4 +24,7 @@ from .gen import (  # noqa: F401
     BATCH_STEP_LEN,
     BATCH_MAX_STEPS,
     BATCH_SEED,
+    C4_MUONS,
+    C4_CHUNK,
+    muons_config4_chunk,
 )

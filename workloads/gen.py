@@ -411,3 +411,13 @@ BATCH_SEED = 11
 def batched_hist(hist_samples: Optional[int] = None) -> dict:
     """Histogram set of the batched workload (iron, air, concrete, as config1)."""
     return histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
+
+
+C4_MUONS = 100_000_000
+C4_CHUNK = 16_000_000
+
+
+def muons_config4_chunk(c: int, n: int) -> dict:
+    """Chunk c (n muons, ids c * C4_CHUNK + m) of the 1e8-muon config4 stream: config1's
+    spectrum, each chunk from its own seed so chunks can be made one at a time."""
+    return muons_config1(n, seed=1234 * 1000 + c)
