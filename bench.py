@@ -225,7 +225,7 @@ def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32
     return out
 
 
-def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True):
+def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True, block=0, spp=0):
     """Batched form (config2): n_inst worlds, each its own 64x64x512 voxel geometry
     and 100x100x300 field map, one shared histogram set, instance sizes log-uniform
     in [1e3, 1e6].  One mt_transport_batched call (autotuned launch shape, CUDA
@@ -254,13 +254,16 @@ def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True
     out = dict(instances=n_inst, muons=sum(counts), min_instance=min(counts), max_instance=max(counts))
     with torch.cuda.stream(stream):
         reset()
-        blk, S = b.autotune(works, *args, sample_per_instance=4096, id_offsets=ids, stream=stream)
+        if block and spp:
+            blk, S = block, spp
+        else:
+            blk, S = b.autotune(works, *args, sample_per_instance=4096, id_offsets=ids, stream=stream)
         times = []
         for r in range(reps + 1):
             reset()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            b.transport(works, *args, use_graph=True, id_offsets=ids, stream=stream)
+            b.transport(works, *args, use_graph=True, id_offsets=ids, stream=stream, block=blk, steps_per_pass=S)
             e1.record(stream)
             torch.cuda.synchronize()
             if r:
@@ -462,12 +465,25 @@ def run_mine(args):
     if args.batch_only:
         with ClockSampler(local) as clk:
             res = time_batched_form(mt, torch.cuda.Stream(device=dev), dev, n_inst=args.batch_instances,
-                                    rank=rank, separate=not args.no_separate)
+                                    rank=rank, separate=not args.no_separate, block=args.batch_block,
+                                    spp=args.batch_spp)
         if rank == 0:
             print(json.dumps({"form": "batched", "clocks": clk.summary(), **res}))
         return 0
     wl = gen.workload("config1", n=args.muons)
     n = wl.n
+    if args.adjoint_only:
+        world = mt.World.from_workload(wl)
+        init = mt.muons_to_device(wl.muons, device=dev)
+        work = empty_like_soa(n, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        with ClockSampler(local) as clk:
+            adj = time_adjoint_form(mt, world, wl, init, work, stream, rank * n, K=args.ckpt_every,
+                                    tape=not args.no_tape)
+        world.close()
+        if rank == 0:
+            print(json.dumps({"form": "fwd_adjoint", "muons": n, "clocks": clk.summary(), **adj}))
+        return 0
     id_offset = rank * n
     stream = torch.cuda.Stream(device=dev)
     world = mt.World.from_workload(wl)
@@ -641,6 +657,10 @@ def main(argv=None):
     ap.add_argument("--no-c4", action="store_true", help="skip the config4 (1e8 muons) form")
     ap.add_argument("--c4-only", action="store_true", help="run only the config4 form (one JSON line)")
     ap.add_argument("--c4-muons", type=int, default=None, help="muons of the config4 form (default 1e8)")
+    ap.add_argument("--batch-block", type=int, default=0, help="batched form: block size (with --batch-spp: no autotune)")
+    ap.add_argument("--batch-spp", type=int, default=0, help="batched form: steps per pass")
+    ap.add_argument("--adjoint-only", action="store_true", help="run only the fwd+adjoint forms (one JSON line)")
+    ap.add_argument("--no-tape", action="store_true", help="fwd+adjoint form: skip the full-tape variant")
     ap.add_argument("--no-separate", action="store_true",
                     help="batched form: skip timing one mt_transport call per instance")
     args = ap.parse_args(argv)

@@ -21,6 +21,13 @@
 
 #include "compact.cuh"
 
+// Resident threads per SM the compiler must allow for in batch_pass (register
+// budget: 768 threads = 85 registers; measured on 16 config2 instances: 45.8 ms
+// against 46.9 ms at 1280 threads = 48 registers, which spill).
+#ifndef MT_BATCH_THREADS_PER_SM
+#define MT_BATCH_THREADS_PER_SM 768
+#endif
+
 struct mt_batch {
     int device = 0;
     int n_inst = 0;
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, u
 }
 
 template <int GEOM, int FIELD, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, MT_PASS_MIN_BLOCKS * 256 / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
+__global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
                                                    const unsigned long long *off, int n_inst, RunParams rp,
                                                    LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
                                                    unsigned int *cnt_out, const unsigned int *cof,
