@@ -48,6 +48,7 @@ class World(C.Structure):
         ("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("nf", C.c_int32), ("ntheta", C.c_int32),
         ("p_lo", C.c_double), ("p_hi", C.c_double),
         ("f_max", C.c_void_p), ("theta_max", C.c_void_p), ("T", C.c_void_p),
+        ("sampler", C.c_int32), ("alias_prob", C.c_void_p), ("alias_idx", C.c_void_p),
     ]
 
 
@@ -65,6 +66,10 @@ def lib():
             L.or_build_thresholds.restype = C.c_int
             L.or_sample_cell.argtypes = [P, C.c_int32, C.c_uint32]
             L.or_sample_cell.restype = C.c_int32
+            L.or_build_alias.argtypes = [C.c_int64, C.c_int32, P, P, P]
+            L.or_build_alias.restype = C.c_int
+            L.or_sample_alias.argtypes = [P, P, C.c_int32, C.c_uint32]
+            L.or_sample_alias.restype = C.c_int32
             L.or_momentum_bin.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
             L.or_momentum_bin.restype = C.c_int32
             L.or_material.argtypes = [P, P, P]
@@ -130,6 +135,25 @@ def build_thresholds(weights: np.ndarray) -> np.ndarray:
 def sample_cell(T_row: np.ndarray, w0: int) -> int:
     T = np.ascontiguousarray(T_row, dtype=np.uint64)
     return lib().or_sample_cell(_p(T), T.shape[-1] + 1, int(w0))
+
+
+def build_alias(T: np.ndarray, ncell: int):
+    """uint64 thresholds [..., ncell-1] -> alias tables (prob uint32 [..., ncell], alias int32 [..., ncell])."""
+    T = np.ascontiguousarray(T, dtype=np.uint64)
+    lead = T.shape[:-1]
+    n_hist = int(np.prod(lead)) if lead else 1
+    prob = np.zeros(lead + (ncell,), np.uint32)
+    alias = np.zeros(lead + (ncell,), np.int32)
+    rc = lib().or_build_alias(n_hist, int(ncell), _p(T), _p(prob), _p(alias))
+    if rc != 0:
+        raise ValueError(f"or_build_alias failed ({rc})")
+    return prob, alias
+
+
+def sample_alias(prob_row: np.ndarray, alias_row: np.ndarray, w0: int) -> int:
+    P = np.ascontiguousarray(prob_row, dtype=np.uint32)
+    A = np.ascontiguousarray(alias_row, dtype=np.int32)
+    return lib().or_sample_alias(_p(P), _p(A), P.shape[-1], int(w0))
 
 
 def momentum_bin(P: float, p_lo: float, p_hi: float, n_pbin: int) -> int:
@@ -217,6 +241,13 @@ class OracleWorld:
         w.theta_max = _p(arr(hist["theta_max"], np.float64))
         self.T = arr(build_thresholds(hist["weights"]), np.uint64)
         w.T = _p(self.T)
+        if hist.get("sampler", "icdf") == "alias":
+            prob, alias = build_alias(self.T, w.nf * w.ntheta)
+            w.sampler = 1
+            w.alias_prob = _p(arr(prob, np.uint32))
+            w.alias_idx = _p(arr(alias, np.int32))
+        elif hist.get("sampler", "icdf") != "icdf":
+            raise ValueError(hist["sampler"])
         self.w = w
         self._keep = keep
 

@@ -18,6 +18,7 @@
  *       i = GetMomentumBin(P), log10 bins                 (Sec. Momentum binning)
  *       (w0..w3) = Philox4x32-10(key = seed, ctr = (k, id_lo, id_hi, instance))
  *       cell = #{ j < ncell-1 : T_j <= w0 }               (inverse CDF of H_{M,i})
+ *         or the alias column of w0 (Sec. Methodology, "The Alias Method")
  *       f, theta = cell centre axes + uniform jitter      (Sec. Simulation, item 2)
  *       phi = 2 pi U                                      (isotropic azimuth)
  *       p <- p + Rot(dp), dp = [dt cos phi, dt sin phi, dz]   (Eq. 3, Rodrigues)
@@ -86,6 +87,9 @@ typedef struct or_world {
     const double *f_max;        /* [n_mat][n_pbin] */
     const double *theta_max;    /* [n_mat][n_pbin] */
     const uint64_t *T;          /* [n_mat][n_pbin][nf*ntheta-1] from or_build_thresholds */
+    int32_t sampler;            /* 0: inverse CDF over T, 1: alias tables below */
+    const uint32_t *alias_prob; /* [n_mat][n_pbin][nf*ntheta] from or_build_alias */
+    const int32_t *alias_idx;   /* [n_mat][n_pbin][nf*ntheta] */
 } or_world;
 
 /* ------------------------------------------------------------------------ */
@@ -152,6 +156,97 @@ int32_t or_sample_cell(const uint64_t *T, int32_t ncell, uint32_t w0)
     for (int32_t j = 0; j < ncell - 1; ++j)
         if (T[j] <= (uint64_t)w0) ++c;
     return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Walker's alias method (Sec. Methodology, "The Alias Method"): the N cells */
+/* become N equiprobable columns, each holding at most two outcomes, the    */
+/* column's own cell (taken with probability Prob_j) and an alias cell.     */
+/* Built here in integers from the masses m_c = T_c - T_{c-1} of the        */
+/* thresholds above (T_{-1} = 0, T_{N-1} = 2^32), which sum to 2^32, so the  */
+/* alias map draws from exactly the quantised distribution that the inverse */
+/* CDF draws from; only the draw -> cell map differs.  N must be a power of  */
+/* two, N = 2^n; a column then holds C = 2^(32-n) units of mass.            */
+/* Construction (Vose's variant of Walker's): every cell starts with        */
+/* q_c = m_c; the cells with q_c < C go on a "small" stack and the others on */
+/* a "large" stack, each pushed in increasing cell order.  While both are   */
+/* non-empty: pop s (small) and l (large); column s keeps q_s of its own    */
+/* cell and takes the remaining C - q_s from l (Alias_s = l); q_l drops by  */
+/* C - q_s and l is pushed on the small stack if q_l < C, else back on the  */
+/* large one.  Columns still on the large stack hold C of their own cell.   */
+/* In integers no cell is left on the small stack (the masses sum to N C).  */
+/* Prob_j = q_j 2^n is column j's own share in units of 2^-32 of the        */
+/* column, stored as min(Prob_j, 2^32 - 1).  A draw w0 picks column         */
+/* j = w0 >> (32 - n) at position r = (w0 << n) mod 2^32; the cell is j when */
+/* r < Prob_j, else Alias_j.  Returns 0, or -3 if N is not a power of two.  */
+/* ------------------------------------------------------------------------ */
+int or_build_alias(int64_t n_hist, int32_t ncell, const uint64_t *T, uint32_t *prob, int32_t *alias)
+{
+    if (ncell < 2 || (ncell & (ncell - 1)) != 0) return -3;
+    int32_t n = 0;
+    while ((1 << n) < ncell) ++n;
+    const uint64_t C = 1ull << (32 - n);
+    uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)ncell);
+    int32_t *small = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    int32_t *large = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    if (!q || !small || !large) {
+        free(q);
+        free(small);
+        free(large);
+        return -4;
+    }
+    for (int64_t h = 0; h < n_hist; ++h) {
+        const uint64_t *Th = T + h * (int64_t)(ncell - 1);
+        uint32_t *P = prob + h * (int64_t)ncell;
+        int32_t *A = alias + h * (int64_t)ncell;
+        int32_t ns = 0, nl = 0;
+        uint64_t prev = 0;
+        for (int32_t c = 0; c < ncell; ++c) {
+            uint64_t t = c < ncell - 1 ? Th[c] : (1ull << 32);
+            if (t < prev) t = prev;       /* thresholds never decrease; guard anyway */
+            q[c] = t - prev;
+            prev = t;
+            if (q[c] < C)
+                small[ns++] = c;
+            else
+                large[nl++] = c;
+        }
+        while (ns > 0 && nl > 0) {
+            const int32_t sc = small[--ns];
+            const int32_t lc = large[--nl];
+            P[sc] = (uint32_t)(q[sc] << n);
+            A[sc] = lc;
+            q[lc] -= C - q[sc];
+            if (q[lc] < C)
+                small[ns++] = lc;
+            else
+                large[nl++] = lc;
+        }
+        while (nl > 0) {
+            const int32_t lc = large[--nl];
+            P[lc] = 0xFFFFFFFFu;
+            A[lc] = lc;
+        }
+        while (ns > 0) {                  /* unreachable with exact integer masses */
+            const int32_t sc = small[--ns];
+            P[sc] = 0xFFFFFFFFu;
+            A[sc] = sc;
+        }
+    }
+    free(q);
+    free(small);
+    free(large);
+    return 0;
+}
+
+/* Alias draw: column j = w0 >> (32 - n), position r = (w0 << n) mod 2^32. */
+int32_t or_sample_alias(const uint32_t *prob, const int32_t *alias, int32_t ncell, uint32_t w0)
+{
+    int32_t n = 0;
+    while ((1 << n) < ncell) ++n;
+    const uint32_t j = w0 >> (32 - n);
+    const uint32_t r = w0 << n;
+    return r < prob[j] ? (int32_t)j : alias[j];
 }
 
 /* GetMomentumBin: base-10 logarithmic bins on [p_lo, p_hi], clamped. */
@@ -313,7 +408,8 @@ static int or_draw_step(const or_world *w, const double r[3], const double p[3],
     or_philox4x32_10(ctr, key, u);
     const int32_t ncell = w->nf * w->ntheta;
     const int64_t hidx = (int64_t)(d->mat - 1) * w->n_pbin + i;
-    int32_t c = or_sample_cell(w->T + hidx * (ncell - 1), ncell, u[0]);
+    int32_t c = w->sampler == 1 ? or_sample_alias(w->alias_prob + hidx * ncell, w->alias_idx + hidx * ncell, ncell, u[0])
+                                : or_sample_cell(w->T + hidx * (ncell - 1), ncell, u[0]);
     int32_t a = c / w->ntheta, b = c % w->ntheta;
     d->pbin = i;
     d->cell = c;
