@@ -225,6 +225,28 @@ def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32
     return out
 
 
+def time_alias_form(mt, wl, init, work, stream, id_offset, reps=3):
+    """The plain transport of the same workload with the alias sampler
+    (Sec. Methodology, "The Alias Method") in place of the inverse CDF."""
+    import torch
+    times = []
+    with mt.World(wl.geometry, wl.field, dict(wl.hist, sampler="alias")) as world, torch.cuda.stream(stream):
+        for r in range(reps + 1):
+            for k in work:
+                work[k].copy_(init[k], non_blocking=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                times.append(a.elapsed_time(b) / 1e3)
+        t = float(np.mean(times))
+        steps = float(work["steps"].sum().item())
+    return dict(value=steps / t, unit=UNIT, kernel_ms=1e3 * t, muon_steps=steps,
+                roofline_frac=BYTES_PER_STEP * steps / t / 1e9 / _peaks()[0]["hbm_gbs"])
+
+
 def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True, block=0, spp=0):
     """Batched form (config2): n_inst worlds, each its own 64x64x512 voxel geometry
     and 100x100x300 field map, one shared histogram set, instance sizes log-uniform
@@ -581,6 +603,11 @@ def run_mine(args):
                       adjoint_over_forward=tp["t_adjoint_ms"] / (kernel_s * 1e3),
                       total_over_forward=t_tape / kernel_s)
         forms["plain"] = dict(value=value, unit=UNIT, kernel_ms=kernel_s * 1e3)
+        al = time_alias_form(mt, wl, init, work, stream, id_offset)
+        al["value"] = _barrier_sum(al["muon_steps"], ws, dev) / _barrier_max(al["kernel_ms"] / 1e3, ws, dev)
+        al["workload"] = "config1 with the alias sampler (8 B column per draw) instead of the inverse CDF"
+        al["vs_inverse_cdf"] = al["value"] / value
+        forms["alias"] = al
         bt = time_batched_form(mt, stream, dev, n_inst=args.batch_instances, rank=rank,
                                separate=not args.no_separate)
         bt["value"] = _barrier_sum(bt["muon_steps"], ws, dev) / _barrier_max(bt["batched_ms"] / 1e3, ws, dev)

@@ -115,7 +115,23 @@ typedef struct mt_hist_desc {
     const double *weights;        /* host, [n_mat][n_pbin][nf][ntheta]                */
     const double *f_max;          /* host, [n_mat][n_pbin], > 0                       */
     const double *theta_max;      /* host, [n_mat][n_pbin], > 0                       */
+    int32_t sampler;              /* MT_SAMPLER_ICDF (0, default) or MT_SAMPLER_ALIAS */
+    int32_t reserved;             /* 0                                                */
 } mt_hist_desc;
+
+/* Samplers of a histogram cell from the draw w0 (Philox word 0).  Both use the
+ * integer masses m_c = T_c - T_{c-1} of the thresholds T_c = floor(2^32 S_c /
+ * S_total) (S_c the FP64 prefix sums of the weights, T_{ncell-1} = 2^32), so
+ * both draw from exactly one quantised distribution:
+ *  - MT_SAMPLER_ICDF: inverse CDF, cell = #{c < ncell-1 : T_c <= w0};
+ *  - MT_SAMPLER_ALIAS: Walker's alias method (Sec. Methodology, "The Alias
+ *    Method"), O(1): ncell = 2^n equiprobable columns, built by Vose's
+ *    construction in integers (small/large stacks filled in cell order, popped
+ *    from the top); column j = w0 >> (32-n) keeps its own cell when
+ *    (w0 << n) mod 2^32 < Prob_j and takes Alias_j otherwise.  Needs nf and
+ *    ntheta powers of two (MT_ERR_INVALID_ARG otherwise). */
+#define MT_SAMPLER_ICDF 0
+#define MT_SAMPLER_ALIAS 1
 
 /* Muon state, structure of arrays in device memory, caller-owned, updated in
  * place (Algorithm 1's inputs r and p).  Muon m has the global id

@@ -51,7 +51,11 @@ class mt_field_desc(C.Structure):
 class mt_hist_desc(C.Structure):
     _fields_ = [("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("p_lo", C.c_double), ("p_hi", C.c_double),
                 ("nf", C.c_int32), ("ntheta", C.c_int32), ("weights", C.c_void_p), ("f_max", C.c_void_p),
-                ("theta_max", C.c_void_p)]
+                ("theta_max", C.c_void_p), ("sampler", C.c_int32), ("reserved", C.c_int32)]
+
+
+MT_SAMPLER_ICDF, MT_SAMPLER_ALIAS = 0, 1
+SAMPLERS = {"icdf": MT_SAMPLER_ICDF, "alias": MT_SAMPLER_ALIAS}
 
 
 class mt_launch_cfg(C.Structure):
@@ -242,6 +246,7 @@ class _Descs:
         h.weights = arr(hist["weights"], np.float64).ctypes.data
         h.f_max = arr(hist["f_max"], np.float64).ctypes.data
         h.theta_max = arr(hist["theta_max"], np.float64).ctypes.data
+        h.sampler = SAMPLERS[hist.get("sampler", "icdf")]
         return h
 
 

@@ -47,9 +47,52 @@ static bool finite3(const double v[3])
 // their upper thresholds U_k form the pair list; the guide table over the
 // 2^gbits equal slices of the draw space stores either the answer cell (when
 // no threshold falls inside the slice) or the pair range to search.
-static mt_status build_tables(const mt_hist_desc *h, int gbits, std::vector<HistRec> &rec,
-                              std::vector<uint32_t> &guide, std::vector<uint2> &pairs)
+static int log2_exact(int64_t v)
 {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return ((int64_t)1 << b) == v ? b : -1;
+}
+
+// Alias columns of one histogram from its thresholds T (T[ncell-1] = 2^32):
+// the cells' integer masses T_c - T_{c-1} are dealt into ncell columns of
+// capacity 2^(32-n) by Vose's construction (small/large stacks filled in cell
+// order, popped from the top); column j keeps q_j of its own cell, Prob_j =
+// q_j 2^n (saturated at 2^32 - 1 for a full column), and takes the rest from
+// its alias.  Entries {Prob_j, alias cell encoded (a << 16) | b}.
+static void alias_columns(const std::vector<uint64_t> &T, int ncell, int ntheta, uint2 *out)
+{
+    const int n = log2_exact(ncell);
+    const uint64_t cap = 1ull << (32 - n);
+    std::vector<uint64_t> q(ncell);
+    std::vector<int> small, large;
+    small.reserve(ncell);
+    large.reserve(ncell);
+    uint64_t prev = 0;
+    for (int c = 0; c < ncell; ++c) {
+        const uint64_t t = std::max(T[c], prev);
+        q[c] = t - prev;
+        prev = t;
+        (q[c] < cap ? small : large).push_back(c);
+    }
+    auto enc = [ntheta](int c) { return ((uint32_t)(c / ntheta) << 16) | (uint32_t)(c % ntheta); };
+    while (!small.empty() && !large.empty()) {
+        const int sc = small.back();
+        small.pop_back();
+        const int lc = large.back();
+        large.pop_back();
+        out[sc] = make_uint2((uint32_t)(q[sc] << n), enc(lc));
+        q[lc] -= cap - q[sc];
+        (q[lc] < cap ? small : large).push_back(lc);
+    }
+    for (const int c : large) out[c] = make_uint2(0xFFFFFFFFu, enc(c));
+    for (const int c : small) out[c] = make_uint2(0xFFFFFFFFu, enc(c));   // not reached with exact masses
+}
+
+static mt_status build_tables(const mt_hist_desc *h, int gbits, std::vector<HistRec> &rec,
+                              std::vector<uint32_t> &guide, std::vector<uint2> &pairs, std::vector<uint2> &alias)
+{
+    const bool use_alias = h->sampler == MT_SAMPLER_ALIAS;
     const int ncell = h->nf * h->ntheta;
     const int64_t n_hist = (int64_t)h->n_mat * h->n_pbin;
     const int G = 1 << gbits;
@@ -58,8 +101,9 @@ static mt_status build_tables(const mt_hist_desc *h, int gbits, std::vector<Hist
     std::vector<uint64_t> U;
     std::vector<uint32_t> cells;
     rec.resize(n_hist);
-    guide.resize((size_t)n_hist * G);
+    guide.resize(use_alias ? 0 : (size_t)n_hist * G);
     pairs.clear();
+    alias.resize(use_alias ? (size_t)n_hist * ncell : 0);
     for (int64_t hi = 0; hi < n_hist; ++hi) {
         const double *w = h->weights + hi * ncell;
         double total = 0.0;
@@ -80,6 +124,14 @@ static mt_status build_tables(const mt_hist_desc *h, int gbits, std::vector<Hist
             T[j] = (uint64_t)std::floor(S / total * 4294967296.0);
         }
         T[ncell - 1] = 1ull << 32;
+        if (use_alias) {
+            alias_columns(T, ncell, h->ntheta, alias.data() + (size_t)hi * ncell);
+            rec[hi].guide_off = (uint32_t)(hi * ncell);
+            rec[hi].pair_off = 0;
+            rec[hi].fscale = (float)(h->f_max[hi] / h->nf);
+            rec[hi].tscale = (float)(h->theta_max[hi] / h->ntheta);
+            continue;
+        }
         U.clear();
         cells.clear();
         uint64_t prev = 0;
@@ -128,6 +180,14 @@ mt_status validate_hist(const mt_hist_desc *h)
     }
     if (h->nf < 1 || h->ntheta < 1 || (int64_t)h->nf * h->ntheta < 2 || (int64_t)h->nf * h->ntheta > MT_MAX_CELLS) {
         set_error("hist: nf*ntheta = %lld outside [2, %d]", (long long)h->nf * h->ntheta, MT_MAX_CELLS);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h->sampler != MT_SAMPLER_ICDF && h->sampler != MT_SAMPLER_ALIAS) {
+        set_error("hist: unknown sampler %d", h->sampler);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h->sampler == MT_SAMPLER_ALIAS && (log2_exact(h->nf) < 0 || log2_exact(h->ntheta) < 0)) {
+        set_error("hist: the alias sampler needs nf and ntheta powers of two (got %d x %d)", h->nf, h->ntheta);
         return MT_ERR_INVALID_ARG;
     }
     if (!(h->p_lo > 0.0) || !(h->p_hi > h->p_lo) || !std::isfinite(h->p_hi)) {
@@ -260,7 +320,8 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
     std::vector<HistRec> rec;
     std::vector<uint32_t> guide;
     std::vector<uint2> pairs;
-    mt_status st = build_tables(hd, gbits, rec, guide, pairs);
+    std::vector<uint2> alias;
+    mt_status st = build_tables(hd, gbits, rec, guide, pairs, alias);
     if (st != MT_OK) return st;
     std::vector<float2> e2(hd->n_pbin + 1);
     for (int k = 0; k <= hd->n_pbin; ++k) {
@@ -270,8 +331,15 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
         e2[k] = make_float2(a, b);
     }
     if ((st = upload(own, rec.data(), rec.size(), "histogram records", &w.hist)) != MT_OK) return st;
-    if ((st = upload(own, guide.data(), guide.size(), "guide tables", &w.guide)) != MT_OK) return st;
-    if ((st = upload(own, pairs.data(), pairs.size(), "threshold pairs", &w.pairs)) != MT_OK) return st;
+    w.sampler = hd->sampler;
+    if (hd->sampler == MT_SAMPLER_ALIAS) {
+        if ((st = upload(own, alias.data(), alias.size(), "alias tables", &w.alias)) != MT_OK) return st;
+        w.alias_bits = log2_exact((int64_t)hd->nf * hd->ntheta);
+        w.theta_bits = log2_exact(hd->ntheta);
+    } else {
+        if ((st = upload(own, guide.data(), guide.size(), "guide tables", &w.guide)) != MT_OK) return st;
+        if ((st = upload(own, pairs.data(), pairs.size(), "threshold pairs", &w.pairs)) != MT_OK) return st;
+    }
     if ((st = upload(own, e2.data(), e2.size(), "bin edges", &w.e2)) != MT_OK) return st;
     w.n_mat = hd->n_mat;
     w.n_pbin = hd->n_pbin;

@@ -75,6 +75,10 @@ struct WorldParams {
     int32_t nf;
     int32_t ntheta;
     int32_t gshift;
+    int32_t sampler;          // MT_SAMPLER_ICDF or MT_SAMPLER_ALIAS
+    const uint2 *alias;       // alias columns {Prob_j, alias cell (a << 16) | b}, at HistRec.guide_off
+    int32_t alias_bits;       // log2(nf * ntheta)
+    int32_t theta_bits;       // log2(ntheta)
     float log2_plo;
     float pbin_scale;   // n_pbin / log2(p_hi / p_lo)
 };

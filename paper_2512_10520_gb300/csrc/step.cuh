@@ -211,6 +211,17 @@ __device__ __forceinline__ uint32_t sample_cell(const uint32_t *guide, const uin
     return __ldg(&pairs[lo].y);
 }
 
+// Alias draw (Sec. Methodology, "The Alias Method"): one load of column
+// j = w0 >> (32 - n); the column's own cell when (w0 << n) mod 2^32 < Prob_j,
+// else its alias.  Returns the cell as (a << 16) | b.
+__device__ __forceinline__ uint32_t sample_alias(const uint2 *col, int nbits, int tbits, uint32_t w0)
+{
+    const uint32_t j = w0 >> (32 - nbits);
+    const uint2 e = __ldg(col + j);
+    if ((w0 << nbits) < e.x) return ((j >> tbits) << 16) | (j & ((1u << tbits) - 1u));
+    return e.y;
+}
+
 // sin(t) and 1 - cos(t).  For |t| <= 0.5 (every scattering angle of the
 // stored histograms in practice) the Maclaurin series, truncated after the
 // t^9 and t^10 terms (remainders below 2e-11 relative), evaluated in Horner
@@ -394,7 +405,9 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, id_lo, id_hi, (uint32_t)rp.instance), rp.key0, rp.key1);
         const uint4 hraw = __ldg(reinterpret_cast<const uint4 *>(w.hist + (mat - 1) * w.n_pbin + ib));
         const HistRec hr = {hraw.x, hraw.y, __uint_as_float(hraw.z), __uint_as_float(hraw.w)};
-        const uint32_t ab = sample_cell(w.guide + hr.guide_off, w.pairs + hr.pair_off, w.gshift, rnd.x);
+        const uint32_t ab = w.sampler == MT_SAMPLER_ALIAS
+                                ? sample_alias(w.alias + hr.guide_off, w.alias_bits, w.theta_bits, rnd.x)
+                                : sample_cell(w.guide + hr.guide_off, w.pairs + hr.pair_off, w.gshift, rnd.x);
         const float f = ((float)(ab >> 16) + u01(rnd.y)) * hr.fscale;
         const float th = ((float)(ab & 0xFFFFu) + u01(rnd.z)) * hr.tscale;
         const float phs = fmaf(6.283185307179586f, u01(rnd.w), -3.14159265358979f);   // phi - pi

@@ -100,3 +100,16 @@ def test_batch_host_errors(lib):
     assert st == B.MT_ERR_INVALID_ARG and "null batch" in mt.mt_last_error()
     st = lib.mt_batch_autotune(None, None, n, 0.02, 10, 1, 0, None, None)
     assert st == B.MT_ERR_INVALID_ARG
+
+
+def test_alias_sampler_needs_power_of_two_cells(lib):
+    from workloads import gen
+    h = gen.histogram_set(["iron"], n_pbin=2, nf=6, ntheta=4, n_samples=1000, cache=False)
+    geo = gen.geometry_config0()
+    geo["boxes"][0]["material"] = 1
+    geo["world_material"] = 0
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_create(geo, dict(kind="box"), dict(h, sampler="alias"))
+    assert e.value.status == B.MT_ERR_INVALID_ARG and "power" in mt.mt_last_error()
+    with pytest.raises(KeyError):
+        mt.mt_create(geo, dict(kind="box"), dict(h, sampler="walker"))
