@@ -39,7 +39,8 @@ class World(C.Structure):
     _fields_ = [
         ("geom_kind", C.c_int32), ("n_box", C.c_int32),
         ("box_lo", C.c_void_p), ("box_hi", C.c_void_p), ("box_mat", C.c_void_p),
-        ("box_block", C.c_void_p), ("box_B", C.c_void_p), ("world_mat", C.c_int32),
+        ("box_block", C.c_void_p), ("box_B", C.c_void_p), ("poly_z", C.c_void_p), ("poly_xy", C.c_void_p),
+        ("world_mat", C.c_int32),
         ("vox_dims", C.c_int32 * 3), ("vox_origin", C.c_double * 3), ("vox_spacing", C.c_double * 3),
         ("vox", C.c_void_p),
         ("x_max", C.c_double), ("y_max", C.c_double), ("z_max", C.c_double), ("p_min", C.c_double),
@@ -74,6 +75,8 @@ def lib():
             L.or_momentum_bin.restype = C.c_int32
             L.or_material.argtypes = [P, P, P]
             L.or_material.restype = C.c_int32
+            L.or_in_solid.argtypes = [P, C.c_int32, P]
+            L.or_in_solid.restype = C.c_int
             L.or_field.argtypes = [P, P, C.c_int32, P]
             L.or_field.restype = None
             L.or_scatter.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
@@ -200,6 +203,16 @@ class OracleWorld:
                 w.box_mat = _p(arr([b["material"] for b in boxes], np.int32))
                 w.box_block = _p(arr([b.get("block_id", -1) for b in boxes], np.int32))
                 w.box_B = _p(arr([b.get("B", [0, 0, 0]) for b in boxes], np.float64))
+        elif geometry["kind"] == "polyhedra":
+            solids = geometry["solids"]
+            w.geom_kind = 2
+            w.n_box = len(solids)
+            if solids:
+                w.poly_z = _p(arr([[s_["z0"], s_["z1"]] for s_ in solids], np.float64))
+                w.poly_xy = _p(arr([[s_["bottom"], s_["top"]] for s_ in solids], np.float64))
+                w.box_mat = _p(arr([s_["material"] for s_ in solids], np.int32))
+                w.box_block = _p(arr([s_.get("block_id", -1) for s_ in solids], np.int32))
+                w.box_B = _p(arr([s_.get("B", [0, 0, 0]) for s_ in solids], np.float64))
         elif geometry["kind"] == "voxels":
             w.geom_kind = 1
             w.n_box = 0

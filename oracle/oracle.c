@@ -13,7 +13,8 @@
  *   for k = steps_done .. max_steps-1:
  *     P = |p|; break with a status if P < p_min, z >= z_max, |x| >= x_max
  *       or |y| >= y_max                                   (termination test)
- *     M = GetMaterial(r)                                  (Sec. Simulation, item 1)
+ *     M = GetMaterial(r): first containing box or solid,  (Sec. Simulation, item 1;
+ *         or a voxel                                       solids by Eq. 2)
  *     if M is not vacuum:
  *       i = GetMomentumBin(P), log10 bins                 (Sec. Momentum binning)
  *       (w0..w3) = Philox4x32-10(key = seed, ctr = (k, id_lo, id_hi, instance))
@@ -60,13 +61,15 @@ enum { OR_ALIVE = 0, OR_STOPPED = 1, OR_EXIT_Z = 2, OR_EXIT_XY = 3, OR_MAX_STEPS
 
 typedef struct or_world {
     /* geometry */
-    int32_t geom_kind;          /* 0: ordered axis-aligned boxes, 1: voxel grid */
-    int32_t n_box;
+    int32_t geom_kind;          /* 0: ordered axis-aligned boxes, 1: voxel grid, 2: ordered solids */
+    int32_t n_box;              /* boxes, or solids (geom_kind 2) */
     const double *box_lo;       /* [n_box][3], half-open boxes lo <= r < hi */
     const double *box_hi;       /* [n_box][3] */
     const int32_t *box_mat;     /* [n_box] material id (0 = vacuum) */
     const int32_t *box_block;   /* [n_box] field-scale block id or -1 */
-    const double *box_B;        /* [n_box][3] uniform field inside the box (field_kind 1) */
+    const double *box_B;        /* [n_box][3] uniform field inside the box / solid (field_kind 1) */
+    const double *poly_z;       /* solids: [n_box][2] z0 < z1 */
+    const double *poly_xy;      /* solids: [n_box][2][4][2] bottom (z0) then top (z1) quadrilateral */
     int32_t world_mat;
     int32_t vox_dims[3];        /* nx, ny, nz */
     double vox_origin[3];
@@ -261,9 +264,44 @@ int32_t or_momentum_bin(double P, double p_lo, double p_hi, int32_t n_pbin)
 
 /* GetMaterial: first box (list order) with lo <= r < hi, else the world;
  * or the voxel holding r, else the world.  *box receives the box index or -1. */
+/* Containment in solid b (Sec. Simulation item 1, Eq. 2): the solid spans
+ * z0 <= z < z1; its cross-section at height z is the quadrilateral with
+ * vertices v_i = bottom_i + t (top_i - bottom_i), t = (z - z0) / (z1 - z0);
+ * with e_i = v_{i+1} - v_i (indices mod 4), the point is inside when every
+ * S_i = e_ix (y - v_iy) - e_iy (x - v_ix) has the same sign.  The vertices are
+ * counter-clockwise seen from +z, so that sign is non-negative: a point on an
+ * edge is inside. */
+int or_in_solid(const or_world *w, int32_t b, const double r[3])
+{
+    const double z0 = w->poly_z[2 * b], z1 = w->poly_z[2 * b + 1];
+    if (!(r[2] >= z0 && r[2] < z1)) return 0;
+    const double t = (r[2] - z0) / (z1 - z0);
+    const double *bot = w->poly_xy + 16 * (int64_t)b, *top = bot + 8;
+    double vx[4], vy[4];
+    for (int i = 0; i < 4; ++i) {
+        vx[i] = bot[2 * i] + t * (top[2 * i] - bot[2 * i]);
+        vy[i] = bot[2 * i + 1] + t * (top[2 * i + 1] - bot[2 * i + 1]);
+    }
+    for (int i = 0; i < 4; ++i) {
+        const int j = (i + 1) % 4;
+        const double ex = vx[j] - vx[i], ey = vy[j] - vy[i];
+        const double S = ex * (r[1] - vy[i]) - ey * (r[0] - vx[i]);
+        if (S < 0.0) return 0;
+    }
+    return 1;
+}
+
 int32_t or_material(const or_world *w, const double r[3], int32_t *box)
 {
     *box = -1;
+    if (w->geom_kind == 2) {
+        for (int32_t b = 0; b < w->n_box; ++b)
+            if (or_in_solid(w, b, r)) {
+                *box = b;
+                return w->box_mat[b];
+            }
+        return w->world_mat;
+    }
     if (w->geom_kind == 0) {
         for (int32_t b = 0; b < w->n_box; ++b) {
             const double *lo = w->box_lo + 3 * b, *hi = w->box_hi + 3 * b;

@@ -14,6 +14,8 @@ from .gen import (  # noqa: F401
     muons_config1,
     geometry_config0,
     geometry_config1,
+    geometry_tapered,
+    solid,
     field_map_config1,
     workload,
     batched_instances,

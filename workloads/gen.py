@@ -189,6 +189,40 @@ def geometry_config1() -> dict:
     return dict(kind="boxes", boxes=boxes, world_material=2, x_max=3.0, y_max=3.0, z_max=30.0, p_min=0.5)
 
 
+def solid(z0: float, z1: float, bottom, top, material: int, block_id: int = -1, B=(0.0, 0.0, 0.0)) -> dict:
+    """A solid of the polyhedra geometry: cross-section at height z interpolates the
+    counter-clockwise quadrilateral ``bottom`` (at z0) to ``top`` (at z1), vertex by vertex."""
+    return dict(z0=float(z0), z1=float(z1), bottom=[list(map(float, v)) for v in bottom],
+                top=[list(map(float, v)) for v in top], material=int(material), block_id=int(block_id),
+                B=list(map(float, B)))
+
+
+def _trapezoid(hx_lo: float, hx_hi: float, hy: float, dx: float = 0.0):
+    """Counter-clockwise quadrilateral: half-width hx_lo at y = -hy, hx_hi at y = +hy, shifted by dx."""
+    return [(-hx_lo + dx, -hy), (hx_lo + dx, -hy), (hx_hi + dx, hy), (-hx_hi + dx, hy)]
+
+
+def geometry_tapered() -> dict:
+    """Config1's layout with tapered magnets (the paper's convex-polyhedron geometry,
+    Sec. Simulation item 1): six iron solids in z in [4.5k, 4.5k + 4], whose
+    cross-sections are trapezoids (wider at -y than at +y) that narrow along z
+    and shift sideways by 2 cm per block, B_y = +-1.7 T alternating; the concrete
+    wall z in [27, 29], |x|, |y| <= 3 as a solid with a rectangular section.
+    Materials: 1 iron, 2 air (world), 3 concrete.  World |x|, |y| < 3 m, z < 30 m."""
+    solids = []
+    for k, z0 in enumerate(MAGNET_Z0):
+        s = 1.0 if k % 2 == 0 else -1.0
+        h0 = 0.75 - 0.04 * k
+        h1 = h0 - 0.12
+        bot = _trapezoid(h0, h0 - 0.10, 0.60, 0.02 * k)
+        top = _trapezoid(h1, h1 - 0.08, 0.55, 0.02 * k + 0.02)
+        solids.append(solid(z0, z0 + MAGNET_LEN, bot, top, 1, k, (0.0, 1.7 * s, 0.0)))
+    wall = _trapezoid(3.0, 3.0, 3.0)
+    solids.append(solid(27.0, 29.0, wall, wall, 3, -1))
+    return dict(kind="polyhedra", solids=solids, world_material=2, x_max=3.0, y_max=3.0, z_max=30.0, p_min=0.5,
+                hash_dims=[8, 8, 64])
+
+
 def _smooth_box(u: np.ndarray, a: float, b: float, w: float) -> np.ndarray:
     return 0.5 * (np.tanh((u - a) / w) - np.tanh((u - b) / w))
 
@@ -319,6 +353,7 @@ def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = N
       iron+air histograms (64 log bins on 1-400 GeV, 128x64 cells, 1e6 samples each).
     * ``config1``: 1e6 muons through the six-magnet shield and concrete wall, trilinear
       200x200x600 field map, iron/air/concrete histograms, 1500 steps.
+    * ``config1p``: config1 with tapered magnets (``geometry_tapered``, polyhedra).
     * ``config4``: config1's spectrum and geometry with a 400x400x1200 map and
       4 materials x 128 bins x 256x128 cells (a 4th material, lead, is present in the
       table set but not placed in the geometry).
@@ -336,6 +371,12 @@ def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = N
         h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
         mu = muons_config1(n or 1_000_000)
         geo = geometry_config1()
+        fld = dict(kind="box") if field == "box" else field_map_config1()
+        return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
+    if name == "config1p":
+        h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
+        mu = muons_config1(n or 1_000_000)
+        geo = geometry_tapered()
         fld = dict(kind="box") if field == "box" else field_map_config1()
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
     if name == "config4":
