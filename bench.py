@@ -247,6 +247,52 @@ def time_alias_form(mt, wl, init, work, stream, id_offset, reps=3):
                 roofline_frac=BYTES_PER_STEP * steps / t / 1e9 / _peaks()[0]["hbm_gbs"])
 
 
+def _time_world(mt, wl, geometry, dev, stream, reps, id_offset):
+    import torch
+    from paper_2512_10520_gb300.api import empty_like_soa
+    init = mt.muons_to_device(wl.muons, device=dev)
+    work = empty_like_soa(wl.n, device=dev)
+    times = []
+    with mt.World(geometry, wl.field, wl.hist) as world, torch.cuda.stream(stream):
+        for r in range(reps + 1):
+            for k in work:
+                work[k].copy_(init[k], non_blocking=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                times.append(a.elapsed_time(b) / 1e3)
+        return float(np.mean(times)), float(work["steps"].sum().item())
+
+
+def boxes_as_solids(geo):
+    """The same boxes as polyhedron solids with equal rectangular ends."""
+    from workloads import gen
+    solids = []
+    for b in geo["boxes"]:
+        (x0, y0, z0), (x1, y1, z1) = b["lo"], b["hi"]
+        q = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+        solids.append(gen.solid(z0, z1, q, q, b["material"], b.get("block_id", -1), b.get("B", (0, 0, 0))))
+    return dict(geo, kind="polyhedra", solids=solids, boxes=None)
+
+
+def time_polyhedra_form(mt, dev, stream, n=None, reps=3, id_offset=0):
+    """config1p: config1 with tapered magnets as convex solids (Sec. Simulation
+    item 1, Eq. 2), same field map and spectrum.  Also timed: config1's own
+    boxes given as solids with rectangular ends (same results as the boxes, so
+    the difference to the plain form is the cost of the solid lookup alone)."""
+    from workloads import gen
+    wl = gen.workload("config1p", n=n)
+    t, steps = _time_world(mt, wl, wl.geometry, dev, stream, reps, id_offset)
+    w1 = gen.workload("config1", n=n)
+    t1, steps1 = _time_world(mt, w1, boxes_as_solids(w1.geometry), dev, stream, reps, id_offset)
+    return dict(value=steps / t, unit=UNIT, kernel_ms=1e3 * t, muon_steps=steps,
+                roofline_frac=BYTES_PER_STEP * steps / t / 1e9 / _peaks()[0]["hbm_gbs"],
+                config1_as_solids=dict(value=steps1 / t1, kernel_ms=1e3 * t1, muon_steps=steps1))
+
+
 def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True, block=0, spp=0):
     """Batched form (config2): n_inst worlds, each its own 64x64x512 voxel geometry
     and 100x100x300 field map, one shared histogram set, instance sizes log-uniform
@@ -484,6 +530,12 @@ def run_mine(args):
         if rank == 0:
             print(json.dumps({"form": "c4", "clocks": clk.summary(), **res}))
         return 0
+    if args.only == "polyhedra":
+        with ClockSampler(local) as clk:
+            res = time_polyhedra_form(mt, dev, torch.cuda.Stream(device=dev), n=args.muons, id_offset=rank * (args.muons or 0))
+        if rank == 0:
+            print(json.dumps({"form": "polyhedra", "clocks": clk.summary(), **res}))
+        return 0
     if args.batch_only:
         with ClockSampler(local) as clk:
             res = time_batched_form(mt, torch.cuda.Stream(device=dev), dev, n_inst=args.batch_instances,
@@ -608,6 +660,12 @@ def run_mine(args):
         al["workload"] = "config1 with the alias sampler (8 B column per draw) instead of the inverse CDF"
         al["vs_inverse_cdf"] = al["value"] / value
         forms["alias"] = al
+        ph = time_polyhedra_form(mt, dev, stream, n=args.muons, id_offset=id_offset)
+        ph["value"] = _barrier_sum(ph["muon_steps"], ws, dev) / _barrier_max(ph["kernel_ms"] / 1e3, ws, dev)
+        ph["workload"] = ("config1p: config1 with the six magnets as tapered convex solids (trapezoid sections "
+                          "narrowing along z), spatial-hash pruning, 200x200x600 map")
+        ph["vs_boxes"] = ph["value"] / value
+        forms["polyhedra"] = ph
         bt = time_batched_form(mt, stream, dev, n_inst=args.batch_instances, rank=rank,
                                separate=not args.no_separate)
         bt["value"] = _barrier_sum(bt["muon_steps"], ws, dev) / _barrier_max(bt["batched_ms"] / 1e3, ws, dev)
@@ -688,6 +746,7 @@ def main(argv=None):
     ap.add_argument("--batch-spp", type=int, default=0, help="batched form: steps per pass")
     ap.add_argument("--adjoint-only", action="store_true", help="run only the fwd+adjoint forms (one JSON line)")
     ap.add_argument("--no-tape", action="store_true", help="fwd+adjoint form: skip the full-tape variant")
+    ap.add_argument("--only", default=None, choices=["polyhedra"], help="run only this form (one JSON line)")
     ap.add_argument("--no-separate", action="store_true",
                     help="batched form: skip timing one mt_transport call per instance")
     args = ap.parse_args(argv)

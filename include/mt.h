@@ -55,7 +55,7 @@ enum {
     MT_INVALID = 5     /* non-finite position or momentum on entry                */
 };
 
-enum { MT_GEOM_BOXES = 0, MT_GEOM_VOXELS = 1 };
+enum { MT_GEOM_BOXES = 0, MT_GEOM_VOXELS = 1, MT_GEOM_POLYHEDRA = 2 };
 enum { MT_FIELD_NONE = 0, MT_FIELD_BOX = 1, MT_FIELD_MAP = 2 };
 
 #define MT_MAX_BOXES 32
@@ -76,9 +76,27 @@ typedef struct mt_box {
     double B[3];
 } mt_box;
 
+/* A solid of the convex-polyhedron geometry (Sec. Simulation item 1): it spans
+ * z0 <= z < z1, and its cross-section at height z is the quadrilateral whose
+ * vertices move linearly from bottom[i] (at z0) to top[i] (at z1), with
+ * t = (z - z0) / (z1 - z0).  Both quadrilaterals are strictly convex and
+ * counter-clockwise seen from +z.  A point is inside when, for every edge
+ * e_i = v_{i+1} - v_i of its slice, S_i = e_ix (y - v_iy) - e_iy (x - v_ix) >= 0
+ * (Eq. 2: all signs consistent; points on the side faces are inside).  Solids
+ * are tested in list order and the first containing one gives the material;
+ * material, block_id and B as for mt_box. */
+typedef struct mt_polyhedron {
+    double z0, z1;
+    double bottom[4][2];
+    double top[4][2];
+    int32_t material;
+    int32_t block_id;
+    double B[3];
+} mt_polyhedron;
+
 /* Geometry and the break conditions of Algorithm 1 (inputs p_min, r_max). */
 typedef struct mt_geometry_desc {
-    int32_t kind;                 /* MT_GEOM_BOXES or MT_GEOM_VOXELS                     */
+    int32_t kind;                 /* MT_GEOM_BOXES, MT_GEOM_VOXELS or MT_GEOM_POLYHEDRA  */
     int32_t n_boxes;              /* boxes: 0..MT_MAX_BOXES                              */
     const mt_box *boxes;          /* host, n_boxes entries                               */
     int32_t world_material;       /* material outside every box / voxel grid             */
@@ -88,6 +106,9 @@ typedef struct mt_geometry_desc {
     const uint8_t *voxels;        /* host, [nz][ny][nx] material ids                     */
     double x_max, y_max, z_max;   /* stop when |x| >= x_max, |y| >= y_max or z >= z_max  */
     double p_min;                 /* stop when |p| < p_min                               */
+    const mt_polyhedron *polys;   /* polyhedra: host, n_polys entries                    */
+    int32_t n_polys;              /* polyhedra: 0..MT_MAX_BOXES                          */
+    int32_t reserved;             /* 0                                                   */
 } mt_geometry_desc;
 
 /* Magnetic field.  MT_FIELD_MAP: node-based map, node (i,j,k) at

@@ -19,7 +19,7 @@ from . import _build
 
 MT_OK, MT_ERR_INVALID_ARG, MT_ERR_CUDA, MT_ERR_OOM, MT_ERR_TIMEOUT, MT_ERR_TABLE, MT_ERR_DEVICE = range(7)
 MT_ALIVE, MT_STOPPED, MT_EXIT_Z, MT_EXIT_XY, MT_MAX_STEPS, MT_INVALID = range(6)
-MT_GEOM_BOXES, MT_GEOM_VOXELS = 0, 1
+MT_GEOM_BOXES, MT_GEOM_VOXELS, MT_GEOM_POLYHEDRA = 0, 1, 2
 MT_FIELD_NONE, MT_FIELD_BOX, MT_FIELD_MAP = 0, 1, 2
 STATUS_NAMES = {0: "MT_OK", 1: "MT_ERR_INVALID_ARG", 2: "MT_ERR_CUDA", 3: "MT_ERR_OOM", 4: "MT_ERR_TIMEOUT",
                 5: "MT_ERR_TABLE", 6: "MT_ERR_DEVICE"}
@@ -36,11 +36,18 @@ class mt_box(C.Structure):
                 ("block_id", C.c_int32), ("B", C.c_double * 3)]
 
 
+class mt_polyhedron(C.Structure):
+    _fields_ = [("z0", C.c_double), ("z1", C.c_double), ("bottom", (C.c_double * 2) * 4),
+                ("top", (C.c_double * 2) * 4), ("material", C.c_int32), ("block_id", C.c_int32),
+                ("B", C.c_double * 3)]
+
+
 class mt_geometry_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_boxes", C.c_int32), ("boxes", C.POINTER(mt_box)),
                 ("world_material", C.c_int32), ("vox_dims", C.c_int32 * 3), ("vox_origin", C.c_double * 3),
                 ("vox_spacing", C.c_double * 3), ("voxels", C.c_void_p), ("x_max", C.c_double),
-                ("y_max", C.c_double), ("z_max", C.c_double), ("p_min", C.c_double)]
+                ("y_max", C.c_double), ("z_max", C.c_double), ("p_min", C.c_double),
+                ("polys", C.POINTER(mt_polyhedron)), ("n_polys", C.c_int32), ("reserved", C.c_int32)]
 
 
 class mt_field_desc(C.Structure):
@@ -209,6 +216,21 @@ class _Descs:
                 barr[i].B[:] = list(map(float, b.get("B", [0.0, 0.0, 0.0])))
             keep.append(barr)
             g.boxes = C.cast(barr, C.POINTER(mt_box))
+        elif geometry["kind"] == "polyhedra":
+            solids = geometry["solids"]
+            g.kind = MT_GEOM_POLYHEDRA
+            g.n_polys = len(solids)
+            parr = (mt_polyhedron * max(1, len(solids)))()
+            for i, sd in enumerate(solids):
+                parr[i].z0, parr[i].z1 = float(sd["z0"]), float(sd["z1"])
+                for v in range(4):
+                    parr[i].bottom[v][:] = list(map(float, sd["bottom"][v]))
+                    parr[i].top[v][:] = list(map(float, sd["top"][v]))
+                parr[i].material = int(sd["material"])
+                parr[i].block_id = int(sd.get("block_id", -1))
+                parr[i].B[:] = list(map(float, sd.get("B", [0.0, 0.0, 0.0])))
+            keep.append(parr)
+            g.polys = C.cast(parr, C.POINTER(mt_polyhedron))
         elif geometry["kind"] == "voxels":
             vox = arr(geometry["voxels"], np.uint8)
             nz, ny, nx = vox.shape

@@ -315,7 +315,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     if (scat) scatter_fp32(p, f, th, cphi, sphi, ps);
     int blk = -1;
     float sc[3] = {1.0f, 1.0f, 1.0f};
-    if (GEOM == MT_GEOM_BOXES && FIELD != MT_FIELD_NONE && box >= 0) {
+    if (GEOM != MT_GEOM_VOXELS && FIELD != MT_FIELD_NONE && box >= 0) {
         blk = sw.block[box];
         if (blk >= 0) {
             sc[0] = sw.alpha[0][blk];
@@ -437,7 +437,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
 template <int GEOM, int FIELD, bool FWD>
-__global__ void __launch_bounds__(kBlock, MT_PASS_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
               const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
               unsigned long long *tape_off, int64_t region_cap, unsigned int *flag)
@@ -717,13 +717,15 @@ __global__ void alpha_out(const double *src, float *dst, int m, const unsigned i
     if (t < m) dst[t] = (flag && *flag) ? __int_as_float(0x7FC00000) : (float)src[t];
 }
 
+#define MT_DISPATCH_FIELDS(FN, G, ...)                                          \
+    (w.field_kind == MT_FIELD_MAP   ? FN<G, MT_FIELD_MAP>(__VA_ARGS__)           \
+     : w.field_kind == MT_FIELD_BOX ? FN<G, MT_FIELD_BOX>(__VA_ARGS__)           \
+                                    : FN<G, MT_FIELD_NONE>(__VA_ARGS__))
 #define MT_DISPATCH(FN, ...)                                                           \
-    (w.geom_kind == MT_GEOM_BOXES                                                      \
-         ? (w.field_kind == MT_FIELD_MAP   ? FN<MT_GEOM_BOXES, MT_FIELD_MAP>(__VA_ARGS__) \
-            : w.field_kind == MT_FIELD_BOX ? FN<MT_GEOM_BOXES, MT_FIELD_BOX>(__VA_ARGS__) \
-                                           : FN<MT_GEOM_BOXES, MT_FIELD_NONE>(__VA_ARGS__)) \
-         : (w.field_kind == MT_FIELD_MAP ? FN<MT_GEOM_VOXELS, MT_FIELD_MAP>(__VA_ARGS__)   \
-                                         : FN<MT_GEOM_VOXELS, MT_FIELD_NONE>(__VA_ARGS__)))
+    (w.geom_kind == MT_GEOM_BOXES       ? MT_DISPATCH_FIELDS(FN, MT_GEOM_BOXES, __VA_ARGS__)     \
+     : w.geom_kind == MT_GEOM_POLYHEDRA ? MT_DISPATCH_FIELDS(FN, MT_GEOM_POLYHEDRA, __VA_ARGS__) \
+     : (w.field_kind == MT_FIELD_MAP ? FN<MT_GEOM_VOXELS, MT_FIELD_MAP>(__VA_ARGS__)            \
+                                     : FN<MT_GEOM_VOXELS, MT_FIELD_NONE>(__VA_ARGS__)))
 
 }  // namespace mt
 

@@ -248,6 +248,31 @@ mt_status validate_geometry(const mt_geometry_desc *g, int n_mat)
                 set_error("geometry: voxel %lld material %d > n_mat", (long long)i, g->voxels[i]);
                 return MT_ERR_INVALID_ARG;
             }
+    } else if (g->kind == MT_GEOM_POLYHEDRA) {
+        if (g->n_polys < 0 || g->n_polys > MT_MAX_BOXES || (g->n_polys > 0 && !g->polys)) {
+            set_error("geometry: n_polys %d outside [0, %d] or null polys", g->n_polys, MT_MAX_BOXES);
+            return MT_ERR_INVALID_ARG;
+        }
+        for (int b = 0; b < g->n_polys; ++b) {
+            const mt_polyhedron &P = g->polys[b];
+            bool ok = std::isfinite(P.z0) && std::isfinite(P.z1) && P.z1 > P.z0 && finite3(P.B) &&
+                      P.material >= 0 && P.material <= n_mat && P.block_id >= -1 && P.block_id < MT_MAX_BOXES;
+            for (int end = 0; end < 2 && ok; ++end) {
+                const double(*q)[2] = end ? P.top : P.bottom;
+                for (int i = 0; i < 4 && ok; ++i) {
+                    const int j = (i + 1) % 4, k = (i + 2) % 4;
+                    ok = std::isfinite(q[i][0]) && std::isfinite(q[i][1]);
+                    // strictly convex and counter-clockwise: every turn is to the left
+                    const double c = (q[j][0] - q[i][0]) * (q[k][1] - q[j][1]) - (q[j][1] - q[i][1]) * (q[k][0] - q[j][0]);
+                    ok = ok && c > 0.0;
+                }
+            }
+            if (!ok) {
+                set_error("geometry: solid %d invalid (z0 < z1, strictly convex counter-clockwise quadrilaterals, "
+                          "material %d, block %d)", b, P.material, P.block_id);
+                return MT_ERR_INVALID_ARG;
+            }
+        }
     } else {
         set_error("geometry: unknown kind %d", g->kind);
         return MT_ERR_INVALID_ARG;
@@ -274,8 +299,8 @@ mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g)
                 return MT_ERR_INVALID_ARG;
             }
     } else if (f->kind == MT_FIELD_BOX) {
-        if (g->kind != MT_GEOM_BOXES) {
-            set_error("field: per-box field needs box geometry");
+        if (g->kind == MT_GEOM_VOXELS) {
+            set_error("field: per-box field needs box or polyhedron geometry");
             return MT_ERR_INVALID_ARG;
         }
     } else if (f->kind != MT_FIELD_NONE) {
@@ -351,6 +376,111 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
     return MT_OK;
 }
 
+// Smallest value over t in [0, 1] of S_i(c, t) for edge i of solid P at the
+// point c, with the slice interpolated linearly in t (Eq. 2's S_i is then a
+// quadratic in t).
+static double edge_min_over_z(const mt_polyhedron &P, int i, const double c[2])
+{
+    const int j = (i + 1) % 4;
+    const double e0x = P.bottom[j][0] - P.bottom[i][0], e0y = P.bottom[j][1] - P.bottom[i][1];
+    const double e1x = P.top[j][0] - P.top[i][0], e1y = P.top[j][1] - P.top[i][1];
+    const double dex = e1x - e0x, dey = e1y - e0y;
+    const double dvx = P.top[i][0] - P.bottom[i][0], dvy = P.top[i][1] - P.bottom[i][1];
+    const double d0x = c[0] - P.bottom[i][0], d0y = c[1] - P.bottom[i][1];
+    const double A = e0x * d0y - e0y * d0x;
+    const double B = dex * d0y - e0x * dvy - dey * d0x + e0y * dvx;
+    const double C = -dex * dvy + dey * dvx;
+    double m = std::min(A, A + B + C);
+    if (C > 0.0) {
+        const double t = -B / (2.0 * C);
+        if (t > 0.0 && t < 1.0) m = std::min(m, A + t * (B + t * C));
+    }
+    return m;
+}
+
+// An axis-aligned rectangle inside every slice of solid P, shrunk by `margin`
+// on each side: the largest rectangle centred on the mean of the eight
+// vertices, with the half-widths of the narrower end scaled by s, for which
+// every edge's S_i stays positive at all four corners and every z (checked
+// with edge_min_over_z; S_i is linear in the point, so the corners bound the
+// rectangle).  Empty (lo > hi) when no s in [0, 1] passes.
+static void inner_box(const mt_polyhedron &P, double margin, double out[4])
+{
+    double cx = 0.0, cy = 0.0, hx = 1e300, hy = 1e300;
+    for (int end = 0; end < 2; ++end) {
+        const double(*v)[2] = end ? P.top : P.bottom;
+        double x0 = v[0][0], x1 = v[0][0], y0 = v[0][1], y1 = v[0][1];
+        for (int i = 0; i < 4; ++i) {
+            cx += v[i][0] / 8.0;
+            cy += v[i][1] / 8.0;
+            x0 = std::min(x0, v[i][0]);
+            x1 = std::max(x1, v[i][0]);
+            y0 = std::min(y0, v[i][1]);
+            y1 = std::max(y1, v[i][1]);
+        }
+        hx = std::min(hx, 0.5 * (x1 - x0));
+        hy = std::min(hy, 0.5 * (y1 - y0));
+    }
+    auto ok = [&](double s) {
+        const double r[4] = {cx - s * hx - margin, cx + s * hx + margin, cy - s * hy - margin, cy + s * hy + margin};
+        for (int i = 0; i < 4; ++i)
+            for (int k = 0; k < 4; ++k) {
+                const double c[2] = {r[k & 1], r[2 + (k >> 1)]};
+                if (!(edge_min_over_z(P, i, c) > 0.0)) return false;
+            }
+        return true;
+    };
+    double lo = 0.0, hi = 1.0;
+    if (!ok(0.0)) {
+        out[0] = 1.0;
+        out[1] = -1.0;
+        out[2] = 1.0;
+        out[3] = -1.0;
+        return;
+    }
+    for (int it = 0; it < 40; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        (ok(mid) ? lo : hi) = mid;
+    }
+    out[0] = cx - lo * hx;
+    out[1] = cx + lo * hx;
+    out[2] = cy - lo * hy;
+    out[3] = cy + lo * hy;
+}
+
+// z-slab candidate index of boxes or solids with z ranges [zlo_b, zhi_b):
+// slab s of kZSlabs over the union of the ranges holds every volume whose z
+// range meets the slab or its two neighbours (the slab of a point is computed
+// in FP32 and may be off by one near a slab face; the exact test decides).
+static mt_status build_zslabs(const double *zlo_b, const double *zhi_b, int n, WorldParams &w, DevOwner &own)
+{
+    std::vector<uint32_t> zmask(kZSlabs, 0u);
+    double zlo = 0.0, zhi = 1.0;
+    if (n > 0) {
+        zlo = zlo_b[0];
+        zhi = zhi_b[0];
+        for (int b = 1; b < n; ++b) {
+            zlo = std::min(zlo, zlo_b[b]);
+            zhi = std::max(zhi, zhi_b[b]);
+        }
+        if (!(zhi > zlo)) zhi = zlo + 1.0;
+    }
+    const double dz = (zhi - zlo) / kZSlabs;
+    for (int b = 0; b < n; ++b) {
+        if (!(zhi_b[b] > zlo_b[b])) continue;   // empty: never contains a point
+        int s0 = (int)std::floor((zlo_b[b] - zlo) / dz) - 1;
+        int s1 = (int)std::floor((zhi_b[b] - zlo) / dz) + 1;
+        s0 = std::max(s0, 0);
+        s1 = std::min(s1, kZSlabs - 1);
+        for (int sl = s0; sl <= s1; ++sl) zmask[sl] |= 1u << b;
+    }
+    mt_status st = upload(own, zmask.data(), zmask.size(), "z-slab index", &w.zmask);
+    if (st != MT_OK) return st;
+    w.zslab_lo = (float)zlo;
+    w.zslab_inv = (float)(1.0 / dz);
+    return MT_OK;
+}
+
 // Geometry and world bounds (validated) into w.
 mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &own)
 {
@@ -377,32 +507,97 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
         }
         w.n_box = g->n_boxes;
         if ((st = upload(own, boxes.data(), boxes.size(), "boxes", &w.boxes)) != MT_OK) return st;
-        // z-slab candidate index: slab s holds every box whose z range meets the
-        // slab or its two neighbours (the slab of a point is computed in FP32 and
-        // may be off by one near a slab face; the exact box test decides).
-        std::vector<uint32_t> zmask(kZSlabs, 0u);
-        double zlo = 0.0, zhi = 1.0;
-        if (g->n_boxes > 0) {
-            zlo = g->boxes[0].lo[2];
-            zhi = g->boxes[0].hi[2];
-            for (int b = 1; b < g->n_boxes; ++b) {
-                zlo = std::min(zlo, g->boxes[b].lo[2]);
-                zhi = std::max(zhi, g->boxes[b].hi[2]);
-            }
-            if (!(zhi > zlo)) zhi = zlo + 1.0;
-        }
-        const double dz = (zhi - zlo) / kZSlabs;
+        std::vector<double> zlo(g->n_boxes), zhi(g->n_boxes);
         for (int b = 0; b < g->n_boxes; ++b) {
-            if (!(g->boxes[b].hi[2] > g->boxes[b].lo[2])) continue;   // empty box: never contains a point
-            int s0 = (int)std::floor((g->boxes[b].lo[2] - zlo) / dz) - 1;
-            int s1 = (int)std::floor((g->boxes[b].hi[2] - zlo) / dz) + 1;
-            s0 = std::max(s0, 0);
-            s1 = std::min(s1, kZSlabs - 1);
-            for (int sl = s0; sl <= s1; ++sl) zmask[sl] |= 1u << b;
+            zlo[b] = g->boxes[b].lo[2];
+            zhi[b] = g->boxes[b].hi[2];
         }
-        if ((st = upload(own, zmask.data(), zmask.size(), "z-slab index", &w.zmask)) != MT_OK) return st;
-        w.zslab_lo = (float)zlo;
-        w.zslab_inv = (float)(1.0 / dz);
+        if ((st = build_zslabs(zlo.data(), zhi.data(), g->n_boxes, w, own)) != MT_OK) return st;
+    } else if (g->kind == MT_GEOM_POLYHEDRA) {
+        // Per solid:
+        //  - a DevBox record with the bounding box (x, y grown by 1e-4 m, z exactly
+        //    [z0, z1)), material, block and field, staged into shared memory and
+        //    indexed by the z-slab grid like boxes;
+        //  - the inner rectangle (shared memory), a rectangle inside every slice,
+        //    1e-4 m clear of the sides;
+        //  - five float4 for the FP32 side test: {z0 hi, z0 lo, 1/(z1 - z0), bound},
+        //    {bx0, by0, bx1, by1}, {bx2, by2, bx3, by3} (bottom vertices),
+        //    {dx0, dy0, dx1, dy1}, {dx2, dy2, dx3, dy3} (top - bottom), and a spare;
+        //  - the FP64 data z0, z1, bottom[4][2], top[4][2] for undecided tests.
+        const int n = g->n_polys;
+        const double margin = 1e-4;
+        std::vector<DevBox> recs(n);
+        std::vector<float4> pf((size_t)n * 6), pin(n);
+        std::vector<double> pd((size_t)n * 18), zlo(n), zhi(n);
+        for (int b = 0; b < n; ++b) {
+            const mt_polyhedron &P = g->polys[b];
+            double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300, M1 = 0.0, M2 = 0.0, E = 0.0;
+            for (int end = 0; end < 2; ++end) {
+                const double(*v)[2] = end ? P.top : P.bottom;
+                for (int i = 0; i < 4; ++i) {
+                    const int j = (i + 1) % 4;
+                    x0 = std::min(x0, v[i][0]);
+                    x1 = std::max(x1, v[i][0]);
+                    y0 = std::min(y0, v[i][1]);
+                    y1 = std::max(y1, v[i][1]);
+                    M1 = std::max(M1, std::max(std::fabs(v[i][0]), std::fabs(v[i][1])));
+                    E = std::max(E, std::fabs(v[j][0] - v[i][0]) + std::fabs(v[j][1] - v[i][1]));
+                }
+            }
+            for (int i = 0; i < 4; ++i)
+                for (int c = 0; c < 2; ++c) M2 = std::max(M2, std::fabs(P.top[i][c] - P.bottom[i][c]));
+            DevBox &d = recs[b];
+            memset(&d, 0, sizeof(d));
+            const double lo3[3] = {x0 - margin, y0 - margin, P.z0}, hi3[3] = {x1 + margin, y1 + margin, P.z1};
+            for (int a = 0; a < 3; ++a) {
+                split(lo3[a], d.lo_hi[a], d.lo_lo[a]);
+                split(hi3[a], d.hi_hi[a], d.hi_lo[a]);
+                d.B[a] = (float)P.B[a];
+            }
+            d.material = P.material;
+            d.block = P.block_id;
+            zlo[b] = P.z0;
+            zhi[b] = P.z1;
+            // error bound of the FP32 side test (step.cuh: in_solid_sides):
+            // 100 eps (E + 2M)(D + 2M), E the largest |e_x| + |e_y| of an edge at
+            // either end (edges move linearly in z), D the largest |dx| + |dy|
+            // over the bounding box, M = M1 + M2
+            const double M = M1 + M2;
+            const double D = (x1 - x0) + (y1 - y0) + 4.0 * margin;
+            const double bound = 100.0 * std::ldexp(1.0, -24) * (E + 2.0 * M) * (D + 2.0 * M);
+            float z0h, z0l;
+            split(P.z0, z0h, z0l);
+            float bv[8], dv[8];
+            for (int i = 0; i < 4; ++i)
+                for (int c = 0; c < 2; ++c) {
+                    bv[2 * i + c] = (float)P.bottom[i][c];
+                    dv[2 * i + c] = (float)(P.top[i][c] - P.bottom[i][c]);
+                }
+            float4 *q = &pf[(size_t)b * 6];
+            q[0] = make_float4(z0h, z0l, (float)(1.0 / (P.z1 - P.z0)), (float)(bound * (1.0 + 1e-6)));
+            q[1] = make_float4(bv[0], bv[1], bv[2], bv[3]);
+            q[2] = make_float4(bv[4], bv[5], bv[6], bv[7]);
+            q[3] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+            q[4] = make_float4(dv[4], dv[5], dv[6], dv[7]);
+            q[5] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            double ib[4];
+            inner_box(P, margin, ib);
+            pin[b] = make_float4((float)ib[0], (float)ib[1], (float)ib[2], (float)ib[3]);
+            double *r = &pd[(size_t)b * 18];
+            r[0] = P.z0;
+            r[1] = P.z1;
+            for (int i = 0; i < 4; ++i)
+                for (int c = 0; c < 2; ++c) {
+                    r[2 + 2 * i + c] = P.bottom[i][c];
+                    r[10 + 2 * i + c] = P.top[i][c];
+                }
+        }
+        w.n_box = n;
+        if ((st = upload(own, recs.data(), recs.size(), "solid records", &w.boxes)) != MT_OK) return st;
+        if ((st = upload(own, pf.data(), pf.size(), "solids", &w.poly)) != MT_OK) return st;
+        if ((st = upload(own, pin.data(), pin.size(), "solid inner rectangles", &w.pinner)) != MT_OK) return st;
+        if ((st = upload(own, pd.data(), pd.size(), "solids (FP64)", &w.poly64)) != MT_OK) return st;
+        if ((st = build_zslabs(zlo.data(), zhi.data(), n, w, own)) != MT_OK) return st;
     } else {
         const size_t nv = (size_t)g->vox_dims[0] * g->vox_dims[1] * g->vox_dims[2];
         if ((st = upload(own, g->voxels, nv, "voxels", &w.vox)) != MT_OK) return st;

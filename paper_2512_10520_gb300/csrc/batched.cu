@@ -321,6 +321,11 @@ static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, co
         if (b->field_kind == MT_FIELD_BOX) return run_batch<MT_GEOM_BOXES, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st);
         return run_batch<MT_GEOM_BOXES, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
     }
+    if (b->geom_kind == MT_GEOM_POLYHEDRA) {
+        if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_POLYHEDRA, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
+        if (b->field_kind == MT_FIELD_BOX) return run_batch<MT_GEOM_POLYHEDRA, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st);
+        return run_batch<MT_GEOM_POLYHEDRA, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
+    }
     if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
     return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
 }

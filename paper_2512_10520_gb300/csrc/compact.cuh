@@ -11,6 +11,20 @@
 #ifndef MT_PASS_MIN_BLOCKS
 #define MT_PASS_MIN_BLOCKS 5
 #endif
+// The same for the polyhedron geometry, whose containment test needs more
+// registers (measured on config1p: 4 blocks = 64 registers, 33.2 ms; 5 blocks
+// spill, 36.8 ms).
+#ifndef MT_PASS_MIN_BLOCKS_POLY
+#define MT_PASS_MIN_BLOCKS_POLY 4
+#endif
+
+namespace mt {
+template <int GEOM>
+constexpr int pass_min_blocks()
+{
+    return GEOM == MT_GEOM_POLYHEDRA ? MT_PASS_MIN_BLOCKS_POLY : MT_PASS_MIN_BLOCKS;
+}
+}  // namespace mt
 
 namespace mt {
 
@@ -35,7 +49,7 @@ static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa 
 // One pass: live count from *cin, survivors appended at *cout; *czero (if not
 // null) is cleared for the pass after this one.
 template <int GEOM, int FIELD>
-__global__ void __launch_bounds__(kBlock, MT_PASS_MIN_BLOCKS) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
+__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM>()) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
                                                        LiveBuf in, LiveBuf out, const unsigned long long *cin,
                                                        unsigned long long *cout, unsigned long long *czero, int S)
 {

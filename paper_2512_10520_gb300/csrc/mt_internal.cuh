@@ -55,6 +55,9 @@ struct WorldParams {
     float vorigin_lo[3];
     float vspacing[3];
     float vspacing_lo[3];
+    const float4 *poly;            // solids: [n_box][6] float4 (see api.cu: build_geometry)
+    const double *poly64;          // solids: [n_box][18] z0, z1, bottom[4][2], top[4][2]
+    const float4 *pinner;          // solids: [n_box] inner rectangle (x0, x1, y0, y1)
     float xmax_hi, xmax_lo, ymax_hi, ymax_lo, zmax_hi, zmax_lo;
     float pmin2;
     // field

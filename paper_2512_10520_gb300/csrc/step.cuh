@@ -70,6 +70,7 @@ struct SmemWorld {
     float alpha[3][MT_MAX_BOXES];
     float2 e2[MT_MAX_PBINS + 1];
     uint32_t zmask[kZSlabs];
+    float4 inner[MT_MAX_BOXES];   // solids: (x0, x1, y0, y1) of a rectangle inside every slice
 };
 
 __device__ __forceinline__ void stage_world(SmemWorld &sw, const WorldParams &w, const RunParams &rp)
@@ -91,7 +92,9 @@ __device__ __forceinline__ void stage_world(SmemWorld &sw, const WorldParams &w,
 #pragma unroll
         for (int a = 0; a < 3; ++a) sw.alpha[a][t] = (rp.alpha && t < rp.n_block) ? rp.alpha[3 * t + a] : 1.0f;
     for (int t = threadIdx.x; t <= w.n_pbin; t += blockDim.x) sw.e2[t] = w.e2[t];
-    for (int t = threadIdx.x; t < kZSlabs; t += blockDim.x) sw.zmask[t] = w.n_box > 0 ? w.zmask[t] : 0u;
+    for (int t = threadIdx.x; t < kZSlabs; t += blockDim.x) sw.zmask[t] = w.zmask ? w.zmask[t] : 0u;
+    if (w.pinner)
+        for (int t = threadIdx.x; t < w.n_box; t += blockDim.x) sw.inner[t] = w.pinner[t];
 }
 
 // GetMaterial for ordered boxes: first box with lo <= r < hi on all axes.  Only
@@ -147,6 +150,99 @@ __device__ __forceinline__ int voxel_material(const WorldParams &w, const State 
         idx[a] = i;
     }
     return __ldg(w.vox + ((int64_t)idx[2] * w.vdims[1] + idx[1]) * w.vdims[0] + idx[0]);
+}
+
+// Containment in solid b of the polyhedron geometry (Sec. Simulation item 1,
+// Eq. 2), in FP64 from the solid's original double-precision data: the
+// definition's arithmetic, used when the FP32 filter below cannot decide.
+// z0 <= z < z1 has been decided already.
+// Inlined (measured on config1p at 64 registers: 33.2 ms against 36.0 ms for a
+// call, whose register saves cost more than the rarely run code itself).
+#ifndef MT_SOLID_FP64_INLINE
+#define MT_SOLID_FP64_INLINE 1
+#endif
+#if MT_SOLID_FP64_INLINE
+static __device__ __forceinline__ bool in_solid_fp64(
+#else
+static __device__ __noinline__ bool in_solid_fp64(
+#endif
+    const WorldParams &w, int b, const State &s)
+{
+    // one edge at a time, both ends recomputed from memory: few values live
+    const double *d = w.poly64 + 18 * b;
+    const double x = (double)s.x + (double)s.xl, y = (double)s.y + (double)s.yl, z = (double)s.z + (double)s.zl;
+    const double z0 = __ldg(d), z1 = __ldg(d + 1);
+    const double t = (z - z0) / (z1 - z0);
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const int j = (i + 1) & 3;
+        const double bix = __ldg(d + 2 + 2 * i), biy = __ldg(d + 3 + 2 * i);
+        const double bjx = __ldg(d + 2 + 2 * j), bjy = __ldg(d + 3 + 2 * j);
+        const double vix = bix + t * (__ldg(d + 10 + 2 * i) - bix), viy = biy + t * (__ldg(d + 11 + 2 * i) - biy);
+        const double vjx = bjx + t * (__ldg(d + 10 + 2 * j) - bjx), vjy = bjy + t * (__ldg(d + 11 + 2 * j) - bjy);
+        const double ex = vjx - vix, ey = vjy - viy;
+        if (ex * (y - viy) - ey * (x - vix) < 0.0) return false;
+    }
+    return true;
+}
+
+// Eq. 2 with a certified FP32 filter, for a point already known to lie in the
+// solid's z range.  Each S_i is formed in FP32 from the hi + lo position and
+// the interpolated slice.  Its rounding error (from t, v_i, e_i, dx, dy and S)
+// is at most 14 eps (|e_x| + |e_y| + 2M) (|dx| + |dy| + 2M), eps = 2^-24, M the
+// solid's coordinate scale; the solid's constant bound is 100 eps times that
+// product's maximum over the points that reach the test (its bounding box).
+// S_i < -bound proves the point outside; when every S_i > bound it is inside;
+// otherwise (the point within ~1e-4 m of a side face) the FP64 test decides,
+// so the decision is the definition's at the GPU's position.
+__device__ __forceinline__ bool in_solid_sides(const WorldParams &w, int b, const State &s)
+{
+    const float4 *P = w.poly + 6 * b;
+    const float4 zz = __ldg(P);   // z0 hi, z0 lo, 1 / (z1 - z0), bound
+    float dzh, dze;
+    two_sum(s.z, -zz.x, dzh, dze);
+    const float t = (dzh + (dze + (s.zl - zz.y))) * zz.z;
+    const float4 b0 = __ldg(P + 1), b1 = __ldg(P + 2), d0 = __ldg(P + 3), d1 = __ldg(P + 4);
+    const float vx[4] = {fmaf(t, d0.x, b0.x), fmaf(t, d0.z, b0.z), fmaf(t, d1.x, b1.x), fmaf(t, d1.z, b1.z)};
+    const float vy[4] = {fmaf(t, d0.y, b0.y), fmaf(t, d0.w, b0.w), fmaf(t, d1.y, b1.y), fmaf(t, d1.w, b1.w)};
+    const float bound = zz.w;
+    bool undecided = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int j = (i + 1) & 3;
+        const float ex = vx[j] - vx[i], ey = vy[j] - vy[i];
+        const float dx = (s.x - vx[i]) + s.xl, dy = (s.y - vy[i]) + s.yl;
+        const float S = fmaf(ex, dy, -(ey * dx));
+        if (S < -bound) return false;
+        undecided |= S <= bound;
+    }
+    return !undecided || in_solid_fp64(w, b, s);
+}
+
+// GetMaterial for solids.  The candidates come from the z-slab grid of
+// candidate masks in shared memory (a one-dimensional spatial hash; the paper
+// prunes its polyhedra with a spatial grid before the exact test), in list
+// order.  A candidate is skipped unless the point lies in its bounding box
+// (x and y grown by 1e-4 m, z exactly [z0, z1), tested on the hi + lo pairs);
+// a point inside the solid's inner rectangle (1e-4 m clear of every slice's
+// sides, so the FP32 comparison decides) is inside; otherwise Eq. 2 decides.
+// The first containing solid wins.
+__device__ __forceinline__ int find_solid(const WorldParams &w, const SmemWorld &sw, const State &s)
+{
+    const int slab = min(max(__float2int_rd((s.z - w.zslab_lo) * w.zslab_inv), 0), kZSlabs - 1);
+    uint32_t cand = sw.zmask[slab];
+    while (cand) {
+        const int b = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        if (!(ge2(s.z, s.zl, sw.lo_hi[2][b], sw.lo_lo[2][b]) && !ge2(s.z, s.zl, sw.hi_hi[2][b], sw.hi_lo[2][b]) &&
+              ge2(s.x, s.xl, sw.lo_hi[0][b], sw.lo_lo[0][b]) && !ge2(s.x, s.xl, sw.hi_hi[0][b], sw.hi_lo[0][b]) &&
+              ge2(s.y, s.yl, sw.lo_hi[1][b], sw.lo_lo[1][b]) && !ge2(s.y, s.yl, sw.hi_hi[1][b], sw.hi_lo[1][b])))
+            continue;
+        const float4 in = sw.inner[b];
+        if (s.x > in.x && s.x < in.y && s.y > in.z && s.y < in.w) return b;
+        if (in_solid_sides(w, b, s)) return b;
+    }
+    return -1;
 }
 
 // |p|^2 of the hi + lo momentum to first order in lo.
@@ -395,6 +491,9 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
     if (GEOM == MT_GEOM_BOXES) {
         box = find_box(w, sw, s);
         mat = box >= 0 ? sw.mat[box] : w.world_mat;
+    } else if (GEOM == MT_GEOM_POLYHEDRA) {
+        box = find_solid(w, sw, s);
+        mat = box >= 0 ? sw.mat[box] : w.world_mat;
     } else {
         const int vm = voxel_material(w, s);
         mat = vm >= 0 ? vm : w.world_mat;
@@ -423,7 +522,7 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         B = field_map(w, s);
     }
     rec.field(B);   // before the block scale
-    if (GEOM == MT_GEOM_BOXES && FIELD != MT_FIELD_NONE && box >= 0) {
+    if (GEOM != MT_GEOM_VOXELS && FIELD != MT_FIELD_NONE && box >= 0) {
         const int blk = sw.block[box];
         if (blk >= 0) {
             B.x *= sw.alpha[0][blk];

@@ -113,3 +113,25 @@ def test_alias_sampler_needs_power_of_two_cells(lib):
     assert e.value.status == B.MT_ERR_INVALID_ARG and "power" in mt.mt_last_error()
     with pytest.raises(KeyError):
         mt.mt_create(geo, dict(kind="box"), dict(h, sampler="walker"))
+
+
+def test_polyhedra_descriptor_checks_on_host(lib):
+    from workloads import gen
+    h = gen.histogram_set(["iron", "air", "concrete"], n_pbin=2, nf=4, ntheta=4, n_samples=1000, cache=False)
+    geo = gen.geometry_tapered()
+    bad = dict(geo, solids=[dict(geo["solids"][0], bottom=geo["solids"][0]["bottom"][::-1])])   # clockwise
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_create(bad, dict(kind="box"), h)
+    assert e.value.status == B.MT_ERR_INVALID_ARG and "solid 0" in mt.mt_last_error()
+    s0 = geo["solids"][0]
+    bowtie = dict(s0, top=[s0["top"][0], s0["top"][2], s0["top"][1], s0["top"][3]])            # not convex
+    with pytest.raises(mt.MtError):
+        mt.mt_create(dict(geo, solids=[bowtie]), dict(kind="box"), h)
+    with pytest.raises(mt.MtError):
+        mt.mt_create(dict(geo, solids=[dict(s0, z1=s0["z0"])]), dict(kind="box"), h)
+    assert ctypes_size_ok()
+
+
+def ctypes_size_ok():
+    # the descriptor the binding builds has the C layout of include/mt.h (8-byte aligned tail)
+    return C.sizeof(B.mt_polyhedron) == 8 * (2 + 8 + 8) + 8 + 24 and C.sizeof(B.mt_geometry_desc) % 8 == 0

@@ -219,8 +219,7 @@ def geometry_tapered() -> dict:
         solids.append(solid(z0, z0 + MAGNET_LEN, bot, top, 1, k, (0.0, 1.7 * s, 0.0)))
     wall = _trapezoid(3.0, 3.0, 3.0)
     solids.append(solid(27.0, 29.0, wall, wall, 3, -1))
-    return dict(kind="polyhedra", solids=solids, world_material=2, x_max=3.0, y_max=3.0, z_max=30.0, p_min=0.5,
-                hash_dims=[8, 8, 64])
+    return dict(kind="polyhedra", solids=solids, world_material=2, x_max=3.0, y_max=3.0, z_max=30.0, p_min=0.5)
 
 
 def _smooth_box(u: np.ndarray, a: float, b: float, w: float) -> np.ndarray:
