@@ -49,6 +49,7 @@ class World(C.Structure):
         ("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("nf", C.c_int32), ("ntheta", C.c_int32),
         ("p_lo", C.c_double), ("p_hi", C.c_double),
         ("f_max", C.c_void_p), ("theta_max", C.c_void_p), ("T", C.c_void_p),
+        ("axes", C.c_int32), ("f_min", C.c_void_p), ("theta_min", C.c_void_p),
         ("sampler", C.c_int32), ("alias_prob", C.c_void_p), ("alias_idx", C.c_void_p),
     ]
 
@@ -81,6 +82,10 @@ def lib():
             L.or_field.restype = None
             L.or_scatter.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
             L.or_scatter.restype = None
+            L.or_scatter_c.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
+            L.or_scatter_c.restype = None
+            L.or_dp_coeffs.argtypes = [C.c_int32, C.c_double, C.c_double, P, P]
+            L.or_dp_coeffs.restype = None
             L.or_rk4.argtypes = [P, P, P, C.c_int32, C.c_double]
             L.or_rk4.restype = None
             L.or_transport.argtypes = [P, C.c_int64] + [P] * 9 + [C.c_int64, C.c_int32, C.c_double,
@@ -170,6 +175,21 @@ def scatter(p, f, theta, phi) -> np.ndarray:
     return out
 
 
+def scatter_c(p, cz, ct, phi) -> np.ndarray:
+    """p + Rot([P ct cos phi, P ct sin phi, P cz]) (Algorithm 1's dp with dz = P cz, dt = P ct; Eq. 3)."""
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.zeros(3)
+    lib().or_scatter_c(_p(pp), float(cz), float(ct), float(phi), _p(out))
+    return out
+
+
+def dp_coeffs(axes: str, f: float, theta_or_t: float):
+    cz = C.c_double()
+    ct = C.c_double()
+    lib().or_dp_coeffs(1 if axes == "log" else 0, float(f), float(theta_or_t), C.byref(cz), C.byref(ct))
+    return cz.value, ct.value
+
+
 def rk4(r, p, B, q, d):
     rr = np.array(r, dtype=np.float64)
     pp = np.array(p, dtype=np.float64)
@@ -233,8 +253,8 @@ class OracleWorld:
             w.field_kind = 0
         elif fk == "box":
             w.field_kind = 1
-        elif fk == "map":
-            w.field_kind = 2
+        elif fk in ("map", "map_nearest"):
+            w.field_kind = 2 if fk == "map" else 3
             B = arr(field["B"], np.float32)
             w.fdims[:] = list(map(int, field["dims"]))
             w.forigin[:] = list(map(float, field["origin"]))
@@ -252,6 +272,13 @@ class OracleWorld:
         w.p_lo, w.p_hi = float(hist["p_lo"]), float(hist["p_hi"])
         w.f_max = _p(arr(hist["f_max"], np.float64))
         w.theta_max = _p(arr(hist["theta_max"], np.float64))
+        axes = hist.get("axes", "linear")
+        if axes == "log":
+            w.axes = 1
+            w.f_min = _p(arr(hist["f_min"], np.float64))
+            w.theta_min = _p(arr(hist["theta_min"], np.float64))
+        elif axes != "linear":
+            raise ValueError(axes)
         self.T = arr(build_thresholds(hist["weights"]), np.uint64)
         w.T = _p(self.T)
         if hist.get("sampler", "icdf") == "alias":

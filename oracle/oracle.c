@@ -77,7 +77,7 @@ typedef struct or_world {
     const uint8_t *vox;         /* [nz][ny][nx] material ids */
     double x_max, y_max, z_max, p_min;
     /* field */
-    int32_t field_kind;         /* 0: none, 1: per-box uniform, 2: trilinear node map */
+    int32_t field_kind;         /* 0: none, 1: per-box uniform, 2: trilinear node map, 3: nearest node */
     int32_t fdims[3];
     double forigin[3];
     double fspacing[3];
@@ -90,6 +90,9 @@ typedef struct or_world {
     const double *f_max;        /* [n_mat][n_pbin] */
     const double *theta_max;    /* [n_mat][n_pbin] */
     const uint64_t *T;          /* [n_mat][n_pbin][nf*ntheta-1] from or_build_thresholds */
+    int32_t axes;               /* 0: linear (f = dp/p, theta); 1: log (f = -dPz/P, t = dPt/P) */
+    const double *f_min;        /* log axes: [n_mat][n_pbin] lower edge of the f axis */
+    const double *theta_min;    /* log axes: [n_mat][n_pbin] lower edge of the t axis */
     int32_t sampler;            /* 0: inverse CDF over T, 1: alias tables below */
     const uint32_t *alias_prob; /* [n_mat][n_pbin][nf*ntheta] from or_build_alias */
     const int32_t *alias_idx;   /* [n_mat][n_pbin][nf*ntheta] */
@@ -349,7 +352,23 @@ static void or_field_map(const or_world *w, const double r[3], double B[3])
             }
 }
 
-/* GetField: none / per-box uniform / trilinear map, then the per-block scale
+/* Nearest-node lookup of the map (the paper's grid retrieval, Sec. Simulation
+ * item 3): node i of an axis owns [origin + (i - 1/2) s, origin + (i + 1/2) s),
+ * i = floor((r - origin)/s + 1/2); zero when that node is outside the map. */
+static void or_field_nearest(const or_world *w, const double r[3], double B[3])
+{
+    int64_t i[3];
+    B[0] = B[1] = B[2] = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double u = floor((r[a] - w->forigin[a]) / w->fspacing[a] + 0.5);
+        if (!(u >= 0.0 && u <= (double)(w->fdims[a] - 1))) return;
+        i[a] = (int64_t)u;
+    }
+    const float *node = w->Bmap + 3 * ((i[2] * w->fdims[1] + i[1]) * w->fdims[0] + i[0]);
+    for (int c = 0; c < 3; ++c) B[c] = (double)node[c];
+}
+
+/* GetField: none / per-box uniform / trilinear map / nearest node, then the per-block scale
  * alpha[block][c] when r lies in a box that carries a block id. */
 void or_field(const or_world *w, const double r[3], int32_t box, double B[3])
 {
@@ -359,6 +378,8 @@ void or_field(const or_world *w, const double r[3], int32_t box, double B[3])
             for (int c = 0; c < 3; ++c) B[c] = w->box_B[3 * box + c];
     } else if (w->field_kind == 2) {
         or_field_map(w, r, B);
+    } else if (w->field_kind == 3) {
+        or_field_nearest(w, r, B);
     }
     if (w->alpha && box >= 0 && w->box_block) {
         int32_t blk = w->box_block[box];
@@ -367,14 +388,15 @@ void or_field(const or_world *w, const double r[3], int32_t box, double B[3])
     }
 }
 
-/* Eq. 3: p <- p + Rot(dp) with dp = [dt cos phi, dt sin phi, dz] in the frame
- * whose z axis is the direction of travel. */
-void or_scatter(const double p[3], double f, double theta, double phi, double out[3])
+/* Eq. 3 (Rodrigues): p <- p + Rot(dp), dp = [dt cos phi, dt sin phi, dz] in
+ * the frame whose z axis is the direction of travel, rotated into the global
+ * frame; here dz = P cz and dt = P ct. */
+void or_scatter_c(const double p[3], double cz, double ct, double phi, double out[3])
 {
     double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
     double ph[3] = {p[0] / P, p[1] / P, p[2] / P};
-    double dt = P * (1.0 - f) * sin(theta);
-    double dz = P * ((1.0 - f) * cos(theta) - 1.0);
+    double dt = P * ct;
+    double dz = P * cz;
     double dp[3] = {dt * cos(phi), dt * sin(phi), dz};
     double rot[3];
     double s = sqrt(ph[0] * ph[0] + ph[1] * ph[1]);
@@ -392,6 +414,29 @@ void or_scatter(const double p[3], double f, double theta, double phi, double ou
         for (int c = 0; c < 3; ++c) rot[c] = dp[c] * ca + kxv[c] * sa + k[c] * kv * (1.0 - ca);
     }
     for (int c = 0; c < 3; ++c) out[c] = p[c] + rot[c];
+}
+
+/* dz / P and dt / P of Algorithm 1 from a draw: linear axes (f = dp/p, theta):
+ * cz = (1-f) cos theta - 1, ct = (1-f) sin theta, so |p_new| = (1-f) P and
+ * angle(p, p_new) = theta; log axes (f = -dPz/P, t = dPt/P, the histogram
+ * variables of Sec. Building histograms): cz = -f, ct = t. */
+void or_dp_coeffs(int32_t axes, double f, double theta_or_t, double *cz, double *ct)
+{
+    if (axes == 1) {
+        *cz = -f;
+        *ct = theta_or_t;
+    } else {
+        *cz = (1.0 - f) * cos(theta_or_t) - 1.0;
+        *ct = (1.0 - f) * sin(theta_or_t);
+    }
+}
+
+/* Linear-axes scattering from (f, theta). */
+void or_scatter(const double p[3], double f, double theta, double phi, double out[3])
+{
+    double cz, ct;
+    or_dp_coeffs(0, f, theta, &cz, &ct);
+    or_scatter_c(p, cz, ct, phi, out);
 }
 
 /* Eq. 4 with E = 0, integrated by classical RK4 over the path length d with B
@@ -451,10 +496,26 @@ static int or_draw_step(const or_world *w, const double r[3], const double p[3],
     int32_t a = c / w->ntheta, b = c % w->ntheta;
     d->pbin = i;
     d->cell = c;
-    d->f = ((double)a + or_uniform(u[1])) / (double)w->nf * w->f_max[hidx];
-    d->theta = ((double)b + or_uniform(u[2])) / (double)w->ntheta * w->theta_max[hidx];
+    if (w->axes == 1) {
+        /* log-spaced axes: jitter uniform in log f and log t inside the cell */
+        const double lf0 = log(w->f_min[hidx]), lf1 = log(w->f_max[hidx]);
+        const double lt0 = log(w->theta_min[hidx]), lt1 = log(w->theta_max[hidx]);
+        d->f = exp(lf0 + ((double)a + or_uniform(u[1])) / (double)w->nf * (lf1 - lf0));
+        d->theta = exp(lt0 + ((double)b + or_uniform(u[2])) / (double)w->ntheta * (lt1 - lt0));
+    } else {
+        d->f = ((double)a + or_uniform(u[1])) / (double)w->nf * w->f_max[hidx];
+        d->theta = ((double)b + or_uniform(u[2])) / (double)w->ntheta * w->theta_max[hidx];
+    }
     d->phi = OR_TWO_PI * or_uniform(u[3]);
     return 1;
+}
+
+/* The scattering update of a step's draw (Algorithm 1: dz, dt, then Eq. 3). */
+static void or_scatter_draw(const or_world *w, const double p[3], const or_step_draw *d, double out[3])
+{
+    double cz, ct;
+    or_dp_coeffs(w->axes, d->f, d->theta, &cz, &ct);
+    or_scatter_c(p, cz, ct, d->phi, out);
 }
 
 /* Termination test at the start of a step; returns a status or OR_ALIVE. */
@@ -487,7 +548,7 @@ void or_transport_one(const or_world *w, double r[3], double p[3], int32_t q, in
             break;
         }
         or_step_draw dr;
-        if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter(p, dr.f, dr.theta, dr.phi, p);
+        if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter_draw(w, p, &dr, p);
         double B[3];
         or_field(w, r, dr.box, B);
         or_rk4(r, p, B, q, d);
@@ -559,7 +620,7 @@ int32_t or_trace(const or_world *w, double r[3], double p[3], int32_t q, int32_t
         if (or_check(w, r, p) != OR_ALIVE) break;
         or_step_draw dr;
         for (int c = 0; c < 3; ++c) dbuf[9 * s + c] = r[c];
-        if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter(p, dr.f, dr.theta, dr.phi, p);
+        if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter_draw(w, p, &dr, p);
         for (int c = 0; c < 3; ++c) dbuf[9 * s + 3 + c] = p[c];
         double B[3];
         or_field(w, r, dr.box, B);
@@ -647,6 +708,10 @@ static void or_field_unscaled(const or_world *w, const double r[3], int32_t box,
             for (int c = 0; c < 3; ++c) Bm[c] = w->box_B[3 * box + c];
         return;
     }
+    if (w->field_kind == 3) {          /* piecewise constant: J = 0 */
+        or_field_nearest(w, r, Bm);
+        return;
+    }
     if (w->field_kind != 2) return;
     int64_t i0[3];
     double t[3];
@@ -683,13 +748,13 @@ static int32_t or_block_of(const or_world *w, int32_t box)
     return (blk >= 0 && blk < w->n_block) ? blk : -1;
 }
 
-/* Reverse of or_scatter with (f, theta, phi) fixed: pbar += (d out/d p)^T obar. */
-static void or_scatter_vjp(const double p[3], double f, double theta, double phi, const double obar[3], double pbar[3])
+/* Reverse of or_scatter_c with (cz, ct, phi) fixed: pbar += (d out/d p)^T obar. */
+static void or_scatter_vjp(const double p[3], double cz, double ct, double phi, const double obar[3], double pbar[3])
 {
     double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
     double ph[3] = {p[0] / P, p[1] / P, p[2] / P};
-    double sT = sin(theta), cT = cos(theta), cp = cos(phi), sp = sin(phi);
-    double dt = P * (1.0 - f) * sT, dz = P * ((1.0 - f) * cT - 1.0);
+    double cp = cos(phi), sp = sin(phi);
+    double dt = P * ct, dz = P * cz;
     double dp[3] = {dt * cp, dt * sp, dz};
     double s = sqrt(ph[0] * ph[0] + ph[1] * ph[1]);
     double dpbar[3] = {0, 0, 0}, phbar[3] = {0, 0, 0}, Pbar = 0.0;
@@ -736,7 +801,7 @@ static void or_scatter_vjp(const double p[3], double f, double theta, double phi
         phbar[1] += sbar * ph[1] / s;
     }
     double dtbar = dpbar[0] * cp + dpbar[1] * sp, dzbar = dpbar[2];
-    Pbar += dtbar * (1.0 - f) * sT + dzbar * ((1.0 - f) * cT - 1.0);
+    Pbar += dtbar * ct + dzbar * cz;
     double php = phbar[0] * p[0] + phbar[1] * p[1] + phbar[2] * p[2];
     for (int c = 0; c < 3; ++c) pbar[c] += phbar[c] / P;       /* ph = p / P */
     Pbar -= php / (P * P);
@@ -838,7 +903,7 @@ static void or_adjoint_one(const or_world *w, const double r0[3], const double p
         t->f = dr.f;
         t->theta = dr.theta;
         t->phi = dr.phi;
-        if (t->scattered) or_scatter(p, dr.f, dr.theta, dr.phi, p);
+        if (t->scattered) or_scatter_draw(w, p, &dr, p);
         double B[3];
         or_field(w, r, dr.box, B);
         or_rk4(r, p, B, q, d);
@@ -847,7 +912,11 @@ static void or_adjoint_one(const or_world *w, const double r0[3], const double p
     for (int32_t s = ns - 1; s >= 0; --s) {
         const or_tape *t = &tape[s];
         double ps[3] = {t->p[0], t->p[1], t->p[2]};
-        if (t->scattered) or_scatter(t->p, t->f, t->theta, t->phi, ps);
+        double cz = 0.0, ct = 0.0;
+        if (t->scattered) {
+            or_dp_coeffs(w->axes, t->f, t->theta, &cz, &ct);
+            or_scatter_c(t->p, cz, ct, t->phi, ps);
+        }
         double Bm[3], J[3][3], B[3];
         or_field_unscaled(w, t->r, t->box, Bm, J);
         int32_t blk = or_block_of(w, t->box);
@@ -861,7 +930,7 @@ static void or_adjoint_one(const or_world *w, const double r0[3], const double p
         }
         if (t->scattered) {
             double pb[3] = {0, 0, 0};
-            or_scatter_vjp(t->p, t->f, t->theta, t->phi, pbar, pb);
+            or_scatter_vjp(t->p, cz, ct, t->phi, pbar, pb);
             for (int c = 0; c < 3; ++c) pbar[c] = pb[c];
         }
     }
@@ -968,12 +1037,12 @@ static or_dual dsqrt(or_dual a)
 }
 static or_dual dnorm3(const or_dual v[3]) { return dsqrt(dadd(dadd(dmul(v[0], v[0]), dmul(v[1], v[1])), dmul(v[2], v[2]))); }
 
-static void dscatter(or_dual p[3], double f, double theta, double phi)
+static void dscatter(or_dual p[3], double cz, double ct, double phi)
 {
     or_dual P = dnorm3(p);
     or_dual ph[3] = {ddiv(p[0], P), ddiv(p[1], P), ddiv(p[2], P)};
-    or_dual dt = dscale(P, (1.0 - f) * sin(theta));
-    or_dual dz = dscale(P, (1.0 - f) * cos(theta) - 1.0);
+    or_dual dt = dscale(P, ct);
+    or_dual dz = dscale(P, cz);
     or_dual dp[3] = {dscale(dt, cos(phi)), dscale(dt, sin(phi)), dz};
     or_dual rot[3];
     or_dual s = dsqrt(dadd(dmul(ph[0], ph[0]), dmul(ph[1], ph[1])));
@@ -1052,6 +1121,11 @@ static void dfield(const or_world *w, const or_dual r[3], int32_t box, or_dual B
                         for (int c = 0; c < 3; ++c) B[c] = dadd(B[c], dscale(wgt, (double)node[c]));
                     }
         }
+    } else if (w->field_kind == 3) {
+        const double rv[3] = {r[0].v, r[1].v, r[2].v};
+        double Bn[3];
+        or_field_nearest(w, rv, Bn);
+        for (int c = 0; c < 3; ++c) B[c] = dc(Bn[c]);
     }
     int32_t blk = or_block_of(w, box);
     if (blk >= 0)
@@ -1079,7 +1153,11 @@ int32_t or_transport_tangent(const or_world *w, const double r0[3], const double
         double rv[3] = {r[0].v, r[1].v, r[2].v}, pv[3] = {p[0].v, p[1].v, p[2].v};
         if (or_check(w, rv, pv) != OR_ALIVE) break;
         or_step_draw dr;
-        if (or_draw_step(w, rv, pv, k, id, inst, seed, &dr)) dscatter(p, dr.f, dr.theta, dr.phi);
+        if (or_draw_step(w, rv, pv, k, id, inst, seed, &dr)) {
+            double cz, ct;
+            or_dp_coeffs(w->axes, dr.f, dr.theta, &cz, &ct);
+            dscatter(p, cz, ct, dr.phi);
+        }
         or_dual B[3];
         dfield(w, r, dr.box, B);
         drk4(r, p, B, q, d);

@@ -71,9 +71,17 @@ def _highland(p_gev: np.ndarray, x_cm: float, X0: float) -> np.ndarray:
     return 13.6 / (beta * p) * np.sqrt(t) * (1.0 + 0.038 * np.log(t))
 
 
+LOG_F_RANGE = (1e-10, 1.0)      # -dPz/P axis of the log-axes histograms
+LOG_T_RANGE = (1e-9, 1.0)       # dPt/P axis
+
+
 def _hist_one(rng: np.random.Generator, mat: Dict[str, float], p_a: float, p_b: float,
-              x_cm: float, f_max: float, nf: int, ntheta: int, n_samples: int):
-    """One (material, momentum-bin) histogram of counts [nf][ntheta] plus its theta axis."""
+              x_cm: float, f_max: float, nf: int, ntheta: int, n_samples: int, axes: str = "linear"):
+    """One (material, momentum-bin) histogram of counts [nf][ntheta] plus its theta axis.
+
+    axes = "linear": f = dp/p on [0, f_max), theta on [0, 5 theta0(p_lo)).
+    axes = "log": the paper's variables -dPz/P = 1 - (1-f) cos(theta) and
+    dPt/P = (1-f) sin(theta), log-spaced on LOG_F_RANGE and LOG_T_RANGE."""
     p = rng.uniform(p_a, p_b, n_samples)                     # GeV, Pz ~ U(p_i, p_i+1)
     pm = p * 1e3
     E = np.sqrt(pm * pm + _MMU * _MMU)
@@ -103,6 +111,18 @@ def _hist_one(rng: np.random.Generator, mat: Dict[str, float], p_a: float, p_b: 
     single = rng.random(n_samples) < 0.01
     theta = np.where(single, 2.0 * th0 / np.sqrt(u2), th0 * np.sqrt(-2.0 * np.log(u1)))
     theta_max = 5.0 * float(_highland(np.array([p_a]), x_cm, mat["X0"])[0])
+    if axes == "log":
+        fc = np.clip(f, 0.0, 1.0)
+        fz = fc + (1.0 - fc) * 2.0 * np.sin(0.5 * theta) ** 2       # 1 - (1-f) cos(theta), without cancellation
+        t = (1.0 - fc) * np.sin(np.minimum(theta, 0.5 * np.pi))
+        (f0, f1), (t0, t1) = LOG_F_RANGE, LOG_T_RANGE
+        with np.errstate(divide="ignore"):
+            a = np.floor(np.log(np.maximum(fz, 1e-300) / f0) / np.log(f1 / f0) * nf)
+            b = np.floor(np.log(np.maximum(t, 1e-300) / t0) / np.log(t1 / t0) * ntheta)
+        a = np.clip(a, 0, nf - 1).astype(np.int64)
+        b = np.clip(b, 0, ntheta - 1).astype(np.int64)
+        counts = np.bincount(a * ntheta + b, minlength=nf * ntheta).astype(np.float64)
+        return counts.reshape(nf, ntheta), t1
     a = np.clip(np.floor(f / f_max * nf), 0, nf - 1).astype(np.int64)
     b = np.clip(np.floor(theta / theta_max * ntheta), 0, ntheta - 1).astype(np.int64)
     counts = np.bincount(a * ntheta + b, minlength=nf * ntheta).astype(np.float64)
@@ -111,7 +131,7 @@ def _hist_one(rng: np.random.Generator, mat: Dict[str, float], p_a: float, p_b: 
 
 def histogram_set(materials: List[str], n_pbin: int = 64, p_lo: float = 1.0, p_hi: float = 400.0,
                   nf: int = 128, ntheta: int = 64, f_max: float = 0.2, n_samples: int = 10**6,
-                  step_len: float = 0.02, seed: int = 42, cache: bool = True) -> dict:
+                  step_len: float = 0.02, seed: int = 42, cache: bool = True, axes: str = "linear") -> dict:
     """Histogram set H[M][i] for materials 1..len(materials) (material 0 is vacuum).
 
     Returns a dict with ``weights`` [n_mat][n_pbin][nf][ntheta] (float64 counts),
@@ -119,6 +139,8 @@ def histogram_set(materials: List[str], n_pbin: int = 64, p_lo: float = 1.0, p_h
     """
     params = dict(materials=list(materials), n_pbin=n_pbin, p_lo=p_lo, p_hi=p_hi, nf=nf,
                   ntheta=ntheta, f_max=f_max, n_samples=n_samples, step_len=step_len, seed=seed, v=1)
+    if axes != "linear":
+        params["axes"] = axes
     path = _cache_path("hist", params)
     if cache and os.path.exists(path):
         z = np.load(path)
@@ -135,7 +157,7 @@ def histogram_set(materials: List[str], n_pbin: int = 64, p_lo: float = 1.0, p_h
             m, i = mi
             rng = np.random.default_rng([seed, m, i])
             W[m, i], TM[m, i] = _hist_one(rng, MATERIALS[materials[m]], edges[i], edges[i + 1],
-                                          x_cm, f_max, nf, ntheta, n_samples)
+                                          x_cm, f_max, nf, ntheta, n_samples, axes)
 
         # each (material, bin) has its own seeded stream, so threading keeps results fixed
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
@@ -145,10 +167,15 @@ def histogram_set(materials: List[str], n_pbin: int = 64, p_lo: float = 1.0, p_h
             tmp = path + f".tmp{os.getpid()}.npz"
             np.savez(tmp, weights=W, f_max=FM, theta_max=TM)
             os.replace(tmp, path)
-    return dict(n_mat=W.shape[0], n_pbin=n_pbin, p_lo=float(p_lo), p_hi=float(p_hi),
-                nf=nf, ntheta=ntheta, weights=np.ascontiguousarray(W),
-                f_max=np.ascontiguousarray(FM), theta_max=np.ascontiguousarray(TM),
-                materials=list(materials))
+    out = dict(n_mat=W.shape[0], n_pbin=n_pbin, p_lo=float(p_lo), p_hi=float(p_hi),
+               nf=nf, ntheta=ntheta, weights=np.ascontiguousarray(W),
+               f_max=np.ascontiguousarray(FM), theta_max=np.ascontiguousarray(TM),
+               materials=list(materials))
+    if axes == "log":
+        shape = W.shape[:2]
+        out.update(axes="log", f_min=np.full(shape, LOG_F_RANGE[0]), f_max=np.full(shape, LOG_F_RANGE[1]),
+                   theta_min=np.full(shape, LOG_T_RANGE[0]), theta_max=np.full(shape, LOG_T_RANGE[1]))
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -344,8 +371,13 @@ class Workload:
         return len(self.muons["x"])
 
 
+def _nearest(field: Optional[str], fmap: dict) -> dict:
+    """The map read at the nearest node when field == "nearest"."""
+    return dict(fmap, kind="map_nearest") if field == "nearest" else fmap
+
+
 def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = None,
-             field: Optional[str] = None) -> Workload:
+             field: Optional[str] = None, axes: str = "linear") -> Workload:
     """Named workloads.
 
     * ``config0``: 1e4 muons, one iron block in air, analytic per-box field, 200 steps,
@@ -358,32 +390,33 @@ def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = N
       table set but not placed in the geometry).
 
     ``n`` and ``hist_samples`` shrink a workload for tests; ``field`` = "box" swaps the map
-    for the analytic per-box field.
+    for the analytic per-box field and "nearest" reads the map at the nearest node;
+    ``axes`` = "log" builds the histograms on the paper's log-scaled axes.
     """
     if name == "config0":
-        h = histogram_set(["iron", "air"], n_samples=hist_samples or 10**6)
+        h = histogram_set(["iron", "air"], n_samples=hist_samples or 10**6, axes=axes)
         mu = muons_config0(n or 10_000)
         geo = geometry_config0()
         fld = dict(kind="box")
         return Workload(name, geo, fld, h, mu, 0.02, 200, 7)
     if name in ("config1", "config3"):
-        h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
+        h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6, axes=axes)
         mu = muons_config1(n or 1_000_000)
         geo = geometry_config1()
-        fld = dict(kind="box") if field == "box" else field_map_config1()
+        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_config1())
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
     if name == "config1p":
-        h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
+        h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6, axes=axes)
         mu = muons_config1(n or 1_000_000)
         geo = geometry_tapered()
-        fld = dict(kind="box") if field == "box" else field_map_config1()
+        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_config1())
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
     if name == "config4":
-        h = histogram_set(["iron", "air", "concrete", "lead"], n_pbin=128, nf=256, ntheta=128,
+        h = histogram_set(["iron", "air", "concrete", "lead"], n_pbin=128, nf=256, ntheta=128, axes=axes,
                           n_samples=hist_samples or 10**6)
         mu = muons_config1(n or 100_000_000)
         geo = geometry_config1()
-        fld = dict(kind="box") if field == "box" else field_map_config1(400, 400, 1200)
+        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_config1(400, 400, 1200))
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
     raise KeyError(name)
 
