@@ -666,6 +666,14 @@ def run_mine(args):
                           "narrowing along z), spatial-hash pruning, 200x200x600 map")
         ph["vs_boxes"] = ph["value"] / value
         forms["polyhedra"] = ph
+        for name, kw, desc in (("nearest_field", dict(field="nearest"),
+                                "config1 with the map read at the nearest node (the paper's lookup, 1 gather)"),
+                               ("log_axes", dict(axes="log"),
+                                "config1 with histograms on log-scaled (-dPz/P, dPt/P) axes, additive dp")):
+            wv = gen.workload("config1", n=args.muons, **kw)
+            tv, sv = _time_world(mt, wv, wv.geometry, dev, stream, 3, id_offset)
+            forms[name] = dict(value=_barrier_sum(sv, ws, dev) / _barrier_max(tv, ws, dev), unit=UNIT,
+                               kernel_ms=1e3 * tv, muon_steps=sv, vs_plain=(sv / tv) / value, workload=desc)
         bt = time_batched_form(mt, stream, dev, n_inst=args.batch_instances, rank=rank,
                                separate=not args.no_separate)
         bt["value"] = _barrier_sum(bt["muon_steps"], ws, dev) / _barrier_max(bt["batched_ms"] / 1e3, ws, dev)

@@ -56,7 +56,7 @@ enum {
 };
 
 enum { MT_GEOM_BOXES = 0, MT_GEOM_VOXELS = 1, MT_GEOM_POLYHEDRA = 2 };
-enum { MT_FIELD_NONE = 0, MT_FIELD_BOX = 1, MT_FIELD_MAP = 2 };
+enum { MT_FIELD_NONE = 0, MT_FIELD_BOX = 1, MT_FIELD_MAP = 2, MT_FIELD_MAP_NEAREST = 3 };
 
 #define MT_MAX_BOXES 32
 #define MT_MAX_MATERIALS 15
@@ -113,7 +113,11 @@ typedef struct mt_geometry_desc {
 
 /* Magnetic field.  MT_FIELD_MAP: node-based map, node (i,j,k) at
  * origin + (i,j,k)*spacing, trilinear interpolation, zero outside the node box
- * (the paper's regular-grid field, Sec. Simulation item 3). */
+ * (the paper's regular-grid field, Sec. Simulation item 3).
+ * MT_FIELD_MAP_NEAREST: the same map read at the nearest node, the paper's own
+ * lookup: along each axis node i owns [origin + (i - 1/2) s, origin + (i + 1/2) s);
+ * zero where that node is outside the map.  No dB/dr (piecewise constant).
+ * MT_FIELD_BOX: the uniform field B of the box or solid holding the point. */
 typedef struct mt_field_desc {
     int32_t kind;                 /* MT_FIELD_NONE / MT_FIELD_BOX / MT_FIELD_MAP      */
     int32_t dims[3];              /* map: nx, ny, nz (each >= 2)                      */
@@ -137,8 +141,19 @@ typedef struct mt_hist_desc {
     const double *f_max;          /* host, [n_mat][n_pbin], > 0                       */
     const double *theta_max;      /* host, [n_mat][n_pbin], > 0                       */
     int32_t sampler;              /* MT_SAMPLER_ICDF (0, default) or MT_SAMPLER_ALIAS */
-    int32_t reserved;             /* 0                                                */
+    int32_t axes;                 /* MT_AXES_LINEAR (0, default) or MT_AXES_LOG       */
+    const double *f_min;          /* log axes: host, [n_mat][n_pbin], 0 < f_min < f_max */
+    const double *theta_min;      /* log axes: host, [n_mat][n_pbin], 0 < t_min < t_max */
 } mt_hist_desc;
+
+/* Histogram axes.  MT_AXES_LINEAR: f = dp/p on [0, f_max) and the polar angle
+ * theta on [0, theta_max), linear bins; the step sets |p| to (1 - f) |p| at
+ * angle theta.  MT_AXES_LOG: the paper's variables (Sec. Building histograms)
+ * f = -dPz/|P| on [f_min, f_max) and t = dPt/|P| on [theta_min, theta_max),
+ * log-spaced bins with the jitter uniform in log f and log t; the step adds
+ * Algorithm 1's dp = [P t cos phi, P t sin phi, -P f] in the muon's frame. */
+#define MT_AXES_LINEAR 0
+#define MT_AXES_LOG 1
 
 /* Samplers of a histogram cell from the draw w0 (Philox word 0).  Both use the
  * integer masses m_c = T_c - T_{c-1} of the thresholds T_c = floor(2^32 S_c /

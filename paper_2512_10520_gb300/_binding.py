@@ -20,7 +20,7 @@ from . import _build
 MT_OK, MT_ERR_INVALID_ARG, MT_ERR_CUDA, MT_ERR_OOM, MT_ERR_TIMEOUT, MT_ERR_TABLE, MT_ERR_DEVICE = range(7)
 MT_ALIVE, MT_STOPPED, MT_EXIT_Z, MT_EXIT_XY, MT_MAX_STEPS, MT_INVALID = range(6)
 MT_GEOM_BOXES, MT_GEOM_VOXELS, MT_GEOM_POLYHEDRA = 0, 1, 2
-MT_FIELD_NONE, MT_FIELD_BOX, MT_FIELD_MAP = 0, 1, 2
+MT_FIELD_NONE, MT_FIELD_BOX, MT_FIELD_MAP, MT_FIELD_MAP_NEAREST = 0, 1, 2, 3
 STATUS_NAMES = {0: "MT_OK", 1: "MT_ERR_INVALID_ARG", 2: "MT_ERR_CUDA", 3: "MT_ERR_OOM", 4: "MT_ERR_TIMEOUT",
                 5: "MT_ERR_TABLE", 6: "MT_ERR_DEVICE"}
 
@@ -58,11 +58,14 @@ class mt_field_desc(C.Structure):
 class mt_hist_desc(C.Structure):
     _fields_ = [("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("p_lo", C.c_double), ("p_hi", C.c_double),
                 ("nf", C.c_int32), ("ntheta", C.c_int32), ("weights", C.c_void_p), ("f_max", C.c_void_p),
-                ("theta_max", C.c_void_p), ("sampler", C.c_int32), ("reserved", C.c_int32)]
+                ("theta_max", C.c_void_p), ("sampler", C.c_int32), ("axes", C.c_int32), ("f_min", C.c_void_p),
+                ("theta_min", C.c_void_p)]
 
 
 MT_SAMPLER_ICDF, MT_SAMPLER_ALIAS = 0, 1
 SAMPLERS = {"icdf": MT_SAMPLER_ICDF, "alias": MT_SAMPLER_ALIAS}
+MT_AXES_LINEAR, MT_AXES_LOG = 0, 1
+AXES = {"linear": MT_AXES_LINEAR, "log": MT_AXES_LOG}
 
 
 class mt_launch_cfg(C.Structure):
@@ -250,8 +253,9 @@ class _Descs:
     def _field(field, arr):
         f = mt_field_desc()
         kind = field["kind"]
-        f.kind = {"none": MT_FIELD_NONE, "box": MT_FIELD_BOX, "map": MT_FIELD_MAP}[kind]
-        if kind == "map":
+        f.kind = {"none": MT_FIELD_NONE, "box": MT_FIELD_BOX, "map": MT_FIELD_MAP,
+                  "map_nearest": MT_FIELD_MAP_NEAREST}[kind]
+        if kind in ("map", "map_nearest"):
             B = arr(field["B"], np.float32)
             f.dims[:] = list(map(int, field["dims"]))
             f.origin[:] = list(map(float, field["origin"]))
@@ -269,6 +273,10 @@ class _Descs:
         h.f_max = arr(hist["f_max"], np.float64).ctypes.data
         h.theta_max = arr(hist["theta_max"], np.float64).ctypes.data
         h.sampler = SAMPLERS[hist.get("sampler", "icdf")]
+        h.axes = AXES[hist.get("axes", "linear")]
+        if h.axes == MT_AXES_LOG:
+            h.f_min = arr(hist["f_min"], np.float64).ctypes.data
+            h.theta_min = arr(hist["theta_min"], np.float64).ctypes.data
         return h
 
 

@@ -95,8 +95,9 @@ static TapeLayout tape_layout(int64_t n, int32_t max_steps, int32_t K)
 
 // One recorded step takes 40 (or 56) bytes in three (four) planes, so that a
 // warp's stores and loads are contiguous: plane a = (rx, ry, rz, meta), plane
-// b = (px, py, pz, f), plane c = (theta, phi - pi), plane d = (Bx, By, Bz, -)
-// when the field is recorded, with r and p at the step's start, B there before
+// b = (px, py, pz, c1), plane c = (c2, phi - pi), plane d = (Bx, By, Bz, -)
+// when the field is recorded, with r and p at the step's start, (c1, c2) the
+// coefficients of the scattering update (step.cuh: scatter), B there before
 // the block scale, and meta bit 0 = scattered, bits 8..15 = box + 1.  Step j of
 // entry t sits at base + step_bytes j T (T entries per plane, a multiple of
 // 32).  Written and read once with streaming (evict-first) hints, so it passes
@@ -118,7 +119,7 @@ struct TapeWriter {
     const TapeRef<RB> *tr;
     int j;
     bool on = true;
-    float f = 0.0f, th = 0.0f, phs = 0.0f;
+    float c1 = 0.0f, c2 = 0.0f, phs = 0.0f;
     float pxs = 0.0f, pys = 0.0f, pzs = 0.0f;
     bool scat = false;
     __device__ __forceinline__ void begin(const State &s, int box, bool scattered)
@@ -130,17 +131,17 @@ struct TapeWriter {
         pys = s.py + s.pyl;
         pzs = s.pz + s.pzl;
     }
-    __device__ __forceinline__ void draw(float f_, float th_, float phs_)
+    __device__ __forceinline__ void draw(float c1_, float c2_, float phs_)
     {
-        f = f_;
-        th = th_;
+        c1 = c1_;
+        c2 = c2_;
         phs = phs_;
     }
     __device__ __forceinline__ void field(float3 B)
     {
         if (!on) return;
-        __stcs(tr->b(j), make_float4(pxs, pys, pzs, f));
-        if (scat) __stcs(tr->c(j), make_float2(th, phs));
+        __stcs(tr->b(j), make_float4(pxs, pys, pzs, c1));
+        if (scat) __stcs(tr->c(j), make_float2(c2, phs));
         if (RB) __stcs(tr->d(j), make_float4(B.x, B.y, B.z, 0.0f));
     }
 };
@@ -206,17 +207,14 @@ __device__ __forceinline__ void field_map_jt(const WorldParams &w, const float r
 }
 
 // The forward's scattering update in plain FP32 on a recorded momentum.
-__device__ __forceinline__ void scatter_fp32(const float p[3], float f, float th, float cphi, float sphi, float ps[3])
+__device__ __forceinline__ void scatter_fp32(const float p[3], float c1, float c2, float cphi, float sphi, float ps[3])
 {
     const float P2 = dot3(p, p);
     float rP = rsqrtf(P2);
     rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
     const float P = P2 * rP;
     const float ux = p[0] * rP, uy = p[1] * rP, uz = p[2] * rP;
-    float st, omc;
-    sin_omc(th, st, omc);
-    const float sm1 = -fmaf(f, 1.0f - omc, omc);
-    const float kick = P * (1.0f - f) * st;
+    const float kick = P * c2;
     const float s2 = fmaf(ux, ux, uy * uy);
     float tx, ty, tz;
     if (uz < 0.0f && s2 < 1e-24f) {
@@ -230,9 +228,9 @@ __device__ __forceinline__ void scatter_fp32(const float p[3], float f, float th
         ty = fmaf(-(uy * wv), g, sphi);
         tz = -wv;
     }
-    ps[0] = fmaf(sm1, p[0], fmaf(kick, tx, p[0]));
-    ps[1] = fmaf(sm1, p[1], fmaf(kick, ty, p[1]));
-    ps[2] = fmaf(sm1, p[2], fmaf(kick, tz, p[2]));
+    ps[0] = fmaf(c1, p[0], fmaf(kick, tx, p[0]));
+    ps[1] = fmaf(c1, p[1], fmaf(kick, ty, p[1]));
+    ps[2] = fmaf(c1, p[2], fmaf(kick, tz, p[2]));
 }
 
 // dL/dalpha of the current magnet block, flushed to shared memory when the
@@ -280,7 +278,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     const bool scat = meta & 1;
     const float r[3] = {t.a.x, t.a.y, t.a.z};
     const float p[3] = {t.b.x, t.b.y, t.b.z};
-    const float f = t.b.w, th = t.c.x;
+    const float sm1 = t.b.w, kf = t.c.x;   // scattering coefficients c1, c2
     // -- field before the block scale, evaluated again at the recorded r
     float Bm[3] = {0.0f, 0.0f, 0.0f};
     if (RB) {
@@ -293,13 +291,13 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
             Bm[1] = sw.B[1][box];
             Bm[2] = sw.B[2][box];
         }
-    } else if (FIELD == MT_FIELD_MAP) {
+    } else if (FIELD == MT_FIELD_MAP || FIELD == MT_FIELD_MAP_NEAREST) {
         State at;
         at.x = r[0];
         at.y = r[1];
         at.z = r[2];
         at.xl = at.yl = at.zl = 0.0f;
-        const float3 b = field_map(w, at);
+        const float3 b = FIELD == MT_FIELD_MAP ? field_map(w, at) : field_map_nearest(w, at);
         Bm[0] = b.x;
         Bm[1] = b.y;
         Bm[2] = b.z;
@@ -312,7 +310,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     }
     // -- scattered momentum ps = p + sm1 p + P kf tv(u) (recomputed in FP32)
     float ps[3] = {p[0], p[1], p[2]};
-    if (scat) scatter_fp32(p, f, th, cphi, sphi, ps);
+    if (scat) scatter_fp32(p, sm1, kf, cphi, sphi, ps);
     int blk = -1;
     float sc[3] = {1.0f, 1.0f, 1.0f};
     if (GEOM != MT_GEOM_VOXELS && FIELD != MT_FIELD_NONE && box >= 0) {
@@ -384,7 +382,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
         const float Bmb[3] = {sc[0] * Bb[0], sc[1] * Bb[1], sc[2] * Bb[2]};
         field_map_jt(w, r, Bmb, rb);
     }
-    // -- scattering: ps = (1 + sm1) p + P kf tv(u), u = p / P, held draws (f, theta, phi)
+    // -- scattering: ps = (1 + sm1) p + P kf tv(u), u = p / P, held draws (sm1, kf, phi)
     if (!scat) {
         pb[0] = psb[0];
         pb[1] = psb[1];
@@ -396,10 +394,6 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     rPs = rPs * fmaf(-0.5f * P2 * rPs, rPs, 1.5f);
     const float P = P2 * rPs;
     const float u[3] = {p[0] * rPs, p[1] * rPs, p[2] * rPs};
-    float st, omc;
-    sin_omc(th, st, omc);
-    const float sm1 = -fmaf(f, 1.0f - omc, omc);
-    const float kf = (1.0f - f) * st;
     const float s2 = fmaf(u[0], u[0], u[1] * u[1]);
     float tv[3], ub[3] = {0.0f, 0.0f, 0.0f};
     if (u[2] < 0.0f && s2 < 1e-24f) {
@@ -717,15 +711,17 @@ __global__ void alpha_out(const double *src, float *dst, int m, const unsigned i
     if (t < m) dst[t] = (flag && *flag) ? __int_as_float(0x7FC00000) : (float)src[t];
 }
 
-#define MT_DISPATCH_FIELDS(FN, G, ...)                                          \
-    (w.field_kind == MT_FIELD_MAP   ? FN<G, MT_FIELD_MAP>(__VA_ARGS__)           \
-     : w.field_kind == MT_FIELD_BOX ? FN<G, MT_FIELD_BOX>(__VA_ARGS__)           \
-                                    : FN<G, MT_FIELD_NONE>(__VA_ARGS__))
+#define MT_DISPATCH_FIELDS(FN, G, ...)                                                  \
+    (w.field_kind == MT_FIELD_MAP           ? FN<G, MT_FIELD_MAP>(__VA_ARGS__)           \
+     : w.field_kind == MT_FIELD_MAP_NEAREST ? FN<G, MT_FIELD_MAP_NEAREST>(__VA_ARGS__)   \
+     : w.field_kind == MT_FIELD_BOX         ? FN<G, MT_FIELD_BOX>(__VA_ARGS__)           \
+                                            : FN<G, MT_FIELD_NONE>(__VA_ARGS__))
 #define MT_DISPATCH(FN, ...)                                                           \
     (w.geom_kind == MT_GEOM_BOXES       ? MT_DISPATCH_FIELDS(FN, MT_GEOM_BOXES, __VA_ARGS__)     \
      : w.geom_kind == MT_GEOM_POLYHEDRA ? MT_DISPATCH_FIELDS(FN, MT_GEOM_POLYHEDRA, __VA_ARGS__) \
-     : (w.field_kind == MT_FIELD_MAP ? FN<MT_GEOM_VOXELS, MT_FIELD_MAP>(__VA_ARGS__)            \
-                                     : FN<MT_GEOM_VOXELS, MT_FIELD_NONE>(__VA_ARGS__)))
+     : w.field_kind == MT_FIELD_MAP     ? FN<MT_GEOM_VOXELS, MT_FIELD_MAP>(__VA_ARGS__)          \
+     : w.field_kind == MT_FIELD_MAP_NEAREST ? FN<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(__VA_ARGS__) \
+                                        : FN<MT_GEOM_VOXELS, MT_FIELD_NONE>(__VA_ARGS__))
 
 }  // namespace mt
 

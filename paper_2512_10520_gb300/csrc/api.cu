@@ -182,6 +182,23 @@ mt_status validate_hist(const mt_hist_desc *h)
         set_error("hist: nf*ntheta = %lld outside [2, %d]", (long long)h->nf * h->ntheta, MT_MAX_CELLS);
         return MT_ERR_INVALID_ARG;
     }
+    if (h->axes != MT_AXES_LINEAR && h->axes != MT_AXES_LOG) {
+        set_error("hist: unknown axes %d", h->axes);
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h->axes == MT_AXES_LOG) {
+        if (!h->f_min || !h->theta_min) {
+            set_error("hist: log axes need f_min and theta_min");
+            return MT_ERR_INVALID_ARG;
+        }
+        for (int64_t i = 0; i < (int64_t)h->n_mat * h->n_pbin; ++i)
+            if (!(h->f_min[i] > 0.0) || !(h->f_min[i] < h->f_max[i]) || !(h->theta_min[i] > 0.0) ||
+                !(h->theta_min[i] < h->theta_max[i])) {
+                set_error("hist: log axes need 0 < f_min < f_max and 0 < theta_min < theta_max (histogram %lld)",
+                          (long long)i);
+                return MT_ERR_INVALID_ARG;
+            }
+    }
     if (h->sampler != MT_SAMPLER_ICDF && h->sampler != MT_SAMPLER_ALIAS) {
         set_error("hist: unknown sampler %d", h->sampler);
         return MT_ERR_INVALID_ARG;
@@ -286,7 +303,7 @@ mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g)
         set_error("null field descriptor");
         return MT_ERR_INVALID_ARG;
     }
-    if (f->kind == MT_FIELD_MAP) {
+    if (f->kind == MT_FIELD_MAP || f->kind == MT_FIELD_MAP_NEAREST) {
         if (!f->B || f->dims[0] < 2 || f->dims[1] < 2 || f->dims[2] < 2 || !finite3(f->origin) ||
             !(f->spacing[0] > 0) || !(f->spacing[1] > 0) || !(f->spacing[2] > 0)) {
             set_error("field: bad map (dims >= 2, spacing > 0, B non-null)");
@@ -356,6 +373,20 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
         e2[k] = make_float2(a, b);
     }
     if ((st = upload(own, rec.data(), rec.size(), "histogram records", &w.hist)) != MT_OK) return st;
+    w.axes = hd->axes;
+    if (hd->axes == MT_AXES_LOG) {
+        const int64_t nh = (int64_t)hd->n_mat * hd->n_pbin;
+        // per histogram two records (v0, log2 cell width as hi + lo, 0) for f and t
+        std::vector<float4> hl(2 * nh);
+        for (int64_t i = 0; i < nh; ++i) {
+            float dh, dl;
+            split(std::log2(hd->f_max[i] / hd->f_min[i]) / hd->nf, dh, dl);
+            hl[2 * i] = make_float4((float)hd->f_min[i], dh, dl, 0.0f);
+            split(std::log2(hd->theta_max[i] / hd->theta_min[i]) / hd->ntheta, dh, dl);
+            hl[2 * i + 1] = make_float4((float)hd->theta_min[i], dh, dl, 0.0f);
+        }
+        if ((st = upload(own, hl.data(), hl.size(), "log axes", &w.hist_log)) != MT_OK) return st;
+    }
     w.sampler = hd->sampler;
     if (hd->sampler == MT_SAMPLER_ALIAS) {
         if ((st = upload(own, alias.data(), alias.size(), "alias tables", &w.alias)) != MT_OK) return st;
@@ -616,6 +647,22 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
 {
     w.field_kind = f->kind;
+    if (f->kind == MT_FIELD_MAP_NEAREST) {
+        // nodes as float4 (Bx, By, Bz, 0); cells of the nearest-node lookup are the
+        // nodes' Voronoi cells, i.e. a grid whose origin is half a spacing below
+        const int64_t nn = (int64_t)f->dims[0] * f->dims[1] * f->dims[2];
+        std::vector<float4> nodes(nn);
+        for (int64_t i = 0; i < nn; ++i) nodes[i] = make_float4(f->B[3 * i], f->B[3 * i + 1], f->B[3 * i + 2], 0.0f);
+        mt_status st = upload(own, nodes.data(), nodes.size(), "field nodes", &w.fmap);
+        if (st != MT_OK) return st;
+        for (int a = 0; a < 3; ++a) {
+            w.fdims[a] = f->dims[a];
+            split(f->origin[a] - 0.5 * f->spacing[a], w.forigin[a], w.forigin_lo[a]);
+            split(f->spacing[a], w.fspacing[a], w.fspacing_lo[a]);
+            w.finv[a] = (float)(1.0 / f->spacing[a]);
+        }
+        return MT_OK;
+    }
     if (f->kind != MT_FIELD_MAP) return MT_OK;
     const int nx = f->dims[0], ny = f->dims[1], nz = f->dims[2];
     const size_t nraw = 3ull * nx * ny * nz;

@@ -316,17 +316,17 @@ template <int BLOCK>
 static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
                                   cudaStream_t st)
 {
-    if (b->geom_kind == MT_GEOM_BOXES) {
-        if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_BOXES, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
-        if (b->field_kind == MT_FIELD_BOX) return run_batch<MT_GEOM_BOXES, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st);
-        return run_batch<MT_GEOM_BOXES, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
-    }
-    if (b->geom_kind == MT_GEOM_POLYHEDRA) {
-        if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_POLYHEDRA, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
-        if (b->field_kind == MT_FIELD_BOX) return run_batch<MT_GEOM_POLYHEDRA, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st);
-        return run_batch<MT_GEOM_POLYHEDRA, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
-    }
-    if (b->field_kind == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
+    const int f = b->field_kind;
+#define MT_BATCH_FIELDS(G)                                                                                 \
+    return f == MT_FIELD_MAP           ? run_batch<G, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st)          \
+           : f == MT_FIELD_MAP_NEAREST ? run_batch<G, MT_FIELD_MAP_NEAREST, BLOCK>(b, ws, n_inst, rp, S, st)  \
+           : f == MT_FIELD_BOX         ? run_batch<G, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st)          \
+                                       : run_batch<G, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st)
+    if (b->geom_kind == MT_GEOM_BOXES) MT_BATCH_FIELDS(MT_GEOM_BOXES);
+    if (b->geom_kind == MT_GEOM_POLYHEDRA) MT_BATCH_FIELDS(MT_GEOM_POLYHEDRA);
+#undef MT_BATCH_FIELDS
+    if (f == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
+    if (f == MT_FIELD_MAP_NEAREST) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST, BLOCK>(b, ws, n_inst, rp, S, st);
     return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
 }
 

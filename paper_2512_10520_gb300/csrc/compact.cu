@@ -79,6 +79,8 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
     if (w.geom_kind == MT_GEOM_BOXES) {
         if (w.field_kind == MT_FIELD_MAP)
             e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+        else if (w.field_kind == MT_FIELD_MAP_NEAREST)
+            e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else if (w.field_kind == MT_FIELD_BOX)
             e = run_passes<MT_GEOM_BOXES, MT_FIELD_BOX>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else
@@ -86,6 +88,8 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
     } else if (w.geom_kind == MT_GEOM_POLYHEDRA) {
         if (w.field_kind == MT_FIELD_MAP)
             e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+        else if (w.field_kind == MT_FIELD_MAP_NEAREST)
+            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else if (w.field_kind == MT_FIELD_BOX)
             e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_BOX>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else
@@ -93,6 +97,8 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
     } else {
         if (w.field_kind == MT_FIELD_MAP)
             e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+        else if (w.field_kind == MT_FIELD_MAP_NEAREST)
+            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else
             e = run_passes<MT_GEOM_VOXELS, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, buf);
     }

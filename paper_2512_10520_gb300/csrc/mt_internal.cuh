@@ -62,7 +62,7 @@ struct WorldParams {
     float pmin2;
     // field
     int32_t field_kind;
-    const float4 *fmap;
+    const float4 *fmap;            // trilinear: x-adjacent node pairs; nearest: nodes [nz][ny][nx]
     int32_t fdims[3];
     float forigin[3];
     float forigin_lo[3];
@@ -78,6 +78,8 @@ struct WorldParams {
     int32_t nf;
     int32_t ntheta;
     int32_t gshift;
+    int32_t axes;             // MT_AXES_LINEAR or MT_AXES_LOG
+    const float4 *hist_log;   // log axes: per histogram {f_min, d hi, d lo, 0}, {t_min, d hi, d lo, 0}, d = log2 cell width
     int32_t sampler;          // MT_SAMPLER_ICDF or MT_SAMPLER_ALIAS
     const uint2 *alias;       // alias columns {Prob_j, alias cell (a << 16) | b}, at HistRec.guide_off
     int32_t alias_bits;       // log2(nf * ntheta)

@@ -122,10 +122,30 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// floor((x - origin) / spacing) of a point given as a hi + lo pair, for a
+// grid whose origin and spacing are hi + lo pairs as well.  The offset
+// x - origin is formed as a pair; when the cell coordinate lies within 1e-4
+// of a face, the face position (index * spacing, also as a pair) settles which
+// side of it the point is on.
+__device__ __forceinline__ int grid_cell(float xh, float xl, float oh, float ol, float sh, float sl, float inv)
+{
+    float dh, de;
+    two_sum(xh, -oh, dh, de);
+    const float dl = de + (xl - ol);
+    const float u = (dh + dl) * inv;
+    int i = __float2int_rd(u);
+    const float fr = u - (float)i;
+    if (fr < 1e-4f || fr > 0.9999f) {
+        const int ic = __float2int_rn(u);
+        const float fic = (float)ic;
+        const float fh = fic * sh;
+        const float fl = fmaf(fic, sl, fmaf(fic, sh, -fh));
+        i = ((dh - fh) + (dl - fl)) >= 0.0f ? ic : ic - 1;
+    }
+    return i;
+}
+
 // GetMaterial for a voxel grid: floor((r - origin) / spacing) inside the grid.
-// The offset r - origin is formed as a hi + lo pair; when the cell coordinate
-// lies within 1e-4 of a face, the face position (index * spacing, also as a
-// pair) settles which side of it the muon is on.
 __device__ __forceinline__ int voxel_material(const WorldParams &w, const State &s)
 {
     const float r[3] = {s.x, s.y, s.z};
@@ -133,23 +153,29 @@ __device__ __forceinline__ int voxel_material(const WorldParams &w, const State 
     int idx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float dh, de;
-        two_sum(r[a], -w.vorigin[a], dh, de);
-        const float dl = de + (rl[a] - w.vorigin_lo[a]);
-        const float u = (dh + dl) * w.vinv[a];
-        int i = __float2int_rd(u);
-        const float fr = u - (float)i;
-        if (fr < 1e-4f || fr > 0.9999f) {
-            const int ic = __float2int_rn(u);
-            const float fic = (float)ic;
-            const float fh = fic * w.vspacing[a];
-            const float fl = fmaf(fic, w.vspacing_lo[a], fmaf(fic, w.vspacing[a], -fh));
-            i = ((dh - fh) + (dl - fl)) >= 0.0f ? ic : ic - 1;
-        }
+        const int i = grid_cell(r[a], rl[a], w.vorigin[a], w.vorigin_lo[a], w.vspacing[a], w.vspacing_lo[a], w.vinv[a]);
         if (i < 0 || i >= w.vdims[a]) return -1;
         idx[a] = i;
     }
     return __ldg(w.vox + ((int64_t)idx[2] * w.vdims[1] + idx[1]) * w.vdims[0] + idx[0]);
+}
+
+// Nearest-node field (the paper's lookup, Sec. Simulation item 3): the node
+// whose Voronoi cell holds the point, found as the cell of a grid shifted by
+// half a spacing (origin stored shifted); zero when that node is off the map.
+__device__ __forceinline__ float3 field_map_nearest(const WorldParams &w, const State &s)
+{
+    const float r[3] = {s.x, s.y, s.z};
+    const float rl[3] = {s.xl, s.yl, s.zl};
+    int idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int i = grid_cell(r[a], rl[a], w.forigin[a], w.forigin_lo[a], w.fspacing[a], w.fspacing_lo[a], w.finv[a]);
+        if (i < 0 || i >= w.fdims[a]) return make_float3(0.0f, 0.0f, 0.0f);
+        idx[a] = i;
+    }
+    const float4 b = __ldg(w.fmap + ((int64_t)idx[2] * w.fdims[1] + idx[1]) * w.fdims[0] + idx[0]);
+    return make_float3(b.x, b.y, b.z);
 }
 
 // Containment in solid b of the polyhedron geometry (Sec. Simulation item 1,
@@ -337,23 +363,49 @@ __device__ __forceinline__ void sin_omc(float t, float &s, float &omc)
     }
 }
 
+// Coefficients of the scattering update p <- (1 + c1) p + P c2 t^ (see
+// scatter) from a sampled cell.  Linear axes (f = dp/p, theta):
+// c1 = (1 - f) cos(theta) - 1 and c2 = (1 - f) sin(theta), so |p| becomes
+// (1 - f) P at angle theta.  Log axes (f = -dPz/P, t = dPt/P, the paper's
+// histogram variables): c1 = -f and c2 = t, Algorithm 1's dz = -P f and
+// dt = P t added as they are.
+__device__ __forceinline__ void coeffs_angle(float f, float theta, float &c1, float &c2)
+{
+    float st, omc;
+    sin_omc(theta, st, omc);
+    c1 = -fmaf(f, 1.0f - omc, omc);
+    c2 = (1.0f - f) * st;
+}
+
+// Value at cell a + jitter u of a log-spaced axis with lower edge v0 and
+// log2 cell width d: v0 2^((a + u) d).  a d is split off exactly (d held as
+// hi + lo, the product as a pair) and its integer part applied by ldexpf, so
+// exp2f sees only a fraction below ~2 and the value carries ~1e-7 relative
+// error (a plain FP32 exponent of up to ~33 would carry ~2e-6).
+// h = (v0, d hi, d lo, -).
+__device__ __forceinline__ float log_axis_value(float4 h, int a, float u)
+{
+    const float fa = (float)a;
+    const float p = fa * h.y;
+    const float e = fmaf(fa, h.z, fmaf(fa, h.y, -p));
+    const float n = floorf(p);
+    const float r = fmaf(u, h.y, (p - n) + e);
+    return ldexpf(h.x * exp2f(r), (int)n);
+}
+
 // Eq. 3: p <- p + Rot(dp) with dp = [dt cos phi, dt sin phi, dz] in the frame whose
-// z axis is p^.  Written as p <- p + (s - 1) p + P (1-f) sin(theta) t, where
-// s = (1-f) cos(theta) and t = R x^ cos(phi) + R y^ sin(phi) is the rotated
-// transverse unit vector (R: the Rodrigues rotation taking z^ to p^).  The whole
-// increment is small, so it is accumulated into the hi + lo momentum.
-__device__ __forceinline__ void scatter(State &s, float f, float theta, float cphi, float sphi)
+// z axis is p^.  Written as p <- p + c1 p + P c2 t, with dz = P c1 and dt = P c2,
+// where t = R x^ cos(phi) + R y^ sin(phi) is the rotated transverse unit vector
+// (R: the Rodrigues rotation taking z^ to p^).  The whole increment is small,
+// so it is accumulated into the hi + lo momentum.
+__device__ __forceinline__ void scatter(State &s, float c1, float c2, float cphi, float sphi)
 {
     const float P2 = p2_of(s);
     float rP = rsqrtf(P2);
     rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
     const float P = P2 * rP;
     const float ux = s.px * rP, uy = s.py * rP, uz = s.pz * rP;
-    float st, omc;
-    sin_omc(theta, st, omc);
-    const float ct = 1.0f - omc;
-    const float sm1 = -fmaf(f, ct, omc);              // (1-f) cos(theta) - 1
-    const float kick = P * (1.0f - f) * st;
+    const float kick = P * c2;
     const float s2 = fmaf(ux, ux, uy * uy);
     float tx, ty, tz;
     if (uz < 0.0f && s2 < 1e-24f) {                   // p^ = -z^: R = diag(1,-1,-1)
@@ -367,9 +419,9 @@ __device__ __forceinline__ void scatter(State &s, float f, float theta, float cp
         ty = fmaf(-(uy * wv), g, sphi);
         tz = -wv;
     }
-    acc(s.px, s.pxl, fmaf(sm1, s.px, kick * tx));
-    acc(s.py, s.pyl, fmaf(sm1, s.py, kick * ty));
-    acc(s.pz, s.pzl, fmaf(sm1, s.pz, kick * tz));
+    acc(s.px, s.pxl, fmaf(c1, s.px, kick * tx));
+    acc(s.py, s.pyl, fmaf(c1, s.py, kick * ty));
+    acc(s.pz, s.pzl, fmaf(c1, s.pz, kick * tz));
 }
 
 // a + t (b - a)
@@ -512,14 +564,27 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         const float phs = fmaf(6.283185307179586f, u01(rnd.w), -3.14159265358979f);   // phi - pi
         float sp, cp;
         __sincosf(phs, &sp, &cp);
-        rec.draw(f, th, phs);
-        scatter(s, f, th, -cp, -sp);
+        float c1, c2;
+        if (w.axes == MT_AXES_LOG) {
+            // f and t log-spaced: cell + jitter in log f, log t (the cell's
+            // linear values f, th above are not used)
+            const float4 *hl = w.hist_log + 2 * ((mat - 1) * w.n_pbin + ib);
+            const float4 hf = __ldg(hl), ht = __ldg(hl + 1);
+            c1 = -log_axis_value(hf, (int)(ab >> 16), u01(rnd.y));
+            c2 = log_axis_value(ht, (int)(ab & 0xFFFFu), u01(rnd.z));
+        } else {
+            coeffs_angle(f, th, c1, c2);
+        }
+        rec.draw(c1, c2, phs);
+        scatter(s, c1, c2, -cp, -sp);
     }
     float3 B = make_float3(0.0f, 0.0f, 0.0f);
     if (FIELD == MT_FIELD_BOX) {
         if (box >= 0) B = make_float3(sw.B[0][box], sw.B[1][box], sw.B[2][box]);
     } else if (FIELD == MT_FIELD_MAP) {
         B = field_map(w, s);
+    } else if (FIELD == MT_FIELD_MAP_NEAREST) {
+        B = field_map_nearest(w, s);
     }
     rec.field(B);   // before the block scale
     if (GEOM != MT_GEOM_VOXELS && FIELD != MT_FIELD_NONE && box >= 0) {

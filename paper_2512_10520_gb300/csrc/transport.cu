@@ -249,6 +249,8 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     if (w.geom_kind == MT_GEOM_BOXES) {
         if (w.field_kind == MT_FIELD_MAP)
             e = launch<MT_GEOM_BOXES, MT_FIELD_MAP>(w, *s, n, rp, cs, lc);
+        else if (w.field_kind == MT_FIELD_MAP_NEAREST)
+            e = launch<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>(w, *s, n, rp, cs, lc);
         else if (w.field_kind == MT_FIELD_BOX)
             e = launch<MT_GEOM_BOXES, MT_FIELD_BOX>(w, *s, n, rp, cs, lc);
         else
@@ -256,6 +258,8 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     } else if (w.geom_kind == MT_GEOM_POLYHEDRA) {
         if (w.field_kind == MT_FIELD_MAP)
             e = launch<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>(w, *s, n, rp, cs, lc);
+        else if (w.field_kind == MT_FIELD_MAP_NEAREST)
+            e = launch<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>(w, *s, n, rp, cs, lc);
         else if (w.field_kind == MT_FIELD_BOX)
             e = launch<MT_GEOM_POLYHEDRA, MT_FIELD_BOX>(w, *s, n, rp, cs, lc);
         else
@@ -263,6 +267,8 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     } else {
         if (w.field_kind == MT_FIELD_MAP)
             e = launch<MT_GEOM_VOXELS, MT_FIELD_MAP>(w, *s, n, rp, cs, lc);
+        else if (w.field_kind == MT_FIELD_MAP_NEAREST)
+            e = launch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(w, *s, n, rp, cs, lc);
         else
             e = launch<MT_GEOM_VOXELS, MT_FIELD_NONE>(w, *s, n, rp, cs, lc);
     }
