@@ -45,7 +45,8 @@ class World(C.Structure):
         ("vox", C.c_void_p),
         ("x_max", C.c_double), ("y_max", C.c_double), ("z_max", C.c_double), ("p_min", C.c_double),
         ("field_kind", C.c_int32), ("fdims", C.c_int32 * 3), ("forigin", C.c_double * 3),
-        ("fspacing", C.c_double * 3), ("Bmap", C.c_void_p), ("alpha", C.c_void_p), ("n_block", C.c_int32),
+        ("fspacing", C.c_double * 3), ("Bmap", C.c_void_p), ("field_per_stage", C.c_int32), ("alpha", C.c_void_p),
+        ("n_block", C.c_int32),
         ("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("nf", C.c_int32), ("ntheta", C.c_int32),
         ("p_lo", C.c_double), ("p_hi", C.c_double),
         ("f_max", C.c_void_p), ("theta_max", C.c_void_p), ("T", C.c_void_p),
@@ -260,6 +261,7 @@ class OracleWorld:
             w.forigin[:] = list(map(float, field["origin"]))
             w.fspacing[:] = list(map(float, field["spacing"]))
             w.Bmap = _p(B)
+            w.field_per_stage = int(bool(field.get("per_stage", False)))
         else:
             raise ValueError(fk)
         if alpha is not None:

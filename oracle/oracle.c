@@ -82,6 +82,7 @@ typedef struct or_world {
     double forigin[3];
     double fspacing[3];
     const float *Bmap;          /* [nz][ny][nx][3] */
+    int32_t field_per_stage;    /* 1: RK4 reads the map at each stage's position (map kinds only) */
     const double *alpha;        /* [n_block][3] field scales, or NULL */
     int32_t n_block;
     /* histograms */
@@ -467,6 +468,43 @@ void or_rk4(double r[3], double p[3], const double B[3], int32_t q, double d)
     }
 }
 
+/* RK4 with the field read at each stage's position (a variant of the step:
+ * Algorithm 1 reads the field once, at the start of the step): classical RK4
+ * on y = (r, p) with F(r, p) = (p/P0, kappa q p x B(r)/P0), P0 = |p| at the
+ * start of the step, B(r) the map at r times the scale of the block that
+ * holds the step's start (box), the stages at r + d/2 k1r, r + d/2 k2r and
+ * r + d k3r. */
+void or_rk4_staged(const or_world *w, double r[3], double p[3], int32_t box, int32_t q, double d)
+{
+    double P0 = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    double qk = OR_KAPPA * (double)q;
+    double k1r[3], k1p[3], k2r[3], k2p[3], k3r[3], k3p[3], k4r[3], k4p[3], tr[3], tp[3], B[3];
+    or_field(w, r, box, B);
+    or_deriv(p, B, qk, P0, k1r, k1p);
+    for (int c = 0; c < 3; ++c) {
+        tr[c] = r[c] + 0.5 * d * k1r[c];
+        tp[c] = p[c] + 0.5 * d * k1p[c];
+    }
+    or_field(w, tr, box, B);
+    or_deriv(tp, B, qk, P0, k2r, k2p);
+    for (int c = 0; c < 3; ++c) {
+        tr[c] = r[c] + 0.5 * d * k2r[c];
+        tp[c] = p[c] + 0.5 * d * k2p[c];
+    }
+    or_field(w, tr, box, B);
+    or_deriv(tp, B, qk, P0, k3r, k3p);
+    for (int c = 0; c < 3; ++c) {
+        tr[c] = r[c] + d * k3r[c];
+        tp[c] = p[c] + d * k3p[c];
+    }
+    or_field(w, tr, box, B);
+    or_deriv(tp, B, qk, P0, k4r, k4p);
+    for (int c = 0; c < 3; ++c) {
+        r[c] += d / 6.0 * (k1r[c] + 2.0 * k2r[c] + 2.0 * k3r[c] + k4r[c]);
+        p[c] += d / 6.0 * (k1p[c] + 2.0 * k2p[c] + 2.0 * k3p[c] + k4p[c]);
+    }
+}
+
 /* One step's random choices (recorded for the adjoint and for tests). */
 typedef struct or_step_draw {
     int32_t mat, box, pbin, cell;
@@ -550,8 +588,13 @@ void or_transport_one(const or_world *w, double r[3], double p[3], int32_t q, in
         or_step_draw dr;
         if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter_draw(w, p, &dr, p);
         double B[3];
-        or_field(w, r, dr.box, B);
-        or_rk4(r, p, B, q, d);
+        if (w->field_per_stage) {
+            or_field(w, r, dr.box, B);
+            or_rk4_staged(w, r, p, dr.box, q, d);
+        } else {
+            or_field(w, r, dr.box, B);
+            or_rk4(r, p, B, q, d);
+        }
         *steps = k + 1;
     }
     *status = (uint8_t)st;
@@ -627,7 +670,10 @@ int32_t or_trace(const or_world *w, double r[3], double p[3], int32_t q, int32_t
         for (int c = 0; c < 3; ++c) dbuf[9 * s + 6 + c] = B[c];
         ibuf[4 * s + 0] = dr.mat; ibuf[4 * s + 1] = dr.box; ibuf[4 * s + 2] = dr.pbin; ibuf[4 * s + 3] = dr.cell;
         fbuf[3 * s + 0] = dr.f; fbuf[3 * s + 1] = dr.theta; fbuf[3 * s + 2] = dr.phi;
-        or_rk4(r, p, B, q, d);
+        if (w->field_per_stage)
+            or_rk4_staged(w, r, p, dr.box, q, d);
+        else
+            or_rk4(r, p, B, q, d);
         ++s;
     }
     return s;
@@ -905,8 +951,13 @@ static void or_adjoint_one(const or_world *w, const double r0[3], const double p
         t->phi = dr.phi;
         if (t->scattered) or_scatter_draw(w, p, &dr, p);
         double B[3];
-        or_field(w, r, dr.box, B);
-        or_rk4(r, p, B, q, d);
+        if (w->field_per_stage) {
+            or_field(w, r, dr.box, B);
+            or_rk4_staged(w, r, p, dr.box, q, d);
+        } else {
+            or_field(w, r, dr.box, B);
+            or_rk4(r, p, B, q, d);
+        }
     }
     double rbar[3] = {g6[0], g6[1], g6[2]}, pbar[3] = {g6[3], g6[4], g6[5]};
     for (int32_t s = ns - 1; s >= 0; --s) {
@@ -977,6 +1028,7 @@ int or_adjoint(const or_world *w, int64_t n, const double *x, const double *y, c
                double *dalpha, int32_t n_threads)
 {
     if (!w || !w->alpha || w->n_block < 1 || w->n_block > 64 || n < 0 || n_threads < 1) return -1;
+    if (w->field_per_stage) return -3;          /* the adjoint holds the field over the step */
     for (int i = 0; i < 3 * w->n_block; ++i) dalpha[i] = 0.0;
     if (n == 0) return 0;
     if (n_threads > 256) n_threads = 256;

@@ -139,3 +139,59 @@ def test_adjoint_of_variants_matches_dual_numbers(variant):
     scale = np.abs(dual).max()
     assert scale > 0
     np.testing.assert_allclose(adj.ravel(), dual, rtol=1e-9, atol=1e-12 * scale)
+
+
+def _linear_field_map(b0=1.25, b1=0.75, per_stage=True):
+    """A node map of B = (b1 z / 8, b0 + b1 z, 0), trilinear reproduces it exactly;
+    dyadic nodes and coefficients make the float32 node values exact."""
+    nx, ny, nz = 3, 3, 33
+    z = -0.5 + 0.125 * np.arange(nz)
+    B = np.zeros((nz, ny, nx, 3), np.float32)
+    B[..., 0] = (0.125 * b1 * z)[:, None, None]
+    B[..., 1] = (b0 + b1 * z)[:, None, None]
+    return dict(kind="map", dims=[nx, ny, nz], origin=[-5.0, -5.0, -0.5], spacing=[5.0, 5.0, 0.125],
+                B=np.ascontiguousarray(B), per_stage=per_stage)
+
+
+def _ode_reference(r0, p0, q, L, b0=1.25, b1=0.75):
+    from scipy.integrate import solve_ivp
+    P0 = np.linalg.norm(p0)
+
+    def rhs(s, y):
+        r, p = y[:3], y[3:]
+        Bv = np.array([0.125 * b1 * r[2], b0 + b1 * r[2], 0.0])
+        return np.concatenate([p / P0, 0.299792458 * q * np.cross(p, Bv) / P0])
+    sol = solve_ivp(rhs, (0.0, L), np.concatenate([r0, p0]), method="DOP853", rtol=1e-13, atol=1e-15)
+    return sol.y[:, -1]
+
+
+def _run(field, d, n_steps, r0, p0, q):
+    geo = dict(kind="boxes", boxes=[], world_material=0, x_max=100.0, y_max=100.0, z_max=1e6, p_min=0.1)
+    w = oracle.OracleWorld(geo, field, tiny_hist())
+    mu = {k: np.array([v], np.float32) for k, v in zip(("x", "y", "z", "px", "py", "pz"), list(r0) + list(p0))}
+    mu.update(q=np.array([q], np.int8), steps=np.zeros(1, np.int32), status=np.zeros(1, np.uint8))
+    out = oracle.transport(w, mu, d, n_steps, 1)
+    return np.array([out[k][0] for k in ("x", "y", "z", "px", "py", "pz")])
+
+
+def test_per_stage_field_equals_fixed_field_in_a_uniform_map():
+    fld_u = _linear_field_map(b1=0.0, per_stage=True)
+    fld_f = dict(fld_u, per_stage=False)
+    r0, p0 = np.array([0.1, -0.2, 0.0]), np.array([0.3, 0.1, 2.0])
+    a = _run(fld_u, 0.02, 50, r0, p0, -1)
+    b = _run(fld_f, 0.02, 50, r0, p0, -1)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_per_stage_field_is_fourth_order_in_a_varying_field():
+    r0, p0, q, L = np.array([0.125, -0.25, 0.0]), np.array([0.25, 0.125, 2.0]), -1, 2.0   # exact in float32
+    ref = _ode_reference(r0, p0, q, L)
+    err = {}
+    for per_stage in (True, False):
+        fld = _linear_field_map(per_stage=per_stage)
+        err[per_stage] = [np.abs(_run(fld, L / n, n, r0, p0, q) - ref).max() for n in (40, 80, 160)]
+    e = err[True]
+    assert 10.0 < e[0] / e[1] < 24.0 and 10.0 < e[1] / e[2] < 24.0, e       # ~16: fourth order
+    f = err[False]
+    assert 1.6 < f[0] / f[1] < 2.6 and 1.6 < f[1] / f[2] < 2.6, f           # ~2: the held field is first order
+    assert e[0] < 1e-3 * f[0]
