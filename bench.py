@@ -669,8 +669,12 @@ def run_mine(args):
         for name, kw, desc in (("nearest_field", dict(field="nearest"),
                                 "config1 with the map read at the nearest node (the paper's lookup, 1 gather)"),
                                ("log_axes", dict(axes="log"),
-                                "config1 with histograms on log-scaled (-dPz/P, dPt/P) axes, additive dp")):
+                                "config1 with histograms on log-scaled (-dPz/P, dPt/P) axes, additive dp"),
+                               ("per_stage_field", dict(),
+                                "config1 with the map read at every RK4 stage (4 trilinear lookups per step)")):
             wv = gen.workload("config1", n=args.muons, **kw)
+            if name == "per_stage_field":
+                wv.field = dict(wv.field, per_stage=True)
             tv, sv = _time_world(mt, wv, wv.geometry, dev, stream, 3, id_offset)
             forms[name] = dict(value=_barrier_sum(sv, ws, dev) / _barrier_max(tv, ws, dev), unit=UNIT,
                                kernel_ms=1e3 * tv, muon_steps=sv, vs_plain=(sv / tv) / value, workload=desc)

@@ -119,12 +119,21 @@ typedef struct mt_geometry_desc {
  * zero where that node is outside the map.  No dB/dr (piecewise constant).
  * MT_FIELD_BOX: the uniform field B of the box or solid holding the point. */
 typedef struct mt_field_desc {
-    int32_t kind;                 /* MT_FIELD_NONE / MT_FIELD_BOX / MT_FIELD_MAP      */
+    int32_t kind;                 /* MT_FIELD_NONE / _BOX / _MAP / _MAP_NEAREST       */
     int32_t dims[3];              /* map: nx, ny, nz (each >= 2)                      */
     double origin[3];
     double spacing[3];            /* > 0                                             */
     const float *B;               /* host, [nz][ny][nx][3] float32 (Bx, By, Bz)       */
+    int32_t per_stage;            /* MT_FIELD_MAP only: 1 = RK4 reads the map at each */
+    int32_t reserved;             /*   stage's position (see below); 0 = once a step  */
 } mt_field_desc;
+
+/* per_stage = 1 is a variant of the step: Algorithm 1 reads the field once, at
+ * the start of the step, and holds it over the RK4 stages (the default); with
+ * per_stage the stages at r + d/2 k1, r + d/2 k2 and r + d k3 read the map
+ * there (scaled by the block of the step's start), which makes the step fourth
+ * order in a varying field.  The differentiable form does not take it
+ * (MT_ERR_INVALID_ARG). */
 
 /* Histogram set H_{M,i} (Sec. Building histograms): for materials M = 1..n_mat
  * and log10 momentum bins i = 0..n_pbin-1 on [p_lo, p_hi] (edges

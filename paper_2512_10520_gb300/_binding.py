@@ -52,7 +52,7 @@ class mt_geometry_desc(C.Structure):
 
 class mt_field_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dims", C.c_int32 * 3), ("origin", C.c_double * 3),
-                ("spacing", C.c_double * 3), ("B", C.c_void_p)]
+                ("spacing", C.c_double * 3), ("B", C.c_void_p), ("per_stage", C.c_int32), ("reserved", C.c_int32)]
 
 
 class mt_hist_desc(C.Structure):
@@ -261,6 +261,7 @@ class _Descs:
             f.origin[:] = list(map(float, field["origin"]))
             f.spacing[:] = list(map(float, field["spacing"]))
             f.B = B.ctypes.data
+        f.per_stage = int(bool(field.get("per_stage", False)))
         return f
 
     @staticmethod

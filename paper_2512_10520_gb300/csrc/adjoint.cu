@@ -431,7 +431,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
 template <int GEOM, int FIELD, bool FWD>
-__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM>())
+__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM, FIELD>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
               const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
               unsigned long long *tape_off, int64_t region_cap, unsigned int *flag)
@@ -805,6 +805,10 @@ extern "C" mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64
         set_error("null muon array with n > 0");
         return MT_ERR_INVALID_ARG;
     }
+    if (h && h->w.field_per_stage) {
+        set_error("the differentiable form holds the field over each step: per_stage is not supported");
+        return MT_ERR_INVALID_ARG;
+    }
     RunParams rp;
     mt_status stt = fill_run(rp, step_len, max_steps, seed, alpha, n_block, s->id_offset, s->instance);
     if (stt != MT_OK) return stt;
@@ -825,6 +829,10 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
 {
     if (!h) {
         set_error("null handle");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h && h->w.field_per_stage) {
+        set_error("the differentiable form holds the field over each step: per_stage is not supported");
         return MT_ERR_INVALID_ARG;
     }
     RunParams rp;
@@ -912,6 +920,10 @@ extern "C" mt_status mt_transport_tape(mt_handle *h, const mt_muon_soa *s, int64
         set_error("null muon array with n > 0");
         return MT_ERR_INVALID_ARG;
     }
+    if (h && h->w.field_per_stage) {
+        set_error("the differentiable form holds the field over each step: per_stage is not supported");
+        return MT_ERR_INVALID_ARG;
+    }
     RunParams rp;
     mt_status stt = fill_run(rp, step_len, max_steps, seed, alpha, n_block, s->id_offset, s->instance);
     if (stt != MT_OK) return stt;
@@ -931,6 +943,10 @@ extern "C" mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, in
 {
     if (!h) {
         set_error("null handle");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h && h->w.field_per_stage) {
+        set_error("the differentiable form holds the field over each step: per_stage is not supported");
         return MT_ERR_INVALID_ARG;
     }
     RunParams rp;
@@ -984,6 +1000,10 @@ extern "C" mt_status mt_transport_adjoint(mt_handle *h, const mt_muon_soa *s0, i
 {
     if (!h || !s0) {
         set_error("null handle or muon SoA");
+        return MT_ERR_INVALID_ARG;
+    }
+    if (h && h->w.field_per_stage) {
+        set_error("the differentiable form holds the field over each step: per_stage is not supported");
         return MT_ERR_INVALID_ARG;
     }
     if (ckpt_every < 1 || ckpt_every > kTapeMax || n < 0 || n >= ((int64_t)1 << 31)) {

@@ -303,6 +303,10 @@ mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g)
         set_error("null field descriptor");
         return MT_ERR_INVALID_ARG;
     }
+    if (f->per_stage != 0 && (f->per_stage != 1 || f->kind != MT_FIELD_MAP)) {
+        set_error("field: per_stage must be 0, or 1 with MT_FIELD_MAP");
+        return MT_ERR_INVALID_ARG;
+    }
     if (f->kind == MT_FIELD_MAP || f->kind == MT_FIELD_MAP_NEAREST) {
         if (!f->B || f->dims[0] < 2 || f->dims[1] < 2 || f->dims[2] < 2 || !finite3(f->origin) ||
             !(f->spacing[0] > 0) || !(f->spacing[1] > 0) || !(f->spacing[2] > 0)) {
@@ -647,6 +651,7 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
 {
     w.field_kind = f->kind;
+    w.field_per_stage = f->per_stage;
     if (f->kind == MT_FIELD_MAP_NEAREST) {
         // nodes as float4 (Bx, By, Bz, 0); cells of the nearest-node lookup are the
         // nodes' Voronoi cells, i.e. a grid whose origin is half a spacing below

@@ -31,7 +31,7 @@
 struct mt_batch {
     int device = 0;
     int n_inst = 0;
-    int geom_kind = -1, field_kind = -1;
+    int geom_kind = -1, field_kind = -1, field_per_stage = -1;
     int hist_n_mat = 0;
     mt::WorldParams tables;                 // histogram part shared by every instance
     mt::DevOwner own_tables;
@@ -317,14 +317,17 @@ static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, co
                                   cudaStream_t st)
 {
     const int f = b->field_kind;
+    const bool staged = b->field_per_stage != 0;
 #define MT_BATCH_FIELDS(G)                                                                                 \
-    return f == MT_FIELD_MAP           ? run_batch<G, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st)          \
+    return f == MT_FIELD_MAP && staged ? run_batch<G, kFieldMapStaged, BLOCK>(b, ws, n_inst, rp, S, st)       \
+           : f == MT_FIELD_MAP         ? run_batch<G, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st)          \
            : f == MT_FIELD_MAP_NEAREST ? run_batch<G, MT_FIELD_MAP_NEAREST, BLOCK>(b, ws, n_inst, rp, S, st)  \
            : f == MT_FIELD_BOX         ? run_batch<G, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st)          \
                                        : run_batch<G, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st)
     if (b->geom_kind == MT_GEOM_BOXES) MT_BATCH_FIELDS(MT_GEOM_BOXES);
     if (b->geom_kind == MT_GEOM_POLYHEDRA) MT_BATCH_FIELDS(MT_GEOM_POLYHEDRA);
 #undef MT_BATCH_FIELDS
+    if (f == MT_FIELD_MAP && staged) return run_batch<MT_GEOM_VOXELS, kFieldMapStaged, BLOCK>(b, ws, n_inst, rp, S, st);
     if (f == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
     if (f == MT_FIELD_MAP_NEAREST) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST, BLOCK>(b, ws, n_inst, rp, S, st);
     return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
@@ -414,7 +417,8 @@ mt_status mt_batch_set_instance(mt_batch *b, int32_t i, const mt_geometry_desc *
     mt_status st = validate_geometry(g, b->hist_n_mat);
     if (st == MT_OK) st = validate_field(f, g);
     if (st != MT_OK) return st;
-    if ((b->geom_kind >= 0 && g->kind != b->geom_kind) || (b->field_kind >= 0 && f->kind != b->field_kind)) {
+    if ((b->geom_kind >= 0 && g->kind != b->geom_kind) || (b->field_kind >= 0 && f->kind != b->field_kind) ||
+        (b->field_per_stage >= 0 && f->per_stage != b->field_per_stage)) {
         set_error("every instance of a batch needs the same geometry kind and field kind");
         return MT_ERR_INVALID_ARG;
     }
@@ -432,6 +436,7 @@ mt_status mt_batch_set_instance(mt_batch *b, int32_t i, const mt_geometry_desc *
     b->is_set[i] = 1;
     b->geom_kind = g->kind;
     b->field_kind = f->kind;
+    b->field_per_stage = f->per_stage;
     b->dirty = true;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);

@@ -77,7 +77,9 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
     }
     cudaError_t e;
     if (w.geom_kind == MT_GEOM_BOXES) {
-        if (w.field_kind == MT_FIELD_MAP)
+        if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
+            e = run_passes<MT_GEOM_BOXES, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+        else if (w.field_kind == MT_FIELD_MAP)
             e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
             e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
@@ -86,7 +88,9 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
         else
             e = run_passes<MT_GEOM_BOXES, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, buf);
     } else if (w.geom_kind == MT_GEOM_POLYHEDRA) {
-        if (w.field_kind == MT_FIELD_MAP)
+        if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
+            e = run_passes<MT_GEOM_POLYHEDRA, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+        else if (w.field_kind == MT_FIELD_MAP)
             e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
             e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
@@ -95,7 +99,9 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
         else
             e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, buf);
     } else {
-        if (w.field_kind == MT_FIELD_MAP)
+        if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
+            e = run_passes<MT_GEOM_VOXELS, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+        else if (w.field_kind == MT_FIELD_MAP)
             e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
             e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);

@@ -19,10 +19,12 @@
 #endif
 
 namespace mt {
-template <int GEOM>
+// Per-stage field reads (three more map lookups live in the RK4 step) take
+// the polyhedron budget as well.
+template <int GEOM, int FIELD>
 constexpr int pass_min_blocks()
 {
-    return GEOM == MT_GEOM_POLYHEDRA ? MT_PASS_MIN_BLOCKS_POLY : MT_PASS_MIN_BLOCKS;
+    return (GEOM == MT_GEOM_POLYHEDRA || FIELD == kFieldMapStaged) ? MT_PASS_MIN_BLOCKS_POLY : MT_PASS_MIN_BLOCKS;
 }
 }  // namespace mt
 
@@ -49,7 +51,7 @@ static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa 
 // One pass: live count from *cin, survivors appended at *cout; *czero (if not
 // null) is cleared for the pass after this one.
 template <int GEOM, int FIELD>
-__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM>()) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
+__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM, FIELD>()) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
                                                        LiveBuf in, LiveBuf out, const unsigned long long *cin,
                                                        unsigned long long *cout, unsigned long long *czero, int S)
 {

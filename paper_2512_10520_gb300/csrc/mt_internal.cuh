@@ -39,6 +39,9 @@ struct HistRec {
 
 constexpr int kZSlabs = 256;   // z slabs of the box-candidate index
 
+// Field template value of the kernels for MT_FIELD_MAP with per_stage set.
+constexpr int kFieldMapStaged = 4;
+
 struct WorldParams {
     // geometry
     int32_t geom_kind;
@@ -62,6 +65,7 @@ struct WorldParams {
     float pmin2;
     // field
     int32_t field_kind;
+    int32_t field_per_stage;       // MT_FIELD_MAP read at every RK4 stage (kernels: kFieldMapStaged)
     const float4 *fmap;            // trilinear: x-adjacent node pairs; nearest: nodes [nz][ny][nx]
     int32_t fdims[3];
     float forigin[3];

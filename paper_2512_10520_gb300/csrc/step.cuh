@@ -511,6 +511,51 @@ float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
     acc(s.pz, s.pzl, sixth * (k1z + 2.0f * (k2z + k3z) + k4z));
 }
 
+// RK4 with the field read at each stage's position (variant of the step, see
+// mt_field_desc.per_stage): B1 is the scaled field at the step's start and sc
+// the block scale applied to the later stages.  Stage positions are carried in
+// the lo words (r + (d/2) p/P0, r + (d/2) p2/P0, r + d p3/P0), which the map
+// lookup reads as hi + lo pairs.  The updates are those of rk4 with h_i from
+// each stage's field.
+__device__ __forceinline__ void rk4_staged(const WorldParams &w, State &s, float3 B1, float3 sc, float q, float d,
+                                           float kd)
+{
+    const float px = s.px, py = s.py, pz = s.pz;
+    const float P2 = p2_of(s);
+    float rP = rsqrtf(P2);
+    rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
+    const float c = (kd * q) * rP;
+    const float a = d * rP;
+    float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+    cross_h(px, py, pz, c * B1.x, c * B1.y, c * B1.z, k1x, k1y, k1z);
+    State t = s;
+    const float ha = 0.5f * a;
+    t.xl = fmaf(ha, px, s.xl);
+    t.yl = fmaf(ha, py, s.yl);
+    t.zl = fmaf(ha, pz, s.zl);
+    float3 B = field_map(w, t);
+    const float p2x = fmaf(0.5f, k1x, px), p2y = fmaf(0.5f, k1y, py), p2z = fmaf(0.5f, k1z, pz);
+    cross_h(p2x, p2y, p2z, c * (sc.x * B.x), c * (sc.y * B.y), c * (sc.z * B.z), k2x, k2y, k2z);
+    t.xl = fmaf(ha, p2x, s.xl);
+    t.yl = fmaf(ha, p2y, s.yl);
+    t.zl = fmaf(ha, p2z, s.zl);
+    B = field_map(w, t);
+    const float p3x = fmaf(0.5f, k2x, px), p3y = fmaf(0.5f, k2y, py), p3z = fmaf(0.5f, k2z, pz);
+    cross_h(p3x, p3y, p3z, c * (sc.x * B.x), c * (sc.y * B.y), c * (sc.z * B.z), k3x, k3y, k3z);
+    t.xl = fmaf(a, p3x, s.xl);
+    t.yl = fmaf(a, p3y, s.yl);
+    t.zl = fmaf(a, p3z, s.zl);
+    B = field_map(w, t);
+    cross_h(px + k3x, py + k3y, pz + k3z, c * (sc.x * B.x), c * (sc.y * B.y), c * (sc.z * B.z), k4x, k4y, k4z);
+    const float sixth = 1.0f / 6.0f;
+    acc(s.x, s.xl, a * fmaf(sixth, k1x + k2x + k3x, px));
+    acc(s.y, s.yl, a * fmaf(sixth, k1y + k2y + k3y, py));
+    acc(s.z, s.zl, a * fmaf(sixth, k1z + k2z + k3z, pz));
+    acc(s.px, s.pxl, sixth * (k1x + 2.0f * (k2x + k3x) + k4x));
+    acc(s.py, s.pyl, sixth * (k1y + 2.0f * (k2y + k3y) + k4y));
+    acc(s.pz, s.pzl, sixth * (k1z + 2.0f * (k2z + k3z) + k4z));
+}
+
 // Termination test of Algorithm 1 at the start of a step.
 __device__ __forceinline__ int check_stop(const WorldParams &w, const State &s, float P2)
 {
@@ -581,21 +626,26 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
     float3 B = make_float3(0.0f, 0.0f, 0.0f);
     if (FIELD == MT_FIELD_BOX) {
         if (box >= 0) B = make_float3(sw.B[0][box], sw.B[1][box], sw.B[2][box]);
-    } else if (FIELD == MT_FIELD_MAP) {
+    } else if (FIELD == MT_FIELD_MAP || FIELD == kFieldMapStaged) {
         B = field_map(w, s);
     } else if (FIELD == MT_FIELD_MAP_NEAREST) {
         B = field_map_nearest(w, s);
     }
     rec.field(B);   // before the block scale
+    float3 sc = make_float3(1.0f, 1.0f, 1.0f);
     if (GEOM != MT_GEOM_VOXELS && FIELD != MT_FIELD_NONE && box >= 0) {
         const int blk = sw.block[box];
         if (blk >= 0) {
-            B.x *= sw.alpha[0][blk];
-            B.y *= sw.alpha[1][blk];
-            B.z *= sw.alpha[2][blk];
+            sc = make_float3(sw.alpha[0][blk], sw.alpha[1][blk], sw.alpha[2][blk]);
+            B.x *= sc.x;
+            B.y *= sc.y;
+            B.z *= sc.z;
         }
     }
-    rk4(s, B, q, rp.d, rp.kd);
+    if (FIELD == kFieldMapStaged)
+        rk4_staged(w, s, B, sc, q, rp.d, rp.kd);
+    else
+        rk4(s, B, q, rp.d, rp.kd);
     return MT_ALIVE;
 }
 

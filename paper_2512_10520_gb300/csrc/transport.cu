@@ -247,7 +247,9 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
         return MT_OK;
     }
     if (w.geom_kind == MT_GEOM_BOXES) {
-        if (w.field_kind == MT_FIELD_MAP)
+        if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
+            e = launch<MT_GEOM_BOXES, kFieldMapStaged>(w, *s, n, rp, cs, lc);
+        else if (w.field_kind == MT_FIELD_MAP)
             e = launch<MT_GEOM_BOXES, MT_FIELD_MAP>(w, *s, n, rp, cs, lc);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
             e = launch<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>(w, *s, n, rp, cs, lc);
@@ -256,7 +258,9 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
         else
             e = launch<MT_GEOM_BOXES, MT_FIELD_NONE>(w, *s, n, rp, cs, lc);
     } else if (w.geom_kind == MT_GEOM_POLYHEDRA) {
-        if (w.field_kind == MT_FIELD_MAP)
+        if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
+            e = launch<MT_GEOM_POLYHEDRA, kFieldMapStaged>(w, *s, n, rp, cs, lc);
+        else if (w.field_kind == MT_FIELD_MAP)
             e = launch<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>(w, *s, n, rp, cs, lc);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
             e = launch<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>(w, *s, n, rp, cs, lc);
@@ -265,7 +269,9 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
         else
             e = launch<MT_GEOM_POLYHEDRA, MT_FIELD_NONE>(w, *s, n, rp, cs, lc);
     } else {
-        if (w.field_kind == MT_FIELD_MAP)
+        if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
+            e = launch<MT_GEOM_VOXELS, kFieldMapStaged>(w, *s, n, rp, cs, lc);
+        else if (w.field_kind == MT_FIELD_MAP)
             e = launch<MT_GEOM_VOXELS, MT_FIELD_MAP>(w, *s, n, rp, cs, lc);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
             e = launch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(w, *s, n, rp, cs, lc);

@@ -94,3 +94,49 @@ def test_variant_adjoint_matches_fp64_oracle_adjoint(variant):
     rel = np.linalg.norm(g_gpu - g_ora) / np.linalg.norm(g_ora)
     print(variant, "adjoint rel", rel)
     assert rel <= 1e-3, (rel, g_gpu.ravel().tolist(), g_ora.ravel().tolist())
+
+
+def _per_stage(wl):
+    wl.field = dict(wl.field, per_stage=True)
+    return wl
+
+
+def test_per_stage_field_parity():
+    wl = _per_stage(gen.workload("config1", n=20000))
+    ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
+    gpu = gpu_transport(wl)
+    ok, err = compare(gpu, ora)
+    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    assert np.median(err["pos_err"]) < 1e-5
+
+
+def test_per_stage_in_a_uniform_map_is_bit_identical_to_the_held_field():
+    wl = gen.workload("config1", n=3000)
+    B = np.zeros((3, 3, 3, 3), np.float32)
+    B[..., 1] = 1.5
+    # one uniform map cell around the whole world, so no stage reads past its edge
+    wl.field = dict(kind="map", dims=[3, 3, 3], origin=[-10.0, -10.0, -10.0], spacing=[10.0, 10.0, 25.0], B=B)
+    ref = gpu_transport(wl)
+    out = gpu_transport(_per_stage(wl))
+    for k in FIELDS:
+        np.testing.assert_array_equal(ref[k], out[k], err_msg=k)
+
+
+def test_per_stage_launch_shapes_and_differentiable_form():
+    import torch
+    import paper_2512_10520_gb300 as mt
+    wl = _per_stage(gen.workload("config1", n=3000))
+    outs = [gpu_transport(wl)]
+    with mt.World.from_workload(wl) as world:
+        for mode in (mt.MT_LAUNCH_STATIC, mt.MT_LAUNCH_PERSISTENT):
+            dev = mt.muons_to_device(wl.muons)
+            world.transport(dev, wl.step_len, wl.max_steps, wl.seed, mode=mode)
+            outs.append(mt.muons_to_host(dev))
+        dev = mt.muons_to_device(wl.muons)
+        a = torch.ones((6, 3), dtype=torch.float32, device="cuda")
+        ck = torch.empty(mt.mt_ckpt_bytes(wl.n, wl.max_steps, 32), dtype=torch.uint8, device="cuda")
+        with pytest.raises(mt.MtError):
+            mt.mt_transport_ckpt(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, 32, ck)
+    for o in outs[1:]:
+        for k in FIELDS:
+            np.testing.assert_array_equal(outs[0][k], o[k], err_msg=k)
