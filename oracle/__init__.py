@@ -48,7 +48,7 @@ class World(C.Structure):
         ("fspacing", C.c_double * 3), ("Bmap", C.c_void_p), ("field_per_stage", C.c_int32), ("alpha", C.c_void_p),
         ("n_block", C.c_int32),
         ("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("nf", C.c_int32), ("ntheta", C.c_int32),
-        ("p_lo", C.c_double), ("p_hi", C.c_double),
+        ("p_lo", C.c_double), ("p_hi", C.c_double), ("p_edges", C.c_void_p),
         ("f_max", C.c_void_p), ("theta_max", C.c_void_p), ("T", C.c_void_p),
         ("axes", C.c_int32), ("f_min", C.c_void_p), ("theta_min", C.c_void_p),
         ("sampler", C.c_int32), ("alias_prob", C.c_void_p), ("alias_idx", C.c_void_p),
@@ -75,6 +75,19 @@ def lib():
             L.or_sample_alias.restype = C.c_int32
             L.or_momentum_bin.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
             L.or_momentum_bin.restype = C.c_int32
+            L.or_momentum_bin_edges.argtypes = [C.c_double, P, C.c_int32]
+            L.or_momentum_bin_edges.restype = C.c_int32
+            L.or_highland.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.or_highland.restype = C.c_double
+            L.or_physics_sample.argtypes = [P, C.c_double, C.c_double, P, P, P]
+            L.or_physics_sample.restype = None
+            L.or_build_histograms.argtypes = [P, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32, C.c_double,
+                                              C.c_double, C.c_int64, C.c_uint64, P, P]
+            L.or_build_histograms.restype = C.c_int
+            L.or_pilot_phi.argtypes = [P, P, C.c_int32, C.c_int64, C.c_double, C.c_uint64, P]
+            L.or_pilot_phi.restype = C.c_int
+            L.or_bv_edges.argtypes = [P, P, C.c_int32, C.c_double, P, C.c_int32]
+            L.or_bv_edges.restype = C.c_int32
             L.or_material.argtypes = [P, P, P]
             L.or_material.restype = C.c_int32
             L.or_in_solid.argtypes = [P, C.c_int32, P]
@@ -272,6 +285,8 @@ class OracleWorld:
         w.n_mat, w.n_pbin = int(hist["n_mat"]), int(hist["n_pbin"])
         w.nf, w.ntheta = int(hist["nf"]), int(hist["ntheta"])
         w.p_lo, w.p_hi = float(hist["p_lo"]), float(hist["p_hi"])
+        if hist.get("p_edges") is not None:
+            w.p_edges = _p(arr(hist["p_edges"], np.float64))
         w.f_max = _p(arr(hist["f_max"], np.float64))
         w.theta_max = _p(arr(hist["theta_max"], np.float64))
         axes = hist.get("axes", "linear")
@@ -441,3 +456,60 @@ def transport_tangent(world: OracleWorld, r, p, q: int, max_steps: int, step_len
     ns = lib().or_transport_tangent(world.ptr, _p(rr), _p(pp), int(q), int(steps0), int(mid), int(instance),
                                     float(step_len), int(max_steps), int(seed), _p(out), _p(tan))
     return out, tan, ns
+
+
+# --------------------------------------------------------------------------
+# offline phase: parametric physics sampler, histograms, pilot estimator, binning
+# --------------------------------------------------------------------------
+def _material_array(materials):
+    """Materials as a packed (rho, Z/A, I [MeV], X0 [cm], b) float64 array (dicts as in workloads.MATERIALS)."""
+    return np.ascontiguousarray([[m["rho"], m["ZA"], m["I"], m["X0"], m["b"]] for m in materials], np.float64)
+
+
+def momentum_bin_edges(P: float, edges) -> int:
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    return lib().or_momentum_bin_edges(float(P), _p(e), len(e) - 1)
+
+
+def highland(p: float, x_cm: float, X0: float) -> float:
+    return lib().or_highland(float(p), float(x_cm), float(X0))
+
+
+def physics_sample(material: dict, p: float, x_cm: float, u):
+    m = _material_array([material])
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    f = C.c_double()
+    th = C.c_double()
+    lib().or_physics_sample(_p(m), float(p), float(x_cm), _p(uu), C.byref(f), C.byref(th))
+    return f.value, th.value
+
+
+def build_histograms(materials, edges, nf: int, ntheta: int, f_max: float, step_len: float, n_samples: int,
+                     seed: int):
+    """(counts [n_mat][n_pbin][nf][ntheta], theta_max [n_mat][n_pbin]) from the parametric sampler."""
+    m = _material_array(materials)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    n_pbin = len(e) - 1
+    counts = np.zeros((len(materials), n_pbin, nf, ntheta))
+    tmax = np.zeros((len(materials), n_pbin))
+    lib().or_build_histograms(_p(m), len(materials), n_pbin, _p(e), nf, ntheta, float(f_max), step_len * 100.0,
+                              int(n_samples), int(seed), _p(counts), _p(tmax))
+    return counts, tmax
+
+
+def pilot_phi(material: dict, probes, K: int, step_len: float, seed: int) -> np.ndarray:
+    m = _material_array([material])
+    pr = np.ascontiguousarray(probes, dtype=np.float64)
+    phi = np.zeros(len(pr))
+    lib().or_pilot_phi(_p(m), _p(pr), len(pr), int(K), step_len * 100.0, int(seed), _p(phi))
+    return phi
+
+
+def bv_edges(probes, phi, eps: float) -> np.ndarray:
+    pr = np.ascontiguousarray(probes, dtype=np.float64)
+    ph = np.ascontiguousarray(phi, dtype=np.float64)
+    out = np.zeros(len(pr))
+    n = lib().or_bv_edges(_p(pr), _p(ph), len(pr), float(eps), _p(out), len(pr))
+    if n < 0:
+        raise ValueError("or_bv_edges failed")
+    return out[:n].copy()

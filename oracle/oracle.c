@@ -88,6 +88,7 @@ typedef struct or_world {
     /* histograms */
     int32_t n_mat, n_pbin, nf, ntheta;
     double p_lo, p_hi;
+    const double *p_edges;      /* [n_pbin + 1] momentum-bin edges, or NULL for log10 bins */
     const double *f_max;        /* [n_mat][n_pbin] */
     const double *theta_max;    /* [n_mat][n_pbin] */
     const uint64_t *T;          /* [n_mat][n_pbin][nf*ntheta-1] from or_build_thresholds */
@@ -264,6 +265,24 @@ int32_t or_momentum_bin(double P, double p_lo, double p_hi, int32_t n_pbin)
     if (!(i >= 0.0)) return 0;          /* also catches NaN */
     if (i > (double)(n_pbin - 1)) return n_pbin - 1;
     return (int32_t)i;
+}
+
+/* GetMomentumBin over explicit edges (the bounded-variation bins of Appendix
+ * A): the i with edges[i] <= P < edges[i+1], found by binary search, clamped
+ * to the edge bins. */
+int32_t or_momentum_bin_edges(double P, const double *edges, int32_t n_pbin)
+{
+    if (!(P >= edges[1])) return 0;    /* also catches NaN */
+    if (P >= edges[n_pbin - 1]) return n_pbin - 1;
+    int32_t lo = 1, hi = n_pbin - 1;   /* edges[lo] <= P < edges[hi] */
+    while (hi - lo > 1) {
+        int32_t mid = (lo + hi) / 2;
+        if (edges[mid] <= P)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
 }
 
 /* GetMaterial: first box (list order) with lo <= r < hi, else the world;
@@ -522,7 +541,8 @@ static int or_draw_step(const or_world *w, const double r[3], const double p[3],
     d->f = d->theta = d->phi = 0.0;
     if (d->mat == 0) return 0;
     double P = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    int32_t i = or_momentum_bin(P, w->p_lo, w->p_hi, w->n_pbin);
+    int32_t i = w->p_edges ? or_momentum_bin_edges(P, w->p_edges, w->n_pbin)
+                           : or_momentum_bin(P, w->p_lo, w->p_hi, w->n_pbin);
     uint32_t ctr[4] = {(uint32_t)k, (uint32_t)id, (uint32_t)(id >> 32), (uint32_t)inst};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t u[4];
@@ -1224,4 +1244,155 @@ int32_t or_transport_tangent(const or_world *w, const double r0[3], const double
         }
     }
     return ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Offline phase (Sec. Building histograms, Appendix A) with a parametric    */
+/* stand-in for the paper's Geant4 runs.  One sample of the step of a muon of */
+/* momentum p [GeV] through x [cm] of a material (rho [g/cm^3], Z/A, I [MeV],  */
+/* X0 [cm], b [cm^2/g]) draws from eight uniforms u[0..7]:                    */
+/*   ionisation: a Moyal loss of the PDG thin-absorber width xi and most      */
+/*     probable value dmp (density effect with the plasma energy), from a      */
+/*     normal z = sqrt(-2 ln u1) cos(2 pi u2) as xi (-ln z^2) + dmp, floored   */
+/*     at 0, f = dE / p;                                                       */
+/*   radiative tail: with probability b rho x / <v>, v ~ v^-2 on [1e-3, 1)     */
+/*     (inverse CDF of u4) is added to f when u3 is below that probability;   */
+/*   scattering: theta = theta0 sqrt(-2 ln u7) (a Rayleigh space angle of the */
+/*     Highland width theta0), or 2 theta0 / sqrt(u6) when u5 < 0.01 (single  */
+/*     scatter tail).                                                          */
+/* Uniforms are (w >> 8 + 1/2) 2^-24 of the words of Philox4x32-10 with key   */
+/* = seed and counters (s, h, 0x0FF1, 0) and (s, h, 0x0FF1, 1) for sample s of */
+/* stream h.                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct or_material_c {
+    double rho, za, I, X0, b;
+} or_material_c;
+
+#define OR_K_BETHE 0.307075
+#define OR_ME 0.51099895
+#define OR_MMU 105.6583755
+
+static double or_u_open(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+double or_highland(double p_gev, double x_cm, double X0)
+{
+    double pm = p_gev * 1e3, E = sqrt(pm * pm + OR_MMU * OR_MMU), beta = pm / E, t = x_cm / X0;
+    return 13.6 / (beta * pm) * sqrt(t) * (1.0 + 0.038 * log(t));
+}
+
+void or_physics_sample(const or_material_c *m, double p, double x_cm, const double u[8], double *f, double *theta)
+{
+    double pm = p * 1e3;
+    double E = sqrt(pm * pm + OR_MMU * OR_MMU);
+    double beta2 = (pm / E) * (pm / E);
+    double bg = pm / OR_MMU;
+    double xi = 0.5 * OR_K_BETHE * m->za * m->rho * x_cm / beta2;
+    double hw = 28.816e-6 * sqrt(m->rho * m->za);
+    double delta = 2.0 * log(bg) + 2.0 * log(hw / m->I) - 1.0;
+    if (delta < 0.0) delta = 0.0;
+    double dmp = xi * (log(2.0 * OR_ME * bg * bg / m->I) + log(xi / m->I) + 0.2 - beta2 - delta);
+    double z = sqrt(-2.0 * log(u[1])) * cos(OR_TWO_PI * u[2]);
+    double z2 = z * z;
+    if (z2 < 1e-300) z2 = 1e-300;
+    double dE = dmp + xi * (-log(z2));
+    if (dE < 0.0) dE = 0.0;
+    double ff = dE / pm;
+    const double v0 = 1e-3;
+    double mean_v = log(1.0 / v0) / (1.0 / v0 - 1.0);
+    double p_rad = m->b * m->rho * x_cm / mean_v;
+    if (p_rad > 1.0) p_rad = 1.0;
+    if (u[3] < p_rad) ff += 1.0 / (1.0 / v0 - u[4] * (1.0 / v0 - 1.0));
+    double th0 = or_highland(p, x_cm, m->X0);
+    *theta = u[5] < 0.01 ? 2.0 * th0 / sqrt(u[6]) : th0 * sqrt(-2.0 * log(u[7]));
+    *f = ff;
+}
+
+static void or_physics_uniforms(uint64_t seed, uint64_t s, uint32_t h, double u[8])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    for (int half = 0; half < 2; ++half) {
+        uint32_t ctr[4] = {(uint32_t)s, h, 0x0FF1u, (uint32_t)half};
+        or_philox4x32_10(ctr, key, w);
+        for (int j = 0; j < 4; ++j) u[4 * half + j] = or_u_open(w[j]);
+    }
+}
+
+/* Histograms H[m][i] (linear axes) from n_samples samples each: p ~ U(edge_i,
+ * edge_{i+1}) from u0, stream h = m n_pbin + i; f binned on [0, f_max) and
+ * theta on [0, theta_max[m][i]) with theta_max = 5 theta0(edge_i); samples
+ * outside the axes are counted in the edge cells.  counts [n_mat][n_pbin][nf][ntheta]. */
+int or_build_histograms(const or_material_c *mats, int32_t n_mat, int32_t n_pbin, const double *edges, int32_t nf,
+                        int32_t ntheta, double f_max, double x_cm, int64_t n_samples, uint64_t seed, double *counts,
+                        double *theta_max)
+{
+    for (int32_t m = 0; m < n_mat; ++m)
+        for (int32_t i = 0; i < n_pbin; ++i) {
+            const uint32_t h = (uint32_t)(m * n_pbin + i);
+            const double tm = 5.0 * or_highland(edges[i], x_cm, mats[m].X0);
+            theta_max[h] = tm;
+            double *H = counts + (int64_t)h * nf * ntheta;
+            for (int64_t k = 0; k < (int64_t)nf * ntheta; ++k) H[k] = 0.0;
+            for (int64_t s = 0; s < n_samples; ++s) {
+                double u[8], f, th;
+                or_physics_uniforms(seed, (uint64_t)s, h, u);
+                const double p = edges[i] + u[0] * (edges[i + 1] - edges[i]);
+                or_physics_sample(&mats[m], p, x_cm, u, &f, &th);
+                double a = floor(f / f_max * nf), b = floor(th / tm * ntheta);
+                if (!(a >= 0.0)) a = 0.0;
+                if (a > nf - 1) a = nf - 1;
+                if (!(b >= 0.0)) b = 0.0;
+                if (b > ntheta - 1) b = ntheta - 1;
+                H[(int64_t)a * ntheta + (int64_t)b] += 1.0;
+            }
+        }
+    return 0;
+}
+
+/* Pilot estimator of Appendix A: phi(p) = (1/K) sum_k log(-dPz_k/P) for K
+ * samples at the probe momentum p (stream h = probe index), with
+ * -dPz/P = 1 - (1 - f) cos theta = f + (1 - f) 2 sin^2(theta/2), f capped at 1. */
+int or_pilot_phi(const or_material_c *m, const double *probes, int32_t n_probe, int64_t K, double x_cm, uint64_t seed,
+                 double *phi)
+{
+    for (int32_t j = 0; j < n_probe; ++j) {
+        double acc = 0.0;
+        for (int64_t s = 0; s < K; ++s) {
+            double u[8], f, th;
+            or_physics_uniforms(seed, (uint64_t)s, (uint32_t)j, u);
+            or_physics_sample(m, probes[j], x_cm, u, &f, &th);
+            if (f > 1.0) f = 1.0;
+            const double sh = sin(0.5 * th);
+            acc += log(f + (1.0 - f) * 2.0 * sh * sh);
+        }
+        phi[j] = acc / (double)K;
+    }
+    return 0;
+}
+
+/* Bounded-variation bin edges (Appendix A) on a probe grid: from edge p_i the
+ * next edge is the largest probe p_j with max_{i <= k <= j} |phi_k - phi_i| <=
+ * eps (at least the next probe, the grid's resolution); the last edge is the
+ * last probe.  Returns the number of edges written (<= max_edges), or -1 if
+ * they do not fit. */
+int32_t or_bv_edges(const double *probes, const double *phi, int32_t n_probe, double eps, double *edges,
+                    int32_t max_edges)
+{
+    if (n_probe < 2 || max_edges < 2) return -1;
+    int32_t n = 0, i = 0;
+    edges[n++] = probes[0];
+    while (i < n_probe - 1) {
+        int32_t j = i + 1;
+        while (j + 1 < n_probe && fabs(phi[j + 1] - phi[i]) <= eps) {
+            int ok = 1;
+            for (int32_t k = i + 1; k <= j + 1; ++k)
+                if (fabs(phi[k] - phi[i]) > eps) ok = 0;
+            if (!ok) break;
+            ++j;
+        }
+        if (n >= max_edges) return -1;
+        edges[n++] = probes[j];
+        i = j;
+    }
+    return n;
 }
