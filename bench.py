@@ -293,6 +293,44 @@ def time_polyhedra_form(mt, dev, stream, n=None, reps=3, id_offset=0):
                 config1_as_solids=dict(value=steps1 / t1, kernel_ms=1e3 * t1, muon_steps=steps1))
 
 
+def time_offline_form(mt, stream, cpu=True):
+    """Offline phase on the GPU (Sec. Building histograms, Appendix A): config1's
+    histogram set (3 materials x 64 bins x 128x64 cells, 1e6 samples each) from
+    the parametric sampler, and the Appendix A pilot (1024 probes x 1e5 samples)
+    with its bounded-variation edges; CUDA events.  CPU: the numpy fixture of
+    the same model on one material x 4 bins (4e6 samples), scaled per sample."""
+    import torch
+    from workloads import gen
+    mats = [gen.MATERIALS[m] for m in ("iron", "air", "concrete")]
+    edges = gen.pbin_edges(1.0, 400.0, 64)
+    w = torch.empty((3, 64, 128, 64), dtype=torch.float64, device="cuda")
+    mt.mt_build_histograms(mats, edges, 128, 64, 0.2, 0.02, 10**5, 42, w, stream)      # warm-up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    mt.mt_build_histograms(mats, edges, 128, 64, 0.2, 0.02, 10**6, 42, w, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_hist = a.elapsed_time(b) / 1e3
+    n_samples = 3 * 64 * 10**6
+    probes = np.geomspace(1.0, 400.0, 1024)
+    t0 = time.perf_counter()
+    phi = mt.mt_pilot_phi(mats[0], probes, 10**5, 0.02, 7, stream)
+    t_pilot = time.perf_counter() - t0
+    e = mt.mt_bv_edges(probes, phi, 0.05)
+    out = dict(value=n_samples / t_hist, unit="samples/s", histograms_ms=1e3 * t_hist, samples=n_samples,
+               pilot_ms=1e3 * t_pilot, pilot_samples=1024 * 10**5, bv_bins_iron_eps_0p05=len(e) - 1)
+    if cpu:
+        rng = np.random.default_rng(1)
+        t0 = time.perf_counter()
+        for i in range(4):
+            gen._hist_one(rng, mats[0], edges[i], edges[i + 1], 2.0, 0.2, 128, 64, 10**6)
+        dt = time.perf_counter() - t0
+        out["cpu_fixture"] = dict(value=4e6 / dt, unit="samples/s", sample="numpy fixture, iron, 4 bins x 1e6",
+                                  cores=1)
+    return out
+
+
 def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True, block=0, spp=0):
     """Batched form (config2): n_inst worlds, each its own 64x64x512 voxel geometry
     and 100x100x300 field map, one shared histogram set, instance sizes log-uniform
@@ -666,6 +704,7 @@ def run_mine(args):
                           "narrowing along z), spatial-hash pruning, 200x200x600 map")
         ph["vs_boxes"] = ph["value"] / value
         forms["polyhedra"] = ph
+        forms["offline"] = time_offline_form(mt, stream, cpu=not args.no_cpu)
         for name, kw, desc in (("nearest_field", dict(field="nearest"),
                                 "config1 with the map read at the nearest node (the paper's lookup, 1 gather)"),
                                ("log_axes", dict(axes="log"),

@@ -153,7 +153,15 @@ typedef struct mt_hist_desc {
     int32_t axes;                 /* MT_AXES_LINEAR (0, default) or MT_AXES_LOG       */
     const double *f_min;          /* log axes: host, [n_mat][n_pbin], 0 < f_min < f_max */
     const double *theta_min;      /* log axes: host, [n_mat][n_pbin], 0 < t_min < t_max */
+    const double *p_edges;        /* host, n_pbin + 1 momentum-bin edges, or NULL for */
+                                  /*   log10 bins (see below)                         */
 } mt_hist_desc;
+
+/* Momentum bins.  p_edges NULL: n_pbin log10 bins on [p_lo, p_hi].  Otherwise
+ * explicit edges (e.g. the bounded-variation bins of Appendix A, mt_bv_edges):
+ * strictly increasing, p_edges[0] = p_lo, p_edges[n_pbin] = p_hi, neighbours at
+ * least 1e-5 apart relatively; the step finds the bin by binary search (the
+ * run-time search Appendix A calls for).  Momenta outside use the edge bins. */
 
 /* Histogram axes.  MT_AXES_LINEAR: f = dp/p on [0, f_max) and the polar angle
  * theta on [0, theta_max), linear bins; the step sets |p| to (1 - f) |p| at
@@ -426,6 +434,54 @@ mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, int32_t max_s
  * receives dL/d(x, y, z, px, py, pz).  Reads x..pz and status of s only. */
 mt_status mt_acceptance_loss(const mt_muon_soa *s, int64_t n, double z_plane, double half_width, double edge,
                              double *loss, float *dL_dfinal, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Offline phase (Sec. Building histograms, Appendix A) on the GPU, with a
+ * parametric physics sampler standing in for the paper's Geant4 runs.  A
+ * sample of the step of a muon of momentum p through step_len of a material:
+ * a Moyal ionisation loss (PDG thin-absorber width and most probable loss with
+ * the density effect), a radiative loss v ~ v^-2 on [1e-3, 1) added with
+ * probability b rho x / <v>, and a Rayleigh space angle of the Highland width
+ * theta0 (or, 1 % of samples, a single-scatter tail 2 theta0 / sqrt(u)); its
+ * eight uniforms come from Philox4x32-10 with key = seed and counters
+ * (s, h, 0x0FF1, 0|1) for sample s of stream h.  FP64 arithmetic.
+ * ------------------------------------------------------------------------- */
+typedef struct mt_material {
+    double rho;        /* density [g/cm^3]                         */
+    double z_over_a;   /* Z/A                                      */
+    double I_mev;      /* mean excitation energy [MeV]             */
+    double X0_cm;      /* radiation length [cm]                    */
+    double b_rad;      /* radiative loss coefficient [cm^2/g]      */
+} mt_material;
+
+/* Histograms H[m][i] of n_samples samples each (stream h = m n_pbin + i),
+ * p uniform in [edges[i], edges[i+1]) (host, n_pbin + 1 increasing edges),
+ * f = dp/p binned on [0, f_max) into nf bins and theta on [0, theta_max) into
+ * ntheta bins, theta_max[h] = 5 theta0(edges[i]) (written to the host array
+ * theta_max [n_mat][n_pbin]); samples off the axes go to the edge cells.
+ * weights: device [n_mat][n_pbin][nf][ntheta] doubles (counts), overwritten.
+ * Ready for mt_hist_desc (copy weights to the host).  Asynchronous on stream;
+ * theta_max is written before return.  Errors: MT_ERR_INVALID_ARG,
+ * MT_ERR_OOM, MT_ERR_CUDA. */
+mt_status mt_build_histograms(const mt_material *mats, int32_t n_mat, int32_t n_pbin, const double *edges,
+                              int32_t nf, int32_t ntheta, double f_max, double step_len, int64_t n_samples,
+                              uint64_t seed, double *weights, double *theta_max, void *stream);
+
+/* Pilot estimator of Appendix A: phi[j] = (1/K) sum over K samples at momentum
+ * probes[j] (stream j) of log(-dPz/P), -dPz/P = f + (1 - f) 2 sin^2(theta/2)
+ * with f capped at 1.  probes, phi: host arrays of n_probe (<= 65535).
+ * Synchronises stream. */
+mt_status mt_pilot_phi(const mt_material *mat, const double *probes, int32_t n_probe, int64_t K, double step_len,
+                       uint64_t seed, double *phi, void *stream);
+
+/* Bounded-variation bin edges of Appendix A on an increasing probe grid: from
+ * edge p_i the next edge is the largest probe p_j with |phi_k - phi_i| <= eps
+ * for every probe i < k <= j (at least the next probe, the grid's
+ * resolution); the first and last edges are the first and last probes.
+ * Writes the edges to edges (host, max_edges) and returns their number, or -1
+ * (bad arguments, or more than max_edges; mt_last_error says which). */
+int32_t mt_bv_edges(const double *probes, const double *phi, int32_t n_probe, double eps, double *edges,
+                    int32_t max_edges);
 
 /* Largest n that mt_transport_noalloc accepts. */
 #define MT_NOALLOC_MAX_MUONS 65536

@@ -13,8 +13,10 @@ from ._binding import (  # noqa: F401
     mt_transport_noalloc, MT_NOALLOC_MAX_MUONS,
     mt_ckpt_bytes, mt_transport_ckpt, mt_adjoint_ckpt, mt_transport_adjoint, mt_acceptance_loss,
     mt_tape_bytes, mt_transport_tape, mt_adjoint_tape,
+    mt_build_histograms, mt_pilot_phi, mt_bv_edges,
     mt_batch_create, mt_batch_set_instance, mt_batch_destroy, mt_batch_device_bytes, mt_batch_workspace_bytes,
     mt_transport_batched, mt_batch_autotune,
 )
-from .api import World, Batch, muons_to_device, muons_to_host, empty_like_soa  # noqa: F401
+from .api import (World, Batch, muons_to_device, muons_to_host, empty_like_soa,  # noqa: F401
+                  build_histogram_set, bounded_variation_edges)
 from .autograd import MuonTransportFn, AcceptanceLossFn, transport_differentiable, acceptance_loss  # noqa: F401,E402

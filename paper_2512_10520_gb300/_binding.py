@@ -59,7 +59,12 @@ class mt_hist_desc(C.Structure):
     _fields_ = [("n_mat", C.c_int32), ("n_pbin", C.c_int32), ("p_lo", C.c_double), ("p_hi", C.c_double),
                 ("nf", C.c_int32), ("ntheta", C.c_int32), ("weights", C.c_void_p), ("f_max", C.c_void_p),
                 ("theta_max", C.c_void_p), ("sampler", C.c_int32), ("axes", C.c_int32), ("f_min", C.c_void_p),
-                ("theta_min", C.c_void_p)]
+                ("theta_min", C.c_void_p), ("p_edges", C.c_void_p)]
+
+
+class mt_material(C.Structure):
+    _fields_ = [("rho", C.c_double), ("z_over_a", C.c_double), ("I_mev", C.c_double), ("X0_cm", C.c_double),
+                ("b_rad", C.c_double)]
 
 
 MT_SAMPLER_ICDF, MT_SAMPLER_ALIAS = 0, 1
@@ -121,6 +126,10 @@ _SIGNATURES = {
                            C.c_int32, _P, C.c_int64, _P], C.c_int),
     "mt_adjoint_tape": ([_P, C.c_int64, C.c_float, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int64, _P, _P, _P,
                          _P], C.c_int),
+    "mt_build_histograms": ([C.POINTER(mt_material), C.c_int32, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double,
+                             C.c_double, C.c_int64, C.c_uint64, _P, _P, _P], C.c_int),
+    "mt_pilot_phi": ([C.POINTER(mt_material), _P, C.c_int32, C.c_int64, C.c_double, C.c_uint64, _P, _P], C.c_int),
+    "mt_bv_edges": ([_P, _P, C.c_int32, C.c_double, _P, C.c_int32], C.c_int32),
     "mt_batch_create": ([C.POINTER(mt_hist_desc), C.c_int32, C.POINTER(_P)], C.c_int),
     "mt_batch_set_instance": ([_P, C.c_int32, C.POINTER(mt_geometry_desc), C.POINTER(mt_field_desc)], C.c_int),
     "mt_batch_destroy": ([_P], None),
@@ -275,6 +284,8 @@ class _Descs:
         h.theta_max = arr(hist["theta_max"], np.float64).ctypes.data
         h.sampler = SAMPLERS[hist.get("sampler", "icdf")]
         h.axes = AXES[hist.get("axes", "linear")]
+        if hist.get("p_edges") is not None:
+            h.p_edges = arr(hist["p_edges"], np.float64).ctypes.data
         if h.axes == MT_AXES_LOG:
             h.f_min = arr(hist["f_min"], np.float64).ctypes.data
             h.theta_min = arr(hist["theta_min"], np.float64).ctypes.data
@@ -562,3 +573,50 @@ def mt_batch_autotune(batch: int, muons_list, step_len: float, max_steps: int, s
                                             int(seed) & 0xFFFFFFFFFFFFFFFF, int(sample_per_instance),
                                             C.byref(best), C.c_void_p(_stream_ptr(stream))), "mt_batch_autotune")
     return int(best.block), int(best.steps_per_pass)
+
+
+# --------------------------------------------------------------------------
+# offline phase
+# --------------------------------------------------------------------------
+def _materials(materials):
+    arr = (mt_material * len(materials))()
+    for i, m in enumerate(materials):
+        arr[i] = mt_material(float(m["rho"]), float(m["ZA"]), float(m["I"]), float(m["X0"]), float(m["b"]))
+    return arr
+
+
+def mt_build_histograms(materials, edges, nf: int, ntheta: int, f_max: float, step_len: float, n_samples: int,
+                        seed: int, weights, stream=None):
+    """Histograms of the parametric sampler into `weights` (float64 CUDA tensor [n_mat][n_pbin][nf][ntheta]);
+    returns theta_max [n_mat][n_pbin] (numpy)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    n_pbin = len(e) - 1
+    if not weights.is_cuda or str(weights.dtype) != "torch.float64" or not weights.is_contiguous() or \
+            weights.numel() != len(materials) * n_pbin * nf * ntheta:
+        raise TypeError("weights must be a contiguous float64 CUDA tensor [n_mat][n_pbin][nf][ntheta]")
+    tmax = np.zeros((len(materials), n_pbin))
+    _check(load_library().mt_build_histograms(_materials(materials), len(materials), n_pbin, e.ctypes.data, int(nf),
+                                              int(ntheta), float(f_max), float(step_len), int(n_samples),
+                                              int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(weights.data_ptr()),
+                                              tmax.ctypes.data, C.c_void_p(_stream_ptr(stream))),
+           "mt_build_histograms")
+    return tmax
+
+
+def mt_pilot_phi(material, probes, K: int, step_len: float, seed: int, stream=None) -> np.ndarray:
+    pr = np.ascontiguousarray(probes, dtype=np.float64)
+    phi = np.zeros(len(pr))
+    _check(load_library().mt_pilot_phi(_materials([material]), pr.ctypes.data, len(pr), int(K), float(step_len),
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF, phi.ctypes.data,
+                                       C.c_void_p(_stream_ptr(stream))), "mt_pilot_phi")
+    return phi
+
+
+def mt_bv_edges(probes, phi, eps: float) -> np.ndarray:
+    pr = np.ascontiguousarray(probes, dtype=np.float64)
+    ph = np.ascontiguousarray(phi, dtype=np.float64)
+    out = np.zeros(len(pr))
+    n = load_library().mt_bv_edges(pr.ctypes.data, ph.ctypes.data, len(pr), float(eps), out.ctypes.data, len(pr))
+    if n < 0:
+        raise MtError(MT_ERR_INVALID_ARG, "mt_bv_edges", mt_last_error())
+    return out[:n].copy()

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libmt.so")
-SOURCES = ["api.cu", "transport.cu", "compact.cu", "noalloc.cu", "adjoint.cu", "batched.cu"]
+SOURCES = ["api.cu", "transport.cu", "compact.cu", "noalloc.cu", "adjoint.cu", "batched.cu", "offline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -94,6 +94,45 @@ class Batch:
             pass
 
 
+def build_histogram_set(materials, p_lo: float = 1.0, p_hi: float = 400.0, n_pbin: int = 64, edges=None,
+                        nf: int = 128, ntheta: int = 64, f_max: float = 0.2, step_len: float = 0.02,
+                        n_samples: int = 10**6, seed: int = 42, material_table=None, stream=None) -> dict:
+    """A histogram set (the dict mt_create takes) built on the GPU by the parametric
+    sampler (mt_build_histograms): log10 bins on [p_lo, p_hi], or the given edges
+    (e.g. bounded-variation edges), which the transport then searches."""
+    import torch
+    if material_table is None:
+        from workloads import MATERIALS as material_table
+    mats = [material_table[m] if isinstance(m, str) else m for m in materials]
+    if edges is None:
+        k = np.arange(n_pbin + 1, dtype=np.float64)
+        e = p_lo * (p_hi / p_lo) ** (k / n_pbin)
+        custom = None
+    else:
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        n_pbin, p_lo, p_hi = len(e) - 1, float(e[0]), float(e[-1])
+        custom = e
+    w = torch.empty((len(mats), n_pbin, nf, ntheta), dtype=torch.float64, device="cuda")
+    tmax = B.mt_build_histograms(mats, e, nf, ntheta, f_max, step_len, n_samples, seed, w, stream)
+    out = dict(n_mat=len(mats), n_pbin=n_pbin, p_lo=float(p_lo), p_hi=float(p_hi), nf=nf, ntheta=ntheta,
+               weights=w.cpu().numpy(), f_max=np.full((len(mats), n_pbin), float(f_max)), theta_max=tmax)
+    if custom is not None:
+        out["p_edges"] = custom
+    return out
+
+
+def bounded_variation_edges(material, p_lo: float, p_hi: float, eps: float, n_probe: int = 1024,
+                            K: int = 100000, step_len: float = 0.02, seed: int = 7, material_table=None):
+    """Appendix A: pilot estimator on n_probe log-spaced probes (mt_pilot_phi),
+    then the bounded-variation edges with tolerance eps (mt_bv_edges)."""
+    if material_table is None:
+        from workloads import MATERIALS as material_table
+    m = material_table[material] if isinstance(material, str) else material
+    probes = np.geomspace(p_lo, p_hi, n_probe)
+    phi = B.mt_pilot_phi(m, probes, K, step_len, seed)
+    return B.mt_bv_edges(probes, phi, eps), probes, phi
+
+
 def muons_to_device(soa: Dict[str, np.ndarray], device="cuda", pin: bool = False) -> Dict:
     """Copy a numpy SoA (fields of mt_muon_soa) to CUDA tensors."""
     import torch

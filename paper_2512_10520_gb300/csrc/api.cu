@@ -182,6 +182,17 @@ mt_status validate_hist(const mt_hist_desc *h)
         set_error("hist: nf*ntheta = %lld outside [2, %d]", (long long)h->nf * h->ntheta, MT_MAX_CELLS);
         return MT_ERR_INVALID_ARG;
     }
+    if (h->p_edges) {
+        if (h->p_edges[0] != h->p_lo || h->p_edges[h->n_pbin] != h->p_hi) {
+            set_error("hist: p_edges must start at p_lo and end at p_hi");
+            return MT_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < h->n_pbin; ++i)
+            if (!(h->p_edges[i + 1] > h->p_edges[i] * (1.0 + 1e-5))) {
+                set_error("hist: p_edges must increase by at least 1e-5 relatively (edge %d)", i + 1);
+                return MT_ERR_INVALID_ARG;
+            }
+    }
     if (h->axes != MT_AXES_LINEAR && h->axes != MT_AXES_LOG) {
         set_error("hist: unknown axes %d", h->axes);
         return MT_ERR_INVALID_ARG;
@@ -370,8 +381,9 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
     mt_status st = build_tables(hd, gbits, rec, guide, pairs, alias);
     if (st != MT_OK) return st;
     std::vector<float2> e2(hd->n_pbin + 1);
+    w.pbin_custom = hd->p_edges ? 1 : 0;
     for (int k = 0; k <= hd->n_pbin; ++k) {
-        const double E = hd->p_lo * std::pow(hd->p_hi / hd->p_lo, (double)k / hd->n_pbin);
+        const double E = hd->p_edges ? hd->p_edges[k] : hd->p_lo * std::pow(hd->p_hi / hd->p_lo, (double)k / hd->n_pbin);
         float a, b;
         split(E * E, a, b);
         e2[k] = make_float2(a, b);

@@ -88,6 +88,7 @@ struct WorldParams {
     const uint2 *alias;       // alias columns {Prob_j, alias cell (a << 16) | b}, at HistRec.guide_off
     int32_t alias_bits;       // log2(nf * ntheta)
     int32_t theta_bits;       // log2(ntheta)
+    int32_t pbin_custom;      // 1: explicit bin edges (binary search over e2), 0: log10 bins
     float log2_plo;
     float pbin_scale;   // n_pbin / log2(p_hi / p_lo)
 };

@@ -286,12 +286,28 @@ __device__ __forceinline__ void sq2(float h, float l, float &sh, float &sl)
 }
 
 
-// GetMomentumBin on log10 bins: a fast FP32 estimate, confirmed against the
-// squared edges held as hi + lo pairs whenever |p|^2 lies within 4e-6 of one.
+// GetMomentumBin on log10 bins (a fast FP32 estimate) or over explicit edges
+// (binary search), confirmed against the squared edges held as hi + lo pairs
+// whenever |p|^2 lies within 4e-6 of one.
 __device__ __forceinline__ int momentum_bin(const WorldParams &w, const SmemWorld &sw, const State &s, float P2)
 {
-    int i = __float2int_rd(fmaf(0.5f, __log2f(P2), -w.log2_plo) * w.pbin_scale);
-    i = min(max(i, 0), w.n_pbin - 1);
+    int i;
+    if (w.pbin_custom) {
+        // explicit edges: binary search of P^2 over the squared edges (hi words);
+        // the exact hi + lo test below settles a P^2 within 4e-6 of an edge
+        int lo = 0, hi = w.n_pbin;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sw.e2[mid].x <= P2)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        i = lo;
+    } else {
+        i = __float2int_rd(fmaf(0.5f, __log2f(P2), -w.log2_plo) * w.pbin_scale);
+        i = min(max(i, 0), w.n_pbin - 1);
+    }
     const float elo = sw.e2[i].x, ehi = sw.e2[i + 1].x;
     const bool near_lo = i > 0 && P2 < elo * 1.000004f;
     const bool near_hi = i < w.n_pbin - 1 && P2 > ehi * 0.999996f;

@@ -135,3 +135,35 @@ def test_polyhedra_descriptor_checks_on_host(lib):
 def ctypes_size_ok():
     # the descriptor the binding builds has the C layout of include/mt.h (8-byte aligned tail)
     return C.sizeof(B.mt_polyhedron) == 8 * (2 + 8 + 8) + 8 + 24 and C.sizeof(B.mt_geometry_desc) % 8 == 0
+
+
+def test_bv_edges_host_recursion_matches_the_oracle(lib):
+    """mt_bv_edges is host code: same edges as the oracle's recursion."""
+    import oracle
+    rng = np.random.default_rng(4)
+    for _ in range(30):
+        n = int(rng.integers(3, 400))
+        probes = np.sort(rng.uniform(1, 400, n))
+        probes = probes[np.concatenate([[True], np.diff(probes) > 0])]
+        phi = np.cumsum(rng.normal(0, 0.05, len(probes)))
+        eps = float(rng.uniform(0.01, 0.3))
+        np.testing.assert_array_equal(mt.mt_bv_edges(probes, phi, eps), oracle.bv_edges(probes, phi, eps))
+    with pytest.raises(mt.MtError):
+        mt.mt_bv_edges([1.0, 1.0, 2.0], [0.0, 0.0, 0.0], 0.1)
+
+
+def test_offline_and_edges_host_checks(lib):
+    from workloads import gen
+    h = gen.histogram_set(["iron"], n_pbin=2, nf=4, ntheta=4, n_samples=1000, cache=False)
+    geo, fld, _ = _descs()
+    bad = dict(h, p_edges=np.array([1.0, 0.5, 400.0]))
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_create(geo, fld, bad)
+    assert "p_edges" in mt.mt_last_error()
+    bad = dict(h, p_edges=np.array([2.0, 20.0, 400.0]))          # must start at p_lo
+    with pytest.raises(mt.MtError):
+        mt.mt_create(geo, fld, bad)
+    st = lib.mt_pilot_phi(None, None, 0, 0, 0.02, 1, None, None)
+    assert st == B.MT_ERR_INVALID_ARG
+    st = lib.mt_build_histograms(None, 1, 1, None, 4, 4, 0.2, 0.02, 10, 1, None, None, None)
+    assert st == B.MT_ERR_INVALID_ARG
