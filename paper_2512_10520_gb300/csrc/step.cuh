@@ -615,11 +615,15 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
     if (mat != 0) {
         const int ib = momentum_bin(w, sw, s, P2);
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, id_lo, id_hi, (uint32_t)rp.instance), rp.key0, rp.key1);
-        const uint4 hraw = __ldg(reinterpret_cast<const uint4 *>(w.hist + (mat - 1) * w.n_pbin + ib));
+        // the guide (or alias) row of histogram h sits at h * its length, so its
+        // load need not wait for the histogram record's
+        const int h = (mat - 1) * w.n_pbin + ib;
+        const uint4 hraw = __ldg(reinterpret_cast<const uint4 *>(w.hist + h));
         const HistRec hr = {hraw.x, hraw.y, __uint_as_float(hraw.z), __uint_as_float(hraw.w)};
-        const uint32_t ab = w.sampler == MT_SAMPLER_ALIAS
-                                ? sample_alias(w.alias + hr.guide_off, w.alias_bits, w.theta_bits, rnd.x)
-                                : sample_cell(w.guide + hr.guide_off, w.pairs + hr.pair_off, w.gshift, rnd.x);
+        const uint32_t ab =
+            w.sampler == MT_SAMPLER_ALIAS
+                ? sample_alias(w.alias + ((int64_t)h << w.alias_bits), w.alias_bits, w.theta_bits, rnd.x)
+                : sample_cell(w.guide + ((int64_t)h << (32 - w.gshift)), w.pairs + hr.pair_off, w.gshift, rnd.x);
         const float f = ((float)(ab >> 16) + u01(rnd.y)) * hr.fscale;
         const float th = ((float)(ab & 0xFFFFu) + u01(rnd.z)) * hr.tscale;
         const float phs = fmaf(6.283185307179586f, u01(rnd.w), -3.14159265358979f);   // phi - pi
