@@ -44,11 +44,19 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# the sources of the plain transport's kernels (compact_init, compact_pass) and their build flags
+_TRANSPORT_SOURCES = ("paper_2512_10520_gb300/csrc/step.cuh", "paper_2512_10520_gb300/csrc/compact.cuh",
+                      "paper_2512_10520_gb300/csrc/compact.cu", "paper_2512_10520_gb300/csrc/transport.cu",
+                      "paper_2512_10520_gb300/csrc/mt_internal.cuh", "include/mt.h",
+                      "paper_2512_10520_gb300/_build.py")
+
+
 def _csrc_hash() -> str:
+    """Hash of the plain transport's kernel sources: the committed DRAM traffic is
+    used only while it matches."""
     h = hashlib.sha1()
-    d = os.path.join(ROOT, "paper_2512_10520_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
+    for f in _TRANSPORT_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:12]

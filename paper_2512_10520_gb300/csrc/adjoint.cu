@@ -192,11 +192,13 @@ __device__ __forceinline__ void field_map_jt(const WorldParams &w, const float r
     const float4 *p11 = p01 + 2 * row;
     // project the corners on Bb first: v_q = Bb . B(corner q)
     float v[8];
-    const float4 *src[8] = {p00, p00 + 1, p10, p10 + 1, p01, p01 + 1, p11, p11 + 1};
+    const float4 *src[4] = {p00, p10, p01, p11};
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float4 c = __ldg(src[q]);
-        v[q] = fmaf(Bb[0], c.x, fmaf(Bb[1], c.y, Bb[2] * c.z));
+    for (int q = 0; q < 4; ++q) {
+        float4 c, e;
+        load_pair(src[q], c, e);
+        v[2 * q] = fmaf(Bb[0], c.x, fmaf(Bb[1], c.y, Bb[2] * c.z));
+        v[2 * q + 1] = fmaf(Bb[0], e.x, fmaf(Bb[1], e.y, Bb[2] * e.z));
     }
     // v: (i,j,k) (i+1,j,k) (i,j+1,k) (i+1,j+1,k) (i,j,k+1) (i+1,j,k+1) (i,j+1,k+1) (i+1,j+1,k+1)
     const float a = lerp(tx, v[0], v[1]), b = lerp(tx, v[2], v[3]);

@@ -464,6 +464,25 @@ __device__ __forceinline__ bool map_axis(float xh, float xl, float oh, float ol,
     return true;
 }
 
+// One x-adjacent node pair (two float4, 32 bytes, 32-byte aligned) of the
+// read-only field map.  With MT_FIELD_V8 the pair is one 256-bit load, which
+// takes one L1 wavefront per lane where two 128-bit loads take two (the
+// scattered corner gathers keep the L1/TEX pipeline at ~85 % of its peak).
+#ifndef MT_FIELD_V8
+#define MT_FIELD_V8 1
+#endif
+__device__ __forceinline__ void load_pair(const float4 *p, float4 &a, float4 &b)
+{
+#if MT_FIELD_V8
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+#else
+    a = __ldg(p);
+    b = __ldg(p + 1);
+#endif
+}
+
 // Trilinear field from the pair layout; zero outside the node box.
 __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s)
 {
@@ -479,10 +498,11 @@ __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s
     const float4 *p10 = p00 + 2 * row;                 // j + 1
     const float4 *p01 = p00 + 2 * row * ny;            // k + 1
     const float4 *p11 = p01 + 2 * row;                 // j + 1, k + 1
-    const float4 a0 = __ldg(p00), a1 = __ldg(p00 + 1);
-    const float4 b0 = __ldg(p10), b1 = __ldg(p10 + 1);
-    const float4 c0 = __ldg(p01), c1 = __ldg(p01 + 1);
-    const float4 d0 = __ldg(p11), d1 = __ldg(p11 + 1);
+    float4 a0, a1, b0, b1, c0, c1, d0, d1;
+    load_pair(p00, a0, a1);
+    load_pair(p10, b0, b1);
+    load_pair(p01, c0, c1);
+    load_pair(p11, d0, d1);
     const float ax = lerp(tx, a0.x, a1.x), ay = lerp(tx, a0.y, a1.y), az = lerp(tx, a0.z, a1.z);
     const float bx = lerp(tx, b0.x, b1.x), by = lerp(tx, b0.y, b1.y), bz = lerp(tx, b0.z, b1.z);
     const float cx = lerp(tx, c0.x, c1.x), cy = lerp(tx, c0.y, c1.y), cz = lerp(tx, c0.z, c1.z);
