@@ -432,8 +432,21 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // FWD: the full-tape forward (finished muons stored, survivors appended to
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
+// Resident blocks per SM of the recorded pass: 4 (64 registers), for the
+// recorder's state kept across the step (measured on config3: full-tape
+// forward 33.0 ms against 35.4 ms at the plain pass's 48 registers, which
+// spill; checkpoint backward 64.1 against 66.2 ms).  0: the plain pass's.
+#ifndef MT_TAPE_MIN_BLOCKS
+#define MT_TAPE_MIN_BLOCKS 4
+#endif
+template <int GEOM, int FIELD>
+constexpr int tape_min_blocks()
+{
+    return MT_TAPE_MIN_BLOCKS > 0 ? MT_TAPE_MIN_BLOCKS : pass_min_blocks<GEOM, FIELD>();
+}
+
 template <int GEOM, int FIELD, bool FWD>
-__global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM, FIELD>())
+__global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
               const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
               unsigned long long *tape_off, int64_t region_cap, unsigned int *flag)
