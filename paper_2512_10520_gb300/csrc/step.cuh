@@ -483,6 +483,12 @@ __device__ __forceinline__ void load_pair(const float4 *p, float4 &a, float4 &b)
 #endif
 }
 
+// Trilinear value as the weighted sum of the eight corners (1: measured 1.5 %
+// faster on config1 than nested lerps, 0).
+#ifndef MT_TRILINEAR_WEIGHTS
+#define MT_TRILINEAR_WEIGHTS 1
+#endif
+
 // Trilinear field from the pair layout; zero outside the node box.
 __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s)
 {
@@ -503,6 +509,17 @@ __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s
     load_pair(p10, b0, b1);
     load_pair(p01, c0, c1);
     load_pair(p11, d0, d1);
+#if MT_TRILINEAR_WEIGHTS
+    const float ux = 1.0f - tx, uy = 1.0f - ty, uz = 1.0f - tz;
+    const float w00 = uy * uz, w10 = ty * uz, w01 = uy * tz, w11 = ty * tz;
+    const float wa0 = ux * w00, wa1 = tx * w00, wb0 = ux * w10, wb1 = tx * w10;
+    const float wc0 = ux * w01, wc1 = tx * w01, wd0 = ux * w11, wd1 = tx * w11;
+#define MT_TRI(c)                                                                                              \
+    fmaf(wd1, d1.c, fmaf(wd0, d0.c, fmaf(wc1, c1.c, fmaf(wc0, c0.c, fmaf(wb1, b1.c, fmaf(wb0, b0.c,             \
+                                                                                      fmaf(wa1, a1.c, wa0 * a0.c)))))))
+    return make_float3(MT_TRI(x), MT_TRI(y), MT_TRI(z));
+#undef MT_TRI
+#endif
     const float ax = lerp(tx, a0.x, a1.x), ay = lerp(tx, a0.y, a1.y), az = lerp(tx, a0.z, a1.z);
     const float bx = lerp(tx, b0.x, b1.x), by = lerp(tx, b0.y, b1.y), bz = lerp(tx, b0.z, b1.z);
     const float cx = lerp(tx, c0.x, c1.x), cy = lerp(tx, c0.y, c1.y), cz = lerp(tx, c0.z, c1.z);

@@ -110,7 +110,11 @@ def test_per_stage_field_parity():
     assert np.median(err["pos_err"]) < 1e-5
 
 
-def test_per_stage_in_a_uniform_map_is_bit_identical_to_the_held_field():
+def test_per_stage_in_a_uniform_map_equals_the_held_field():
+    """In a uniform map every stage reads the same field, so the per-stage step
+    is the held-field step up to the rounding of the interpolation weights
+    (the trilinear weighted sum reproduces a constant to a few ulp): identical
+    step counts and statuses, states to 1e-6 relative."""
     wl = gen.workload("config1", n=3000)
     B = np.zeros((3, 3, 3, 3), np.float32)
     B[..., 1] = 1.5
@@ -118,8 +122,10 @@ def test_per_stage_in_a_uniform_map_is_bit_identical_to_the_held_field():
     wl.field = dict(kind="map", dims=[3, 3, 3], origin=[-10.0, -10.0, -10.0], spacing=[10.0, 10.0, 25.0], B=B)
     ref = gpu_transport(wl)
     out = gpu_transport(_per_stage(wl))
-    for k in FIELDS:
+    for k in ("steps", "status"):
         np.testing.assert_array_equal(ref[k], out[k], err_msg=k)
+    for k in ("x", "y", "z", "px", "py", "pz"):
+        np.testing.assert_allclose(out[k], ref[k], rtol=1e-6, atol=1e-6, err_msg=k)
 
 
 def test_per_stage_launch_shapes_and_differentiable_form():
