@@ -303,7 +303,10 @@ typedef struct mt_batch_cfg {
     int32_t use_graph;        /* 1 = capture the launch sequence in a CUDA graph once */
     int32_t reserved;         /*     per (workspace, sizes, arguments) and replay it  */
     void *workspace;          /* device scratch (256-byte aligned) of at least        */
-    int64_t workspace_bytes;  /*   mt_batch_workspace_bytes, or NULL = stream-ordered  */
+    int64_t workspace_bytes;  /*   mt_batch_workspace_bytes, or NULL: stream-ordered  */
+                              /*   scratch per call, or with use_graph the batch's    */
+                              /*   own, kept for replays (growing it synchronises the */
+                              /*   device)                                            */
 } mt_batch_cfg;
 
 /* A batch of n_inst worlds sharing the histogram set `hist` (copied, as in

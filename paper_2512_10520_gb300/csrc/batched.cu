@@ -45,6 +45,10 @@ struct mt_batch {
     // CUDA graph of the last launch sequence and the arguments it was made for
     cudaGraphExec_t graph = nullptr;
     std::vector<char> graph_key;
+    // scratch the batch keeps for graph replays without a caller workspace
+    // (a captured graph holds its addresses), grown as needed
+    char *graph_ws = nullptr;
+    int64_t graph_ws_bytes = 0;
 };
 
 namespace mt {
@@ -452,6 +456,7 @@ void mt_batch_destroy(mt_batch *b)
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_ws) cudaFree(b->graph_ws);
     for (auto &o : b->inst_own) o.release();
     b->own_tables.release();
     if (b->d_inst) cudaFree(b->d_inst);
@@ -522,7 +527,25 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     char *base = reinterpret_cast<char *>(c.workspace);
     bool own = false;
     cudaError_t e = cudaSuccess;
-    if (!base) {
+    if (!base && c.use_graph) {
+        if (b->graph_ws_bytes < need) {
+            // the old scratch may still be in use by earlier work on any stream
+            if (b->graph_ws) {
+                e = cudaDeviceSynchronize();
+                if (e == cudaSuccess) e = cudaFree(b->graph_ws);
+                b->graph_ws = nullptr;
+                b->graph_ws_bytes = 0;
+                if (b->graph) {
+                    cudaGraphExecDestroy(b->graph);
+                    b->graph = nullptr;
+                }
+            }
+            if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->graph_ws), (size_t)need);
+            if (e != cudaSuccess) return cuda_fail(e, "batch graph workspace");
+            b->graph_ws_bytes = need;
+        }
+        base = b->graph_ws;
+    } else if (!base) {
         e = cudaMallocAsync(reinterpret_cast<void **>(&base), (size_t)need, cs);
         if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
         own = true;

@@ -111,8 +111,25 @@ def test_graph_replay_equals_plain_launches(instances, batch):
     devs = _dev(instances)
     batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
     ref = _host(devs)
-    for _ in range(2):   # capture, then replay of the cached graph
+    import torch
+    junk = []
+    for _ in range(3):   # capture, then replays of the cached graph
         devs = _dev(instances)
+        batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, use_graph=True)
+        _assert_same(_host(devs), ref)
+        # other allocations between calls must not disturb the scratch the graph holds
+        junk.append(torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
+
+
+def test_graph_scratch_grows_with_the_instances(hist, instances, batch):
+    """A graph call with more muons than the last one grows the batch's scratch and
+    recaptures; smaller calls after it reuse the larger scratch."""
+    big = [gen.batched_instance(i, n=2 * inst["n"] + 5) for i, inst in enumerate(instances)]
+    for insts in (instances, big, instances):
+        devs = _dev(insts)
+        batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
+        ref = _host(devs)
+        devs = _dev(insts)
         batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, use_graph=True)
         _assert_same(_host(devs), ref)
 
