@@ -51,7 +51,8 @@ static CkptLayout ckpt_layout(int64_t n, int32_t max_steps, int32_t K)
     CkptLayout L;
     const int64_t cap = n > 0 ? n : 1;
     L.passes = max_steps > 0 ? (max_steps + K - 1) / K : 1;
-    L.alpha_off = round_up((int64_t)(L.passes + 1) * 8, 256);
+    // live counts of every pass, then the passes' work counters
+    L.alpha_off = round_up((int64_t)(L.passes + 1) * 16, 256);
     L.lists_off = round_up(L.alpha_off + 3 * MT_MAX_BOXES * 8, 256);
     L.list_bytes = 4 * cap * (int64_t)sizeof(float4);
     L.total = L.lists_off + (L.passes + 1) * L.list_bytes;
@@ -628,7 +629,8 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
     for (int p = 0; p < L.passes; ++p) {
         compact_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(
             w, soa, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
-            live_buf_at(ck + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, nullptr, K);
+            live_buf_at(ck + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, nullptr,
+            ctr + L.passes + 1 + p, nullptr, K);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -8,8 +8,10 @@
 // more than S steps.
 //
 // Live-list entries (64 B per muon) are described in step.cuh.  Counters:
-// three 64-bit words; pass p reads its live count from ctr[p % 3], appends to
-// ctr[(p+1) % 3] and clears ctr[(p+2) % 3] for the pass after it.
+// six 64-bit words; pass p reads its live count from ctr[p % 3], appends to
+// ctr[(p+1) % 3] and clears ctr[(p+2) % 3] for the pass after it; it takes its
+// work from ctr[3 + p % 3] and clears ctr[3 + (p+1) % 3], last used two passes
+// before.
 #include <cstdio>
 
 #include "compact.cuh"
@@ -28,7 +30,7 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
 {
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ws);
     LiveBuf buf[2] = {live_buf_at(ws + 256, n), live_buf_at(ws + 256 + 4 * n * (int64_t)sizeof(float4), n)};
-    cudaError_t e = cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -48,7 +50,8 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
     for (int p = 0; p < passes; ++p) {
         compact_pass<GEOM, FIELD><<<(unsigned)grid, kBlock, 0, st>>>(w, soa, rp, buf[p & 1], buf[(p + 1) & 1],
                                                                      ctr + p % 3, ctr + (p + 1) % 3,
-                                                                     ctr + (p + 2) % 3, S);
+                                                                     ctr + (p + 2) % 3, ctr + 3 + p % 3,
+                                                                     ctr + 3 + (p + 1) % 3, S);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -49,21 +49,32 @@ static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa 
 }
 
 // One pass: live count from *cin, survivors appended at *cout; *czero (if not
-// null) is cleared for the pass after this one.
+// null) is cleared for the pass after this one.  Warps take the live list in
+// chunks of 32 entries from the counter *work (zero at the start of the pass),
+// so a warp whose muons stop early takes more chunks and the SMs finish the
+// pass together; *wzero (if not null) is cleared for a later pass.
 template <int GEOM, int FIELD>
 __global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM, FIELD>()) compact_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp,
                                                        LiveBuf in, LiveBuf out, const unsigned long long *cin,
-                                                       unsigned long long *cout, unsigned long long *czero, int S)
+                                                       unsigned long long *cout, unsigned long long *czero,
+                                                       unsigned long long *work, unsigned long long *wzero, int S)
 {
     __shared__ SmemWorld sw;
     const int64_t count = (int64_t)*cin;
-    if (czero && blockIdx.x == 0 && threadIdx.x == 0) *czero = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (czero) *czero = 0ull;
+        if (wzero) *wzero = 0ull;
+    }
     if (count == 0) return;
     stage_world(sw, w, rp);
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
-        const int64_t i = base + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    for (;;) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(work, 32ull);
+        const int64_t base = (int64_t)__shfl_sync(0xFFFFFFFFu, b, 0);
+        if (base >= count) break;
+        const int64_t i = base + lane;
         bool keep = false;
         State s;
         float q = 0.0f;
