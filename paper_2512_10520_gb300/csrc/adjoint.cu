@@ -450,22 +450,31 @@ template <int GEOM, int FIELD, bool FWD>
 __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
               const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
-              unsigned long long *tape_off, int64_t region_cap, unsigned int *flag)
+              unsigned long long *tape_off, int64_t region_cap, unsigned int *flag, unsigned long long *work,
+              unsigned long long *wzero)
 {
     __shared__ SmemWorld sw;
     const int64_t count = (int64_t)*cin;
     const unsigned long long off = tape_off[0];
     const int64_t bytes = tape_pass_bytes(count, S);
-    if (blockIdx.x == 0 && threadIdx.x == 0) tape_off[1] = off + (count ? bytes : 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        tape_off[1] = off + (count ? bytes : 0);
+        if (wzero) *wzero = 0ull;
+    }
     if (count == 0) return;
     const bool room = (int64_t)off + bytes <= region_cap;
     if (!room && blockIdx.x == 0 && threadIdx.x == 0) *flag = 1u;
     stage_world(sw, w, rp);
     __syncthreads();
     TapeRef<MT_TAPE_RECORD_B> tr{tape_base + off, round_up(count, 32), 0};
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
-        const int64_t i = base + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    for (;;) {
+        // 32-entry chunks from the pass's work counter (see compact_pass)
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(work, 32ull);
+        const int64_t base = (int64_t)__shfl_sync(0xFFFFFFFFu, b, 0);
+        if (base >= count) break;
+        const int64_t i = base + lane;
         bool keep = false;
         State s;
         float q = 0.0f;
@@ -510,19 +519,27 @@ template <int GEOM, int FIELD>
 __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
     adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck, const unsigned long long *count_p, float *adj,
                  int64_t n, double *dalpha, const char *tape_base, const unsigned long long *tape_off,
-                 const unsigned int *flag)
+                 const unsigned int *flag, unsigned long long *work, unsigned long long *wzero)
 {
     __shared__ SmemWorld sw;
     __shared__ float sacc[3][MT_MAX_BOXES];
     const int64_t count = (int64_t)*count_p;
+    if (wzero && blockIdx.x == 0 && threadIdx.x == 0) *wzero = 0ull;
     if (count == 0 || *flag) return;
     stage_world(sw, w, rp);
     for (int t = threadIdx.x; t < 3 * MT_MAX_BOXES; t += blockDim.x) (&sacc[0][0])[t] = 0.0f;
     __syncthreads();
     AlphaAcc acc;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     TapeRef<MT_TAPE_RECORD_B> tr{const_cast<char *>(tape_base) + *tape_off, round_up(count, 32), 0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const unsigned lane = threadIdx.x & 31u;
+    for (;;) {
+        // 32-entry chunks from the pass's work counter (see compact_pass)
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(work, 32ull);
+        const int64_t base = (int64_t)__shfl_sync(0xFFFFFFFFu, b, 0);
+        if (base >= count) break;
+        const int64_t i = base + lane;
+        if (i >= count) continue;
         tr.tid = i;
         const float q = ck.w0[i].w;
         const int64_t idx = __float_as_int(ck.w2[i].w);
@@ -659,7 +676,7 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
         tape_pass<GEOM, FIELD, true><<<grid, kBlock, 0, st>>>(
             w, soa, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
             live_buf_at(buf + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, K,
-            buf + T.region_off, toff + p, T.region_cap, flag);
+            buf + T.region_off, toff + p, T.region_cap, flag, ctr + L.passes + 1 + p, nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -667,7 +684,9 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
 }
 
 // Scratch of the recompute form's backward: the tape of one pass of up to n
-// entries, after a 256-byte header holding the region offsets and the flag.
+// entries, after a 256-byte header holding the region offsets (bytes 0-15),
+// the flag (64) and three work counters (128-151) that the backward's kernels
+// take in turn: launch j uses counter j % 3 and clears counter (j + 1) % 3.
 static int64_t ckpt_scratch_bytes(int64_t n, int K) { return 256 + tape_pass_bytes(n > 0 ? n : 1, K); }
 
 template <int GEOM, int FIELD>
@@ -685,14 +704,17 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
     const int rgrid = resident_grid((const void *)tape_pass<GEOM, FIELD, false>, n);
     const int agrid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
     const int64_t cap = tape_pass_bytes(n > 0 ? n : 1, K);
-    for (int p = L.passes - 1; p >= 0; --p) {
+    unsigned long long *wc = reinterpret_cast<unsigned long long *>(scratch + 128);
+    int j = 0;
+    for (int p = L.passes - 1; p >= 0; --p, j += 2) {
         const LiveBuf lp = live_buf_at(ck + L.lists_off + p * L.list_bytes, n);
         tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, st>>>(w, mt_muon_soa{}, rp, lp, lp, ctr + p, nullptr, K,
-                                                                scratch + 256, toff, cap, flag);
+                                                                scratch + 256, toff, cap, flag, wc + j % 3,
+                                                                wc + (j + 1) % 3);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, scratch + 256, toff,
-                                                           flag);
+                                                           flag, wc + (j + 1) % 3, wc + (j + 2) % 3);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -705,16 +727,20 @@ static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParam
 {
     const TapeLayout T = tape_layout(n, rp.max_steps, K);
     const CkptLayout &L = T.ck;
-    const unsigned long long *ctr = reinterpret_cast<const unsigned long long *>(buf);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(buf);
     const unsigned long long *toff = reinterpret_cast<const unsigned long long *>(buf + T.off_off);
     const unsigned int *flag = reinterpret_cast<const unsigned int *>(buf + T.flag_off);
     double *dalpha = reinterpret_cast<double *>(buf + L.alpha_off);
+    // the passes' work counters (used by the forward) are cleared for the sweep
+    unsigned long long *wc = ctr + L.passes + 1;
     cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(wc, 0, (size_t)(L.passes + 1) * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     const int grid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
     for (int p = L.passes - 1; p >= 0; --p) {
         adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
-                                                          ctr + p, adj, n, dalpha, buf + T.region_off, toff + p, flag);
+                                                          ctr + p, adj, n, dalpha, buf + T.region_off, toff + p, flag,
+                                                          wc + p, nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
