@@ -55,6 +55,7 @@ namespace mt {
 
 struct BatchWs {
     unsigned int *cnt;          // [3][n_inst] live counts (rotating)
+    unsigned int *sub;          // [n_inst] live entries handed out in the current pass
     unsigned int *cof;          // [n_inst + 1] item offsets of the current pass
     unsigned int *queue;        // [1] next item
     unsigned long long *off;    // [n_inst + 1] region offsets
@@ -70,6 +71,8 @@ static int64_t batch_ws_layout(int n_inst, int64_t N, BatchWs *ws, char *base)
     int64_t o = 0;
     const int64_t c_cnt = o;
     o = round256(o + 3 * (int64_t)n_inst * 4);
+    const int64_t c_sub = o;
+    o = round256(o + (int64_t)n_inst * 4);
     const int64_t c_cof = o;
     o = round256(o + ((int64_t)n_inst + 1) * 4);
     const int64_t c_q = o;
@@ -85,6 +88,7 @@ static int64_t batch_ws_layout(int n_inst, int64_t N, BatchWs *ws, char *base)
     o += 4 * cap * (int64_t)sizeof(float4);
     if (ws && base) {
         ws->cnt = reinterpret_cast<unsigned int *>(base + c_cnt);
+        ws->sub = reinterpret_cast<unsigned int *>(base + c_sub);
         ws->cof = reinterpret_cast<unsigned int *>(base + c_cof);
         ws->queue = reinterpret_cast<unsigned int *>(base + c_q);
         ws->off = reinterpret_cast<unsigned long long *>(base + c_off);
@@ -160,9 +164,11 @@ __global__ void __launch_bounds__(256) batch_init(const unsigned long long *off,
     }
 }
 
-// Items of pass p: ceil(live_i / block) per instance, exclusive scan in cof.
+// Items of pass p: ceil(live_i / block) per instance, exclusive scan in cof;
+// the hand-out counters of the instances are cleared.
 __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, unsigned int *cnt_zero, int n_inst,
-                                                   int block, unsigned int *cof, unsigned int *queue)
+                                                   int block, unsigned int *cof, unsigned int *queue,
+                                                   unsigned int *sub)
 {
     __shared__ unsigned int carry;
     if (threadIdx.x == 0) {
@@ -173,7 +179,10 @@ __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, u
     for (int base = 0; base < n_inst; base += blockDim.x) {
         const int i = base + threadIdx.x;
         const unsigned int items = i < n_inst ? (cnt_in[i] + block - 1) / block : 0u;
-        if (i < n_inst) cnt_zero[i] = 0;
+        if (i < n_inst) {
+            cnt_zero[i] = 0;
+            sub[i] = 0;
+        }
         // block-wide exclusive scan of items
         __shared__ unsigned int warp_sums[32];
         unsigned int v = items;
@@ -202,12 +211,18 @@ __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, u
     if (threadIdx.x == 0) cof[n_inst] = carry;
 }
 
+// One pass over every instance.  A block pops an item from the queue, which
+// names an instance (items of instances are contiguous), stages that world in
+// shared memory if it is not the one staged, and then its warps take chunks
+// of 32 of the instance's live entries from sub[i] until none are left, so a
+// warp whose muons stop early does not wait for the others.  Items whose
+// instance has nothing left to hand out are dropped without staging.
 template <int GEOM, int FIELD, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
                                                    const unsigned long long *off, int n_inst, RunParams rp,
                                                    LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
                                                    unsigned int *cnt_out, const unsigned int *cof,
-                                                   unsigned int *queue, int S)
+                                                   unsigned int *queue, unsigned int *sub, int S)
 {
     __shared__ SmemWorld sw;
     __shared__ WorldParams wi;
@@ -215,6 +230,7 @@ __global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_
     __shared__ mt_muon_soa s_soa;
     int cur = -1;
     const unsigned int total = cof[n_inst];
+    const unsigned lane = threadIdx.x & 31u;
 #pragma unroll 1
     while (true) {
         if (threadIdx.x == 0) {
@@ -232,13 +248,17 @@ __global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_
                 }
                 // lo is the last instance with cof[lo] <= item, so instances without
                 // items (cof[j] == cof[j + 1]) are never chosen
-                s_inst = lo;
+                s_inst = *reinterpret_cast<volatile unsigned int *>(&sub[lo]) < cnt_in[lo] ? lo : -1;
             }
         }
         __syncthreads();
         const unsigned int item = (unsigned int)s_item;
         const int i = s_inst;
         if (item >= total) break;
+        if (i < 0) {
+            __syncthreads();
+            continue;
+        }
         if (i != cur) {
             const int words = (int)(sizeof(WorldParams) / 4);
             const int *src = reinterpret_cast<const int *>(&inst[i]);
@@ -254,31 +274,39 @@ __global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_
         RunParams r = rp;
         r.id_offset = s_soa.id_offset;
         r.instance = s_soa.instance;
-        const int64_t e = (int64_t)(item - cof[i]) * BLOCK + threadIdx.x;
-        bool keep = false;
-        State s;
-        float q = 0.0f;
-        int k = 0;
-        int64_t idx = 0;
-        if (e < (int64_t)cnt_in[i]) {
-            get_live(in, (int64_t)off[i] + e, s, q, k, idx);
-            const uint64_t id = (uint64_t)(r.id_offset + idx);
-            const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
-            const int kend = min(k + S, r.max_steps);
-            int st = MT_ALIVE;
+        const int64_t n_i = (int64_t)cnt_in[i];
 #pragma unroll 1
-            for (; k < kend; ++k) {
-                st = step<GEOM, FIELD>(wi, sw, s, q, k, id_lo, id_hi, r);
-                if (st != MT_ALIVE) break;
+        for (;;) {
+            unsigned int c = 0;
+            if (lane == 0) c = atomicAdd(&sub[i], 32u);
+            c = __shfl_sync(0xFFFFFFFFu, c, 0);
+            if ((int64_t)c >= n_i) break;
+            const int64_t e = (int64_t)c + lane;
+            bool keep = false;
+            State s;
+            float q = 0.0f;
+            int k = 0;
+            int64_t idx = 0;
+            if (e < n_i) {
+                get_live(in, (int64_t)off[i] + e, s, q, k, idx);
+                const uint64_t id = (uint64_t)(r.id_offset + idx);
+                const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+                const int kend = min(k + S, r.max_steps);
+                int st = MT_ALIVE;
+#pragma unroll 1
+                for (; k < kend; ++k) {
+                    st = step<GEOM, FIELD>(wi, sw, s, q, k, id_lo, id_hi, r);
+                    if (st != MT_ALIVE) break;
+                }
+                if (st == MT_ALIVE && k >= r.max_steps) st = MT_MAX_STEPS;
+                if (st != MT_ALIVE)
+                    store_muon(s_soa, idx, s, k, st);
+                else
+                    keep = true;
             }
-            if (st == MT_ALIVE && k >= r.max_steps) st = MT_MAX_STEPS;
-            if (st != MT_ALIVE)
-                store_muon(s_soa, idx, s, k, st);
-            else
-                keep = true;
+            const int64_t slot = warp_append_u32(&cnt_out[i], keep);
+            if (keep) put_live(out, (int64_t)off[i] + slot, s, q, k, idx);
         }
-        const int64_t slot = warp_append_u32(&cnt_out[i], keep);
-        if (keep) put_live(out, (int64_t)off[i] + slot, s, q, k, idx);
         __syncthreads();
     }
 }
@@ -305,12 +333,12 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
         unsigned int *c_in = ws.cnt + (p % 3) * n_inst;
         unsigned int *c_out = ws.cnt + ((p + 1) % 3) * n_inst;
         unsigned int *c_zero = ws.cnt + ((p + 2) % 3) * n_inst;
-        batch_plan<<<1, 1024, 0, st>>>(c_in, c_zero, n_inst, BLOCK, ws.cof, ws.queue);
+        batch_plan<<<1, 1024, 0, st>>>(c_in, c_zero, n_inst, BLOCK, ws.cof, ws.queue, ws.sub);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
         batch_pass<GEOM, FIELD, BLOCK><<<(unsigned)grid, BLOCK, 0, st>>>(b->d_inst, ws.soa, ws.off, n_inst, rp,
                                                                         L[p & 1], L[(p + 1) & 1], c_in, c_out,
-                                                                        ws.cof, ws.queue, S);
+                                                                        ws.cof, ws.queue, ws.sub, S);
         e = cudaGetLastError();
     }
     return e;
