@@ -446,6 +446,11 @@ constexpr int tape_min_blocks()
     return MT_TAPE_MIN_BLOCKS > 0 ? MT_TAPE_MIN_BLOCKS : pass_min_blocks<GEOM, FIELD>();
 }
 
+// Philox round keys from the launch parameters in the recorded passes (see step)
+#ifndef MT_TAPE_RK
+#define MT_TAPE_RK 1
+#endif
+
 template <int GEOM, int FIELD, bool FWD>
 __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
@@ -491,7 +496,8 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
             for (; k < kend; ++k) {
                 TapeWriter<MT_TAPE_RECORD_B> wr{&tr, ns};
                 wr.on = room;
-                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp, wr);
+                r = step<GEOM, FIELD, TapeWriter<MT_TAPE_RECORD_B> &, MT_TAPE_RK>(w, sw, s, q, k, id_lo, id_hi,
+                                                                               (uint32_t)rp.instance, rp, wr);
                 if (r != MT_ALIVE) break;
                 ++ns;
             }
@@ -801,8 +807,7 @@ mt_status fill_run(RunParams &rp, float step_len, int32_t max_steps, uint64_t se
     rp.d = step_len;
     rp.kd = (float)(0.299792458 * (double)step_len);
     rp.max_steps = max_steps;
-    rp.key0 = (uint32_t)seed;
-    rp.key1 = (uint32_t)(seed >> 32);
+    set_seed(rp, seed);
     rp.alpha = alpha;
     rp.n_block = alpha ? n_block : 0;
     rp.instance = instance;

@@ -271,9 +271,8 @@ __global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_
             __syncthreads();
             cur = i;
         }
-        RunParams r = rp;
-        r.id_offset = s_soa.id_offset;
-        r.instance = s_soa.instance;
+        const int64_t id0 = s_soa.id_offset;
+        const uint32_t word = (uint32_t)s_soa.instance;
         const int64_t n_i = (int64_t)cnt_in[i];
 #pragma unroll 1
         for (;;) {
@@ -289,16 +288,16 @@ __global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_
             int64_t idx = 0;
             if (e < n_i) {
                 get_live(in, (int64_t)off[i] + e, s, q, k, idx);
-                const uint64_t id = (uint64_t)(r.id_offset + idx);
+                const uint64_t id = (uint64_t)(id0 + idx);
                 const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
-                const int kend = min(k + S, r.max_steps);
+                const int kend = min(k + S, rp.max_steps);
                 int st = MT_ALIVE;
 #pragma unroll 1
                 for (; k < kend; ++k) {
-                    st = step<GEOM, FIELD>(wi, sw, s, q, k, id_lo, id_hi, r);
+                    st = step<GEOM, FIELD, NoRecord, false>(wi, sw, s, q, k, id_lo, id_hi, word, rp);
                     if (st != MT_ALIVE) break;
                 }
-                if (st == MT_ALIVE && k >= r.max_steps) st = MT_MAX_STEPS;
+                if (st == MT_ALIVE && k >= rp.max_steps) st = MT_MAX_STEPS;
                 if (st != MT_ALIVE)
                     store_muon(s_soa, idx, s, k, st);
                 else
@@ -584,8 +583,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     rp.d = step_len;
     rp.kd = (float)(0.299792458 * (double)step_len);
     rp.max_steps = max_steps;
-    rp.key0 = (uint32_t)seed;
-    rp.key1 = (uint32_t)(seed >> 32);
+    set_seed(rp, seed);
     rp.alpha = nullptr;
     rp.n_block = 0;
     rp.instance = 0;

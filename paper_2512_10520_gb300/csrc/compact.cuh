@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM, FIELD>()) compac
             int r = MT_ALIVE;
 #pragma unroll 1
             for (; k < kend; ++k) {
-                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp);
+                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, (uint32_t)rp.instance, rp);
                 if (r != MT_ALIVE) break;
             }
             if (r == MT_ALIVE && k >= rp.max_steps) r = MT_MAX_STEPS;

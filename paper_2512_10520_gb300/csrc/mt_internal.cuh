@@ -98,11 +98,26 @@ struct RunParams {
     float kd;            // kappa * d
     int32_t max_steps;
     uint32_t key0, key1;
+    // Philox round keys: round r uses (key0 + r * 0x9E3779B9, key1 + r * 0xBB67AE85).
+    // Held in the launch parameters, they enter the round's xor as constant
+    // operands instead of being advanced in registers every step.
+    uint32_t rk[2][10];
     const float *alpha;   // device [n_block][3] or null
     int32_t n_block;
     int32_t instance;
     int64_t id_offset;
 };
+
+// The seed's two key words and the round keys derived from them.
+inline void set_seed(RunParams &rp, uint64_t seed)
+{
+    rp.key0 = (uint32_t)seed;
+    rp.key1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rp.rk[0][r] = rp.key0 + (uint32_t)r * 0x9E3779B9u;
+        rp.rk[1][r] = rp.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
 
 }  // namespace mt
 

@@ -37,6 +37,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same generator with the ten round keys given (see RunParams::rk).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[2][10])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[0][r], lo1, hi0 ^ c.w ^ rk[1][r], lo0);
+    }
+    return c;
+}
+
 // U(w) = (w >> 8) * 2^-24, exact in FP32.
 __device__ __forceinline__ float u01(uint32_t w) { return __uint2float_rz(w >> 8) * 5.9604644775390625e-8f; }
 
@@ -629,10 +641,15 @@ struct NoRecord {
     __device__ __forceinline__ void field(float3) {}
 };
 
-// One full step k of Algorithm 1.  Returns MT_ALIVE or the break status.
-template <int GEOM, int FIELD, class Rec = NoRecord>
+// One full step k of Algorithm 1 for the muon with id (id_hi, id_lo) of
+// instance inst (the Philox counter's words).  Returns MT_ALIVE or the break
+// status.  RK: Philox takes its round keys from rp.rk (measured faster in the
+// compaction passes) or advances them from rp.key0/key1 (faster in the
+// batched pass); both give the same words.
+template <int GEOM, int FIELD, class Rec = NoRecord, bool RK = true>
 __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, State &s, float q, int k,
-                                    uint32_t id_lo, uint32_t id_hi, const RunParams &rp, Rec &&rec = Rec())
+                                    uint32_t id_lo, uint32_t id_hi, uint32_t inst, const RunParams &rp,
+                                    Rec &&rec = Rec())
 {
     const float P2 = fmaf(s.px, s.px, fmaf(s.py, s.py, s.pz * s.pz));
     const int stop = check_stop(w, s, P2);
@@ -651,7 +668,8 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
     rec.begin(s, box, mat != 0);
     if (mat != 0) {
         const int ib = momentum_bin(w, sw, s, P2);
-        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, id_lo, id_hi, (uint32_t)rp.instance), rp.key0, rp.key1);
+        const uint4 ctr = make_uint4((uint32_t)k, id_lo, id_hi, inst);
+        const uint4 rnd = RK ? philox4x32_10(ctr, rp.rk) : philox4x32_10(ctr, rp.key0, rp.key1);
         // the guide (or alias) row of histogram h sits at h * its length, so its
         // load need not wait for the histogram record's
         const int h = (mat - 1) * w.n_pbin + ib;

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kBlock) transport_kernel(const WorldParams w, 
         int out = MT_MAX_STEPS;
 #pragma unroll 1
         for (; k < rp.max_steps; ++k) {
-            const int r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp);
+            const int r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, (uint32_t)rp.instance, rp);
             if (r != MT_ALIVE) {
                 out = r;
                 break;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBlock) transport_persistent(const WorldParams
             if (k >= rp.max_steps)
                 r = MT_MAX_STEPS;
             else
-                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, rp);
+                r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, (uint32_t)rp.instance, rp);
             if (r != MT_ALIVE) {
                 store_muon(soa, m, s, k, r);
                 m = -1;
@@ -224,8 +224,7 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     rp.d = step_len;
     rp.kd = (float)(0.299792458 * (double)step_len);
     rp.max_steps = max_steps;
-    rp.key0 = (uint32_t)seed;
-    rp.key1 = (uint32_t)(seed >> 32);
+    set_seed(rp, seed);
     rp.alpha = alpha;
     rp.n_block = alpha ? n_block : 0;
     rp.instance = s->instance;
