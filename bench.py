@@ -746,7 +746,9 @@ def run_mine(args):
     achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved_gbs / peaks["hbm_gbs"],
-            "traffic": _traffic("transport") if args.mode == "auto" and not args.steps_per_pass else None,
+            # the committed figure is for the default launch on the full 1e6-muon call
+            "traffic": (_traffic("transport") if args.mode == "auto" and not args.steps_per_pass
+                        and not args.blocks_per_sm and args.muons is None else None),
             "peak_kind": peak_kind, "bytes_per_step": BYTES_PER_STEP,
             "kernel_ms": kernel_s * 1e3,
             "timed_unit": "one mt_transport call (all of its kernels), CUDA events on the launching stream"}
