@@ -22,11 +22,25 @@
 #include "compact.cuh"
 
 // Resident threads per SM the compiler must allow for in batch_pass (register
-// budget: 768 threads = 85 registers; measured on 16 config2 instances: 45.8 ms
-// against 46.9 ms at 1280 threads = 48 registers, which spill).
+// budget: 1024 threads = 64 registers; measured on config2, 256 instances with
+// warp chunks: 730 ms against 752 ms at 768 threads = 80 registers).  The
+// variants that spill at 64 registers (per-stage field reads; polyhedra) keep
+// 768.
 #ifndef MT_BATCH_THREADS_PER_SM
-#define MT_BATCH_THREADS_PER_SM 768
+#define MT_BATCH_THREADS_PER_SM 1024
 #endif
+#ifndef MT_BATCH_THREADS_PER_SM_WIDE
+#define MT_BATCH_THREADS_PER_SM_WIDE 768
+#endif
+
+namespace mt {
+template <int GEOM, int FIELD>
+constexpr int batch_threads_per_sm()
+{
+    return (GEOM == MT_GEOM_POLYHEDRA || FIELD == kFieldMapStaged) ? MT_BATCH_THREADS_PER_SM_WIDE
+                                                                   : MT_BATCH_THREADS_PER_SM;
+}
+}  // namespace mt
 
 struct mt_batch {
     int device = 0;
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, u
 // warp whose muons stop early does not wait for the others.  Items whose
 // instance has nothing left to hand out are dropped without staging.
 template <int GEOM, int FIELD, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, MT_BATCH_THREADS_PER_SM / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
+__global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
                                                    const unsigned long long *off, int n_inst, RunParams rp,
                                                    LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
                                                    unsigned int *cnt_out, const unsigned int *cof,
