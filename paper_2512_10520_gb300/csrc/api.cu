@@ -420,6 +420,20 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
     w.gshift = 32 - gbits;
     w.log2_plo = (float)std::log2(hd->p_lo);
     w.pbin_scale = (float)(hd->n_pbin / std::log2(hd->p_hi / hd->p_lo));
+    {
+        // Error of the kernel's bin coordinate u = (0.5 log2(P^2) - log2 p_lo) * scale
+        // near the bin faces (P in [p_lo / 2, 2 p_hi]): the log2 intrinsic (2^-22
+        // absolute on [0.5, 2], else 2 ulp), the roundings of the fma and the
+        // product, and those of log2 p_lo and scale as stored.
+        auto ulp = [](double v) { return v > 0.0 ? std::ldexp(1.0, std::ilogb(v) - 23) : std::ldexp(1.0, -149); };
+        const double lp = std::fabs(std::log2(hd->p_lo)), scale = w.pbin_scale;
+        const double L = std::max(std::fabs(2.0 * std::log2(hd->p_lo) - 2.0), std::fabs(2.0 * std::log2(hd->p_hi) + 2.0));
+        const double umax = hd->n_pbin + 2.0;
+        const double err = 0.5 * std::max(std::ldexp(1.0, -22), 2.0 * ulp(L)) * scale + 0.5 * ulp(0.5 * L + lp) * scale +
+                           0.5 * ulp(umax) + umax * std::ldexp(1.0, -24) + 0.5 * ulp(lp) * scale;
+        const double eps = std::max(4.0 * err, 1e-4);
+        w.pbin_eps = eps < 0.1 ? (float)eps : 1.0f;   // 1: every estimate goes to the edges
+    }
     return MT_OK;
 }
 

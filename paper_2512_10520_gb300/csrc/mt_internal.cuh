@@ -91,6 +91,7 @@ struct WorldParams {
     int32_t pbin_custom;      // 1: explicit bin edges (binary search over e2), 0: log10 bins
     float log2_plo;
     float pbin_scale;   // n_pbin / log2(p_hi / p_lo)
+    float pbin_eps;     // bound on the error of the FP32 bin coordinate (times 4), at least 1e-4
 };
 
 struct RunParams {

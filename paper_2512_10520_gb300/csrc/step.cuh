@@ -300,7 +300,7 @@ __device__ __forceinline__ void sq2(float h, float l, float &sh, float &sl)
 
 // GetMomentumBin on log10 bins (a fast FP32 estimate) or over explicit edges
 // (binary search), confirmed against the squared edges held as hi + lo pairs
-// whenever |p|^2 lies within 4e-6 of one.
+// whenever the estimate is near a bin face or |p|^2 lies within 4e-6 of an edge.
 __device__ __forceinline__ int momentum_bin(const WorldParams &w, const SmemWorld &sw, const State &s, float P2)
 {
     int i;
@@ -317,8 +317,15 @@ __device__ __forceinline__ int momentum_bin(const WorldParams &w, const SmemWorl
         }
         i = lo;
     } else {
-        i = __float2int_rd(fmaf(0.5f, __log2f(P2), -w.log2_plo) * w.pbin_scale);
+        // The estimate's bin coordinate u is within pbin_eps / 4 of the exact one
+        // (the FP32 log2 and the roundings, bounded on the host), so a fraction of
+        // u farther than pbin_eps from an integer settles the bin; otherwise the
+        // squared edges decide below.
+        const float u = fmaf(0.5f, __log2f(P2), -w.log2_plo) * w.pbin_scale;
+        i = __float2int_rd(u);
+        const float fr = u - (float)i;
         i = min(max(i, 0), w.n_pbin - 1);
+        if (fr > w.pbin_eps && fr < 1.0f - w.pbin_eps) return i;
     }
     const float elo = sw.e2[i].x, ehi = sw.e2[i + 1].x;
     const bool near_lo = i > 0 && P2 < elo * 1.000004f;
@@ -635,6 +642,8 @@ __device__ __forceinline__ void rk4_staged(const WorldParams &w, State &s, float
 __device__ __forceinline__ int check_stop(const WorldParams &w, const State &s, float P2)
 {
     if (P2 < w.pmin2) return MT_STOPPED;
+    // strictly inside on the hi words: no pair test below can fire
+    if (s.z < w.zmax_hi && fabsf(s.x) < w.xmax_hi && fabsf(s.y) < w.ymax_hi) return MT_ALIVE;
     if (ge2(s.z, s.zl, w.zmax_hi, w.zmax_lo)) return MT_EXIT_Z;
     const float ax = fabsf(s.x), axl = s.x < 0.0f ? -s.xl : s.xl;
     const float ay = fabsf(s.y), ayl = s.y < 0.0f ? -s.yl : s.yl;
