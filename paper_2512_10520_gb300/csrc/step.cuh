@@ -109,6 +109,21 @@ __device__ __forceinline__ void stage_world(SmemWorld &sw, const WorldParams &w,
         for (int t = threadIdx.x; t < w.n_box; t += blockDim.x) sw.inner[t] = w.pinner[t];
 }
 
+// lo <= r < hi for box (or bounding box) b, r and the faces as hi + lo pairs.
+// Unless a hi word of r equals a face, the test on the hi words is the pair test
+// (ge2 reduces to > and its negation to < without a tie); the lo words are read
+// only on a tie.
+__device__ __forceinline__ bool in_box(const SmemWorld &sw, int b, const State &s)
+{
+    const float z0 = sw.lo_hi[2][b], z1 = sw.hi_hi[2][b], x0 = sw.lo_hi[0][b], x1 = sw.hi_hi[0][b];
+    const float y0 = sw.lo_hi[1][b], y1 = sw.hi_hi[1][b];
+    const bool tie = s.z == z0 || s.z == z1 || s.x == x0 || s.x == x1 || s.y == y0 || s.y == y1;
+    if (!tie) return s.z > z0 && s.z < z1 && s.x > x0 && s.x < x1 && s.y > y0 && s.y < y1;
+    return ge2(s.z, s.zl, z0, sw.lo_lo[2][b]) && !ge2(s.z, s.zl, z1, sw.hi_lo[2][b]) &&
+           ge2(s.x, s.xl, x0, sw.lo_lo[0][b]) && !ge2(s.x, s.xl, x1, sw.hi_lo[0][b]) &&
+           ge2(s.y, s.yl, y0, sw.lo_lo[1][b]) && !ge2(s.y, s.yl, y1, sw.hi_lo[1][b]);
+}
+
 // GetMaterial for ordered boxes: first box with lo <= r < hi on all axes.  Only
 // the boxes listed for the point's z slab are tested (the paper prunes its
 // candidate volumes with a spatial grid the same way), in list order.
@@ -119,10 +134,7 @@ __device__ __forceinline__ int find_box(const WorldParams &w, const SmemWorld &s
     while (cand) {
         const int b = __ffs(cand) - 1;
         cand &= cand - 1u;
-        if (ge2(s.z, s.zl, sw.lo_hi[2][b], sw.lo_lo[2][b]) && !ge2(s.z, s.zl, sw.hi_hi[2][b], sw.hi_lo[2][b]) &&
-            ge2(s.x, s.xl, sw.lo_hi[0][b], sw.lo_lo[0][b]) && !ge2(s.x, s.xl, sw.hi_hi[0][b], sw.hi_lo[0][b]) &&
-            ge2(s.y, s.yl, sw.lo_hi[1][b], sw.lo_lo[1][b]) && !ge2(s.y, s.yl, sw.hi_hi[1][b], sw.hi_lo[1][b]))
-            return b;
+        if (in_box(sw, b, s)) return b;
     }
     return -1;
 }
@@ -272,10 +284,7 @@ __device__ __forceinline__ int find_solid(const WorldParams &w, const SmemWorld 
     while (cand) {
         const int b = __ffs(cand) - 1;
         cand &= cand - 1u;
-        if (!(ge2(s.z, s.zl, sw.lo_hi[2][b], sw.lo_lo[2][b]) && !ge2(s.z, s.zl, sw.hi_hi[2][b], sw.hi_lo[2][b]) &&
-              ge2(s.x, s.xl, sw.lo_hi[0][b], sw.lo_lo[0][b]) && !ge2(s.x, s.xl, sw.hi_hi[0][b], sw.hi_lo[0][b]) &&
-              ge2(s.y, s.yl, sw.lo_hi[1][b], sw.lo_lo[1][b]) && !ge2(s.y, s.yl, sw.hi_hi[1][b], sw.hi_lo[1][b])))
-            continue;
+        if (!in_box(sw, b, s)) continue;
         const float4 in = sw.inner[b];
         if (s.x > in.x && s.x < in.y && s.y > in.z && s.y < in.w) return b;
         if (in_solid_sides(w, b, s)) return b;
