@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "muon-steps/s on 1 GB300: plain, batched, fwd+adjoint; % of memory roofline"
 UNIT = "muon-steps/s"
 BYTES_PER_STEP = 112          # algorithmic bytes per muon-step (8 field corners x 12 B + 16 B sampler)
-WORKLOAD = ("config1: 1e6 muons (p^-2.7 on 10-350 GeV, p_T ~ Exp(1 GeV)), 6 iron magnet blocks "
+WORKLOAD = ("shield1e6: 1e6 muons (p^-2.7 on 10-350 GeV, p_T ~ Exp(1 GeV)), 6 iron magnet blocks "
             "+/-1.7 T + 2 m concrete wall, trilinear 200x200x600 FP32 field map, 3 materials x 64 log10 "
             "p-bins x 128x64 (f, theta) histograms, d = 2 cm, max 1500 steps")
 
@@ -168,7 +168,7 @@ def cpu_oracle_run(wl, n_sample: int, threads: int):
 
 
 def time_adjoint_form(mt, world, wl, init, work, stream, id_offset, reps=3, K=32, tape=True):
-    """fwd+adjoint form (config3: config1 geometry, 18 field scales, checkpoints every K
+    """fwd+adjoint form (diff1e6: shield1e6 geometry, 18 field scales, checkpoints every K
     steps): checkpointing forward + acceptance loss + adjoint, each timed with CUDA events."""
     import torch
     n = wl.n
@@ -287,22 +287,22 @@ def boxes_as_solids(geo):
 
 
 def time_polyhedra_form(mt, dev, stream, n=None, reps=3, id_offset=0):
-    """config1p: config1 with tapered magnets as convex solids (Sec. Simulation
-    item 1, Eq. 2), same field map and spectrum.  Also timed: config1's own
+    """tapered1e6: shield1e6 with tapered magnets as convex solids (Sec. Simulation
+    item 1, Eq. 2), same field map and spectrum.  Also timed: shield1e6's own
     boxes given as solids with rectangular ends (same results as the boxes, so
     the difference to the plain form is the cost of the solid lookup alone)."""
     from workloads import gen
-    wl = gen.workload("config1p", n=n)
+    wl = gen.workload("tapered1e6", n=n)
     t, steps = _time_world(mt, wl, wl.geometry, dev, stream, reps, id_offset)
-    w1 = gen.workload("config1", n=n)
+    w1 = gen.workload("shield1e6", n=n)
     t1, steps1 = _time_world(mt, w1, boxes_as_solids(w1.geometry), dev, stream, reps, id_offset)
     return dict(value=steps / t, unit=UNIT, kernel_ms=1e3 * t, muon_steps=steps,
                 roofline_frac=BYTES_PER_STEP * steps / t / 1e9 / _peaks()[0]["hbm_gbs"],
-                config1_as_solids=dict(value=steps1 / t1, kernel_ms=1e3 * t1, muon_steps=steps1))
+                shield1e6_as_solids=dict(value=steps1 / t1, kernel_ms=1e3 * t1, muon_steps=steps1))
 
 
 def time_offline_form(mt, stream, cpu=True):
-    """Offline phase on the GPU (Sec. Building histograms, Appendix A): config1's
+    """Offline phase on the GPU (Sec. Building histograms, Appendix A): shield1e6's
     histogram set (3 materials x 64 bins x 128x64 cells, 1e6 samples each) from
     the parametric sampler, and the Appendix A pilot (1024 probes x 1e5 samples)
     with its bounded-variation edges; CUDA events.  CPU: the numpy fixture of
@@ -340,7 +340,7 @@ def time_offline_form(mt, stream, cpu=True):
 
 
 def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True, block=0, spp=0):
-    """Batched form (config2): n_inst worlds, each its own 64x64x512 voxel geometry
+    """Batched form (worlds256): n_inst worlds, each its own 64x64x512 voxel geometry
     and 100x100x300 field map, one shared histogram set, instance sizes log-uniform
     in [1e3, 1e6].  One mt_transport_batched call (autotuned launch shape, CUDA
     graph) is timed with CUDA events; the same instances as one mt_transport call
@@ -410,9 +410,9 @@ def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True
     return out
 
 
-def time_c4_form(mt, dev, n_total=None, chunk=None, rank=0, cpu_sample=2000):
-    """Throughput at scale (config4): 1e8 muons of config1's spectrum in 16M-muon chunks
-    through the config1 geometry with a 400x400x1200 map and 4 materials x 128 bins x
+def time_shield1e8_form(mt, dev, n_total=None, chunk=None, rank=0, cpu_sample=2000):
+    """Throughput at scale (shield1e8): 1e8 muons of shield1e6's spectrum in 16M-muon chunks
+    through the shield1e6 geometry with a 400x400x1200 map and 4 materials x 128 bins x
     256x128 tables.  Three timings, CUDA events:
       plain     -- all chunks resident in HBM, one mt_transport call per chunk, one stream;
       batched   -- the same muons as one instance of a batch: one mt_transport_batched call
@@ -423,15 +423,15 @@ def time_c4_form(mt, dev, n_total=None, chunk=None, rank=0, cpu_sample=2000):
     import torch
     from paper_2512_10520_gb300.api import empty_like_soa
     from workloads import gen
-    n_total = n_total or gen.C4_MUONS
-    chunk = min(chunk or gen.C4_CHUNK, n_total)
-    wl = gen.workload("config4", n=1)
+    n_total = n_total or gen.SHIELD1E8_MUONS
+    chunk = min(chunk or gen.SHIELD1E8_CHUNK, n_total)
+    wl = gen.workload("shield1e8", n=1)
     bounds = list(range(0, n_total, chunk)) + [n_total]
     spans = list(zip(bounds[:-1], bounds[1:]))
     base_id = rank * n_total
     host_in = empty_like_soa(n_total, device="cpu", pinned=True)
     for c, (lo, hi) in enumerate(spans):
-        mu = gen.muons_config4_chunk(c, hi - lo)
+        mu = gen.muons_shield1e8_chunk(c, hi - lo)
         for k in host_in:
             host_in[k][lo:hi].copy_(torch.from_numpy(np.ascontiguousarray(mu[k], dtype=mt._binding.SOA_DTYPES[k])))
     host_out = empty_like_soa(n_total, device="cpu", pinned=True)
@@ -518,7 +518,7 @@ def time_c4_form(mt, dev, n_total=None, chunk=None, rank=0, cpu_sample=2000):
         o = oracle.transport(ow, mu, *args, id_offset=base_id, n_threads=os.cpu_count() or 1)
         dt = time.perf_counter() - t0
         out["cpu_oracle"] = {"value": float(o["steps"].sum()) / dt, "unit": UNIT, "cores": os.cpu_count(),
-                             "sample": f"first {cpu_sample} muons of config4"}
+                             "sample": f"first {cpu_sample} muons of shield1e8"}
     out["value"] = out["plain_value"]
     out["unit"] = UNIT
     return out
@@ -529,7 +529,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from workloads import gen
-    wl = gen.workload("config1")
+    wl = gen.workload("shield1e6")
     threads = os.cpu_count() or 1
     n_sample = args.cpu_sample
     for _ in range(args.warmup):
@@ -546,7 +546,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_muons": n_sample, "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"first {n_sample} muons of config1 per step (FP64 C oracle, "
+                         "sample": f"first {n_sample} muons of shield1e6 per step (FP64 C oracle, "
                                    f"{threads} POSIX threads)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -570,11 +570,11 @@ def run_mine(args):
     from paper_2512_10520_gb300.api import empty_like_soa
     from workloads import gen
 
-    if args.c4_only:
+    if args.shield1e8_only:
         with ClockSampler(local) as clk:
-            res = time_c4_form(mt, dev, n_total=args.c4_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
+            res = time_shield1e8_form(mt, dev, n_total=args.shield1e8_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
         if rank == 0:
-            print(json.dumps({"form": "c4", "clocks": clk.summary(), **res}))
+            print(json.dumps({"form": "shield1e8", "clocks": clk.summary(), **res}))
         return 0
     if args.only == "polyhedra":
         with ClockSampler(local) as clk:
@@ -590,7 +590,7 @@ def run_mine(args):
         if rank == 0:
             print(json.dumps({"form": "batched", "clocks": clk.summary(), **res}))
         return 0
-    wl = gen.workload("config1", n=args.muons)
+    wl = gen.workload("shield1e6", n=args.muons)
     n = wl.n
     if args.adjoint_only:
         world = mt.World.from_workload(wl)
@@ -690,7 +690,7 @@ def run_mine(args):
         t_all = (adj["t_forward_ckpt_ms"] + adj["t_loss_ms"] + adj["t_adjoint_ms"]) / 1e3
         forms["fwd_adjoint"] = dict(
             value=_barrier_sum(adj["muon_steps"], ws, dev) / _barrier_max(t_all, ws, dev), unit=UNIT,
-            workload="config3: config1 geometry and map, 18 field scales alpha = 1, 1e6 muons, 1500 steps, "
+            workload="diff1e6: shield1e6 geometry and map, 18 field scales alpha = 1, 1e6 muons, 1500 steps, "
                      "checkpoints every 32 steps, acceptance loss at z = 30 m",
             adjoint_over_forward=adj["t_adjoint_ms"] / (kernel_s * 1e3),
             total_over_forward=t_all / kernel_s, **adj)
@@ -703,23 +703,23 @@ def run_mine(args):
         forms["plain"] = dict(value=value, unit=UNIT, kernel_ms=kernel_s * 1e3)
         al = time_alias_form(mt, wl, init, work, stream, id_offset)
         al["value"] = _barrier_sum(al["muon_steps"], ws, dev) / _barrier_max(al["kernel_ms"] / 1e3, ws, dev)
-        al["workload"] = "config1 with the alias sampler (8 B column per draw) instead of the inverse CDF"
+        al["workload"] = "shield1e6 with the alias sampler (8 B column per draw) instead of the inverse CDF"
         al["vs_inverse_cdf"] = al["value"] / value
         forms["alias"] = al
         ph = time_polyhedra_form(mt, dev, stream, n=args.muons, id_offset=id_offset)
         ph["value"] = _barrier_sum(ph["muon_steps"], ws, dev) / _barrier_max(ph["kernel_ms"] / 1e3, ws, dev)
-        ph["workload"] = ("config1p: config1 with the six magnets as tapered convex solids (trapezoid sections "
+        ph["workload"] = ("tapered1e6: shield1e6 with the six magnets as tapered convex solids (trapezoid sections "
                           "narrowing along z), spatial-hash pruning, 200x200x600 map")
         ph["vs_boxes"] = ph["value"] / value
         forms["polyhedra"] = ph
         forms["offline"] = time_offline_form(mt, stream, cpu=not args.no_cpu)
         for name, kw, desc in (("nearest_field", dict(field="nearest"),
-                                "config1 with the map read at the nearest node (the paper's lookup, 1 gather)"),
+                                "shield1e6 with the map read at the nearest node (the paper's lookup, 1 gather)"),
                                ("log_axes", dict(axes="log"),
-                                "config1 with histograms on log-scaled (-dPz/P, dPt/P) axes, additive dp"),
+                                "shield1e6 with histograms on log-scaled (-dPz/P, dPt/P) axes, additive dp"),
                                ("per_stage_field", dict(),
-                                "config1 with the map read at every RK4 stage (4 trilinear lookups per step)")):
-            wv = gen.workload("config1", n=args.muons, **kw)
+                                "shield1e6 with the map read at every RK4 stage (4 trilinear lookups per step)")):
+            wv = gen.workload("shield1e6", n=args.muons, **kw)
             if name == "per_stage_field":
                 wv.field = dict(wv.field, per_stage=True)
             tv, sv = _time_world(mt, wv, wv.geometry, dev, stream, 3, id_offset)
@@ -728,20 +728,20 @@ def run_mine(args):
         bt = time_batched_form(mt, stream, dev, n_inst=args.batch_instances, rank=rank,
                                separate=not args.no_separate)
         bt["value"] = _barrier_sum(bt["muon_steps"], ws, dev) / _barrier_max(bt["batched_ms"] / 1e3, ws, dev)
-        bt["workload"] = (f"config2: {bt['instances']} worlds (64x64x512 voxels, 100x100x300 map each), shared "
+        bt["workload"] = (f"worlds256: {bt['instances']} worlds (64x64x512 voxels, 100x100x300 map each), shared "
                           f"iron/air/concrete tables, {bt['muons']} muons, log-uniform sizes, 2000 steps")
         forms["batched"] = bt
-        if not args.no_c4:
-            c4 = time_c4_form(mt, dev, n_total=args.c4_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
+        if not args.no_shield1e8:
+            big = time_shield1e8_form(mt, dev, n_total=args.shield1e8_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
             peaks_, _ = _peaks()
             for key in ("plain", "batched", "streamed"):
-                c4[key + "_value"] = (_barrier_sum(c4["muon_steps"], ws, dev)
-                                      / _barrier_max(c4[key + "_ms"] / 1e3, ws, dev))
-            c4["value"] = c4["plain_value"]
-            c4["roofline_frac_plain"] = BYTES_PER_STEP * c4["plain_value"] / ws / 1e9 / peaks_["hbm_gbs"]
-            c4["workload"] = ("config4: 1e8 muons of config1's spectrum in 16M chunks, config1 geometry, "
+                big[key + "_value"] = (_barrier_sum(big["muon_steps"], ws, dev)
+                                      / _barrier_max(big[key + "_ms"] / 1e3, ws, dev))
+            big["value"] = big["plain_value"]
+            big["roofline_frac_plain"] = BYTES_PER_STEP * big["plain_value"] / ws / 1e9 / peaks_["hbm_gbs"]
+            big["workload"] = ("shield1e8: 1e8 muons of shield1e6's spectrum in 16M chunks, shield1e6 geometry, "
                               "400x400x1200 map, 4 materials x 128 bins x 256x128 tables")
-            forms["c4"] = c4
+            forms["shield1e8"] = big
     peaks, peak_kind = _peaks()
     achieved_gbs = BYTES_PER_STEP * steps_per_batch / kernel_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -757,7 +757,7 @@ def run_mine(args):
         threads = os.cpu_count() or 1
         s, dt = cpu_oracle_run(wl, args.cpu_sample, threads)
         cpu = {"value": s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {args.cpu_sample} muons of config1 (FP64 C oracle, {threads} POSIX threads)"}
+               "sample": f"first {args.cpu_sample} muons of shield1e6 (FP64 C oracle, {threads} POSIX threads)"}
     clocks = clk.summary()
     world.close()
     if rank == 0:
@@ -800,9 +800,9 @@ def main(argv=None):
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--batch-instances", type=int, default=256, help="worlds in the batched form")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched form (one JSON line)")
-    ap.add_argument("--no-c4", action="store_true", help="skip the config4 (1e8 muons) form")
-    ap.add_argument("--c4-only", action="store_true", help="run only the config4 form (one JSON line)")
-    ap.add_argument("--c4-muons", type=int, default=None, help="muons of the config4 form (default 1e8)")
+    ap.add_argument("--no-shield1e8", action="store_true", help="skip the shield1e8 (1e8 muons) form")
+    ap.add_argument("--shield1e8-only", action="store_true", help="run only the shield1e8 form (one JSON line)")
+    ap.add_argument("--shield1e8-muons", type=int, default=None, help="muons of the shield1e8 form (default 1e8)")
     ap.add_argument("--batch-block", type=int, default=0, help="batched form: block size (with --batch-spp: no autotune)")
     ap.add_argument("--batch-spp", type=int, default=0, help="batched form: steps per pass")
     ap.add_argument("--adjoint-only", action="store_true", help="run only the fwd+adjoint forms (one JSON line)")

@@ -34,7 +34,7 @@ namespace mt {
 constexpr int kTapeMax = 64;
 
 // Resident blocks per SM of the reverse pass (3 blocks of 256 = 85 registers;
-// measured on config3: 34.5 ms against 38.2 ms with 4 blocks, which spill).
+// measured on diff1e6: 34.5 ms against 38.2 ms with 4 blocks, which spill).
 #ifndef MT_ADJ_MIN_BLOCKS
 #define MT_ADJ_MIN_BLOCKS 3
 #endif
@@ -68,7 +68,7 @@ struct TapeLayout {
 };
 
 // Whether the tape holds the field at each step (16 more bytes per step) or
-// the reverse sweep evaluates it again at the recorded r (measured on config3:
+// the reverse sweep evaluates it again at the recorded r (measured on diff1e6:
 // recording is faster, 38 against 54 ms for the backward).
 #ifndef MT_TAPE_RECORD_B
 #define MT_TAPE_RECORD_B 1
@@ -434,7 +434,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
 // Resident blocks per SM of the recorded pass: 4 (64 registers), for the
-// recorder's state kept across the step (measured on config3: full-tape
+// recorder's state kept across the step (measured on diff1e6: full-tape
 // forward 33.0 ms against 35.4 ms at the plain pass's 48 registers, which
 // spill; checkpoint backward 64.1 against 66.2 ms).  0: the plain pass's.
 #ifndef MT_TAPE_MIN_BLOCKS

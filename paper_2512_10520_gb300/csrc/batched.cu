@@ -22,7 +22,7 @@
 #include "compact.cuh"
 
 // Resident threads per SM the compiler must allow for in batch_pass (register
-// budget: 1024 threads = 64 registers; measured on config2, 256 instances with
+// budget: 1024 threads = 64 registers; measured on worlds256, 256 instances with
 // warp chunks: 730 ms against 752 ms at 768 threads = 80 registers).  The
 // variants that spill at 64 registers (per-stage field reads; polyhedra) keep
 // 768.

@@ -7,12 +7,12 @@
 
 // Resident blocks per SM the compiler must allow for (register budget of the
 // pass kernels): 5 blocks of 256 threads = 48 registers per thread (measured
-// fastest on config1: 40 registers spill and run 8 % slower).
+// fastest on shield1e6: 40 registers spill and run 5 % slower).
 #ifndef MT_PASS_MIN_BLOCKS
 #define MT_PASS_MIN_BLOCKS 5
 #endif
 // The same for the polyhedron geometry, whose containment test needs more
-// registers (measured on config1p: 4 blocks = 64 registers, 33.2 ms; 5 blocks
+// registers (measured on tapered1e6: 4 blocks = 64 registers, 33.2 ms; 5 blocks
 // spill, 36.8 ms).
 #ifndef MT_PASS_MIN_BLOCKS_POLY
 #define MT_PASS_MIN_BLOCKS_POLY 4

@@ -206,7 +206,7 @@ __device__ __forceinline__ float3 field_map_nearest(const WorldParams &w, const 
 // Eq. 2), in FP64 from the solid's original double-precision data: the
 // definition's arithmetic, used when the FP32 filter below cannot decide.
 // z0 <= z < z1 has been decided already.
-// Inlined (measured on config1p at 64 registers: 33.2 ms against 36.0 ms for a
+// Inlined (measured on tapered1e6 at 64 registers: 33.2 ms against 36.0 ms for a
 // call, whose register saves cost more than the rarely run code itself).
 #ifndef MT_SOLID_FP64_INLINE
 #define MT_SOLID_FP64_INLINE 1
@@ -512,7 +512,7 @@ __device__ __forceinline__ void load_pair(const float4 *p, float4 &a, float4 &b)
 }
 
 // Trilinear value as the weighted sum of the eight corners (1: measured 1.5 %
-// faster on config1 than nested lerps, 0).
+// faster on shield1e6 than nested lerps, 0).
 #ifndef MT_TRILINEAR_WEIGHTS
 #define MT_TRILINEAR_WEIGHTS 1
 #endif

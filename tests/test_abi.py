@@ -33,7 +33,7 @@ def _descs(weights=None):
     h = gen.histogram_set(["iron"], n_pbin=2, nf=4, ntheta=4, n_samples=1000, cache=False)
     if weights is not None:
         h["weights"] = weights
-    geo = gen.geometry_config0()
+    geo = gen.geometry_block1e4()
     geo["boxes"][0]["material"] = 1
     geo["world_material"] = 0
     return geo, dict(kind="box"), h
@@ -105,7 +105,7 @@ def test_batch_host_errors(lib):
 def test_alias_sampler_needs_power_of_two_cells(lib):
     from workloads import gen
     h = gen.histogram_set(["iron"], n_pbin=2, nf=6, ntheta=4, n_samples=1000, cache=False)
-    geo = gen.geometry_config0()
+    geo = gen.geometry_block1e4()
     geo["boxes"][0]["material"] = 1
     geo["world_material"] = 0
     with pytest.raises(mt.MtError) as e:

@@ -50,7 +50,7 @@ def _gpu_grad(wl, alpha, K=32, want_initial=False):
 
 
 def test_checkpointing_forward_equals_transport():
-    wl = gen.workload("config1", n=5000)
+    wl = gen.workload("shield1e6", n=5000)
     alpha = _alpha()
     ref = gpu_transport(wl, alpha=alpha)
     _, _, fin, _ = _gpu_grad(wl, alpha)
@@ -59,7 +59,7 @@ def test_checkpointing_forward_equals_transport():
 
 
 def test_loss_kernel_matches_oracle_loss():
-    wl = gen.workload("config1", n=20000)
+    wl = gen.workload("shield1e6", n=20000)
     alpha = _alpha()
     L, _, fin, _ = _gpu_grad(wl, alpha)
     Lo, go = oracle.acceptance_loss({k: np.asarray(v, np.float64) for k, v in fin.items()})
@@ -78,7 +78,7 @@ def test_loss_kernel_matches_oracle_loss():
 
 @pytest.mark.parametrize("field", ["map", "box"])
 def test_adjoint_matches_fp64_oracle_adjoint(field):
-    wl = gen.workload("config1", n=10000, field="box" if field == "box" else None)
+    wl = gen.workload("shield1e6", n=10000, field="box" if field == "box" else None)
     alpha = _alpha()
     _, g_gpu, _, _ = _gpu_grad(wl, alpha)
     world = oracle.world_of(wl, alpha.astype(np.float64))
@@ -115,7 +115,7 @@ def test_adjoint_against_central_differences():
     is run with dL/dfinal of the other muons set to zero."""
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1", n=10000)
+    wl = gen.workload("shield1e6", n=10000)
     alpha = _alpha().astype(np.float32)
     h = 2e-4
     n = wl.n
@@ -164,7 +164,7 @@ def test_adjoint_against_central_differences():
 def test_autograd_function_and_one_call_adjoint():
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1", n=4000)
+    wl = gen.workload("shield1e6", n=4000)
     alpha = _alpha()
     _, g_ref, _, _ = _gpu_grad(wl, alpha)
     with mt.World.from_workload(wl) as world:
@@ -192,7 +192,7 @@ def test_initial_state_gradient_matches_finite_differences():
     """dL/d(initial px) of single muons against central differences on the GPU."""
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1", n=4000)
+    wl = gen.workload("shield1e6", n=4000)
     alpha = _alpha()
     _, _, fin, gi = _gpu_grad(wl, alpha, want_initial=True)
     # muons with a sizeable gradient, i.e. ending near the acceptance edge
@@ -241,7 +241,7 @@ def test_tape_form_equals_checkpoint_form(field, K):
     """The full-tape forward gives the plain transport's results bit for bit, and
     its backward the checkpoint form's gradients (the same recorded quantities
     and reverse arithmetic; only the order of the dL/dalpha atomics differs)."""
-    wl = gen.workload("config1", n=6000, field="box" if field == "box" else None)
+    wl = gen.workload("shield1e6", n=6000, field="box" if field == "box" else None)
     alpha = _alpha()
     ref = gpu_transport(wl, alpha=alpha)
     _, g_ck, _, gi_ck = _gpu_grad(wl, alpha, K=K, want_initial=True)
@@ -253,7 +253,7 @@ def test_tape_form_equals_checkpoint_form(field, K):
 
 
 def test_tape_adjoint_matches_fp64_oracle_adjoint():
-    wl = gen.workload("config1", n=10000)
+    wl = gen.workload("shield1e6", n=10000)
     alpha = _alpha()
     _, g_gpu, _, _ = _gpu_grad_tape(wl, alpha)
     world = oracle.world_of(wl, alpha.astype(np.float64))
@@ -267,7 +267,7 @@ def test_tape_adjoint_matches_fp64_oracle_adjoint():
 def test_tape_buffer_checks_and_autograd_mode():
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1", n=3000)
+    wl = gen.workload("shield1e6", n=3000)
     alpha = _alpha()
     with mt.World.from_workload(wl) as world:
         dev = mt.muons_to_device(wl.muons)

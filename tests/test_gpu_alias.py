@@ -29,16 +29,16 @@ def _alias(wl):
     return wl
 
 
-def test_alias_config0_full_parity():
-    wl = _alias(gen.workload("config0"))
+def test_alias_block1e4_full_parity():
+    wl = _alias(gen.workload("block1e4"))
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
     ok, err = compare(gpu, ora)
     assert ok.mean() >= PASS_FRAC, describe(ok, err)
 
 
-def test_alias_config1_parity_and_distribution():
-    wl = _alias(gen.workload("config1", n=20000))
+def test_alias_shield1e6_parity_and_distribution():
+    wl = _alias(gen.workload("shield1e6", n=20000))
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
     ok, err = compare(gpu, ora)
@@ -46,7 +46,7 @@ def test_alias_config1_parity_and_distribution():
     assert np.median(err["pos_err"]) < 1e-5
     for k in ("x", "y"):
         assert stats.ks_2samp(gpu[k], ora[k]).pvalue > 0.01
-    icdf = gpu_transport(gen.workload("config1", n=20000))
+    icdf = gpu_transport(gen.workload("shield1e6", n=20000))
     P = lambda f: np.sqrt(np.asarray(f["px"], np.float64) ** 2 + f["py"] ** 2 + f["pz"] ** 2)
     assert not np.array_equal(P(gpu), P(icdf))
     assert stats.ks_2samp(P(gpu), P(icdf)).pvalue > 0.01
@@ -54,7 +54,7 @@ def test_alias_config1_parity_and_distribution():
 
 def test_alias_launch_shapes_and_batch_are_bit_identical():
     import paper_2512_10520_gb300 as mt
-    wl = _alias(gen.workload("config1", n=3000))
+    wl = _alias(gen.workload("shield1e6", n=3000))
     outs = [gpu_transport(wl)]
     with mt.World.from_workload(wl) as world:
         for mode in (mt.MT_LAUNCH_STATIC, mt.MT_LAUNCH_PERSISTENT):

@@ -161,7 +161,7 @@ def test_unset_instance_and_mixed_kinds_are_rejected(hist, instances):
         with pytest.raises(mt.MtError) as e:
             b.transport(_dev(instances[:2]), gen.BATCH_STEP_LEN, 10, 1)
         assert "no world" in str(e.value)
-        boxes = gen.geometry_config1()
+        boxes = gen.geometry_shield1e6()
         with pytest.raises(mt.MtError):
             b.set_instance(1, boxes, instances[1]["field"])
 

@@ -24,7 +24,7 @@ def _lib():
     mt.load_library()
 
 
-def test_config2_full_batch_sampled_parity():
+def test_worlds256_full_batch_sampled_parity():
     import torch
     import paper_2512_10520_gb300 as mt
     hist = gen.batched_hist()
@@ -58,10 +58,10 @@ def test_config2_full_batch_sampled_parity():
         assert allok.mean() >= 0.995, allok.mean()
 
 
-def test_config3_full_size_adjoint_sampled():
+def test_diff1e6_full_size_adjoint_sampled():
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1")
+    wl = gen.workload("shield1e6")
     n = wl.n
     assert n == 1_000_000
     rng = np.random.default_rng(5)
@@ -104,17 +104,17 @@ def test_config3_full_size_adjoint_sampled():
         assert rel <= 1e-3, (rel, gg.ravel().tolist(), g_ora.ravel().tolist())
 
 
-def test_config4_chunk_sampled_parity():
+def test_shield1e8_chunk_sampled_parity():
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config4", n=1)
-    mu = gen.muons_config4_chunk(0, gen.C4_CHUNK)
+    wl = gen.workload("shield1e8", n=1)
+    mu = gen.muons_shield1e8_chunk(0, gen.SHIELD1E8_CHUNK)
     with mt.World.from_workload(wl) as world:
         dev = mt.muons_to_device(mu)
         world.transport(dev, wl.step_len, wl.max_steps, wl.seed, id_offset=0)
         torch.cuda.synchronize()
         rng = np.random.default_rng(2)
-        idx = np.sort(rng.choice(gen.C4_CHUNK, size=500, replace=False))
+        idx = np.sort(rng.choice(gen.SHIELD1E8_CHUNK, size=500, replace=False))
         got = {k: v.cpu().numpy()[idx] for k, v in dev.items()}
     ora = oracle.transport(oracle.world_of(wl), mu, wl.step_len, wl.max_steps, wl.seed, index=idx)
     ok, err = compare(got, ora)

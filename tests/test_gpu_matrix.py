@@ -58,10 +58,10 @@ CASES = [
 @pytest.mark.parametrize("geom,field,sampler,axes,edges", CASES)
 def test_combination(geom, field, sampler, axes, edges):
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1p" if geom == "solids" else "config1", n=3000, hist_samples=50000,
+    wl = gen.workload("tapered1e6" if geom == "solids" else "shield1e6", n=3000, hist_samples=50000,
                       field={"box": "box", "nearest": "nearest"}.get(field), axes=axes)
     if geom == "voxels":
-        wl.geometry = _voxelise(gen.geometry_config1())
+        wl.geometry = _voxelise(gen.geometry_shield1e6())
     if field == "none":
         wl.field = dict(kind="none")
     if field == "per_stage":

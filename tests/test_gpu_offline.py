@@ -56,7 +56,7 @@ def test_bounded_variation_bins_through_the_transport():
     assert 20 < len(edges) - 1 <= 256, len(edges)
     np.testing.assert_array_equal(edges, oracle.bv_edges(probes, phi, 0.08))
     hist = mt.build_histogram_set(["iron", "air", "concrete"], edges=edges, n_samples=100000)
-    wl = gen.workload("config1", n=20000)
+    wl = gen.workload("shield1e6", n=20000)
     wl.hist = hist
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
@@ -65,7 +65,7 @@ def test_bounded_variation_bins_through_the_transport():
 
 
 def test_explicit_log_edges_equal_the_implicit_log_bins():
-    wl = gen.workload("config1", n=5000)
+    wl = gen.workload("shield1e6", n=5000)
     ref = gpu_transport(wl)
     wl.hist = dict(wl.hist, p_edges=gen.pbin_edges(wl.hist["p_lo"], wl.hist["p_hi"], wl.hist["n_pbin"]))
     out = gpu_transport(wl)

@@ -25,7 +25,7 @@ def _lib():
 
 @pytest.mark.parametrize("field", ["map", "box"])
 def test_tapered_magnets_parity(field):
-    wl = gen.workload("config1p", n=20000, field="box" if field == "box" else None)
+    wl = gen.workload("tapered1e6", n=20000, field="box" if field == "box" else None)
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
     ok, err = compare(gpu, ora)
@@ -44,7 +44,7 @@ def _as_solids(geo):
 
 @pytest.mark.parametrize("field", ["map", "box"])
 def test_rectangular_solids_equal_boxes(field):
-    wl = gen.workload("config1", n=5000, field="box" if field == "box" else None)
+    wl = gen.workload("shield1e6", n=5000, field="box" if field == "box" else None)
     ref = gpu_transport(wl)
     wl.geometry = _as_solids(wl.geometry)
     out = gpu_transport(wl)
@@ -54,7 +54,7 @@ def test_rectangular_solids_equal_boxes(field):
 
 def test_launch_shapes_and_batch_are_bit_identical():
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1p", n=3000)
+    wl = gen.workload("tapered1e6", n=3000)
     outs = [gpu_transport(wl)]
     with mt.World.from_workload(wl) as world:
         for mode in (mt.MT_LAUNCH_STATIC, mt.MT_LAUNCH_PERSISTENT):
@@ -78,7 +78,7 @@ def test_launch_shapes_and_batch_are_bit_identical():
 def test_adjoint_through_solids_matches_fp64_oracle_adjoint():
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1p", n=6000, field="box")
+    wl = gen.workload("tapered1e6", n=6000, field="box")
     rng = np.random.default_rng(5)
     alpha = (1.0 + 0.2 * rng.standard_normal((6, 3))).astype(np.float32)
     with mt.World.from_workload(wl) as world:

@@ -28,22 +28,22 @@ def _lib():
 
 @pytest.fixture(scope="module")
 def wl0():
-    return gen.workload("config0")
+    return gen.workload("block1e4")
 
 
 @pytest.fixture(scope="module")
 def wl1_small():
-    return gen.workload("config1", n=20000)
+    return gen.workload("shield1e6", n=20000)
 
 
-def test_config0_full_parity(wl0):
+def test_block1e4_full_parity(wl0):
     ora = oracle.transport(oracle.world_of(wl0), wl0.muons, wl0.step_len, wl0.max_steps, wl0.seed)
     gpu = gpu_transport(wl0)
     ok, err = compare(gpu, ora)
     assert ok.mean() >= PASS_FRAC, describe(ok, err)
 
 
-def test_config1_subset_parity_and_ks(wl1_small):
+def test_shield1e6_subset_parity_and_ks(wl1_small):
     ora = oracle.transport(oracle.world_of(wl1_small), wl1_small.muons, wl1_small.step_len,
                            wl1_small.max_steps, wl1_small.seed)
     gpu = gpu_transport(wl1_small)
@@ -56,10 +56,10 @@ def test_config1_subset_parity_and_ks(wl1_small):
     assert stats.ks_2samp(pg, po).pvalue > 0.01
 
 
-def test_config1_full_size_sampled_parity():
+def test_shield1e6_full_size_sampled_parity():
     """The full 1e6-muon workload in the benchmark's launch configuration; the
     oracle recomputes a spread sample of muon ids one by one."""
-    wl = gen.workload("config1")
+    wl = gen.workload("shield1e6")
     gpu = gpu_transport(wl)
     idx = np.unique(np.linspace(0, wl.n - 1, 2000).astype(np.int64))
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed, index=idx)
@@ -140,7 +140,7 @@ def _vacuum_workload(n, field, boxes=(), max_steps=400, z_max=1e5, xy=1e5, world
     h = gen.histogram_set(["iron"], n_pbin=8, nf=16, ntheta=8, n_samples=20000, cache=False)
     geo = dict(kind="boxes", boxes=list(boxes), world_material=world_mat, x_max=xy, y_max=xy, z_max=z_max,
                p_min=0.5)
-    mu = gen.muons_config0(n, seed=seed)
+    mu = gen.muons_block(n, seed=seed)
     return gen.Workload("vac", geo, field, h, mu, 0.02, max_steps, 11)
 
 
@@ -225,9 +225,9 @@ def test_voxel_geometry_with_map_parity():
     vox[45:50, 6:10, 6:10] = 0                          # a vacuum pocket
     geo = dict(kind="voxels", voxels=vox, origin=[-0.8, -0.8, 0.0], spacing=[0.1, 0.1, 0.05],
                world_material=2, x_max=1.0, y_max=1.0, z_max=3.3, p_min=0.5)
-    fld = gen.field_map_config1(nx=20, ny=20, nz=40, z_lo=-0.1, z_hi=3.3, half_xy=1.0,
+    fld = gen.field_map_shield1e6(nx=20, ny=20, nz=40, z_lo=-0.1, z_hi=3.3, half_xy=1.0,
                                 magnet_z0=[0.4], magnet_B=[1.5])
-    mu = gen.muons_config0(3000, seed=21)
+    mu = gen.muons_block(3000, seed=21)
     wl = gen.Workload("vox", geo, fld, h, mu, 0.02, 200, 5)
     ora = oracle.transport(oracle.world_of(wl), mu, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
@@ -239,8 +239,8 @@ def test_field_scaled_transport_parity():
     """Per-block field scales up to 1.4x (fields up to 2.4 T) make more low-momentum
     tracks that skim a magnet edge chaotic, so this test of the scaling itself asks
     for 99.8 % agreement plus tight median / 90th-percentile errors; the 99.9 % bar
-    is held by the unscaled config1 parity test."""
-    wl = gen.workload("config1", n=20000)
+    is held by the unscaled shield1e6 parity test."""
+    wl = gen.workload("shield1e6", n=20000)
     alpha = np.linspace(0.6, 1.4, 18).reshape(6, 3)
     ora = oracle.transport(oracle.world_of(wl, alpha), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl, alpha=alpha)

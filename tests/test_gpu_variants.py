@@ -24,7 +24,7 @@ def _lib():
 
 
 def test_log_axes_parity():
-    wl = gen.workload("config1", n=20000, axes="log")
+    wl = gen.workload("shield1e6", n=20000, axes="log")
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
     ok, err = compare(gpu, ora)
@@ -38,7 +38,7 @@ def test_nearest_field_parity():
     faces on hi + lo pairs), so only trajectories that already differ by
     rounding can straddle a face there.  Same per-muon bar as the trilinear map
     (measured: 99.96 %), plus the distributions."""
-    wl = gen.workload("config1", n=20000, field="nearest")
+    wl = gen.workload("shield1e6", n=20000, field="nearest")
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
     ok, err = compare(gpu, ora)
@@ -53,7 +53,7 @@ def test_nearest_field_parity():
 @pytest.mark.parametrize("variant", ["log_axes", "nearest_field"])
 def test_variant_launch_shapes_are_bit_identical(variant):
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("config1", n=3000, field="nearest" if variant == "nearest_field" else None,
+    wl = gen.workload("shield1e6", n=3000, field="nearest" if variant == "nearest_field" else None,
                       axes="log" if variant == "log_axes" else "linear")
     outs = [gpu_transport(wl)]
     with mt.World.from_workload(wl) as world:
@@ -71,9 +71,9 @@ def test_variant_adjoint_matches_fp64_oracle_adjoint(variant):
     import torch
     import paper_2512_10520_gb300 as mt
     if variant == "log_axes":
-        wl = gen.workload("config1", n=8000, field="box", axes="log")
+        wl = gen.workload("shield1e6", n=8000, field="box", axes="log")
     else:
-        wl = gen.workload("config1", n=8000, field="nearest")
+        wl = gen.workload("shield1e6", n=8000, field="nearest")
     rng = np.random.default_rng(5)
     alpha = (1.0 + 0.2 * rng.standard_normal((6, 3))).astype(np.float32)
     with mt.World.from_workload(wl) as world:
@@ -102,7 +102,7 @@ def _per_stage(wl):
 
 
 def test_per_stage_field_parity():
-    wl = _per_stage(gen.workload("config1", n=20000))
+    wl = _per_stage(gen.workload("shield1e6", n=20000))
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
     ok, err = compare(gpu, ora)
@@ -115,7 +115,7 @@ def test_per_stage_in_a_uniform_map_equals_the_held_field():
     is the held-field step up to the rounding of the interpolation weights
     (the trilinear weighted sum reproduces a constant to a few ulp): identical
     step counts and statuses, states to 1e-6 relative."""
-    wl = gen.workload("config1", n=3000)
+    wl = gen.workload("shield1e6", n=3000)
     B = np.zeros((3, 3, 3, 3), np.float32)
     B[..., 1] = 1.5
     # one uniform map cell around the whole world, so no stage reads past its edge
@@ -131,7 +131,7 @@ def test_per_stage_in_a_uniform_map_equals_the_held_field():
 def test_per_stage_launch_shapes_and_differentiable_form():
     import torch
     import paper_2512_10520_gb300 as mt
-    wl = _per_stage(gen.workload("config1", n=3000))
+    wl = _per_stage(gen.workload("shield1e6", n=3000))
     outs = [gpu_transport(wl)]
     with mt.World.from_workload(wl) as world:
         for mode in (mt.MT_LAUNCH_STATIC, mt.MT_LAUNCH_PERSISTENT):

@@ -35,7 +35,7 @@ def _rank_main(rank, ws, port, n_total, out_dir):
         assert bench._barrier_max(float(rank + 1), ws) == float(ws)
         assert bench._barrier_sum(float(rank + 1), ws) == float(ws * (ws + 1) // 2)
         # shard: rank r takes ids [r*m, (r+1)*m)
-        wl = gen.workload("config0", n=n_total, hist_samples=20000)
+        wl = gen.workload("block1e4", n=n_total, hist_samples=20000)
         m = n_total // ws
         sub = {k: v[rank * m:(rank + 1) * m] for k, v in wl.muons.items()}
         out = oracle.transport(oracle.world_of(wl), sub, wl.step_len, wl.max_steps, wl.seed, id_offset=rank * m,
@@ -55,7 +55,7 @@ def test_two_gloo_ranks_shard_by_muon_id(tmp_path):
     ws, n_total = 2, 256
     tmp.start_processes(_rank_main, args=(ws, _free_port(), n_total, str(tmp_path)), nprocs=ws, join=True,
                         start_method="spawn")
-    wl = gen.workload("config0", n=n_total, hist_samples=20000)
+    wl = gen.workload("block1e4", n=n_total, hist_samples=20000)
     ref = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed, n_threads=2)
     parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(ws)]
     for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):

@@ -12,9 +12,9 @@ from workloads import gen
 
 
 def _world_and_muons(n, field_kind, seed=5):
-    wl = gen.workload("config1", n=n, hist_samples=20000, field="box" if field_kind == "box" else None)
+    wl = gen.workload("shield1e6", n=n, hist_samples=20000, field="box" if field_kind == "box" else None)
     if field_kind == "smallmap":
-        wl.field = gen.field_map_config1(nx=60, ny=60, nz=180)
+        wl.field = gen.field_map_shield1e6(nx=60, ny=60, nz=180)
     rng = np.random.default_rng(seed)
     alpha = 1.0 + 0.2 * rng.standard_normal((6, 3))
     return wl, alpha

@@ -145,7 +145,7 @@ def test_alias_chi_square_through_the_step_draw():
 
 
 def test_alias_transport_matches_inverse_cdf_in_distribution():
-    wl = gen.workload("config0", n=3000, hist_samples=20000)
+    wl = gen.workload("block1e4", n=3000, hist_samples=20000)
     h_alias = dict(wl.hist, sampler="alias")
     a = oracle.transport(oracle.OracleWorld(wl.geometry, wl.field, h_alias), wl.muons, wl.step_len, wl.max_steps,
                          wl.seed)

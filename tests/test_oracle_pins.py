@@ -179,7 +179,7 @@ def _first_box_numpy(geo, pts):
 
 
 def test_material_boxes_lattice():
-    geo = gen.geometry_config1()
+    geo = gen.geometry_shield1e6()
     # overlapping extra box after the others: list order decides
     geo["boxes"].append(dict(lo=[-1.0, -1.0, 3.0], hi=[1.0, 1.0, 5.0], material=3, block_id=-1, B=[0, 0, 0]))
     world = oracle.OracleWorld(geo, dict(kind="none"), tiny_hist())
@@ -253,7 +253,7 @@ def test_field_nodes_random_map():
 
 
 def test_box_field_and_block_scale():
-    geo = gen.geometry_config1()
+    geo = gen.geometry_shield1e6()
     alpha = np.arange(1, 19, dtype=np.float64).reshape(6, 3) / 10.0
     world = oracle.OracleWorld(geo, dict(kind="box"), tiny_hist(), alpha)
     for k in range(6):
@@ -415,7 +415,7 @@ def test_stopping_in_dense_loss():
 
 
 def test_resume_subset_and_threads_are_invariant():
-    wl = gen.workload("config0", n=300, hist_samples=20000)
+    wl = gen.workload("block1e4", n=300, hist_samples=20000)
     world = oracle.world_of(wl)
     full = oracle.transport(world, wl.muons, wl.step_len, wl.max_steps, wl.seed, n_threads=4)
     one = oracle.transport(world, wl.muons, wl.step_len, wl.max_steps, wl.seed, n_threads=1)

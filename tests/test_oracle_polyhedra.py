@@ -99,9 +99,9 @@ def test_first_containing_solid_wins_and_edges_are_inside():
 
 
 def test_tapered_geometry_transport_runs_and_differs_from_boxes():
-    wl = gen.workload("config1p", n=400, hist_samples=20000)
+    wl = gen.workload("tapered1e6", n=400, hist_samples=20000)
     out = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
-    wb = gen.workload("config1", n=400, hist_samples=20000)
+    wb = gen.workload("shield1e6", n=400, hist_samples=20000)
     ob = oracle.transport(oracle.world_of(wb), wb.muons, wb.step_len, wb.max_steps, wb.seed)
     assert (out["steps"] > 0).all()
     assert not np.array_equal(out["x"], ob["x"])

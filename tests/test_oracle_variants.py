@@ -117,10 +117,10 @@ def test_log_axes_step_applies_the_additive_dp():
 @pytest.mark.parametrize("variant", ["log_axes", "nearest_field"])
 def test_adjoint_of_variants_matches_dual_numbers(variant):
     if variant == "log_axes":
-        wl = gen.workload("config1", n=80, hist_samples=20000, field="box", axes="log")
+        wl = gen.workload("shield1e6", n=80, hist_samples=20000, field="box", axes="log")
     else:
-        wl = gen.workload("config1", n=80, hist_samples=20000)
-        wl.field = dict(gen.field_map_config1(nx=60, ny=60, nz=180), kind="map_nearest")
+        wl = gen.workload("shield1e6", n=80, hist_samples=20000)
+        wl.field = dict(gen.field_map_shield1e6(nx=60, ny=60, nz=180), kind="map_nearest")
     rng = np.random.default_rng(5)
     alpha = 1.0 + 0.2 * rng.standard_normal((6, 3))
     world = oracle.world_of(wl, alpha)

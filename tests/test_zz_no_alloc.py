@@ -26,7 +26,7 @@ def mt():
 def test_noalloc_matches_transport_on_consecutive_calls(mt):
     import torch
     from workloads import gen
-    wl = gen.workload("config1", n=2 * 20000, hist_samples=20000)
+    wl = gen.workload("shield1e6", n=2 * 20000, hist_samples=20000)
     halves = [{k: v[:20000].copy() for k, v in wl.muons.items()}, {k: v[20000:].copy() for k, v in wl.muons.items()}]
     with mt.World.from_workload(wl) as world:
         for call, (mu, off) in enumerate(zip(halves, (0, 20000))):
@@ -44,7 +44,7 @@ def test_noalloc_matches_transport_on_consecutive_calls(mt):
 def test_noalloc_rejects_oversized_batches(mt):
     from workloads import gen
     n = mt.MT_NOALLOC_MAX_MUONS + 1
-    wl = gen.workload("config0", n=n, hist_samples=20000)
+    wl = gen.workload("block1e4", n=n, hist_samples=20000)
     with mt.World.from_workload(wl) as world:
         dev = mt.muons_to_device(wl.muons)
         with pytest.raises(mt.MtError) as e:

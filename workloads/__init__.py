@@ -10,13 +10,13 @@ from .gen import (  # noqa: F401
     MATERIALS,
     Workload,
     histogram_set,
-    muons_config0,
-    muons_config1,
-    geometry_config0,
-    geometry_config1,
+    muons_block,
+    muons_shield,
+    geometry_block1e4,
+    geometry_shield1e6,
     geometry_tapered,
     solid,
-    field_map_config1,
+    field_map_shield1e6,
     workload,
     batched_instances,
     batched_instance,
@@ -26,7 +26,7 @@ from .gen import (  # noqa: F401
     BATCH_STEP_LEN,
     BATCH_MAX_STEPS,
     BATCH_SEED,
-    C4_MUONS,
-    C4_CHUNK,
-    muons_config4_chunk,
+    SHIELD1E8_MUONS,
+    SHIELD1E8_CHUNK,
+    muons_shield1e8_chunk,
 )

@@ -186,7 +186,7 @@ def _box(lo, hi, mat, block=-1, B=(0.0, 0.0, 0.0)):
                 block_id=int(block), B=[float(v) for v in B])
 
 
-def geometry_config0() -> dict:
+def geometry_block1e4() -> dict:
     """Iron block 1x1x2 m (x,y in [-0.5,0.5], z in [0,2]) in air; B = (0,1.7,0) T in iron.
 
     Materials: 1 = iron, 2 = air.  World bounds |x|,|y| < 2 m, z < 3 m, p_min 0.5 GeV.
@@ -200,7 +200,7 @@ MAGNET_LEN = 4.0
 MAGNET_HALF = 0.6
 
 
-def geometry_config1() -> dict:
+def geometry_shield1e6() -> dict:
     """Shield-like layout: six iron blocks 1.2x1.2x4 m with 0.5 m air gaps, alternating
     B_y = +-1.7 T (+ for even k), then a 2 m concrete wall z in [27,29], |x|,|y| <= 3 m.
 
@@ -230,7 +230,7 @@ def _trapezoid(hx_lo: float, hx_hi: float, hy: float, dx: float = 0.0):
 
 
 def geometry_tapered() -> dict:
-    """Config1's layout with tapered magnets (the paper's convex-polyhedron geometry,
+    """Shield1e6's layout with tapered magnets (the paper's convex-polyhedron geometry,
     Sec. Simulation item 1): six iron solids in z in [4.5k, 4.5k + 4], whose
     cross-sections are trapezoids (wider at -y than at +y) that narrow along z
     and shift sideways by 2 cm per block, B_y = +-1.7 T alternating; the concrete
@@ -289,7 +289,7 @@ def magnet_field_map(nx: int, ny: int, nz: int, half_xy: float, z_lo: float, z_h
     return dict(kind="map", dims=[nx, ny, nz], origin=[-half_xy, -half_xy, z_lo], spacing=spacing, B=B)
 
 
-def field_map_config1(nx: int = 200, ny: int = 200, nz: int = 600, z_lo: float = -0.5,
+def field_map_shield1e6(nx: int = 200, ny: int = 200, nz: int = 600, z_lo: float = -0.5,
                       z_hi: float = 27.5, half_xy: float = 3.0, magnet_z0=None,
                       magnet_B=None, edge_w: float = 0.03) -> dict:
     """Field map of the six-magnet shield: 200x200x600 nodes over x,y in [-3,3] m and
@@ -311,7 +311,7 @@ def _soa(x, y, z, px, py, pz, q) -> dict:
                 q=q.astype(np.int8), steps=np.zeros(n, np.int32), status=np.zeros(n, np.uint8))
 
 
-def muons_config0(n: int, seed: int = 1234) -> dict:
+def muons_block(n: int, seed: int = 1234) -> dict:
     """p log-uniform 5-300 GeV, q = +-1, x,y ~ U(-0.4,0.4) m, z = 0, px,py ~ N(0,0.5) GeV."""
     rng = np.random.default_rng(seed)
     p = np.exp(rng.uniform(np.log(5.0), np.log(300.0), n))
@@ -329,7 +329,7 @@ def muons_config0(n: int, seed: int = 1234) -> dict:
     return _soa(x, y, np.zeros(n), px, py, pz, q)
 
 
-def muons_config1(n: int, seed: int = 1234, p_lo: float = 10.0, p_hi: float = 350.0) -> dict:
+def muons_shield(n: int, seed: int = 1234, p_lo: float = 10.0, p_hi: float = 350.0) -> dict:
     """dN/dp ~ p^-2.7 on [10,350] GeV (inverse CDF), p_T ~ Exp(1 GeV), uniform azimuth,
     random charge, x,y ~ U(-0.4,0.4) m at z = 0."""
     rng = np.random.default_rng(seed)
@@ -380,12 +380,12 @@ def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = N
              field: Optional[str] = None, axes: str = "linear") -> Workload:
     """Named workloads.
 
-    * ``config0``: 1e4 muons, one iron block in air, analytic per-box field, 200 steps,
+    * ``block1e4``: 1e4 muons, one iron block in air, analytic per-box field, 200 steps,
       iron+air histograms (64 log bins on 1-400 GeV, 128x64 cells, 1e6 samples each).
-    * ``config1``: 1e6 muons through the six-magnet shield and concrete wall, trilinear
+    * ``shield1e6``: 1e6 muons through the six-magnet shield and concrete wall, trilinear
       200x200x600 field map, iron/air/concrete histograms, 1500 steps.
-    * ``config1p``: config1 with tapered magnets (``geometry_tapered``, polyhedra).
-    * ``config4``: config1's spectrum and geometry with a 400x400x1200 map and
+    * ``tapered1e6``: shield1e6 with tapered magnets (``geometry_tapered``, polyhedra).
+    * ``shield1e8``: shield1e6's spectrum and geometry with a 400x400x1200 map and
       4 materials x 128 bins x 256x128 cells (a 4th material, lead, is present in the
       table set but not placed in the geometry).
 
@@ -393,30 +393,30 @@ def workload(name: str, n: Optional[int] = None, hist_samples: Optional[int] = N
     for the analytic per-box field and "nearest" reads the map at the nearest node;
     ``axes`` = "log" builds the histograms on the paper's log-scaled axes.
     """
-    if name == "config0":
+    if name == "block1e4":
         h = histogram_set(["iron", "air"], n_samples=hist_samples or 10**6, axes=axes)
-        mu = muons_config0(n or 10_000)
-        geo = geometry_config0()
+        mu = muons_block(n or 10_000)
+        geo = geometry_block1e4()
         fld = dict(kind="box")
         return Workload(name, geo, fld, h, mu, 0.02, 200, 7)
-    if name in ("config1", "config3"):
+    if name in ("shield1e6", "diff1e6"):
         h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6, axes=axes)
-        mu = muons_config1(n or 1_000_000)
-        geo = geometry_config1()
-        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_config1())
+        mu = muons_shield(n or 1_000_000)
+        geo = geometry_shield1e6()
+        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_shield1e6())
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
-    if name == "config1p":
+    if name == "tapered1e6":
         h = histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6, axes=axes)
-        mu = muons_config1(n or 1_000_000)
+        mu = muons_shield(n or 1_000_000)
         geo = geometry_tapered()
-        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_config1())
+        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_shield1e6())
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
-    if name == "config4":
+    if name == "shield1e8":
         h = histogram_set(["iron", "air", "concrete", "lead"], n_pbin=128, nf=256, ntheta=128, axes=axes,
                           n_samples=hist_samples or 10**6)
-        mu = muons_config1(n or 100_000_000)
-        geo = geometry_config1()
-        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_config1(400, 400, 1200))
+        mu = muons_shield(n or 100_000_000)
+        geo = geometry_shield1e6()
+        fld = dict(kind="box") if field == "box" else _nearest(field, field_map_shield1e6(400, 400, 1200))
         return Workload(name, geo, fld, h, mu, 0.02, 1500, 7)
     raise KeyError(name)
 
@@ -455,7 +455,7 @@ def batched_instance(i: int, seed: int = 2024, vox_dims=(64, 64, 512), map_dims=
     fld = magnet_field_map(map_dims[0], map_dims[1], map_dims[2], half_xy, -0.5, L, z0, list(Bmag))
     if n is None:
         n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
-    mu = muons_config1(n, seed=seed * 7919 + i)
+    mu = muons_shield(n, seed=seed * 7919 + i)
     return dict(geometry=geo, field=fld, muons=mu, n=n, length=L, B=Bmag, gaps=gaps)
 
 
@@ -482,15 +482,15 @@ BATCH_SEED = 11
 
 
 def batched_hist(hist_samples: Optional[int] = None) -> dict:
-    """Histogram set of the batched workload (iron, air, concrete, as config1)."""
+    """Histogram set of the batched workload (iron, air, concrete, as shield1e6)."""
     return histogram_set(["iron", "air", "concrete"], n_samples=hist_samples or 10**6)
 
 
-C4_MUONS = 100_000_000
-C4_CHUNK = 16_000_000
+SHIELD1E8_MUONS = 100_000_000
+SHIELD1E8_CHUNK = 16_000_000
 
 
-def muons_config4_chunk(c: int, n: int) -> dict:
-    """Chunk c (n muons, ids c * C4_CHUNK + m) of the 1e8-muon config4 stream: config1's
+def muons_shield1e8_chunk(c: int, n: int) -> dict:
+    """Chunk c (n muons, ids c * SHIELD1E8_CHUNK + m) of the 1e8-muon shield1e8 stream: shield1e6's
     spectrum, each chunk from its own seed so chunks can be made one at a time."""
-    return muons_config1(n, seed=1234 * 1000 + c)
+    return muons_shield(n, seed=1234 * 1000 + c)
