@@ -357,6 +357,32 @@ def test_rk4_helix_closed_form(q):
     assert abs(math.hypot(r[0], r[1] - yc) - R) < 1e-9
 
 
+@pytest.mark.parametrize("q", [1, -1])
+def test_rk4_equals_taylor_polynomial_of_the_generator(q):
+    """With B and P0 held, dp/ds = A p is linear (A v = kappa q (v x B) / P0), so one
+    classical RK4 step is the degree-4 Taylor polynomial of exp(dA): p1 = T4(dA) p and
+    r1 = r + (d/P0) (I + dA/2 + (dA)^2/6 + (dA)^3/24) p.  Written here with 3x3
+    matrices, independently of the oracle's stage form (a wrong stage weight, sign or
+    operand order there fails it)."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        r = rng.normal(size=3)
+        p = rng.normal(size=3) * np.array([1.0, 1.0, 8.0])
+        B = rng.normal(size=3) * 1.7
+        d = 0.02 * rng.uniform(0.5, 50.0)
+        P0 = np.linalg.norm(p)
+        Bx = np.array([[0.0, B[2], -B[1]], [-B[2], 0.0, B[0]], [B[1], -B[0], 0.0]])   # v -> v x B
+        M = d * KAPPA * q / P0 * Bx
+        I = np.eye(3)
+        M2 = M @ M
+        M3 = M2 @ M
+        p1 = (I + M + M2 / 2 + M3 / 6 + M3 @ M / 24) @ p
+        r1 = r + d / P0 * ((I + M / 2 + M2 / 6 + M3 / 24) @ p)
+        ro, po = oracle.rk4(r, p, B, q, d)
+        np.testing.assert_allclose(po, p1, rtol=0, atol=1e-13 * P0)
+        np.testing.assert_allclose(ro, r1, rtol=0, atol=1e-13 * (1.0 + np.abs(r).max() + d))
+
+
 def test_rk4_momentum_magnitude_conserved():
     rng = np.random.default_rng(8)
     r = np.zeros(3)
