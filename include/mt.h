@@ -257,7 +257,8 @@ mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, flo
  *                       whose lanes pick up the next muon of their block's range
  *                       as soon as the current one stops;
  *  MT_LAUNCH_COMPACT    lockstep passes: every live muon advances steps_per_pass
- *                       steps, then the survivors are compacted into a scratch
+ *                       steps (warps take 32-muon chunks of the live list from
+ *                       a per-pass counter), then the survivors are compacted into a scratch
  *                       list (two 64-byte entries per muon plus 256 bytes, see
  *                       mt_transport_workspace_bytes) for the next pass; n must
  *                       be below 2^31;
@@ -289,9 +290,10 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
  * Batched form: many independent worlds (each its own geometry and field map,
  * all sharing one histogram set) transported in one sequence of launches.
  * The live muons of every instance advance in lockstep passes of
- * steps_per_pass steps; a device work queue hands (instance, chunk) items to a
- * resident grid whose blocks stage one instance's world at a time in shared
- * memory; survivors are compacted per instance between passes.  The paper
+ * steps_per_pass steps; a device work queue hands items naming an instance to
+ * a resident grid whose blocks stage that instance's world in shared memory,
+ * and the block's warps take 32-muon chunks of the instance until none are
+ * left; survivors are compacted per instance between passes.  The paper
  * runs one geometry per launch; scanning many magnet configurations is the
  * design-optimisation use it motivates (Sec. Introduction).
  * ------------------------------------------------------------------------- */
