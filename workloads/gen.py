@@ -47,11 +47,11 @@ MATERIALS: Dict[str, Dict[str, float]] = {
     "lead":     dict(rho=11.35, ZA=0.39575, I=823.0e-6, X0=0.5612, b=6.0e-6),
 }
 
-# generated histogram sets are cached beside the package (git-ignored), or where
-# MT_WORKLOAD_CACHE points
+# generated histogram sets are cached in the repository's _build/ folder (a build
+# product, not source), or where MT_WORKLOAD_CACHE points
 _CACHE_DIR = os.environ.get(
-    "MT_WORKLOAD_CACHE", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".cache",
-                                      "mt_workloads"))
+    "MT_WORKLOAD_CACHE", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build",
+                                      "workload_cache"))
 
 
 def _cache_path(tag: str, params: dict) -> str:
