@@ -484,6 +484,19 @@ def physics_sample(material: dict, p: float, x_cm: float, u):
     return f.value, th.value
 
 
+def physics_samples(material: dict, p: float, x_cm: float, U: np.ndarray):
+    """(f, theta) arrays of or_physics_sample for each row of U (rows of eight uniforms)."""
+    m = _material_array([material])
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    f = np.zeros(len(U))
+    th = np.zeros(len(U))
+    fn = lib().or_physics_sample
+    pm, fb, tb = _p(m), f.ctypes.data, th.ctypes.data
+    for i in range(len(U)):
+        fn(pm, float(p), float(x_cm), U[i].ctypes.data, fb + 8 * i, tb + 8 * i)
+    return f, th
+
+
 def build_histograms(materials, edges, nf: int, ntheta: int, f_max: float, step_len: float, n_samples: int,
                      seed: int):
     """(counts [n_mat][n_pbin][nf][ntheta], theta_max [n_mat][n_pbin]) from the parametric sampler."""

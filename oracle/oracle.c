@@ -607,11 +607,10 @@ void or_transport_one(const or_world *w, double r[3], double p[3], int32_t q, in
         }
         or_step_draw dr;
         if (or_draw_step(w, r, p, k, id, inst, seed, &dr)) or_scatter_draw(w, p, &dr, p);
-        double B[3];
         if (w->field_per_stage) {
-            or_field(w, r, dr.box, B);
-            or_rk4_staged(w, r, p, dr.box, q, d);
+            or_rk4_staged(w, r, p, dr.box, q, d);   /* reads the field at each stage itself */
         } else {
+            double B[3];
             or_field(w, r, dr.box, B);
             or_rk4(r, p, B, q, d);
         }
@@ -970,11 +969,10 @@ static void or_adjoint_one(const or_world *w, const double r0[3], const double p
         t->theta = dr.theta;
         t->phi = dr.phi;
         if (t->scattered) or_scatter_draw(w, p, &dr, p);
-        double B[3];
         if (w->field_per_stage) {
-            or_field(w, r, dr.box, B);
-            or_rk4_staged(w, r, p, dr.box, q, d);
+            or_rk4_staged(w, r, p, dr.box, q, d);   /* reads the field at each stage itself */
         } else {
+            double B[3];
             or_field(w, r, dr.box, B);
             or_rk4(r, p, B, q, d);
         }

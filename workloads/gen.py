@@ -26,6 +26,7 @@ from __future__ import annotations
 import concurrent.futures
 import dataclasses
 import hashlib
+import inspect
 import json
 import os
 from typing import Dict, List, Optional
@@ -140,8 +141,12 @@ def histogram_set(materials: List[str], n_pbin: int = 64, p_lo: float = 1.0, p_h
     Returns a dict with ``weights`` [n_mat][n_pbin][nf][ntheta] (float64 counts),
     ``f_max`` and ``theta_max`` [n_mat][n_pbin] (float64) and the binning scalars.
     """
+    # the key covers the model too: each material's constants and the source of the
+    # sampler, so editing either never reuses histograms of the old model
+    src = hashlib.sha1((inspect.getsource(_hist_one) + inspect.getsource(_highland)).encode()).hexdigest()[:16]
     params = dict(materials=list(materials), n_pbin=n_pbin, p_lo=p_lo, p_hi=p_hi, nf=nf,
-                  ntheta=ntheta, f_max=f_max, n_samples=n_samples, step_len=step_len, seed=seed, v=1)
+                  ntheta=ntheta, f_max=f_max, n_samples=n_samples, step_len=step_len, seed=seed, v=1,
+                  model=[MATERIALS[m] for m in materials], src=src)
     if axes != "linear":
         params["axes"] = axes
     path = _cache_path("hist", params)
