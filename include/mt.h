@@ -498,16 +498,20 @@ int32_t mt_bv_edges(const double *probes, const double *phi, int32_t n_probe, do
  * paper has no counterpart: it describes no allocation policy.)
  * It runs the compacting transport (MT_LAUNCH_COMPACT, 64 steps per pass) with
  * its scratch list in an 8 MiB array that the library reserves in device
- * memory on every GPU that loads it, held until the process exits; it calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * memory, held until the process exits; it calls no cudaMalloc, cudaFree or
+ * other allocating routine.  CUDA creates a library's device objects and loads
+ * its kernels lazily, and that takes device memory, so mt_create (which
+ * allocates anyway) creates the array on its device and loads the kernels this
+ * call launches for its world: no call of this entry point triggers either.
  *  - n may be at most MT_NOALLOC_MAX_MUONS; larger n returns MT_ERR_INVALID_ARG
  *    before anything is enqueued.  Other arguments and errors as mt_transport.
  *  - All calls on one device share that array and leave their contents in it;
  *    each call clears the counters it needs.  Calls that can overlap on the GPU
  *    (different streams, or different host threads without ordering) race on the
  *    array: order them, e.g. on one stream.
- *  - The first call on a device looks up the array's device address (once per
- *    device, thread-safe); make that first call before any stream capture. */
+ *  - The array's device address is looked up once per device (thread-safe),
+ *    by mt_create; should that have failed, the first call here retries it,
+ *    so make the first call before any stream capture. */
 mt_status mt_transport_noalloc(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
                                uint64_t seed, void *stream);
 

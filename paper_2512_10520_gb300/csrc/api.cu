@@ -767,6 +767,7 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
         mt_destroy(h);
         return st;
     }
+    noalloc_prepare(h->w, h->device);
     *out = h;
     return MT_OK;
 }

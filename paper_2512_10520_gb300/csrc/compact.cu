@@ -118,4 +118,40 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
     return e;
 }
 
+// Load compact_init and the pass kernel of this world's geometry and field
+// kind onto the current device.  Kernels are loaded lazily on their first
+// launch, and loading takes device memory; mt_create calls this so that
+// mt_transport_noalloc allocates nothing, also on its first call.
+template <int GEOM, int FIELD>
+static cudaError_t preload_passes()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, compact_init);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, compact_pass<GEOM, FIELD>);
+    return e;
+}
+
+cudaError_t compact_preload(const WorldParams &w)
+{
+    const bool staged = w.field_kind == MT_FIELD_MAP && w.field_per_stage;
+    if (w.geom_kind == MT_GEOM_BOXES) {
+        if (staged) return preload_passes<MT_GEOM_BOXES, kFieldMapStaged>();
+        if (w.field_kind == MT_FIELD_MAP) return preload_passes<MT_GEOM_BOXES, MT_FIELD_MAP>();
+        if (w.field_kind == MT_FIELD_MAP_NEAREST) return preload_passes<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>();
+        if (w.field_kind == MT_FIELD_BOX) return preload_passes<MT_GEOM_BOXES, MT_FIELD_BOX>();
+        return preload_passes<MT_GEOM_BOXES, MT_FIELD_NONE>();
+    }
+    if (w.geom_kind == MT_GEOM_POLYHEDRA) {
+        if (staged) return preload_passes<MT_GEOM_POLYHEDRA, kFieldMapStaged>();
+        if (w.field_kind == MT_FIELD_MAP) return preload_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>();
+        if (w.field_kind == MT_FIELD_MAP_NEAREST) return preload_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>();
+        if (w.field_kind == MT_FIELD_BOX) return preload_passes<MT_GEOM_POLYHEDRA, MT_FIELD_BOX>();
+        return preload_passes<MT_GEOM_POLYHEDRA, MT_FIELD_NONE>();
+    }
+    if (staged) return preload_passes<MT_GEOM_VOXELS, kFieldMapStaged>();
+    if (w.field_kind == MT_FIELD_MAP) return preload_passes<MT_GEOM_VOXELS, MT_FIELD_MAP>();
+    if (w.field_kind == MT_FIELD_MAP_NEAREST) return preload_passes<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>();
+    return preload_passes<MT_GEOM_VOXELS, MT_FIELD_NONE>();
+}
+
 }  // namespace mt

@@ -146,4 +146,5 @@ mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g);
 mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own);
 mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &own);
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own);
+void noalloc_prepare(const WorldParams &w, int dev);   // noalloc.cu
 }  // namespace mt

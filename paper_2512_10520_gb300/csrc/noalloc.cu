@@ -10,15 +10,20 @@
 // this entry point needs beyond them is the compaction list, and that lives in
 // g_noalloc_scratch below.
 //
-// The array is a file-scope __device__ object: every GPU that loads libmt.so
-// holds its MT_NOALLOC_MAX_MUONS-sized copy until the process exits, and all
-// calls on a device share that one copy.
+// The array is a file-scope __device__ object: every GPU on which a handle is
+// created holds its MT_NOALLOC_MAX_MUONS-sized copy until the process exits,
+// and all calls on a device share that one copy.  CUDA loads a library's
+// device code and objects lazily, on first use, and loading takes device
+// memory; so mt_create, which allocates anyway, looks up the array and loads
+// the compacting kernels of its world (noalloc_prepare below), and this entry
+// point itself never triggers a load.
 #include <mutex>
 
 #include "mt_internal.cuh"
 
 namespace mt {
 int64_t compact_workspace_bytes(int64_t n);
+cudaError_t compact_preload(const WorldParams &w);
 }
 
 namespace {
@@ -53,6 +58,18 @@ mt_status scratch_address(int dev, void **out)
 }
 
 }  // namespace
+
+namespace mt {
+// Called by mt_create with the handle's device current: creates the scratch
+// array on that device and loads the kernels mt_transport_noalloc launches for
+// this world.  A failure here is left for mt_transport_noalloc to report.
+void noalloc_prepare(const WorldParams &w, int dev)
+{
+    void *p = nullptr;
+    if (scratch_address(dev, &p) == MT_OK) compact_preload(w);
+    cudaGetLastError();
+}
+}  // namespace mt
 
 extern "C" mt_status mt_transport_noalloc(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len,
                                           int32_t max_steps, uint64_t seed, void *stream)
