@@ -376,13 +376,23 @@ def transport(world: OracleWorld, muons: dict, step_len: float, max_steps: int, 
                 end += 1
             runs.append((start, end))
             start = end
-        for a, b in runs:
+        def run(ab):
+            a, b = ab
             views = [tmp[k][a:b] for k in ("x", "y", "z", "px", "py", "pz")]
-            rc = L.or_transport(world.ptr, b - a, *(_p(v) for v in views), _p(q_s[a:b]), _p(st_s[a:b]),
-                                _p(stat_s[a:b]), int(id_offset + s_sorted[a]), int(instance),
-                                float(step_len), int(max_steps), int(seed), int(min(nt, b - a)))
-            if rc != 0:
-                raise RuntimeError("or_transport failed")
+            return L.or_transport(world.ptr, b - a, *(_p(v) for v in views), _p(q_s[a:b]), _p(st_s[a:b]),
+                                  _p(stat_s[a:b]), int(id_offset + s_sorted[a]), int(instance),
+                                  float(step_len), int(max_steps), int(seed), int(min(nt, b - a)))
+
+        # runs are independent muons: short runs go to a pool of host threads (the
+        # C call releases the GIL), long runs thread inside the oracle
+        short = [r for r in runs if r[1] - r[0] < nt]
+        rcs = [run(r) for r in runs if r[1] - r[0] >= nt]
+        if short:
+            import concurrent.futures
+            with concurrent.futures.ThreadPoolExecutor(max_workers=nt) as ex:
+                rcs += list(ex.map(run, short))
+        if any(rc != 0 for rc in rcs):
+            raise RuntimeError("or_transport failed")
         inv = np.empty_like(order)
         inv[order] = np.arange(n)
         for k in out:

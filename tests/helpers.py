@@ -59,3 +59,30 @@ def describe(ok, err):
             f"max mom err {err['mom_err'].max():.3g}; median pos err {np.median(err['pos_err']):.3g}; "
             f"steps mismatches {(~err['same_steps']).sum()}, status mismatches {(~err['same_status']).sum()}; "
             f"first failures {bad[:8].tolist()}")
+
+
+KS_MIN_P = 0.01     # two-sample KS on final x, y, |p| (distribution agreement)
+
+
+def ks_pvalues(gpu, ora):
+    """Two-sample KS p-values of final x, y and |p|, GPU against oracle."""
+    from scipy import stats
+
+    def P(f):
+        return np.sqrt(np.asarray(f["px"], np.float64) ** 2 + np.asarray(f["py"], np.float64) ** 2
+                       + np.asarray(f["pz"], np.float64) ** 2)
+    return {"x": stats.ks_2samp(np.asarray(gpu["x"], np.float64), np.asarray(ora["x"], np.float64)).pvalue,
+            "y": stats.ks_2samp(np.asarray(gpu["y"], np.float64), np.asarray(ora["y"], np.float64)).pvalue,
+            "|p|": stats.ks_2samp(P(gpu), P(ora)).pvalue}
+
+
+def assert_parity(gpu, ora, idx=None, frac=PASS_FRAC):
+    """The acceptance bar of the GPU path against the FP64 oracle: at least `frac` of
+    muons within (POS_TOL, MOM_TOL) with identical steps and status, and KS p >
+    KS_MIN_P on final x, y and |p|.  Returns the per-muon mask."""
+    ok, err = compare(gpu, ora, idx)
+    assert ok.mean() >= frac, describe(ok, err)
+    g = gpu if idx is None else {k: np.asarray(v)[idx] for k, v in gpu.items()}
+    ks = ks_pvalues(g, ora)
+    assert min(ks.values()) > KS_MIN_P, (ks, describe(ok, err))
+    return ok

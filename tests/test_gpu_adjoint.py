@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import compare, describe, gpu_transport
+from helpers import gpu_transport
 from workloads import gen
 
 pytestmark = pytest.mark.gpu

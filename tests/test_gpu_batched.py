@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import compare, describe
+from helpers import assert_parity, compare, describe
 from workloads import gen
 
 pytestmark = pytest.mark.gpu
@@ -93,7 +93,7 @@ def test_batched_matches_fp64_oracle(hist, instances, batch):
     devs = _dev(instances)
     batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)
     got = _host(devs)
-    oks = []
+    gots, oras = [], []
     for i, inst in enumerate(instances):
         if not inst["n"]:
             continue
@@ -101,10 +101,13 @@ def test_batched_matches_fp64_oracle(hist, instances, batch):
         ora = oracle.transport(w, inst["muons"], gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED,
                                id_offset=0, instance=i)
         ok, err = compare(got[i], ora)
-        oks.append(ok)
-        assert ok.mean() >= 0.995 or (~ok).sum() <= 2, (i, describe(ok, err))
-    allok = np.concatenate(oks)
-    assert allok.mean() >= 0.998, allok.mean()
+        # per instance a gross-error guard (a wrong world or id mapping fails most
+        # muons); the 99.9 % bar applies to the pooled 9163 muons
+        assert ok.mean() >= 0.99 or (~ok).sum() <= 2, (i, describe(ok, err))
+        gots.append(got[i])
+        oras.append(ora)
+    cat = lambda L: {k: np.concatenate([np.asarray(d[k]) for d in L]) for k in L[0]}
+    assert_parity(cat(gots), cat(oras))
 
 
 def test_graph_replay_equals_plain_launches(instances, batch):

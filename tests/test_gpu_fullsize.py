@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import compare, describe
+from helpers import assert_parity, compare, describe
 from workloads import gen
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +29,7 @@ def test_worlds256_full_batch_sampled_parity():
     import paper_2512_10520_gb300 as mt
     hist = gen.batched_hist()
     n_inst = 256
-    check = [0, 3, 17, 64, 101, 150, 199, 255]
+    check = list(range(0, n_inst, 8))          # 32 instances, up to 625 sampled muons each
     kept = {}
     with mt.Batch(hist, n_inst) as b:
         devs = []
@@ -43,19 +43,24 @@ def test_worlds256_full_batch_sampled_parity():
         torch.cuda.synchronize()
         assert sum(int(d["x"].numel()) for d in devs) > 3e7
         rng = np.random.default_rng(1)
-        oks = []
+        gots, oras = [], []
         for i in check:
             inst = kept[i]
             n = inst["n"]
-            idx = np.sort(rng.choice(n, size=min(n, 150), replace=False))
+            idx = np.sort(rng.choice(n, size=min(n, 625), replace=False))
             got = {k: v.cpu().numpy()[idx] for k, v in devs[i].items()}
             ora = oracle.transport(oracle.OracleWorld(inst["geometry"], inst["field"], hist), inst["muons"],
                                    gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, instance=i, index=idx)
             ok, err = compare(got, ora)
-            oks.append(ok)
-            assert ok.mean() >= 0.98, (i, describe(ok, err))
-        allok = np.concatenate(oks)
-        assert allok.mean() >= 0.995, allok.mean()
+            # per instance a gross-error guard (a wrong world or id mapping fails most
+            # muons); the 99.9 % bar is statistical and applies to the pooled sample
+            assert ok.mean() >= 0.99, (i, describe(ok, err))
+            gots.append(got)
+            oras.append(ora)
+        cat = lambda L: {k: np.concatenate([d[k] for d in L]) for k in L[0]}
+        pooled_g, pooled_o = cat(gots), cat(oras)
+        assert len(pooled_g["x"]) >= 10_000
+        assert_parity(pooled_g, pooled_o)
 
 
 def test_diff1e6_full_size_adjoint_sampled():
@@ -114,8 +119,7 @@ def test_shield1e8_chunk_sampled_parity():
         world.transport(dev, wl.step_len, wl.max_steps, wl.seed, id_offset=0)
         torch.cuda.synchronize()
         rng = np.random.default_rng(2)
-        idx = np.sort(rng.choice(gen.SHIELD1E8_CHUNK, size=500, replace=False))
+        idx = np.sort(rng.choice(gen.SHIELD1E8_CHUNK, size=20_000, replace=False))
         got = {k: v.cpu().numpy()[idx] for k, v in dev.items()}
     ora = oracle.transport(oracle.world_of(wl), mu, wl.step_len, wl.max_steps, wl.seed, index=idx)
-    ok, err = compare(got, ora)
-    assert ok.mean() >= 0.995, describe(ok, err)
+    assert_parity(got, ora)

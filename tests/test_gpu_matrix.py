@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import compare, describe, gpu_transport
+from helpers import assert_parity, gpu_transport
 from workloads import gen
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,7 @@ CASES = [
 @pytest.mark.parametrize("geom,field,sampler,axes,edges", CASES)
 def test_combination(geom, field, sampler, axes, edges):
     import paper_2512_10520_gb300 as mt
-    wl = gen.workload("tapered1e6" if geom == "solids" else "shield1e6", n=3000, hist_samples=50000,
+    wl = gen.workload("tapered1e6" if geom == "solids" else "shield1e6", n=20000, hist_samples=50000,
                       field={"box": "box", "nearest": "nearest"}.get(field), axes=axes)
     if geom == "voxels":
         wl.geometry = _voxelise(gen.geometry_shield1e6())
@@ -75,8 +75,7 @@ def test_combination(geom, field, sampler, axes, edges):
     wl.hist = hist
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
-    ok, err = compare(gpu, ora)
-    assert ok.mean() >= 0.997, describe(ok, err)
+    assert_parity(gpu, ora)
     with mt.World.from_workload(wl) as world:
         for mode in (mt.MT_LAUNCH_STATIC, mt.MT_LAUNCH_PERSISTENT):
             dev = mt.muons_to_device(wl.muons)

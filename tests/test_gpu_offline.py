@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import PASS_FRAC, compare, describe, gpu_transport
+from helpers import assert_parity, gpu_transport
 from workloads import gen
 
 pytestmark = pytest.mark.gpu
@@ -60,8 +60,7 @@ def test_bounded_variation_bins_through_the_transport():
     wl.hist = hist
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
-    ok, err = compare(gpu, ora)
-    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    assert_parity(gpu, ora)
 
 
 def test_explicit_log_edges_equal_the_implicit_log_bins():

@@ -6,10 +6,9 @@ import math
 
 import numpy as np
 import pytest
-from scipy import stats
 
 import oracle
-from helpers import PASS_FRAC, compare, describe, gpu_transport
+from helpers import PASS_FRAC, assert_parity, compare, describe, gpu_transport
 from workloads import gen
 
 pytestmark = pytest.mark.gpu
@@ -39,21 +38,14 @@ def wl1_small():
 def test_block1e4_full_parity(wl0):
     ora = oracle.transport(oracle.world_of(wl0), wl0.muons, wl0.step_len, wl0.max_steps, wl0.seed)
     gpu = gpu_transport(wl0)
-    ok, err = compare(gpu, ora)
-    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    assert_parity(gpu, ora)
 
 
 def test_shield1e6_subset_parity_and_ks(wl1_small):
     ora = oracle.transport(oracle.world_of(wl1_small), wl1_small.muons, wl1_small.step_len,
                            wl1_small.max_steps, wl1_small.seed)
     gpu = gpu_transport(wl1_small)
-    ok, err = compare(gpu, ora)
-    assert ok.mean() >= PASS_FRAC, describe(ok, err)
-    for k in ("x", "y"):
-        assert stats.ks_2samp(gpu[k], ora[k]).pvalue > 0.01, k
-    pg = np.sqrt(gpu["px"].astype(np.float64) ** 2 + gpu["py"] ** 2 + gpu["pz"] ** 2)
-    po = np.sqrt(ora["px"] ** 2 + ora["py"] ** 2 + ora["pz"] ** 2)
-    assert stats.ks_2samp(pg, po).pvalue > 0.01
+    assert_parity(gpu, ora)
 
 
 def test_shield1e6_full_size_sampled_parity():
@@ -61,10 +53,9 @@ def test_shield1e6_full_size_sampled_parity():
     oracle recomputes a spread sample of muon ids one by one."""
     wl = gen.workload("shield1e6")
     gpu = gpu_transport(wl)
-    idx = np.unique(np.linspace(0, wl.n - 1, 2000).astype(np.int64))
+    idx = np.unique(np.linspace(0, wl.n - 1, 20000).astype(np.int64))
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed, index=idx)
-    ok, err = compare(gpu, ora, idx)
-    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    assert_parity(gpu, ora, idx)
     # every muon ends in a valid terminal state
     assert set(np.unique(gpu["status"])) <= {1, 2, 3, 4}
     assert gpu["steps"].max() <= wl.max_steps
@@ -231,21 +222,19 @@ def test_voxel_geometry_with_map_parity():
     wl = gen.Workload("vox", geo, fld, h, mu, 0.02, 200, 5)
     ora = oracle.transport(oracle.world_of(wl), mu, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl)
-    ok, err = compare(gpu, ora)
-    assert ok.mean() >= PASS_FRAC, describe(ok, err)
+    assert_parity(gpu, ora)
 
 
 def test_field_scaled_transport_parity():
-    """Per-block field scales up to 1.4x (fields up to 2.4 T) make more low-momentum
-    tracks that skim a magnet edge chaotic, so this test of the scaling itself asks
-    for 99.8 % agreement plus tight median / 90th-percentile errors; the 99.9 % bar
-    is held by the unscaled shield1e6 parity test."""
-    wl = gen.workload("shield1e6", n=20000)
+    """Per-block field scales from 0.6x to 1.4x (fields up to 2.4 T) make more
+    low-momentum tracks that skim a magnet edge chaotic; the 99.9 % bar still
+    holds on 5e4 muons, with tight median / 90th-percentile errors."""
+    wl = gen.workload("shield1e6", n=50000)
     alpha = np.linspace(0.6, 1.4, 18).reshape(6, 3)
     ora = oracle.transport(oracle.world_of(wl, alpha), wl.muons, wl.step_len, wl.max_steps, wl.seed)
     gpu = gpu_transport(wl, alpha=alpha)
+    assert_parity(gpu, ora)
     ok, err = compare(gpu, ora)
-    assert ok.mean() >= 0.998, describe(ok, err)
     assert np.quantile(err["pos_err"], 0.9) < 1e-5 and np.quantile(err["mom_err"], 0.9) < 1e-6, describe(ok, err)
     base = gpu_transport(wl)
     assert not np.array_equal(base["x"], gpu["x"])
