@@ -62,17 +62,42 @@ def _csrc_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+def _profile_entry(kernel: str) -> dict:
+    """The committed ncu figures of a kernel (profiles/traffic.json), if they were
+    taken on this source; else an empty dict."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh)
         e = t.get(kernel)
         if e and e.get("csrc_hash") == _csrc_hash():
-            return e["dram_bytes_per_launch"]
+            return e
     except Exception:
         pass
-    return None
+    return {}
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    return _profile_entry(kernel).get("dram_bytes_per_launch")
+
+
+def issue_roofline(kernel: str, muon_steps_per_s: float, sm_mhz, sms: int):
+    """Instruction-issue ("alu") view of a transport kernel: warp instructions per
+    muon-step (from the committed ncu capture of this source) times the measured
+    muon-steps/s, against the issue peak of 4 warp instructions per cycle per SM
+    (one per SM sub-partition) x the SMs the device reports x the SM clock
+    sampled during the timed region."""
+    e = _profile_entry(kernel)
+    wips = e.get("warp_inst_per_step")
+    if not wips or not sm_mhz or not sms:
+        return {"bound": "alu", "achieved": None, "peak": None, "unit": "warp-instructions/s", "frac": None,
+                "warp_inst_per_step": wips, "sms": sms, "sm_mhz": sm_mhz,
+                "note": "no ncu capture of this source" if not wips else "no clock sample"}
+    achieved = wips * muon_steps_per_s
+    peak = sms * 4 * sm_mhz * 1e6
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
+            "frac": achieved / peak, "warp_inst_per_step": wips, "sms": sms, "sm_mhz": sm_mhz,
+            "source": e.get("summary")}
 
 
 class ClockSampler:
@@ -275,6 +300,42 @@ def _time_world(mt, wl, geometry, dev, stream, reps, id_offset):
         return float(np.mean(times)), float(work["steps"].sum().item())
 
 
+def time_block1e4_form(mt, dev, stream, reps=20, big=1_000_000, id_offset=0):
+    """block1e4: 1e4 muons (log-uniform 5-300 GeV) through one 1x1x2 m iron block
+    in air with a uniform 1.7 T field inside the block (analytic, no map),
+    2 materials x 64 bins x 128x64 tables, 200 steps.  The call as specified
+    (1e4 muons, about a fifth of one wave of the GPU) is timed, and the same
+    configuration with 1e6 muons (distinct ids), which fills the GPU.  CUDA
+    events on the launching stream."""
+    import torch
+    from paper_2512_10520_gb300.api import empty_like_soa
+    from workloads import gen
+    out = {}
+    for key, n, r in (("as_specified", None, reps), ("muons_1e6", big, 5)):
+        wl = gen.workload("block1e4", n=n)
+        init = mt.muons_to_device(wl.muons, device=dev)
+        work = empty_like_soa(wl.n, device=dev)
+        times = []
+        with mt.World.from_workload(wl) as world, torch.cuda.stream(stream):
+            for i in range(r + 2):
+                for k in work:
+                    work[k].copy_(init[k], non_blocking=True)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                world.transport(work, wl.step_len, wl.max_steps, wl.seed, id_offset=id_offset, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if i >= 2:
+                    times.append(a.elapsed_time(b) / 1e3)
+            t = float(np.median(times))
+            steps = float(work["steps"].sum().item())
+        out[key] = dict(muons=wl.n, value=steps / t, unit=UNIT, kernel_ms=1e3 * t, muon_steps=steps,
+                        muons_per_s=wl.n / t, launches_per_call=1 + (wl.max_steps + 63) // 64)
+    out["value"] = out["as_specified"]["value"]
+    out["unit"] = UNIT
+    return out
+
+
 def boxes_as_solids(geo):
     """The same boxes as polyhedron solids with equal rectangular ends."""
     from workloads import gen
@@ -369,15 +430,17 @@ def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True
     with torch.cuda.stream(stream):
         reset()
         if block and spp:
-            blk, S = block, spp
+            blk, S, stg = block, spp, 0
         else:
-            blk, S = b.autotune(works, *args, sample_per_instance=4096, id_offsets=ids, stream=stream)
+            blk, S, stg = b.autotune(works, *args, sample_per_instance=16384, id_offsets=ids, stream=stream,
+                                     cache=False)
         times = []
         for r in range(reps + 1):
             reset()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            b.transport(works, *args, use_graph=True, id_offsets=ids, stream=stream, block=blk, steps_per_pass=S)
+            b.transport(works, *args, use_graph=True, id_offsets=ids, stream=stream, block=blk, steps_per_pass=S,
+                        staging=stg)
             e1.record(stream)
             torch.cuda.synchronize()
             if r:
@@ -386,7 +449,31 @@ def time_batched_form(mt, stream, dev, n_inst=256, reps=3, rank=0, separate=True
         ref_status = [w["status"].clone() for w in works[:8]]
         t = float(np.mean(times)) / 1e3
         out.update(value=steps / t, unit=UNIT, batched_ms=1e3 * t, muon_steps=steps, block=blk, steps_per_pass=S,
+                   staging={0: "default", 1: "shared", 2: "global"}[stg],
                    graph=True, device_bytes=b.device_bytes)
+        # the plain kernel on the same kind of world: the largest instances (each
+        # enough muons to fill the GPU) through one mt_transport call each
+        big = sorted(range(n_inst), key=lambda i: -counts[i])[:max(1, min(16, n_inst // 16))]
+        if separate:
+            bw = [(i, mt.World(insts[i]["geometry"], insts[i]["field"], hist)) for i in big]
+            ptimes, psteps = [], 0.0
+            for r in range(2):
+                reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for i, w in bw:
+                    w.transport(works[i], *args, id_offset=int(ids[i]), instance=i, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    ptimes.append(e0.elapsed_time(e1))
+                    psteps = float(sum(int(works[i]["steps"].sum().item()) for i, _ in bw))
+            for _, w in bw:
+                w.close()
+            tp = float(np.mean(ptimes)) / 1e3
+            out.update(plain_largest=dict(instances=len(big), muons=sum(counts[i] for i in big),
+                                          value=psteps / tp, ms=1e3 * tp, muon_steps=psteps),
+                       vs_plain_same_worlds=(steps / t) / (psteps / tp))
         if separate:
             worlds = [mt.World(inst["geometry"], inst["field"], hist) for inst in insts]
             times = []
@@ -524,6 +611,40 @@ def time_shield1e8_form(mt, dev, n_total=None, chunk=None, rank=0, cpu_sample=20
     return out
 
 
+def forms_summary(value: float, kernel_s: float, forms: dict) -> dict:
+    """The headline figure of every form, short enough to end the JSON line."""
+    def r(x, nd=4):
+        return None if x is None else float(f"{x:.{nd}g}")
+    out = {"plain": {"value": r(value), "ms": r(1e3 * kernel_s)}}
+    if "fwd_adjoint" in forms:
+        f = forms["fwd_adjoint"]
+        out["fwd_adjoint_ckpt"] = {"value": r(f["value"]), "total_over_forward": r(f["total_over_forward"]),
+                                   "fwd_ms": r(f["t_forward_ckpt_ms"]), "adj_ms": r(f["t_adjoint_ms"])}
+        if "tape" in f:
+            t = f["tape"]
+            out["fwd_adjoint_tape"] = {"value": r(t["value"]), "total_over_forward": r(t["total_over_forward"])}
+    for k in ("alias", "polyhedra", "nearest_field", "log_axes", "per_stage_field"):
+        if k in forms:
+            out[k] = {"value": r(forms[k]["value"]),
+                      "vs_plain": r(forms[k]["value"] / value)}
+    if "batched" in forms:
+        b = forms["batched"]
+        out["batched"] = {"value": r(b["value"]), "vs_plain": r(b["value"] / value),
+                          "vs_plain_same_worlds": r(b.get("vs_plain_same_worlds")), "block": b.get("block"),
+                          "steps_per_pass": b.get("steps_per_pass"), "staging": b.get("staging")}
+    if "shield1e8" in forms:
+        b = forms["shield1e8"]
+        out["shield1e8"] = {k: r(b.get(k + "_value")) for k in ("plain", "batched", "streamed")}
+    if "block1e4" in forms:
+        b = forms["block1e4"]
+        out["block1e4"] = {"value": r(b["as_specified"]["value"]), "value_1e6_muons": r(b["muons_1e6"]["value"]),
+                           "issue_frac": r((b["as_specified"].get("issue") or {}).get("frac")),
+                           "issue_frac_1e6_muons": r((b["muons_1e6"].get("issue") or {}).get("frac"))}
+    if "offline" in forms:
+        out["offline_samples_per_s"] = r(forms["offline"]["value"])
+    return out
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -575,6 +696,17 @@ def run_mine(args):
             res = time_shield1e8_form(mt, dev, n_total=args.shield1e8_muons, rank=rank, cpu_sample=0 if args.no_cpu else 2000)
         if rank == 0:
             print(json.dumps({"form": "shield1e8", "clocks": clk.summary(), **res}))
+        return 0
+    if args.only == "block1e4":
+        with ClockSampler(local) as clk:
+            res = time_block1e4_form(mt, dev, torch.cuda.Stream(device=dev), id_offset=rank * 1_000_000)
+        clocks = clk.summary()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        for key, kern in (("as_specified", "transport_block1e4"), ("muons_1e6", "transport_block1e4_1e6")):
+            f = res[key]
+            f["issue"] = issue_roofline(kern, f["muon_steps"] / (f["kernel_ms"] / 1e3), clocks.get("sm_mhz"), sms)
+        if rank == 0:
+            print(json.dumps({"form": "block1e4", "clocks": clocks, **res}))
         return 0
     if args.only == "polyhedra":
         with ClockSampler(local) as clk:
@@ -713,6 +845,14 @@ def run_mine(args):
         ph["vs_boxes"] = ph["value"] / value
         forms["polyhedra"] = ph
         forms["offline"] = time_offline_form(mt, stream, cpu=not args.no_cpu)
+        b4 = time_block1e4_form(mt, dev, stream, id_offset=id_offset)
+        for key in ("as_specified", "muons_1e6"):
+            b4[key]["value"] = (_barrier_sum(b4[key]["muon_steps"], ws, dev)
+                                / _barrier_max(b4[key]["kernel_ms"] / 1e3, ws, dev))
+        b4["value"] = b4["as_specified"]["value"]
+        b4["workload"] = ("block1e4: 1e4 muons (log-uniform 5-300 GeV) through one 1x1x2 m iron block in air, "
+                          "uniform 1.7 T inside the block (no map), 2 materials x 64 bins x 128x64, 200 steps")
+        forms["block1e4"] = b4
         for name, kw, desc in (("nearest_field", dict(field="nearest"),
                                 "shield1e6 with the map read at the nearest node (the paper's lookup, 1 gather)"),
                                ("log_axes", dict(axes="log"),
@@ -752,13 +892,21 @@ def run_mine(args):
             "peak_kind": peak_kind, "bytes_per_step": BYTES_PER_STEP,
             "kernel_ms": kernel_s * 1e3,
             "timed_unit": "one mt_transport call (all of its kernels), CUDA events on the launching stream"}
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof["issue"] = issue_roofline("transport", steps_per_batch / kernel_s, clocks.get("sm_mhz"), sms)
+    if "block1e4" in forms:
+        for key, kern in (("as_specified", "transport_block1e4"), ("muons_1e6", "transport_block1e4_1e6")):
+            f = forms["block1e4"][key]
+            f["issue"] = issue_roofline(kern, f["muon_steps"] / (f["kernel_ms"] / 1e3), clocks.get("sm_mhz"), sms)
+        forms["block1e4"]["roofline"] = dict(forms["block1e4"]["as_specified"]["issue"],
+                                             note="no field map: bound by instruction issue, not bytes")
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         s, dt = cpu_oracle_run(wl, args.cpu_sample, threads)
         cpu = {"value": s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"first {args.cpu_sample} muons of shield1e6 (FP64 C oracle, {threads} POSIX threads)"}
-    clocks = clk.summary()
     world.close()
     if rank == 0:
         line = {
@@ -776,6 +924,7 @@ def run_mine(args):
             "gpu_launches": args.steps * launches_per_call,
             "clocks": clocks,
             "forms": forms,
+            "forms_summary": forms_summary(value, kernel_s, forms),
         }
         print(json.dumps(line))
     if ws > 1:
@@ -807,7 +956,7 @@ def main(argv=None):
     ap.add_argument("--batch-spp", type=int, default=0, help="batched form: steps per pass")
     ap.add_argument("--adjoint-only", action="store_true", help="run only the fwd+adjoint forms (one JSON line)")
     ap.add_argument("--no-tape", action="store_true", help="fwd+adjoint form: skip the full-tape variant")
-    ap.add_argument("--only", default=None, choices=["polyhedra"], help="run only this form (one JSON line)")
+    ap.add_argument("--only", default=None, choices=["polyhedra", "block1e4"], help="run only this form (one JSON line)")
     ap.add_argument("--no-separate", action="store_true",
                     help="batched form: skip timing one mt_transport call per instance")
     args = ap.parse_args(argv)

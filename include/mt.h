@@ -299,11 +299,17 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
  * ------------------------------------------------------------------------- */
 typedef struct mt_batch mt_batch;
 
+/* World staging of the batched pass (mt_batch_cfg.staging): each block copies
+ * the current instance's world parameters into shared memory, or reads them
+ * in place from the device table of instances (through L1). */
+enum { MT_BATCH_STAGE_SHARED = 1, MT_BATCH_STAGE_GLOBAL = 2 };
+
 typedef struct mt_batch_cfg {
     int32_t block;            /* threads per block: 128 or 256; 0 = tuned / 256      */
     int32_t steps_per_pass;   /* steps between compactions; 0 = tuned / 64           */
     int32_t use_graph;        /* 1 = capture the launch sequence in a CUDA graph once */
-    int32_t reserved;         /*     per (workspace, sizes, arguments) and replay it  */
+                              /*     per (workspace, sizes, arguments) and replay it  */
+    int32_t staging;          /* MT_BATCH_STAGE_*; 0 = tuned / shared                 */
     void *workspace;          /* device scratch (256-byte aligned) of at least        */
     int64_t workspace_bytes;  /*   mt_batch_workspace_bytes, or NULL: stream-ordered  */
                               /*   scratch per call, or with use_graph the batch's    */

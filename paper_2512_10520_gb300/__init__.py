@@ -15,7 +15,7 @@ from ._binding import (  # noqa: F401
     mt_tape_bytes, mt_transport_tape, mt_adjoint_tape,
     mt_build_histograms, mt_pilot_phi, mt_bv_edges,
     mt_batch_create, mt_batch_set_instance, mt_batch_destroy, mt_batch_device_bytes, mt_batch_workspace_bytes,
-    mt_transport_batched, mt_batch_autotune,
+    mt_transport_batched, mt_batch_autotune, MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL,
 )
 from .api import (World, Batch, muons_to_device, muons_to_host, empty_like_soa,  # noqa: F401
                   build_histogram_set, bounded_variation_edges)

@@ -1,11 +1,43 @@
 """Owning wrappers around the binding: a World (one mt_handle) and SoA transfers."""
 from __future__ import annotations
 
+import hashlib
+import json
+import os
+import threading
 from typing import Dict, Optional
 
 import numpy as np
 
 from . import _binding as B
+
+# autotune results, one JSON file keyed by (workload fingerprint, GPU name)
+_TUNE_CACHE = os.environ.get("MT_AUTOTUNE_CACHE",
+                             os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build",
+                                          "autotune.json"))
+_tune_lock = threading.Lock()
+
+
+def _fingerprint(h, obj) -> None:
+    """Feed a descriptor dict (numbers, strings, arrays) into hash h: scalars and
+    shapes exactly, large arrays through a strided sample plus their sums."""
+    if isinstance(obj, dict):
+        for k in sorted(obj):
+            h.update(str(k).encode())
+            _fingerprint(h, obj[k])
+    elif isinstance(obj, (list, tuple)):
+        for v in obj:
+            _fingerprint(h, v)
+    elif isinstance(obj, np.ndarray):
+        a = np.ascontiguousarray(obj)
+        h.update(f"{a.dtype}{a.shape}".encode())
+        flat = a.reshape(-1)
+        step = max(1, flat.size // 4096)
+        h.update(np.ascontiguousarray(flat[::step]).tobytes())
+        if a.dtype.kind in "fiu" and flat.size:
+            h.update(np.float64(flat.sum(dtype=np.float64)).tobytes())
+    else:
+        h.update(repr(obj).encode())
 
 
 class World:
@@ -58,9 +90,17 @@ class Batch:
     def __init__(self, hist: dict, n_inst: int):
         self.handle = B.mt_batch_create(hist, n_inst)
         self.n_inst = int(n_inst)
+        self._tables = hashlib.sha1()
+        _fingerprint(self._tables, hist)
+        self._worlds = [b""] * self.n_inst
+        self.tuned = None
 
     def set_instance(self, i: int, geometry: dict, field: dict) -> None:
         B.mt_batch_set_instance(self.handle, i, geometry, field)
+        h = hashlib.sha1()
+        _fingerprint(h, geometry)
+        _fingerprint(h, field)
+        self._worlds[i] = h.digest()
 
     @property
     def device_bytes(self) -> int:
@@ -70,11 +110,54 @@ class Batch:
         return B.mt_batch_workspace_bytes(self.handle, counts)
 
     def transport(self, muons_list, step_len: float, max_steps: int, seed: int, **kw) -> None:
+        if self.tuned is not None:
+            for k, v in zip(("block", "steps_per_pass", "staging"), self.tuned):
+                if not kw.get(k):
+                    kw[k] = v
         B.mt_transport_batched(self.handle, muons_list, step_len, max_steps, seed, **kw)
 
     def autotune(self, muons_list, step_len: float, max_steps: int, seed: int, sample_per_instance: int = 4096,
-                 **kw):
-        return B.mt_batch_autotune(self.handle, muons_list, step_len, max_steps, seed, sample_per_instance, **kw)
+                 cache: bool = True, **kw):
+        """(block, steps_per_pass, staging) fastest on a sample of every instance
+        (mt_batch_autotune); later transports use it unless told otherwise.  With
+        cache, the result is kept in a JSON file keyed by a fingerprint of the
+        worlds, tables, muon counts and run arguments and by the GPU's name, and a
+        later call with the same key reuses it without timing anything."""
+        key = None
+        if cache:
+            import torch
+            h = hashlib.sha1(self._tables.digest())
+            for w in self._worlds:
+                h.update(w)
+            counts = [int(m["x"].numel()) if hasattr(m["x"], "numel") else len(m["x"]) for m in muons_list]
+            h.update(json.dumps([counts, float(step_len), int(max_steps), int(seed), int(sample_per_instance),
+                                 B.mt_abi_version()]).encode())
+            key = f"{h.hexdigest()[:24]}|{torch.cuda.get_device_name()}"
+            with _tune_lock:
+                try:
+                    with open(_TUNE_CACHE) as fh:
+                        hit = json.load(fh).get(key)
+                except (OSError, ValueError):
+                    hit = None
+            if hit:
+                self.tuned = tuple(int(v) for v in hit)
+                return self.tuned
+        self.tuned = B.mt_batch_autotune(self.handle, muons_list, step_len, max_steps, seed, sample_per_instance,
+                                         **kw)
+        if key is not None:
+            with _tune_lock:
+                try:
+                    with open(_TUNE_CACHE) as fh:
+                        table = json.load(fh)
+                except (OSError, ValueError):
+                    table = {}
+                table[key] = list(self.tuned)
+                os.makedirs(os.path.dirname(_TUNE_CACHE), exist_ok=True)
+                tmp = f"{_TUNE_CACHE}.tmp{os.getpid()}"
+                with open(tmp, "w") as fh:
+                    json.dump(table, fh, indent=1, sort_keys=True)
+                os.replace(tmp, _TUNE_CACHE)
+        return self.tuned
 
     def close(self) -> None:
         if getattr(self, "handle", None):

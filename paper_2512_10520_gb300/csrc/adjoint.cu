@@ -26,6 +26,7 @@
 // (step.cuh), each section 256-byte aligned, P = ceil(max_steps / K).  The
 // tape buffer appends the tape region offsets, a flag and the tape region.
 #include <cstdio>
+#include <vector>
 
 #include "compact.cuh"
 
@@ -97,7 +98,8 @@ static TapeLayout tape_layout(int64_t n, int32_t max_steps, int32_t K)
 // One recorded step takes 40 (or 56) bytes in three (four) planes, so that a
 // warp's stores and loads are contiguous: plane a = (rx, ry, rz, meta), plane
 // b = (px, py, pz, c1), plane c = (c2, phi - pi), plane d = (Bx, By, Bz, -)
-// when the field is recorded, with r and p at the step's start, (c1, c2) the
+// when the field is recorded, with r (in the world's frame units) and p at the
+// step's start, (c1, c2) the
 // coefficients of the scattering update (step.cuh: scatter), B there before
 // the block scale, and meta bit 0 = scattered, bits 8..15 = box + 1.  Step j of
 // entry t sits at base + step_bytes j T (T entries per plane, a multiple of
@@ -115,35 +117,30 @@ struct TapeRef {
     __device__ __forceinline__ float4 *d(int j) const { return reinterpret_cast<float4 *>(row(j) + 40 * T) + tid; }
 };
 
+// Each plane is stored as soon as its values exist, so the recorder holds no
+// values across the step: a at the step's start (and b there too when the step
+// does not scatter), b and c at the draw, d at the field lookup.
 template <bool RB>
 struct TapeWriter {
     const TapeRef<RB> *tr;
     int j;
     bool on = true;
-    float c1 = 0.0f, c2 = 0.0f, phs = 0.0f;
-    float pxs = 0.0f, pys = 0.0f, pzs = 0.0f;
-    bool scat = false;
     __device__ __forceinline__ void begin(const State &s, int box, bool scattered)
     {
-        scat = scattered;
+        if (!on) return;
         const int meta = ((box + 1) << 8) | (scattered ? 1 : 0);
-        if (on) __stcs(tr->a(j), make_float4(s.x + s.xl, s.y + s.yl, s.z + s.zl, __int_as_float(meta)));
-        pxs = s.px + s.pxl;
-        pys = s.py + s.pyl;
-        pzs = s.pz + s.pzl;
+        __stcs(tr->a(j), make_float4(s.x + s.xl, s.y + s.yl, s.z + s.zl, __int_as_float(meta)));
+        if (!scattered) __stcs(tr->b(j), make_float4(s.px + s.pxl, s.py + s.pyl, s.pz + s.pzl, 0.0f));
     }
-    __device__ __forceinline__ void draw(float c1_, float c2_, float phs_)
+    __device__ __forceinline__ void draw(const State &s, float c1, float c2, float phs)
     {
-        c1 = c1_;
-        c2 = c2_;
-        phs = phs_;
+        if (!on) return;
+        __stcs(tr->b(j), make_float4(s.px + s.pxl, s.py + s.pyl, s.pz + s.pzl, c1));
+        __stcs(tr->c(j), make_float2(c2, phs));
     }
     __device__ __forceinline__ void field(float3 B)
     {
-        if (!on) return;
-        __stcs(tr->b(j), make_float4(pxs, pys, pzs, c1));
-        if (scat) __stcs(tr->c(j), make_float2(c2, phs));
-        if (RB) __stcs(tr->d(j), make_float4(B.x, B.y, B.z, 0.0f));
+        if (RB && on) __stcs(tr->d(j), make_float4(B.x, B.y, B.z, 0.0f));
     }
 };
 
@@ -151,6 +148,69 @@ struct TapeEntry {
     float4 a, b, d;
     float2 c;
 };
+
+// Two ways for the reverse pass to take the tape's HBM latency off its
+// critical path while it reverses step j: MT_ADJ_CP_ASYNC copies step j - 1
+// into the lane's own slot of shared memory with cp.async (measured on diff1e6:
+// backward 65 ms against 55 ms with direct loads, so off); MT_ADJ_PREFETCH
+// asks L1 for step j - 1's lines (prefetch.global.L1), which holds no register
+// or shared memory (56.0 ms against 57.3 ms without).
+#ifndef MT_ADJ_CP_ASYNC
+#define MT_ADJ_CP_ASYNC 0
+#endif
+#ifndef MT_ADJ_PREFETCH
+#define MT_ADJ_PREFETCH 1
+#endif
+
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// Shared-memory slots of one thread: two stages of four 16-byte planes.
+struct TapeStage {
+    float4 v[2][4];
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Start copying step j of the lane's tape into stage j & 1 of its slot (plane
+// c is copied whether or not the step scattered; it is read only if it did).
+template <bool RB>
+__device__ __forceinline__ void tape_prefetch(const TapeRef<RB> &tr, int j, TapeStage &st)
+{
+    float4 *v = st.v[j & 1];
+    cp_async16(&v[0], tr.a(j));
+    cp_async16(&v[1], tr.b(j));
+    cp_async8(&v[2], tr.c(j));
+    if (RB) cp_async16(&v[3], tr.d(j));
+    cp_async_commit();
+}
+
+template <bool RB>
+__device__ __forceinline__ TapeEntry tape_staged(const TapeStage &st, int j)
+{
+    const float4 *v = st.v[j & 1];
+    TapeEntry t;
+    t.a = v[0];
+    t.b = v[1];
+    t.c = (__float_as_int(t.a.w) & 1) ? make_float2(v[2].x, v[2].y) : make_float2(0.0f, 0.0f);
+    t.d = RB ? v[3] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    return t;
+}
 
 template <bool RB>
 __device__ __forceinline__ TapeEntry load_tape(const TapeRef<RB> &tr, int j)
@@ -176,15 +236,13 @@ __device__ __forceinline__ float dot3(const float a[3], const float b[3])
 }
 
 // rb += J(r)^T Bb with J[c][a] = dB_c/dr_a of the unscaled trilinear map (zero
-// outside the node box).
+// outside the node box); r in the map's cell units, rb per metre.
 __device__ __forceinline__ void field_map_jt(const WorldParams &w, const float r[3], const float Bb[3], float rb[3])
 {
     const int nx = w.fdims[0], ny = w.fdims[1], nz = w.fdims[2];
     int i, j, k;
     float tx, ty, tz;
-    if (!map_axis(r[0], 0.0f, w.forigin[0], w.forigin_lo[0], w.fspacing[0], w.fspacing_lo[0], w.finv[0], nx, i, tx) ||
-        !map_axis(r[1], 0.0f, w.forigin[1], w.forigin_lo[1], w.fspacing[1], w.fspacing_lo[1], w.finv[1], ny, j, ty) ||
-        !map_axis(r[2], 0.0f, w.forigin[2], w.forigin_lo[2], w.fspacing[2], w.fspacing_lo[2], w.finv[2], nz, k, tz))
+    if (!cell_axis(r[0], 0.0f, nx, i, tx) || !cell_axis(r[1], 0.0f, ny, j, ty) || !cell_axis(r[2], 0.0f, nz, k, tz))
         return;
     const int64_t row = nx - 1;
     const float4 *p00 = w.fmap + 2 * (((int64_t)k * ny + j) * row + i);
@@ -225,7 +283,7 @@ __device__ __forceinline__ void scatter_fp32(const float p[3], float c1, float c
         ty = -sphi;
         tz = 0.0f;
     } else {
-        const float g = uz >= 0.0f ? 1.0f / (1.0f + uz) : (1.0f - uz) / s2;
+        const float g = __fdividef(uz >= 0.0f ? 1.0f : 1.0f - uz, uz >= 0.0f ? 1.0f + uz : s2);   // as scatter
         const float wv = fmaf(cphi, ux, sphi * uy);
         tx = fmaf(-(ux * wv), g, cphi);
         ty = fmaf(-(uy * wv), g, sphi);
@@ -351,14 +409,14 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     cross3(h, vb, tmp);
     // v3b = pb/6 + a rb/24 + h x v4b;  v3 = v2 x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vb[c] = fmaf(1.0f / 6.0f, pb[c], fmaf(a / 24.0f, rb[c], tmp[c]));
+    for (int c = 0; c < 3; ++c) vb[c] = fmaf(1.0f / 6.0f, pb[c], fmaf(a * (1.0f / 24.0f), rb[c], tmp[c]));
     cross3(vb, v2, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
     cross3(h, vb, tmp);
     // v2b = pb/2 + a rb/6 + h x v3b;  v2 = v1 x h
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vb[c] = fmaf(0.5f, pb[c], fmaf(a / 6.0f, rb[c], tmp[c]));
+    for (int c = 0; c < 3; ++c) vb[c] = fmaf(0.5f, pb[c], fmaf(a * (1.0f / 6.0f), rb[c], tmp[c]));
     cross3(vb, v1, tmp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) hb[c] += tmp[c];
@@ -404,7 +462,7 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
         tv[1] = -sphi;
         tv[2] = 0.0f;
     } else {
-        const float g = u[2] >= 0.0f ? 1.0f / (1.0f + u[2]) : (1.0f - u[2]) / s2;
+        const float g = __fdividef(u[2] >= 0.0f ? 1.0f : 1.0f - u[2], u[2] >= 0.0f ? 1.0f + u[2] : s2);
         const float wv = fmaf(cphi, u[0], sphi * u[1]);
         tv[0] = fmaf(-(u[0] * wv), g, cphi);
         tv[1] = fmaf(-(u[1] * wv), g, sphi);
@@ -433,10 +491,10 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // FWD: the full-tape forward (finished muons stored, survivors appended to
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
-// Resident blocks per SM of the recorded pass: 4 (64 registers), for the
-// recorder's state kept across the step (measured on diff1e6: full-tape
-// forward 33.0 ms against 35.4 ms at the plain pass's 48 registers, which
-// spill; checkpoint backward 64.1 against 66.2 ms).  0: the plain pass's.
+// Resident blocks per SM of the recorded pass: 4 (64 registers; measured on
+// diff1e6 with the planes stored as soon as their values exist: checkpoint
+// backward 55.4 ms against 55.7 ms at 5 blocks, which spill 8 bytes).
+// 0: the plain pass's.
 #ifndef MT_TAPE_MIN_BLOCKS
 #define MT_TAPE_MIN_BLOCKS 4
 #endif
@@ -505,7 +563,7 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
             if (FWD) {
                 if (r == MT_ALIVE && k >= rp.max_steps) r = MT_MAX_STEPS;
                 if (r != MT_ALIVE)
-                    store_muon(soa, idx, s, k, r);
+                    store_muon(w, soa, idx, s, k, r);
                 else
                     keep = true;
             }
@@ -529,6 +587,9 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
 {
     __shared__ SmemWorld sw;
     __shared__ float sacc[3][MT_MAX_BOXES];
+#if MT_ADJ_CP_ASYNC
+    __shared__ TapeStage stage[kBlock];
+#endif
     const int64_t count = (int64_t)*count_p;
     if (wzero && blockIdx.x == 0 && threadIdx.x == 0) *wzero = 0ull;
     if (count == 0 || *flag) return;
@@ -552,11 +613,35 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
         const int ns = __float_as_int(ck.w3[i].w);
         float rb[3] = {adj[idx], adj[n + idx], adj[2 * n + idx]};
         float pb[3] = {adj[3 * n + idx], adj[4 * n + idx], adj[5 * n + idx]};
+#if MT_ADJ_CP_ASYNC
+        TapeStage &my = stage[threadIdx.x];
+        if (ns > 0) tape_prefetch(tr, ns - 1, my);
+#pragma unroll 1
+        for (int j = ns - 1; j >= 0; --j) {
+            if (j > 0) {
+                tape_prefetch(tr, j - 1, my);
+                cp_async_wait_one();
+            } else {
+                cp_async_wait_all();
+            }
+            const TapeEntry t = tape_staged<MT_TAPE_RECORD_B>(my, j);
+            reverse_step<GEOM, FIELD, MT_TAPE_RECORD_B>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
+        }
+#else
 #pragma unroll 1
         for (int j = ns - 1; j >= 0; --j) {
             const TapeEntry t = load_tape(tr, j);
+#if MT_ADJ_PREFETCH
+            if (j > 0) {
+                prefetch_l1(tr.a(j - 1));
+                prefetch_l1(tr.b(j - 1));
+                prefetch_l1(tr.c(j - 1));
+                if (MT_TAPE_RECORD_B) prefetch_l1(tr.d(j - 1));
+            }
+#endif
             reverse_step<GEOM, FIELD, MT_TAPE_RECORD_B>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
         }
+#endif
         adj[idx] = rb[0];
         adj[n + idx] = rb[1];
         adj[2 * n + idx] = rb[2];
@@ -645,7 +730,7 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
     if (e != cudaSuccess) return e;
     const int64_t need = (n + kBlock - 1) / kBlock;
     compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
-        soa, n, rp, live_buf_at(ck + L.lists_off, n), ctr);
+        w, soa, n, rp, live_buf_at(ck + L.lists_off, n), ctr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int grid = resident_grid((const void *)compact_pass<GEOM, FIELD>, n);
@@ -674,7 +759,7 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
     if (e != cudaSuccess) return e;
     const int64_t need = (n + kBlock - 1) / kBlock;
     compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
-        soa, n, rp, live_buf_at(buf + L.lists_off, n), ctr);
+        w, soa, n, rp, live_buf_at(buf + L.lists_off, n), ctr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int grid = resident_grid((const void *)tape_pass<GEOM, FIELD, true>, n);
@@ -689,12 +774,45 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
     return cudaSuccess;
 }
 
-// Scratch of the recompute form's backward: the tape of one pass of up to n
-// entries, after a 256-byte header holding the region offsets (bytes 0-15),
-// the flag (64) and three work counters (128-151) that the backward's kernels
-// take in turn: launch j uses counter j % 3 and clears counter (j + 1) % 3.
-static int64_t ckpt_scratch_bytes(int64_t n, int K) { return 256 + tape_pass_bytes(n > 0 ? n : 1, K); }
+// Scratch of the recompute form's backward: two slots, each a 256-byte header
+// (region offsets at bytes 0-15, the flag at 64, the recorded pass's and the
+// reverse pass's work counters at 128 and 136) and the tape of one pass of up
+// to n entries.  Pass p uses slot p % 2.
+static int64_t ckpt_slot_bytes(int64_t n, int K) { return 256 + tape_pass_bytes(n > 0 ? n : 1, K); }
+static int64_t ckpt_scratch_bytes(int64_t n, int K) { return 2 * ckpt_slot_bytes(n, K); }
 
+// Resident blocks per SM of the two kernels of the checkpoint backward (0: as
+// many as fit).  The recorded pass of segment p - 1 runs on a second stream
+// while the reverse pass of segment p runs on the caller's, so the one starts
+// as the other's blocks retire.  Both want every warp slot they can get:
+// measured on diff1e6 (K = 32), full grids 55.9 ms; 2 + 1 blocks per SM side
+// by side 77.5 ms, 1 + 2 71.6 ms, 1 + 1 77.2 ms.
+#ifndef MT_ADJ_REC_BLOCKS
+#define MT_ADJ_REC_BLOCKS 0
+#endif
+#ifndef MT_ADJ_SWEEP_BLOCKS
+#define MT_ADJ_SWEEP_BLOCKS 0
+#endif
+
+static int split_grid(const void *kernel, int per_sm_cap, int64_t work)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    if (per_sm_cap > 0 && per_sm_cap < per_sm) per_sm = per_sm_cap;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t need = (work + kBlock - 1) / kBlock;
+    if (grid > need) grid = need;
+    return (int)(grid < 1 ? 1 : grid);
+}
+
+// The reverse sweep over the checkpointed passes, last pass first.  Segment
+// p's recorded pass (slot p % 2) may start once the reverse pass of segment
+// p + 2, the slot's previous user, is done; segment p's reverse pass waits for
+// its recorded pass and (in stream order) for segment p + 1's reverse pass,
+// whose adjoint state it continues.
 template <int GEOM, int FIELD>
 static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
                                  char *ck, float *adj, char *scratch)
@@ -702,29 +820,57 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
     const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
     double *dalpha = reinterpret_cast<double *>(ck + L.alpha_off);
-    unsigned long long *toff = reinterpret_cast<unsigned long long *>(scratch);
-    unsigned int *flag = reinterpret_cast<unsigned int *>(scratch + 64);
-    cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 256, st);
-    if (e != cudaSuccess) return e;
-    const int rgrid = resident_grid((const void *)tape_pass<GEOM, FIELD, false>, n);
-    const int agrid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+    const int64_t slot = ckpt_slot_bytes(n, K);
     const int64_t cap = tape_pass_bytes(n > 0 ? n : 1, K);
-    unsigned long long *wc = reinterpret_cast<unsigned long long *>(scratch + 128);
-    int j = 0;
-    for (int p = L.passes - 1; p >= 0; --p, j += 2) {
+    cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemsetAsync(scratch + s * slot, 0, 256, st);
+    if (e != cudaSuccess) return e;
+    const int rgrid = split_grid((const void *)tape_pass<GEOM, FIELD, false>, MT_ADJ_REC_BLOCKS, n);
+    const int agrid = split_grid((const void *)adjoint_pass<GEOM, FIELD>, MT_ADJ_SWEEP_BLOCKS, n);
+    const int P = L.passes;
+    cudaStream_t aux = nullptr;
+    std::vector<cudaEvent_t> ev(2 * P + 1, nullptr);   // [0, P): recorded, [P, 2P): reversed, 2P: fork
+    e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * P], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[2 * P], 0);
+    auto hdr = [&](int p) { return scratch + (p & 1) * slot; };
+    auto record = [&](int p) {
+        char *h = hdr(p);
+        unsigned long long *wc = reinterpret_cast<unsigned long long *>(h + 128);
         const LiveBuf lp = live_buf_at(ck + L.lists_off + p * L.list_bytes, n);
-        tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, st>>>(w, mt_muon_soa{}, rp, lp, lp, ctr + p, nullptr, K,
-                                                                scratch + 256, toff, cap, flag, wc + j % 3,
-                                                                wc + (j + 1) % 3);
+        if (p + 2 < P && e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[P + p + 2], 0);
+        if (e != cudaSuccess) return;
+        tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, aux>>>(
+            w, mt_muon_soa{}, rp, lp, lp, ctr + p, nullptr, K, h + 256, reinterpret_cast<unsigned long long *>(h), cap,
+            reinterpret_cast<unsigned int *>(h + 64), wc, wc + 1);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, scratch + 256, toff,
-                                                           flag, wc + (j + 1) % 3, wc + (j + 2) % 3);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[p], aux);
+    };
+    auto reverse = [&](int p) {
+        char *h = hdr(p);
+        unsigned long long *wc = reinterpret_cast<unsigned long long *>(h + 128);
+        const LiveBuf lp = live_buf_at(ck + L.lists_off + p * L.list_bytes, n);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[p], 0);
+        if (e != cudaSuccess) return;
+        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, h + 256,
+                                                           reinterpret_cast<const unsigned long long *>(h),
+                                                           reinterpret_cast<const unsigned int *>(h + 64), wc + 1, wc);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if (e == cudaSuccess) e = cudaEventRecord(ev[P + p], st);
+    };
+    // enqueue order: the recording one segment ahead of the reverse pass
+    if (P > 0) record(P - 1);
+    for (int p = P - 1; p >= 0 && e == cudaSuccess; --p) {
+        if (p > 0) record(p - 1);
+        reverse(p);
     }
-    return cudaSuccess;
+    // the caller's stream has waited for every recorded pass (the last is
+    // segment 0's); stream and events are released once their work is done
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (aux) cudaStreamDestroy(aux);
+    return e;
 }
 
 template <int GEOM, int FIELD>

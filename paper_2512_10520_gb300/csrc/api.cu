@@ -542,15 +542,44 @@ static mt_status build_zslabs(const double *zlo_b, const double *zhi_b, int n, W
     return MT_OK;
 }
 
-// Geometry and world bounds (validated) into w.
-mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &own)
+// Position frame of a world (see WorldParams): the field map's node grid when
+// there is a map, else metres.  Positions are converted to frame units in
+// double and stored as hi + lo pairs.
+struct Frame {
+    double o[3], s[3];
+    double u(int a, double v) const { return (v - o[a]) / s[a]; }   // metres -> units
+    double len(int a, double v) const { return v / s[a]; }          // a length along axis a
+};
+
+static Frame frame_of(const mt_field_desc *f)
+{
+    Frame F;
+    const bool map = f && (f->kind == MT_FIELD_MAP || f->kind == MT_FIELD_MAP_NEAREST);
+    for (int a = 0; a < 3; ++a) {
+        F.o[a] = map ? f->origin[a] : 0.0;
+        F.s[a] = map ? f->spacing[a] : 1.0;
+    }
+    return F;
+}
+
+// Geometry and world bounds (validated) into w, in the frame that the field
+// desc f sets (frame_of).
+mt_status build_geometry(const mt_geometry_desc *g, const mt_field_desc *f, WorldParams &w, DevOwner &own)
 {
     mt_status st;
+    const Frame F = frame_of(f);
+    for (int a = 0; a < 3; ++a) {
+        split(F.o[a], w.fro_h[a], w.fro_l[a]);
+        split(F.s[a], w.frs_h[a], w.frs_l[a]);
+        split(1.0 / F.s[a], w.fri_h[a], w.fri_l[a]);
+    }
     w.geom_kind = g->kind;
     w.world_mat = g->world_material;
-    split(g->x_max, w.xmax_hi, w.xmax_lo);
-    split(g->y_max, w.ymax_hi, w.ymax_lo);
-    split(g->z_max, w.zmax_hi, w.zmax_lo);
+    split(F.u(0, g->x_max), w.xmax_hi, w.xmax_lo);
+    split(F.u(0, -g->x_max), w.xmin_hi, w.xmin_lo);
+    split(F.u(1, g->y_max), w.ymax_hi, w.ymax_lo);
+    split(F.u(1, -g->y_max), w.ymin_hi, w.ymin_lo);
+    split(F.u(2, g->z_max), w.zmax_hi, w.zmax_lo);
     w.pmin2 = (float)(g->p_min * g->p_min);
     if (g->kind == MT_GEOM_BOXES) {
         std::vector<DevBox> boxes(g->n_boxes);
@@ -558,8 +587,8 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
             const mt_box &s = g->boxes[b];
             DevBox &d = boxes[b];
             for (int a = 0; a < 3; ++a) {
-                split(s.lo[a], d.lo_hi[a], d.lo_lo[a]);
-                split(s.hi[a], d.hi_hi[a], d.hi_lo[a]);
+                split(F.u(a, s.lo[a]), d.lo_hi[a], d.lo_lo[a]);
+                split(F.u(a, s.hi[a]), d.hi_hi[a], d.hi_lo[a]);
                 d.B[a] = (float)s.B[a];
             }
             d.material = s.material;
@@ -570,8 +599,8 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
         if ((st = upload(own, boxes.data(), boxes.size(), "boxes", &w.boxes)) != MT_OK) return st;
         std::vector<double> zlo(g->n_boxes), zhi(g->n_boxes);
         for (int b = 0; b < g->n_boxes; ++b) {
-            zlo[b] = g->boxes[b].lo[2];
-            zhi[b] = g->boxes[b].hi[2];
+            zlo[b] = F.u(2, g->boxes[b].lo[2]);
+            zhi[b] = F.u(2, g->boxes[b].hi[2]);
         }
         if ((st = build_zslabs(zlo.data(), zhi.data(), g->n_boxes, w, own)) != MT_OK) return st;
     } else if (g->kind == MT_GEOM_POLYHEDRA) {
@@ -585,13 +614,26 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
         //    {bx0, by0, bx1, by1}, {bx2, by2, bx3, by3} (bottom vertices),
         //    {dx0, dy0, dx1, dy1}, {dx2, dy2, dx3, dy3} (top - bottom), and a spare;
         //  - the FP64 data z0, z1, bottom[4][2], top[4][2] for undecided tests.
+        //  All of it is in frame units: the solid is mapped by the frame's
+        //  diagonal scaling, which keeps it a convex solid with the same vertex
+        //  order (so Eq. 2's signs), and its bounding-box margin and the inner
+        //  rectangle's clearance are 1e-4 m along each axis.
         const int n = g->n_polys;
-        const double margin = 1e-4;
+        const double margin_m = 1e-4;
         std::vector<DevBox> recs(n);
         std::vector<float4> pf((size_t)n * 6), pin(n);
         std::vector<double> pd((size_t)n * 18), zlo(n), zhi(n);
         for (int b = 0; b < n; ++b) {
-            const mt_polyhedron &P = g->polys[b];
+            const mt_polyhedron &Pm = g->polys[b];
+            mt_polyhedron P = Pm;
+            P.z0 = F.u(2, Pm.z0);
+            P.z1 = F.u(2, Pm.z1);
+            for (int i = 0; i < 4; ++i)
+                for (int c = 0; c < 2; ++c) {
+                    P.bottom[i][c] = F.u(c, Pm.bottom[i][c]);
+                    P.top[i][c] = F.u(c, Pm.top[i][c]);
+                }
+            const double mx = F.len(0, margin_m), my = F.len(1, margin_m);
             double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300, M1 = 0.0, M2 = 0.0, E = 0.0;
             for (int end = 0; end < 2; ++end) {
                 const double(*v)[2] = end ? P.top : P.bottom;
@@ -609,7 +651,7 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
                 for (int c = 0; c < 2; ++c) M2 = std::max(M2, std::fabs(P.top[i][c] - P.bottom[i][c]));
             DevBox &d = recs[b];
             memset(&d, 0, sizeof(d));
-            const double lo3[3] = {x0 - margin, y0 - margin, P.z0}, hi3[3] = {x1 + margin, y1 + margin, P.z1};
+            const double lo3[3] = {x0 - mx, y0 - my, P.z0}, hi3[3] = {x1 + mx, y1 + my, P.z1};
             for (int a = 0; a < 3; ++a) {
                 split(lo3[a], d.lo_hi[a], d.lo_lo[a]);
                 split(hi3[a], d.hi_hi[a], d.hi_lo[a]);
@@ -624,7 +666,7 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
             // either end (edges move linearly in z), D the largest |dx| + |dy|
             // over the bounding box, M = M1 + M2
             const double M = M1 + M2;
-            const double D = (x1 - x0) + (y1 - y0) + 4.0 * margin;
+            const double D = (x1 - x0) + (y1 - y0) + 2.0 * (mx + my);
             const double bound = 100.0 * std::ldexp(1.0, -24) * (E + 2.0 * M) * (D + 2.0 * M);
             float z0h, z0l;
             split(P.z0, z0h, z0l);
@@ -641,9 +683,18 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
             q[3] = make_float4(dv[0], dv[1], dv[2], dv[3]);
             q[4] = make_float4(dv[4], dv[5], dv[6], dv[7]);
             q[5] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            // inner rectangle found in metres (its clearance is a length), then mapped
             double ib[4];
-            inner_box(P, margin, ib);
-            pin[b] = make_float4((float)ib[0], (float)ib[1], (float)ib[2], (float)ib[3]);
+            inner_box(Pm, margin_m, ib);
+            pin[b] = make_float4((float)F.u(0, ib[0]), (float)F.u(0, ib[1]), (float)F.u(1, ib[2]), (float)F.u(1, ib[3]));
+            if (ib[0] <= ib[1]) {   // keep the float rectangle inside the exact one
+                pin[b].x = std::nextafter(pin[b].x, INFINITY);
+                pin[b].y = std::nextafter(pin[b].y, -INFINITY);
+                pin[b].z = std::nextafter(pin[b].z, INFINITY);
+                pin[b].w = std::nextafter(pin[b].w, -INFINITY);
+            }
+            // the FP64 fallback's data: the solid mapped to frame units in FP64
+            // (Eq. 2's signs are those of the solid as given)
             double *r = &pd[(size_t)b * 18];
             r[0] = P.z0;
             r[1] = P.z1;
@@ -665,9 +716,9 @@ mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &ow
         w.n_box = 0;
         for (int a = 0; a < 3; ++a) {
             w.vdims[a] = g->vox_dims[a];
-            split(g->vox_origin[a], w.vorigin[a], w.vorigin_lo[a]);
-            split(g->vox_spacing[a], w.vspacing[a], w.vspacing_lo[a]);
-            w.vinv[a] = (float)(1.0 / g->vox_spacing[a]);
+            split(F.u(a, g->vox_origin[a]), w.vorigin[a], w.vorigin_lo[a]);
+            split(F.len(a, g->vox_spacing[a]), w.vspacing[a], w.vspacing_lo[a]);
+            w.vinv[a] = (float)(1.0 / F.len(a, g->vox_spacing[a]));
         }
     }
     return MT_OK;
@@ -686,11 +737,13 @@ mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
         for (int64_t i = 0; i < nn; ++i) nodes[i] = make_float4(f->B[3 * i], f->B[3 * i + 1], f->B[3 * i + 2], 0.0f);
         mt_status st = upload(own, nodes.data(), nodes.size(), "field nodes", &w.fmap);
         if (st != MT_OK) return st;
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3; ++a) {   // in frame units, node i at u = i
             w.fdims[a] = f->dims[a];
-            split(f->origin[a] - 0.5 * f->spacing[a], w.forigin[a], w.forigin_lo[a]);
-            split(f->spacing[a], w.fspacing[a], w.fspacing_lo[a]);
-            w.finv[a] = (float)(1.0 / f->spacing[a]);
+            w.forigin[a] = -0.5f;
+            w.forigin_lo[a] = 0.0f;
+            w.fspacing[a] = 1.0f;
+            w.fspacing_lo[a] = 0.0f;
+            w.finv[a] = 1.0f;
         }
         return MT_OK;
     }
@@ -712,10 +765,12 @@ mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
     cudaFree(raw);
     if (e != cudaSuccess) return cuda_fail(e, "field map upload");
     w.fmap = (const float4 *)pairs;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a) {   // the frame is this map's node grid
         w.fdims[a] = f->dims[a];
-        split(f->origin[a], w.forigin[a], w.forigin_lo[a]);
-        split(f->spacing[a], w.fspacing[a], w.fspacing_lo[a]);
+        w.forigin[a] = 0.0f;
+        w.forigin_lo[a] = 0.0f;
+        w.fspacing[a] = 1.0f;
+        w.fspacing_lo[a] = 0.0f;
         w.finv[a] = (float)(1.0 / f->spacing[a]);
     }
     return MT_OK;
@@ -761,7 +816,7 @@ mt_status mt_create(const mt_geometry_desc *g, const mt_field_desc *f, const mt_
     memset(&h->w, 0, sizeof(h->w));
     cudaGetDevice(&h->device);
     st = build_hist(hd, h->w, h->own);
-    if (st == MT_OK) st = build_geometry(g, h->w, h->own);
+    if (st == MT_OK) st = build_geometry(g, f, h->w, h->own);
     if (st == MT_OK) st = build_field(f, h->w, h->own);
     if (st != MT_OK) {
         mt_destroy(h);

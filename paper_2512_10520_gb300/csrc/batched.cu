@@ -55,7 +55,7 @@ struct mt_batch {
     mt::WorldParams *d_inst = nullptr;      // device copy of inst
     bool dirty = true;
     // launch shape chosen by mt_batch_autotune (0 = defaults)
-    int tuned_block = 0, tuned_S = 0;
+    int tuned_block = 0, tuned_S = 0, tuned_staging = 0;
     // CUDA graph of the last launch sequence and the arguments it was made for
     cudaGraphExec_t graph = nullptr;
     std::vector<char> graph_key;
@@ -140,9 +140,11 @@ __device__ __forceinline__ int64_t warp_append_u32(unsigned int *ctr, bool keep)
     return (int64_t)base + __popc(mask & ((1u << lane) - 1u));
 }
 
-// Pack the live muons of every instance into its region of live buffer 0.
-__global__ void __launch_bounds__(256) batch_init(const unsigned long long *off, int n_inst, const mt_muon_soa *soa,
-                                                  RunParams rp, LiveBuf out, unsigned int *cnt)
+// Pack the live muons of every instance into its region of live buffer 0
+// (positions in the instance's frame).
+__global__ void __launch_bounds__(256) batch_init(const WorldParams *inst, const unsigned long long *off, int n_inst,
+                                                  const mt_muon_soa *soa, RunParams rp, LiveBuf out,
+                                                  unsigned int *cnt)
 {
     const unsigned long long N = off[n_inst];
     const unsigned lane = threadIdx.x & 31u;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(256) batch_init(const unsigned long long *off,
             r.id_offset = soa[i].id_offset;
             r.instance = soa[i].instance;
             uint32_t a, b;
-            live = load_muon(soa[i], m, r, s, q, k, a, b);
+            live = load_muon(inst[i], soa[i], m, r, s, q, k, a, b);
         }
         // lanes of one warp may straddle two instances: aggregate per instance
         const unsigned act = __ballot_sync(0xFFFFFFFFu, live);
@@ -226,13 +228,18 @@ __global__ void __launch_bounds__(1024) batch_plan(const unsigned int *cnt_in, u
 }
 
 // One pass over every instance.  A block pops an item from the queue, which
-// names an instance (items of instances are contiguous), stages that world in
-// shared memory if it is not the one staged, and then its warps take chunks
-// of 32 of the instance's live entries from sub[i] until none are left, so a
-// warp whose muons stop early does not wait for the others.  Items whose
-// instance has nothing left to hand out are dropped without staging.
-template <int GEOM, int FIELD, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / BLOCK) batch_pass(const WorldParams *inst, const mt_muon_soa *soa,
+// names an instance (items of instances are contiguous), stages that world if
+// it is not the one staged, and then its warps take chunks of 32 of the
+// instance's live entries from sub[i] until none are left, so a warp whose
+// muons stop early does not wait for the others.  Items whose instance has
+// nothing left to hand out are dropped without staging.
+// WS (world staging): MT_BATCH_STAGE_SHARED copies the instance's
+// WorldParams into shared memory; MT_BATCH_STAGE_GLOBAL reads them in place
+// from the instance table (through L1), which saves the copy and a barrier
+// at every instance change.  The small tables (boxes, bin edges, slab index)
+// go to shared memory either way.
+template <int GEOM, int FIELD, int BLOCK, int WS>
+__global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / BLOCK) batch_pass(const WorldParams *__restrict__ inst, const mt_muon_soa *soa,
                                                    const unsigned long long *off, int n_inst, RunParams rp,
                                                    LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
                                                    unsigned int *cnt_out, const unsigned int *cof,
@@ -273,18 +280,26 @@ __global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / B
             __syncthreads();
             continue;
         }
+        const WorldParams *wp;
+        if constexpr (WS == MT_BATCH_STAGE_GLOBAL)
+            wp = inst + i;
+        else
+            wp = &wi;
         if (i != cur) {
-            const int words = (int)(sizeof(WorldParams) / 4);
-            const int *src = reinterpret_cast<const int *>(&inst[i]);
-            int *dst = reinterpret_cast<int *>(&wi);
-            for (int t = threadIdx.x; t < words; t += BLOCK) dst[t] = src[t];
+            if constexpr (WS != MT_BATCH_STAGE_GLOBAL) {
+                const int words = (int)(sizeof(WorldParams) / 4);
+                const int *src = reinterpret_cast<const int *>(&inst[i]);
+                int *dst = reinterpret_cast<int *>(&wi);
+                for (int t = threadIdx.x; t < words; t += BLOCK) dst[t] = src[t];
+            }
             if (threadIdx.x == 0) s_soa = soa[i];
             __syncthreads();
             RunParams r0 = rp;
-            stage_world(sw, wi, r0);
+            stage_world(sw, *wp, r0);
             __syncthreads();
             cur = i;
         }
+        const WorldParams &wr = *wp;
         const int64_t id0 = s_soa.id_offset;
         const uint32_t word = (uint32_t)s_soa.instance;
         const int64_t n_i = (int64_t)cnt_in[i];
@@ -308,12 +323,12 @@ __global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / B
                 int st = MT_ALIVE;
 #pragma unroll 1
                 for (; k < kend; ++k) {
-                    st = step<GEOM, FIELD, NoRecord, false>(wi, sw, s, q, k, id_lo, id_hi, word, rp);
+                    st = step<GEOM, FIELD, NoRecord, false>(wr, sw, s, q, k, id_lo, id_hi, word, rp);
                     if (st != MT_ALIVE) break;
                 }
                 if (st == MT_ALIVE && k >= rp.max_steps) st = MT_MAX_STEPS;
                 if (st != MT_ALIVE)
-                    store_muon(s_soa, idx, s, k, st);
+                    store_muon(wr, s_soa, idx, s, k, st);
                 else
                     keep = true;
             }
@@ -324,7 +339,7 @@ __global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / B
     }
 }
 
-template <int GEOM, int FIELD, int BLOCK>
+template <int GEOM, int FIELD, int BLOCK, int WS>
 static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
                              cudaStream_t st)
 {
@@ -332,14 +347,14 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_pass<GEOM, FIELD, BLOCK>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_pass<GEOM, FIELD, BLOCK, WS>, BLOCK, 0);
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t need = (ws.N + BLOCK - 1) / BLOCK;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     const int64_t ig = std::min<int64_t>(need < 1 ? 1 : need, 65535 * 8);
-    batch_init<<<(unsigned)ig, 256, 0, st>>>(ws.off, n_inst, ws.soa, rp, L[0], ws.cnt);
+    batch_init<<<(unsigned)ig, 256, 0, st>>>(b->d_inst, ws.off, n_inst, ws.soa, rp, L[0], ws.cnt);
     cudaError_t e = cudaGetLastError();
     const int passes = rp.max_steps > 0 ? (rp.max_steps + S - 1) / S : 1;
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
@@ -349,7 +364,7 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
         batch_plan<<<1, 1024, 0, st>>>(c_in, c_zero, n_inst, BLOCK, ws.cof, ws.queue, ws.sub);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        batch_pass<GEOM, FIELD, BLOCK><<<(unsigned)grid, BLOCK, 0, st>>>(b->d_inst, ws.soa, ws.off, n_inst, rp,
+        batch_pass<GEOM, FIELD, BLOCK, WS><<<(unsigned)grid, BLOCK, 0, st>>>(b->d_inst, ws.soa, ws.off, n_inst, rp,
                                                                         L[p & 1], L[(p + 1) & 1], c_in, c_out,
                                                                         ws.cof, ws.queue, ws.sub, S);
         e = cudaGetLastError();
@@ -357,25 +372,37 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
     return e;
 }
 
-template <int BLOCK>
-static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
-                                  cudaStream_t st)
+template <int BLOCK, int WS>
+static cudaError_t dispatch_batch_ws(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
+                                     cudaStream_t st)
 {
     const int f = b->field_kind;
     const bool staged = b->field_per_stage != 0;
-#define MT_BATCH_FIELDS(G)                                                                                 \
-    return f == MT_FIELD_MAP && staged ? run_batch<G, kFieldMapStaged, BLOCK>(b, ws, n_inst, rp, S, st)       \
-           : f == MT_FIELD_MAP         ? run_batch<G, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st)          \
-           : f == MT_FIELD_MAP_NEAREST ? run_batch<G, MT_FIELD_MAP_NEAREST, BLOCK>(b, ws, n_inst, rp, S, st)  \
-           : f == MT_FIELD_BOX         ? run_batch<G, MT_FIELD_BOX, BLOCK>(b, ws, n_inst, rp, S, st)          \
-                                       : run_batch<G, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st)
+#define MT_BATCH_FIELDS(G)                                                                                     \
+    return f == MT_FIELD_MAP && staged ? run_batch<G, kFieldMapStaged, BLOCK, WS>(b, ws, n_inst, rp, S, st)      \
+           : f == MT_FIELD_MAP         ? run_batch<G, MT_FIELD_MAP, BLOCK, WS>(b, ws, n_inst, rp, S, st)         \
+           : f == MT_FIELD_MAP_NEAREST ? run_batch<G, MT_FIELD_MAP_NEAREST, BLOCK, WS>(b, ws, n_inst, rp, S, st) \
+           : f == MT_FIELD_BOX         ? run_batch<G, MT_FIELD_BOX, BLOCK, WS>(b, ws, n_inst, rp, S, st)         \
+                                       : run_batch<G, MT_FIELD_NONE, BLOCK, WS>(b, ws, n_inst, rp, S, st)
     if (b->geom_kind == MT_GEOM_BOXES) MT_BATCH_FIELDS(MT_GEOM_BOXES);
     if (b->geom_kind == MT_GEOM_POLYHEDRA) MT_BATCH_FIELDS(MT_GEOM_POLYHEDRA);
 #undef MT_BATCH_FIELDS
-    if (f == MT_FIELD_MAP && staged) return run_batch<MT_GEOM_VOXELS, kFieldMapStaged, BLOCK>(b, ws, n_inst, rp, S, st);
-    if (f == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK>(b, ws, n_inst, rp, S, st);
-    if (f == MT_FIELD_MAP_NEAREST) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST, BLOCK>(b, ws, n_inst, rp, S, st);
-    return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK>(b, ws, n_inst, rp, S, st);
+    if (f == MT_FIELD_MAP && staged)
+        return run_batch<MT_GEOM_VOXELS, kFieldMapStaged, BLOCK, WS>(b, ws, n_inst, rp, S, st);
+    if (f == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK, WS>(b, ws, n_inst, rp, S, st);
+    if (f == MT_FIELD_MAP_NEAREST)
+        return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST, BLOCK, WS>(b, ws, n_inst, rp, S, st);
+    return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK, WS>(b, ws, n_inst, rp, S, st);
+}
+
+static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int block, int S,
+                                  int staging, cudaStream_t st)
+{
+    if (staging == MT_BATCH_STAGE_GLOBAL)
+        return block == 128 ? dispatch_batch_ws<128, MT_BATCH_STAGE_GLOBAL>(b, ws, n_inst, rp, S, st)
+                            : dispatch_batch_ws<256, MT_BATCH_STAGE_GLOBAL>(b, ws, n_inst, rp, S, st);
+    return block == 128 ? dispatch_batch_ws<128, MT_BATCH_STAGE_SHARED>(b, ws, n_inst, rp, S, st)
+                        : dispatch_batch_ws<256, MT_BATCH_STAGE_SHARED>(b, ws, n_inst, rp, S, st);
 }
 
 }  // namespace mt
@@ -470,7 +497,7 @@ mt_status mt_batch_set_instance(mt_batch *b, int32_t i, const mt_geometry_desc *
     DevGuardB guard(b->device);
     b->inst_own[i].release();
     WorldParams w = b->tables;
-    st = build_geometry(g, w, b->inst_own[i]);
+    st = build_geometry(g, f, w, b->inst_own[i]);
     if (st == MT_OK) st = build_field(f, w, b->inst_own[i]);
     if (st != MT_OK) {
         b->inst_own[i].release();
@@ -536,8 +563,11 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     if (cfg) c = *cfg;
     int block = c.block ? c.block : (b->tuned_block ? b->tuned_block : 256);
     int S = c.steps_per_pass ? c.steps_per_pass : (b->tuned_S ? b->tuned_S : 64);
-    if ((block != 128 && block != 256) || S < 1) {
-        set_error("batch launch: block must be 128 or 256 and steps_per_pass >= 1 (got %d, %d)", block, S);
+    int staging = c.staging ? c.staging : (b->tuned_staging ? b->tuned_staging : MT_BATCH_STAGE_SHARED);
+    if ((block != 128 && block != 256) || S < 1 ||
+        (staging != MT_BATCH_STAGE_SHARED && staging != MT_BATCH_STAGE_GLOBAL)) {
+        set_error("batch launch: block must be 128 or 256, steps_per_pass >= 1 and staging %d or %d (got %d, %d, %d)",
+                  MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL, block, S, staging);
         return MT_ERR_INVALID_ARG;
     }
     std::vector<unsigned long long> off(b->n_inst + 1, 0);
@@ -610,11 +640,11 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     if (e == cudaSuccess) {
         if (c.use_graph) {
             // capture the launch sequence once per (arguments) and replay it
-            std::vector<char> key(sizeof(void *) + 3 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 8);
+            std::vector<char> key(sizeof(void *) + 4 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 8);
             char *kp = key.data();
             memcpy(kp, &base, sizeof(void *));
             kp += sizeof(void *);
-            const int ints[3] = {block, S, max_steps};
+            const int ints[4] = {block, S, max_steps, staging};
             memcpy(kp, ints, sizeof(ints));
             kp += sizeof(ints);
             memcpy(kp, &step_len, sizeof(float));
@@ -632,8 +662,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
                 cudaGraph_t gr = nullptr;
                 if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    cudaError_t le = block == 128 ? dispatch_batch<128>(b, ws, b->n_inst, rp, S, cap)
-                                                  : dispatch_batch<256>(b, ws, b->n_inst, rp, S, cap);
+                    cudaError_t le = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, cap);
                     e = cudaStreamEndCapture(cap, &gr);
                     if (le != cudaSuccess) e = le;
                 }
@@ -644,8 +673,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
             }
             if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, cs);
         } else {
-            e = block == 128 ? dispatch_batch<128>(b, ws, b->n_inst, rp, S, cs)
-                             : dispatch_batch<256>(b, ws, b->n_inst, rp, S, cs);
+            e = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, cs);
         }
     }
     if (own) {
@@ -677,7 +705,7 @@ mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t 
         M += m[i];
     }
     if (M == 0) {
-        if (best) *best = mt_batch_cfg{256, 64, 0, 0, nullptr, 0};
+        if (best) *best = mt_batch_cfg{256, 64, 0, MT_BATCH_STAGE_SHARED, nullptr, 0};
         return MT_OK;
     }
     const size_t per = 4 * 6 + 1 + 4 + 1;   // bytes per muon over the nine arrays
@@ -723,17 +751,20 @@ mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t 
         for (int a = 0; a < 9 && e == cudaSuccess; ++a)
             e = cudaMemcpyAsync(dst[a], src[a], sz[a], cudaMemcpyDeviceToDevice, cs);
     }
+    // the search: block size x steps per pass x world staging
     const int blocks[2] = {128, 256};
-    const int Ss[3] = {32, 64, 128};
+    const int Ss[5] = {32, 64, 128, 256, 512};
+    const int stagings[2] = {MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL};
     float best_ms = 1e30f;
-    mt_batch_cfg bc = {256, 64, 0, 0, nullptr, 0};
+    mt_batch_cfg bc = {256, 64, 0, MT_BATCH_STAGE_SHARED, nullptr, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     mt_status st = MT_OK;
+    for (int gi = 0; gi < 2 && e == cudaSuccess && st == MT_OK; ++gi)
     for (int bi = 0; bi < 2 && e == cudaSuccess && st == MT_OK; ++bi)
-        for (int si_ = 0; si_ < 3 && e == cudaSuccess && st == MT_OK; ++si_) {
-            mt_batch_cfg c = {blocks[bi], Ss[si_], 0, 0, nullptr, 0};
+        for (int si_ = 0; si_ < 5 && e == cudaSuccess && st == MT_OK; ++si_) {
+            mt_batch_cfg c = {blocks[bi], Ss[si_], 0, stagings[gi], nullptr, 0};
             for (int rep = 0; rep < 2 && e == cudaSuccess && st == MT_OK; ++rep) {   // warm-up, then timed
                 e = cudaMemcpyAsync(work, init, (size_t)M * per + 9 * 256, cudaMemcpyDeviceToDevice, cs);
                 if (e != cudaSuccess) break;
@@ -756,6 +787,7 @@ mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t 
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     b->tuned_block = bc.block;
     b->tuned_S = bc.steps_per_pass;
+    b->tuned_staging = bc.staging;
     if (best) *best = bc;
     return MT_OK;
 }

@@ -42,7 +42,7 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
     const int64_t need = (n + kBlock - 1) / kBlock;
     if (grid > need) grid = need;
     const int64_t init_grid = need < 65535 * 8 ? need : 65535 * 8;
-    compact_init<<<(unsigned)init_grid, kBlock, 0, st>>>(soa, n, rp, buf[0], ctr);
+    compact_init<<<(unsigned)init_grid, kBlock, 0, st>>>(w, soa, n, rp, buf[0], ctr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // a muon that starts at step 0 needs ceil(max_steps / S) passes

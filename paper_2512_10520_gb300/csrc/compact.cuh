@@ -31,9 +31,10 @@ constexpr int pass_min_blocks()
 namespace mt {
 
 // Pack the live muons (status ALIVE or MAX_STEPS, finite state) of the
-// caller's arrays into a live list; non-finite states are marked MT_INVALID.
-static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa soa, int64_t n, const RunParams rp,
-                                                       LiveBuf out, unsigned long long *ctr)
+// caller's arrays into a live list, positions in the world's frame; non-finite
+// states are marked MT_INVALID.
+static __global__ void __launch_bounds__(kBlock) compact_init(const WorldParams w, const mt_muon_soa soa, int64_t n,
+                                                              const RunParams rp, LiveBuf out, unsigned long long *ctr)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -42,7 +43,7 @@ static __global__ void __launch_bounds__(kBlock) compact_init(const mt_muon_soa 
         float q = 0.0f;
         int k = 0;
         uint32_t id_lo, id_hi;
-        const bool live = m < n && load_muon(soa, m, rp, s, q, k, id_lo, id_hi);
+        const bool live = m < n && load_muon(w, soa, m, rp, s, q, k, id_lo, id_hi);
         const int64_t slot = warp_append(&ctr[0], live);
         if (live) put_live(out, slot, s, q, k, m);
     }
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kBlock, pass_min_blocks<GEOM, FIELD>()) compac
             }
             if (r == MT_ALIVE && k >= rp.max_steps) r = MT_MAX_STEPS;
             if (r != MT_ALIVE)
-                store_muon(soa, idx, s, k, r);
+                store_muon(w, soa, idx, s, k, r);
             else
                 keep = true;
         }

@@ -61,18 +61,30 @@ struct WorldParams {
     const float4 *poly;            // solids: [n_box][6] float4 (see api.cu: build_geometry)
     const double *poly64;          // solids: [n_box][18] z0, z1, bottom[4][2], top[4][2]
     const float4 *pinner;          // solids: [n_box] inner rectangle (x0, x1, y0, y1)
+    // world bounds in frame units: the muon leaves where x >= xmax or x <= xmin
+    // (|x| >= x_max in metres), likewise y, or z >= zmax
     float xmax_hi, xmax_lo, ymax_hi, ymax_lo, zmax_hi, zmax_lo;
+    float xmin_hi, xmin_lo, ymin_hi, ymin_lo;
     float pmin2;
+    // Frame of the muon position: the state holds u = (r - o) / s per axis, in
+    // cell units of the field map's node grid when there is a map (node i of an
+    // axis at u = i), else metres (o = 0, s = 1).  Every geometric constant of
+    // the world (faces, bounds, voxel and slab grids, solids) is stored in the
+    // same units.  o, s and 1/s as hi + lo pairs.
+    float fro_h[3], fro_l[3];
+    float frs_h[3], frs_l[3];
+    float fri_h[3], fri_l[3];
     // field
     int32_t field_kind;
     int32_t field_per_stage;       // MT_FIELD_MAP read at every RK4 stage (kernels: kFieldMapStaged)
     const float4 *fmap;            // trilinear: x-adjacent node pairs; nearest: nodes [nz][ny][nx]
     int32_t fdims[3];
+    // nearest-node cells in frame units (origin -1/2, spacing 1)
     float forigin[3];
     float forigin_lo[3];
     float fspacing[3];
     float fspacing_lo[3];
-    float finv[3];
+    float finv[3];                 // trilinear map: 1 / node spacing in 1/m (field gradients)
     // histograms
     const HistRec *hist;
     const uint32_t *guide;
@@ -144,7 +156,7 @@ mt_status validate_hist(const mt_hist_desc *h);
 mt_status validate_geometry(const mt_geometry_desc *g, int n_mat);
 mt_status validate_field(const mt_field_desc *f, const mt_geometry_desc *g);
 mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own);
-mt_status build_geometry(const mt_geometry_desc *g, WorldParams &w, DevOwner &own);
+mt_status build_geometry(const mt_geometry_desc *g, const mt_field_desc *f, WorldParams &w, DevOwner &own);
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own);
 void noalloc_prepare(const WorldParams &w, int dev);   // noalloc.cu
 }  // namespace mt

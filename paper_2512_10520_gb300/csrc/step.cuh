@@ -5,7 +5,9 @@
 // (compensated accumulation), so 1500 steps of FP32 arithmetic stay within
 // ~1e-9 relative of the exact track; every discrete decision (box faces, world
 // bounds, momentum-bin edges, voxel faces) compares the full hi + lo value
-// against bounds also stored as hi + lo pairs.  The only stochastic input is one
+// against bounds also stored as hi + lo pairs.  The position is held in the
+// world's frame (WorldParams): cell units of the field map when there is one,
+// so that the map's cell and in-cell fraction come straight from the state.  The only stochastic input is one
 // Philox4x32-10 call per step in matter, keyed by the seed and counted by
 // (step, muon id, instance), so a muon's track does not depend on which
 // thread, block or launch runs it.
@@ -72,8 +74,15 @@ struct State {
     float xl, yl, zl, pxl, pyl, pzl;
 };
 
+// Histogram records staged in shared memory when the set has at most this many
+// (n_mat x n_pbin); larger sets read them from global memory.  A warp's lanes
+// mostly hold different (material, bin) records, so a global load of them takes
+// one L1 wavefront per lane where shared memory serves 8 lanes per wavefront.
+constexpr int kHistSmem = 512;
+
 // Shared-memory copy of the small per-world tables.
 struct SmemWorld {
+    HistRec hist[kHistSmem];
     float lo_hi[3][MT_MAX_BOXES], lo_lo[3][MT_MAX_BOXES];
     float hi_hi[3][MT_MAX_BOXES], hi_lo[3][MT_MAX_BOXES];
     float B[3][MT_MAX_BOXES];
@@ -104,6 +113,8 @@ __device__ __forceinline__ void stage_world(SmemWorld &sw, const WorldParams &w,
 #pragma unroll
         for (int a = 0; a < 3; ++a) sw.alpha[a][t] = (rp.alpha && t < rp.n_block) ? rp.alpha[3 * t + a] : 1.0f;
     for (int t = threadIdx.x; t <= w.n_pbin; t += blockDim.x) sw.e2[t] = w.e2[t];
+    if (w.n_mat * w.n_pbin <= kHistSmem)
+        for (int t = threadIdx.x; t < w.n_mat * w.n_pbin; t += blockDim.x) sw.hist[t] = w.hist[t];
     for (int t = threadIdx.x; t < kZSlabs; t += blockDim.x) sw.zmask[t] = w.zmask ? w.zmask[t] : 0u;
     if (w.pinner)
         for (int t = threadIdx.x; t < w.n_box; t += blockDim.x) sw.inner[t] = w.pinner[t];
@@ -219,7 +230,7 @@ static __device__ __noinline__ bool in_solid_fp64(
     const WorldParams &w, int b, const State &s)
 {
     // one edge at a time, both ends recomputed from memory: few values live
-    const double *d = w.poly64 + 18 * b;
+    const double *d = w.poly64 + 18 * b;   // the solid in frame units
     const double x = (double)s.x + (double)s.xl, y = (double)s.y + (double)s.yl, z = (double)s.z + (double)s.zl;
     const double z0 = __ldg(d), z1 = __ldg(d + 1);
     const double t = (z - z0) / (z1 - z0);
@@ -238,7 +249,8 @@ static __device__ __noinline__ bool in_solid_fp64(
 
 // Eq. 2 with a certified FP32 filter, for a point already known to lie in the
 // solid's z range.  Each S_i is formed in FP32 from the hi + lo position and
-// the interpolated slice.  Its rounding error (from t, v_i, e_i, dx, dy and S)
+// the interpolated slice, both in frame units (a positive diagonal scaling of
+// the plane keeps the sign of every S_i).  Its rounding error (from t, v_i, e_i, dx, dy and S)
 // is at most 14 eps (|e_x| + |e_y| + 2M) (|dx| + |dy| + 2M), eps = 2^-24, M the
 // solid's coordinate scale; the solid's constant bound is 100 eps times that
 // product's maximum over the points that reach the test (its bounding box).
@@ -441,8 +453,10 @@ __device__ __forceinline__ float log_axis_value(float4 h, int a, float u)
 // z axis is p^.  Written as p <- p + c1 p + P c2 t, with dz = P c1 and dt = P c2,
 // where t = R x^ cos(phi) + R y^ sin(phi) is the rotated transverse unit vector
 // (R: the Rodrigues rotation taking z^ to p^).  The whole increment is small,
-// so it is accumulated into the hi + lo momentum.
-__device__ __forceinline__ void scatter(State &s, float c1, float c2, float cphi, float sphi)
+// so it is accumulated into the hi + lo momentum.  Returns 1/|p| before the
+// update.  g = 1/(1 + uz) scales only the transverse kick (|c2| <~ 1e-2 of |p|),
+// so its 2-ulp fast reciprocal moves p by ~1e-9 relative at most.
+__device__ __forceinline__ float scatter(State &s, float c1, float c2, float cphi, float sphi)
 {
     const float P2 = p2_of(s);
     float rP = rsqrtf(P2);
@@ -457,7 +471,8 @@ __device__ __forceinline__ void scatter(State &s, float c1, float c2, float cphi
         ty = -sphi;
         tz = 0.0f;
     } else {
-        const float g = uz >= 0.0f ? 1.0f / (1.0f + uz) : (1.0f - uz) / s2;   // 1/(1+uz)
+        // 1/(1+uz); for uz < 0, (1 - uz)/s2 avoids the cancellation in 1 + uz
+        const float g = __fdividef(uz >= 0.0f ? 1.0f : 1.0f - uz, uz >= 0.0f ? 1.0f + uz : s2);
         const float wv = fmaf(cphi, ux, sphi * uy);
         tx = fmaf(-(ux * wv), g, cphi);
         ty = fmaf(-(uy * wv), g, sphi);
@@ -466,29 +481,24 @@ __device__ __forceinline__ void scatter(State &s, float c1, float c2, float cphi
     acc(s.px, s.pxl, fmaf(c1, s.px, kick * tx));
     acc(s.py, s.pyl, fmaf(c1, s.py, kick * ty));
     acc(s.pz, s.pzl, fmaf(c1, s.pz, kick * tz));
+    return rP;
 }
 
 // a + t (b - a)
 __device__ __forceinline__ float lerp(float t, float a, float b) { return fmaf(t, b - a, a); }
 
-// Cell index and in-cell fraction of one axis of the node map.  The offset from
-// the cell's lower node, (x - origin) - i * spacing, is formed from hi + lo
-// pairs, so the fraction carries ~1e-7 relative error however far the cell is
-// from the origin (the plain FP32 coordinate would lose ~2e-7 m, which matters
-// where the field changes by tens of T/m at a magnet edge).
-__device__ __forceinline__ bool map_axis(float xh, float xl, float oh, float ol, float sh, float sl, float inv, int n,
-                                         int &i, float &t)
+// Cell index and in-cell fraction of one axis of the node map, from the
+// position in cell units (uh + ul): the cell is floor(uh) (the last cell at the
+// far node) and the fraction (uh - i) + ul, whose subtraction is exact, so the
+// fraction carries the position's full ~1e-14 relative precision however far
+// the cell is from the origin.  False outside [0, n - 1].  (When uh is a whole
+// number and ul < 0 the fraction is a hair below 0 in the upper cell: the
+// trilinear value is continuous across the face, so this is the same value.)
+__device__ __forceinline__ bool cell_axis(float uh, float ul, int n, int &i, float &t)
 {
-    float dh, de;
-    two_sum(xh, -oh, dh, de);
-    const float dl = de + (xl - ol);
-    const float u = (dh + dl) * inv;
-    if (!(u >= 0.0f && u <= (float)(n - 1))) return false;
-    i = min((int)u, n - 2);
-    const float fi = (float)i;
-    const float ph = fi * sh;
-    const float pl = fmaf(fi, sl, fmaf(fi, sh, -ph));
-    t = ((dh - ph) + (dl - pl)) * inv;
+    if (!(uh >= 0.0f && uh <= (float)(n - 1))) return false;
+    i = min(__float2int_rd(uh), n - 2);
+    t = (uh - (float)i) + ul;
     return true;
 }
 
@@ -523,9 +533,7 @@ __device__ __forceinline__ float3 field_map(const WorldParams &w, const State &s
     const int nx = w.fdims[0], ny = w.fdims[1], nz = w.fdims[2];
     int i, j, k;
     float tx, ty, tz;
-    if (!map_axis(s.x, s.xl, w.forigin[0], w.forigin_lo[0], w.fspacing[0], w.fspacing_lo[0], w.finv[0], nx, i, tx) ||
-        !map_axis(s.y, s.yl, w.forigin[1], w.forigin_lo[1], w.fspacing[1], w.fspacing_lo[1], w.finv[1], ny, j, ty) ||
-        !map_axis(s.z, s.zl, w.forigin[2], w.forigin_lo[2], w.fspacing[2], w.fspacing_lo[2], w.finv[2], nz, k, tz))
+    if (!cell_axis(s.x, s.xl, nx, i, tx) || !cell_axis(s.y, s.yl, ny, j, ty) || !cell_axis(s.z, s.zl, nz, k, tz))
         return make_float3(0.0f, 0.0f, 0.0f);
     const int64_t row = nx - 1;
     const float4 *p00 = w.fmap + 2 * (((int64_t)k * ny + j) * row + i);
@@ -578,12 +586,22 @@ __device__ __forceinline__ void cross_h(float ax, float ay, float az, float hx, 
 // dr = (d/P0) w and dp = L w: four cross products and no stage sums.  This is the
 // same map as the stage form in exact arithmetic, with fewer roundings (against
 // an FP64 stage-form transport: smaller position errors; and 2% less time per step).
-__device__ __forceinline__ void rk4(State &s, float3 B, float q, float d, float kd)
+// Position increment dr (metres) in frame units: dr (1/s) with 1/s held as a
+// hi + lo pair, so the frame adds no systematic scale error to the track (a
+// float 1/s alone would stretch every step by up to 3e-8).
+__device__ __forceinline__ float to_units(float dr, float ih, float il) { return fmaf(dr, ih, dr * il); }
+
+// rP0 = 1/P0 when the caller knows it (> 0), else it is computed from p.  w:
+// the world, for its position frame.
+__device__ __forceinline__ void rk4(State &s, float3 B, float q, float d, float kd, float rP0, const WorldParams &w)
 {
     const float px = s.px, py = s.py, pz = s.pz;
-    const float P2 = p2_of(s);
-    float rP = rsqrtf(P2);
-    rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
+    float rP = rP0;
+    if (!(rP > 0.0f)) {
+        const float P2 = p2_of(s);
+        rP = rsqrtf(P2);
+        rP = rP * fmaf(-0.5f * P2 * rP, rP, 1.5f);
+    }
     const float c = (kd * q) * rP;
     const float hx = c * B.x, hy = c * B.y, hz = c * B.z;
     float ax, ay, az, bx, by, bz;
@@ -594,9 +612,9 @@ __device__ __forceinline__ void rk4(State &s, float3 B, float q, float d, float 
     const float wx = px + ax, wy = py + ay, wz = pz + az;                           // w
     cross_h(wx, wy, wz, hx, hy, hz, bx, by, bz);                                  // L w
     const float a = d * rP;
-    acc(s.x, s.xl, a * wx);
-    acc(s.y, s.yl, a * wy);
-    acc(s.z, s.zl, a * wz);
+    acc(s.x, s.xl, to_units(a * wx, w.fri_h[0], w.fri_l[0]));
+    acc(s.y, s.yl, to_units(a * wy, w.fri_h[1], w.fri_l[1]));
+    acc(s.z, s.zl, to_units(a * wz, w.fri_h[2], w.fri_l[2]));
     acc(s.px, s.pxl, bx);
     acc(s.py, s.pyl, by);
     acc(s.pz, s.pzl, bz);
@@ -604,10 +622,18 @@ __device__ __forceinline__ void rk4(State &s, float3 B, float q, float d, float 
 
 // RK4 with the field read at each stage's position (variant of the step, see
 // mt_field_desc.per_stage): B1 is the scaled field at the step's start and sc
-// the block scale applied to the later stages.  Stage positions are carried in
-// the lo words (r + (d/2) p/P0, r + (d/2) p2/P0, r + d p3/P0), which the map
-// lookup reads as hi + lo pairs.  The updates are those of rk4 with h_i from
-// each stage's field.
+// the block scale applied to the later stages.  Stage positions r + (d/2) p/P0,
+// r + (d/2) p2/P0 and r + d p3/P0 are formed as normalised hi + lo pairs (the
+// map lookup takes its cell from the hi word).  The updates are those of rk4
+// with h_i from each stage's field.
+__device__ __forceinline__ void stage_at(State &t, const State &s, float ax, float ay, float az, float px, float py,
+                                         float pz)
+{
+    two_sum(s.x, fmaf(ax, px, s.xl), t.x, t.xl);
+    two_sum(s.y, fmaf(ay, py, s.yl), t.y, t.yl);
+    two_sum(s.z, fmaf(az, pz, s.zl), t.z, t.zl);
+}
+
 __device__ __forceinline__ void rk4_staged(const WorldParams &w, State &s, float3 B1, float3 sc, float q, float d,
                                            float kd)
 {
@@ -620,43 +646,45 @@ __device__ __forceinline__ void rk4_staged(const WorldParams &w, State &s, float
     float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
     cross_h(px, py, pz, c * B1.x, c * B1.y, c * B1.z, k1x, k1y, k1z);
     State t = s;
-    const float ha = 0.5f * a;
-    t.xl = fmaf(ha, px, s.xl);
-    t.yl = fmaf(ha, py, s.yl);
-    t.zl = fmaf(ha, pz, s.zl);
+    const float ax = a * w.fri_h[0], ay = a * w.fri_h[1], az = a * w.fri_h[2];   // metres -> frame units
+    stage_at(t, s, 0.5f * ax, 0.5f * ay, 0.5f * az, px, py, pz);
     float3 B = field_map(w, t);
     const float p2x = fmaf(0.5f, k1x, px), p2y = fmaf(0.5f, k1y, py), p2z = fmaf(0.5f, k1z, pz);
     cross_h(p2x, p2y, p2z, c * (sc.x * B.x), c * (sc.y * B.y), c * (sc.z * B.z), k2x, k2y, k2z);
-    t.xl = fmaf(ha, p2x, s.xl);
-    t.yl = fmaf(ha, p2y, s.yl);
-    t.zl = fmaf(ha, p2z, s.zl);
+    stage_at(t, s, 0.5f * ax, 0.5f * ay, 0.5f * az, p2x, p2y, p2z);
     B = field_map(w, t);
     const float p3x = fmaf(0.5f, k2x, px), p3y = fmaf(0.5f, k2y, py), p3z = fmaf(0.5f, k2z, pz);
     cross_h(p3x, p3y, p3z, c * (sc.x * B.x), c * (sc.y * B.y), c * (sc.z * B.z), k3x, k3y, k3z);
-    t.xl = fmaf(a, p3x, s.xl);
-    t.yl = fmaf(a, p3y, s.yl);
-    t.zl = fmaf(a, p3z, s.zl);
+    stage_at(t, s, ax, ay, az, p3x, p3y, p3z);
     B = field_map(w, t);
     cross_h(px + k3x, py + k3y, pz + k3z, c * (sc.x * B.x), c * (sc.y * B.y), c * (sc.z * B.z), k4x, k4y, k4z);
     const float sixth = 1.0f / 6.0f;
-    acc(s.x, s.xl, a * fmaf(sixth, k1x + k2x + k3x, px));
-    acc(s.y, s.yl, a * fmaf(sixth, k1y + k2y + k3y, py));
-    acc(s.z, s.zl, a * fmaf(sixth, k1z + k2z + k3z, pz));
+    acc(s.x, s.xl, to_units(a * fmaf(sixth, k1x + k2x + k3x, px), w.fri_h[0], w.fri_l[0]));
+    acc(s.y, s.yl, to_units(a * fmaf(sixth, k1y + k2y + k3y, py), w.fri_h[1], w.fri_l[1]));
+    acc(s.z, s.zl, to_units(a * fmaf(sixth, k1z + k2z + k3z, pz), w.fri_h[2], w.fri_l[2]));
     acc(s.px, s.pxl, sixth * (k1x + 2.0f * (k2x + k3x) + k4x));
     acc(s.py, s.pyl, sixth * (k1y + 2.0f * (k2y + k3y) + k4y));
     acc(s.pz, s.pzl, sixth * (k1z + 2.0f * (k2z + k3z) + k4z));
 }
 
-// Termination test of Algorithm 1 at the start of a step.
+// (xh + xl) <= (bh + bl) for normalised pairs.
+__device__ __forceinline__ bool le2(float xh, float xl, float bh, float bl)
+{
+    return xh < bh || (xh == bh && xl <= bl);
+}
+
+// Termination test of Algorithm 1 at the start of a step.  |x| >= x_max in
+// metres is x >= xmax or x <= xmin in frame units.
 __device__ __forceinline__ int check_stop(const WorldParams &w, const State &s, float P2)
 {
     if (P2 < w.pmin2) return MT_STOPPED;
     // strictly inside on the hi words: no pair test below can fire
-    if (s.z < w.zmax_hi && fabsf(s.x) < w.xmax_hi && fabsf(s.y) < w.ymax_hi) return MT_ALIVE;
+    if (s.z < w.zmax_hi && s.x < w.xmax_hi && s.x > w.xmin_hi && s.y < w.ymax_hi && s.y > w.ymin_hi)
+        return MT_ALIVE;
     if (ge2(s.z, s.zl, w.zmax_hi, w.zmax_lo)) return MT_EXIT_Z;
-    const float ax = fabsf(s.x), axl = s.x < 0.0f ? -s.xl : s.xl;
-    const float ay = fabsf(s.y), ayl = s.y < 0.0f ? -s.yl : s.yl;
-    if (ge2(ax, axl, w.xmax_hi, w.xmax_lo) || ge2(ay, ayl, w.ymax_hi, w.ymax_lo)) return MT_EXIT_XY;
+    if (ge2(s.x, s.xl, w.xmax_hi, w.xmax_lo) || le2(s.x, s.xl, w.xmin_hi, w.xmin_lo) ||
+        ge2(s.y, s.yl, w.ymax_hi, w.ymax_lo) || le2(s.y, s.yl, w.ymin_hi, w.ymin_lo))
+        return MT_EXIT_XY;
     return MT_ALIVE;
 }
 
@@ -665,7 +693,7 @@ __device__ __forceinline__ int check_stop(const WorldParams &w, const State &s, 
 // comes from exactly the arithmetic of the forward pass.
 struct NoRecord {
     __device__ __forceinline__ void begin(const State &, int, bool) {}
-    __device__ __forceinline__ void draw(float, float, float) {}
+    __device__ __forceinline__ void draw(const State &, float, float, float) {}
     __device__ __forceinline__ void field(float3) {}
 };
 
@@ -694,6 +722,10 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         mat = vm >= 0 ? vm : w.world_mat;
     }
     rec.begin(s, box, mat != 0);
+    // 1/P0 for the RK4 step when scattering set it: on the linear axes the
+    // update leaves |p| = (1 - f) P exactly (c1 and c2 are built so), so
+    // 1/P0 = (1/P) / (1 - f) and |p| need not be formed again
+    float rP0 = 0.0f;
     if (mat != 0) {
         const int ib = momentum_bin(w, sw, s, P2);
         const uint4 ctr = make_uint4((uint32_t)k, id_lo, id_hi, inst);
@@ -701,8 +733,13 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         // the guide (or alias) row of histogram h sits at h * its length, so its
         // load need not wait for the histogram record's
         const int h = (mat - 1) * w.n_pbin + ib;
-        const uint4 hraw = __ldg(reinterpret_cast<const uint4 *>(w.hist + h));
-        const HistRec hr = {hraw.x, hraw.y, __uint_as_float(hraw.z), __uint_as_float(hraw.w)};
+        HistRec hr;
+        if (w.n_mat * w.n_pbin <= kHistSmem) {
+            hr = sw.hist[h];
+        } else {
+            const uint4 hraw = __ldg(reinterpret_cast<const uint4 *>(w.hist + h));
+            hr = {hraw.x, hraw.y, __uint_as_float(hraw.z), __uint_as_float(hraw.w)};
+        }
         const uint32_t ab =
             w.sampler == MT_SAMPLER_ALIAS
                 ? sample_alias(w.alias + ((int64_t)h << w.alias_bits), w.alias_bits, w.theta_bits, rnd.x)
@@ -723,8 +760,9 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
         } else {
             coeffs_angle(f, th, c1, c2);
         }
-        rec.draw(c1, c2, phs);
-        scatter(s, c1, c2, -cp, -sp);
+        rec.draw(s, c1, c2, phs);   // s: the momentum before scattering
+        const float rP = scatter(s, c1, c2, -cp, -sp);
+        if (w.axes != MT_AXES_LOG) rP0 = __fdividef(rP, 1.0f - f);
     }
     float3 B = make_float3(0.0f, 0.0f, 0.0f);
     if (FIELD == MT_FIELD_BOX) {
@@ -748,29 +786,56 @@ __device__ __forceinline__ int step(const WorldParams &w, const SmemWorld &sw, S
     if (FIELD == kFieldMapStaged)
         rk4_staged(w, s, B, sc, q, rp.d, rp.kd);
     else
-        rk4(s, B, q, rp.d, rp.kd);
+        rk4(s, B, q, rp.d, rp.kd, rP0, w);
     return MT_ALIVE;
 }
 
-// Load muon m into registers.  Returns false (and handles the muon) when there
-// is nothing to transport: a terminal status is left as it is, a non-finite
-// state is marked MT_INVALID.
-__device__ __forceinline__ bool load_muon(const mt_muon_soa &soa, int64_t m, const RunParams &rp, State &s, float &q,
-                                          int &k, uint32_t &id_lo, uint32_t &id_hi)
+// Metres -> frame units: u = (x - o) / s as a hi + lo pair, from the exact
+// difference x - oh (two_sum) and a double-float product with 1/s (~1e-14
+// relative).  With o = 0 and s = 1 it returns (x, 0) exactly.
+__device__ __forceinline__ void to_frame(float x, float oh, float ol, float ih, float il, float &uh, float &ul)
+{
+    float dh, de;
+    two_sum(x, -oh, dh, de);
+    const float dl = de - ol;
+    const float p = dh * ih;
+    const float e = fmaf(dh, il, fmaf(dl, ih, fmaf(dh, ih, -p)));
+    uh = p + e;
+    ul = e - (uh - p);
+}
+
+// Frame units -> metres: o + u s from the hi + lo pairs, rounded once at the
+// end; with o = 0 and s = 1 it returns uh + ul, the plain sum of the pair.
+__device__ __forceinline__ float from_frame(float uh, float ul, float oh, float ol, float sh, float sl)
+{
+    const float p = uh * sh;
+    const float e = fmaf(uh, sl, fmaf(ul, sh, fmaf(uh, sh, -p)));
+    float th, te;
+    two_sum(oh, p, th, te);
+    return th + ((te + e) + ol);
+}
+
+// Load muon m into registers (position converted to the world's frame).
+// Returns false (and handles the muon) when there is nothing to transport: a
+// terminal status is left as it is, a non-finite state is marked MT_INVALID.
+__device__ __forceinline__ bool load_muon(const WorldParams &w, const mt_muon_soa &soa, int64_t m,
+                                          const RunParams &rp, State &s, float &q, int &k, uint32_t &id_lo,
+                                          uint32_t &id_hi)
 {
     const uint8_t st0 = soa.status[m];
     if (st0 != MT_ALIVE && st0 != MT_MAX_STEPS) return false;
-    s.x = soa.x[m];
-    s.y = soa.y[m];
-    s.z = soa.z[m];
+    const float x = soa.x[m], y = soa.y[m], z = soa.z[m];
     s.px = soa.px[m];
     s.py = soa.py[m];
     s.pz = soa.pz[m];
-    s.xl = s.yl = s.zl = s.pxl = s.pyl = s.pzl = 0.0f;
-    if (!(isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.px) && isfinite(s.py) && isfinite(s.pz))) {
+    s.pxl = s.pyl = s.pzl = 0.0f;
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(s.px) && isfinite(s.py) && isfinite(s.pz))) {
         soa.status[m] = MT_INVALID;
         return false;
     }
+    to_frame(x, w.fro_h[0], w.fro_l[0], w.fri_h[0], w.fri_l[0], s.x, s.xl);
+    to_frame(y, w.fro_h[1], w.fro_l[1], w.fri_h[1], w.fri_l[1], s.y, s.yl);
+    to_frame(z, w.fro_h[2], w.fro_l[2], w.fri_h[2], w.fri_l[2], s.z, s.zl);
     q = (float)soa.q[m];
     k = soa.steps[m];
     const uint64_t id = (uint64_t)(rp.id_offset + m);
@@ -779,11 +844,12 @@ __device__ __forceinline__ bool load_muon(const mt_muon_soa &soa, int64_t m, con
     return true;
 }
 
-__device__ __forceinline__ void store_muon(const mt_muon_soa &soa, int64_t m, const State &s, int k, int status)
+__device__ __forceinline__ void store_muon(const WorldParams &w, const mt_muon_soa &soa, int64_t m, const State &s,
+                                           int k, int status)
 {
-    soa.x[m] = s.x + s.xl;
-    soa.y[m] = s.y + s.yl;
-    soa.z[m] = s.z + s.zl;
+    soa.x[m] = from_frame(s.x, s.xl, w.fro_h[0], w.fro_l[0], w.frs_h[0], w.frs_l[0]);
+    soa.y[m] = from_frame(s.y, s.yl, w.fro_h[1], w.fro_l[1], w.frs_h[1], w.frs_l[1]);
+    soa.z[m] = from_frame(s.z, s.zl, w.fro_h[2], w.fro_l[2], w.frs_h[2], w.frs_l[2]);
     soa.px[m] = s.px + s.pxl;
     soa.py[m] = s.py + s.pyl;
     soa.pz[m] = s.pz + s.pzl;
@@ -793,7 +859,8 @@ __device__ __forceinline__ void store_muon(const mt_muon_soa &soa, int64_t m, co
 
 // Live-list entries of the compacting kernels (64 B per muon, four 16-byte
 // words in structure-of-arrays order): w0 = (x, y, z, q), w1 = (px, py, pz, k),
-// w2 = (xl, yl, zl, idx), w3 = (pxl, pyl, pzl, 0).
+// w2 = (xl, yl, zl, idx), w3 = (pxl, pyl, pzl, 0), the position in the world's
+// frame.
 struct LiveBuf {
     float4 *w0, *w1, *w2, *w3;
 };

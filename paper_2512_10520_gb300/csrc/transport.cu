@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kBlock) transport_kernel(const WorldParams w, 
         float q;
         int k;
         uint32_t id_lo, id_hi;
-        if (!load_muon(soa, m, rp, s, q, k, id_lo, id_hi)) continue;
+        if (!load_muon(w, soa, m, rp, s, q, k, id_lo, id_hi)) continue;
         int out = MT_MAX_STEPS;
 #pragma unroll 1
         for (; k < rp.max_steps; ++k) {
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kBlock) transport_kernel(const WorldParams w, 
                 break;
             }
         }
-        store_muon(soa, m, s, k, out);
+        store_muon(w, soa, m, s, k, out);
     }
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kBlock) transport_persistent(const WorldParams
                 const int64_t cand = (int64_t)base + __popc(need_mask & ((1u << lane) - 1u));
                 if (cand >= end)
                     m = end;
-                else if (load_muon(soa, cand, rp, s, q, k, id_lo, id_hi))
+                else if (load_muon(w, soa, cand, rp, s, q, k, id_lo, id_hi))
                     m = cand;
             }
         }
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) transport_persistent(const WorldParams
             else
                 r = step<GEOM, FIELD>(w, sw, s, q, k, id_lo, id_hi, (uint32_t)rp.instance, rp);
             if (r != MT_ALIVE) {
-                store_muon(soa, m, s, k, r);
+                store_muon(w, soa, m, s, k, r);
                 m = -1;
             } else {
                 ++k;

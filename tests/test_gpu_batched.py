@@ -175,11 +175,49 @@ def test_autotune_leaves_muons_and_results_unchanged(instances, batch):
     ref = _host(devs)
     devs = _dev(instances)
     before = _host(devs)
-    blk, S = batch.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, sample_per_instance=300)
-    assert blk in (128, 256) and S in (32, 64, 128)
+    blk, S, stg = batch.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, sample_per_instance=300,
+                                 cache=False)
+    assert blk in (128, 256) and S in (32, 64, 128, 256, 512) and stg in (1, 2)
     _assert_same(_host(devs), before)
     batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED)   # tuned shape
     _assert_same(_host(devs), ref)
+
+
+@pytest.mark.parametrize("staging", [1, 2])
+def test_world_staging_layouts_are_bit_identical(instances, batch, staging):
+    """The world parameters staged in shared memory or read in place from the
+    instance table: the same arithmetic, so the same bits."""
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=256, steps_per_pass=64,
+                    staging=1)
+    ref = _host(devs)
+    for S in (64, 256):
+        devs = _dev(instances)
+        batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=128, steps_per_pass=S,
+                        staging=staging)
+        _assert_same(_host(devs), ref)
+
+
+def test_autotune_cache_reuses_the_tuned_shape(instances, batch, tmp_path, monkeypatch):
+    """The second autotune of the same worlds, muons and arguments on the same GPU
+    reads the JSON cache instead of timing again."""
+    import json
+    from paper_2512_10520_gb300 import api
+    path = tmp_path / "tune.json"
+    monkeypatch.setattr(api, "_TUNE_CACHE", str(path))
+    devs = _dev(instances)
+    first = batch.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, sample_per_instance=200)
+    table = json.loads(path.read_text())
+    assert len(table) == 1 and list(table.values())[0] == list(first)
+    table[next(iter(table))] = [128, 512, 2]          # a planted entry is what the next call returns
+    path.write_text(json.dumps(table))
+    assert batch.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED,
+                          sample_per_instance=200) == (128, 512, 2)
+    assert batch.tuned == (128, 512, 2)
+    # another muon count is another workload
+    other = batch.autotune(devs[:-1] + [_dev(instances[-1:])[0]], gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS - 1,
+                           gen.BATCH_SEED, sample_per_instance=200)
+    assert len(json.loads(path.read_text())) == 2 and other[0] in (128, 256)
 
 
 def test_all_instances_empty(hist, instances):

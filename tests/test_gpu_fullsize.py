@@ -38,7 +38,8 @@ def test_worlds256_full_batch_sampled_parity():
             devs.append(mt.muons_to_device(inst["muons"]))
             if i in check:
                 kept[i] = inst
-        blk, S = b.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, sample_per_instance=2048)
+        blk, S, stg = b.autotune(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED,
+                                 sample_per_instance=2048)
         b.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, use_graph=True)
         torch.cuda.synchronize()
         assert sum(int(d["x"].numel()) for d in devs) > 3e7
