@@ -262,13 +262,15 @@ mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, flo
  *                       list (two 64-byte entries per muon plus 256 bytes, see
  *                       mt_transport_workspace_bytes) for the next pass; n must
  *                       be below 2^31;
- *  MT_LAUNCH_AUTO       the fastest measured form: MT_LAUNCH_COMPACT with 64 steps
- *                       per pass (the static grid for n >= 2^31). */
+ *  MT_LAUNCH_AUTO       the fastest measured form: MT_LAUNCH_COMPACT with the
+ *                       default pass length (the static grid for n >= 2^31). */
 enum { MT_LAUNCH_AUTO = 0, MT_LAUNCH_STATIC = 1, MT_LAUNCH_PERSISTENT = 2, MT_LAUNCH_COMPACT = 3 };
 typedef struct mt_launch_cfg {
     int32_t mode;             /* MT_LAUNCH_*                                              */
     int32_t blocks_per_sm;    /* 0 = as many as fit (occupancy calculator)                */
-    int32_t steps_per_pass;   /* MT_LAUNCH_COMPACT: steps between compactions, 0 = 64     */
+    int32_t steps_per_pass;   /* MT_LAUNCH_COMPACT: steps between compactions, 0 = the    */
+                              /*   longest of 64, 48, 32, 24, 16 whose slab of the field  */
+                              /*   map fits in 3/4 of L2 (64 without a map)               */
     int32_t reserved;
     void *workspace;          /* MT_LAUNCH_COMPACT: device scratch (256-byte aligned), or */
     int64_t workspace_bytes;  /*   NULL = taken from the stream-ordered allocator         */
@@ -306,7 +308,8 @@ enum { MT_BATCH_STAGE_SHARED = 1, MT_BATCH_STAGE_GLOBAL = 2 };
 
 typedef struct mt_batch_cfg {
     int32_t block;            /* threads per block: 128 or 256; 0 = tuned / 256      */
-    int32_t steps_per_pass;   /* steps between compactions; 0 = tuned / 64           */
+    int32_t steps_per_pass;   /* steps between compactions; 0 = tuned, else as the   */
+                              /*   plain transport picks it for the largest map        */
     int32_t use_graph;        /* 1 = capture the launch sequence in a CUDA graph once */
                               /*     per (workspace, sizes, arguments) and replay it  */
     int32_t staging;          /* MT_BATCH_STAGE_*; 0 = tuned / shared                 */
@@ -502,7 +505,7 @@ int32_t mt_bv_edges(const double *probes, const double *phi, int32_t n_probe, do
  * latency-critical path that cannot afford an allocation's synchronisation, or
  * a deployment whose memory use must be fixed when the library is loaded.  (The
  * paper has no counterpart: it describes no allocation policy.)
- * It runs the compacting transport (MT_LAUNCH_COMPACT, 64 steps per pass) with
+ * It runs the compacting transport (MT_LAUNCH_COMPACT, default pass length) with
  * its scratch list in an 8 MiB array that the library reserves in device
  * memory, held until the process exits; it calls no cudaMalloc, cudaFree or
  * other allocating routine.  CUDA creates a library's device objects and loads

@@ -562,7 +562,12 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     mt_batch_cfg c = {0, 0, 0, 0, nullptr, 0};
     if (cfg) c = *cfg;
     int block = c.block ? c.block : (b->tuned_block ? b->tuned_block : 256);
-    int S = c.steps_per_pass ? c.steps_per_pass : (b->tuned_S ? b->tuned_S : 64);
+    int S = c.steps_per_pass ? c.steps_per_pass : b->tuned_S;
+    if (!S) {   // untuned: the plain transport's choice for the instance with the largest map layers
+        S = 64;
+        for (int i = 0; i < b->n_inst; ++i)
+            if (b->is_set[i]) S = std::min(S, default_steps_per_pass(b->inst[i], step_len));
+    }
     int staging = c.staging ? c.staging : (b->tuned_staging ? b->tuned_staging : MT_BATCH_STAGE_SHARED);
     if ((block != 128 && block != 256) || S < 1 ||
         (staging != MT_BATCH_STAGE_SHARED && staging != MT_BATCH_STAGE_GLOBAL)) {

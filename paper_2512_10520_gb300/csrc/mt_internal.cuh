@@ -159,4 +159,5 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own);
 mt_status build_geometry(const mt_geometry_desc *g, const mt_field_desc *f, WorldParams &w, DevOwner &own);
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own);
 void noalloc_prepare(const WorldParams &w, int dev);   // noalloc.cu
+int default_steps_per_pass(const WorldParams &w, float step_len);   // transport.cu
 }  // namespace mt
