@@ -149,68 +149,16 @@ struct TapeEntry {
     float2 c;
 };
 
-// Two ways for the reverse pass to take the tape's HBM latency off its
-// critical path while it reverses step j: MT_ADJ_CP_ASYNC copies step j - 1
-// into the lane's own slot of shared memory with cp.async (measured on diff1e6:
-// backward 65 ms against 55 ms with direct loads, so off); MT_ADJ_PREFETCH
-// asks L1 for step j - 1's lines (prefetch.global.L1), which holds no register
-// or shared memory (56.0 ms against 57.3 ms without).
-#ifndef MT_ADJ_CP_ASYNC
-#define MT_ADJ_CP_ASYNC 0
-#endif
+// The reverse pass asks L1 for the lines of a lane's next tape step
+// (prefetch.global.L1) while it reverses the current one; the prefetch holds no
+// register or shared memory (measured on diff1e6: backward 56.0 ms against
+// 57.3 ms without; copying the next step into shared memory with cp.async
+// instead took 66 ms).
 #ifndef MT_ADJ_PREFETCH
 #define MT_ADJ_PREFETCH 1
 #endif
 
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
-// Shared-memory slots of one thread: two stages of four 16-byte planes.
-struct TapeStage {
-    float4 v[2][4];
-};
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Start copying step j of the lane's tape into stage j & 1 of its slot (plane
-// c is copied whether or not the step scattered; it is read only if it did).
-template <bool RB>
-__device__ __forceinline__ void tape_prefetch(const TapeRef<RB> &tr, int j, TapeStage &st)
-{
-    float4 *v = st.v[j & 1];
-    cp_async16(&v[0], tr.a(j));
-    cp_async16(&v[1], tr.b(j));
-    cp_async8(&v[2], tr.c(j));
-    if (RB) cp_async16(&v[3], tr.d(j));
-    cp_async_commit();
-}
-
-template <bool RB>
-__device__ __forceinline__ TapeEntry tape_staged(const TapeStage &st, int j)
-{
-    const float4 *v = st.v[j & 1];
-    TapeEntry t;
-    t.a = v[0];
-    t.b = v[1];
-    t.c = (__float_as_int(t.a.w) & 1) ? make_float2(v[2].x, v[2].y) : make_float2(0.0f, 0.0f);
-    t.d = RB ? v[3] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    return t;
-}
 
 template <bool RB>
 __device__ __forceinline__ TapeEntry load_tape(const TapeRef<RB> &tr, int j)
@@ -587,9 +535,6 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
 {
     __shared__ SmemWorld sw;
     __shared__ float sacc[3][MT_MAX_BOXES];
-#if MT_ADJ_CP_ASYNC
-    __shared__ TapeStage stage[kBlock];
-#endif
     const int64_t count = (int64_t)*count_p;
     if (wzero && blockIdx.x == 0 && threadIdx.x == 0) *wzero = 0ull;
     if (count == 0 || *flag) return;
@@ -613,21 +558,6 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
         const int ns = __float_as_int(ck.w3[i].w);
         float rb[3] = {adj[idx], adj[n + idx], adj[2 * n + idx]};
         float pb[3] = {adj[3 * n + idx], adj[4 * n + idx], adj[5 * n + idx]};
-#if MT_ADJ_CP_ASYNC
-        TapeStage &my = stage[threadIdx.x];
-        if (ns > 0) tape_prefetch(tr, ns - 1, my);
-#pragma unroll 1
-        for (int j = ns - 1; j >= 0; --j) {
-            if (j > 0) {
-                tape_prefetch(tr, j - 1, my);
-                cp_async_wait_one();
-            } else {
-                cp_async_wait_all();
-            }
-            const TapeEntry t = tape_staged<MT_TAPE_RECORD_B>(my, j);
-            reverse_step<GEOM, FIELD, MT_TAPE_RECORD_B>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
-        }
-#else
 #pragma unroll 1
         for (int j = ns - 1; j >= 0; --j) {
             const TapeEntry t = load_tape(tr, j);
@@ -641,7 +571,6 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
 #endif
             reverse_step<GEOM, FIELD, MT_TAPE_RECORD_B>(w, sw, t, q, rp.d, rp.kd, rb, pb, acc, sacc);
         }
-#endif
         adj[idx] = rb[0];
         adj[n + idx] = rb[1];
         adj[2 * n + idx] = rb[2];
