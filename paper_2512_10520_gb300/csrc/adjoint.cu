@@ -34,10 +34,11 @@ namespace mt {
 
 constexpr int kTapeMax = 64;
 
-// Resident blocks per SM of the reverse pass (3 blocks of 256 = 85 registers;
-// measured on diff1e6: 34.5 ms against 38.2 ms with 4 blocks, which spill).
+// Resident blocks per SM of the reverse pass: 4 blocks of 256 (64 registers, no
+// spill since the step's divides became fast reciprocals; measured on diff1e6,
+// K = 32: backward 52.8 ms against 53.8 ms at 3 blocks and 80 registers).
 #ifndef MT_ADJ_MIN_BLOCKS
-#define MT_ADJ_MIN_BLOCKS 3
+#define MT_ADJ_MIN_BLOCKS 4
 #endif
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -285,9 +286,9 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     const int meta = __float_as_int(t.a.w);
     const int box = (meta >> 8) - 1;
     const bool scat = meta & 1;
-    const float r[3] = {t.a.x, t.a.y, t.a.z};
-    const float p[3] = {t.b.x, t.b.y, t.b.z};
-    const float sm1 = t.b.w, kf = t.c.x;   // scattering coefficients c1, c2
+    const float r0[3] = {t.a.x, t.a.y, t.a.z};
+    const float p0[3] = {t.b.x, t.b.y, t.b.z};
+    const float sm10 = t.b.w, kf0 = t.c.x;   // scattering coefficients c1, c2
     // -- field before the block scale, evaluated again at the recorded r
     float Bm[3] = {0.0f, 0.0f, 0.0f};
     if (RB) {
@@ -302,9 +303,9 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
         }
     } else if (FIELD == MT_FIELD_MAP || FIELD == MT_FIELD_MAP_NEAREST) {
         State at;
-        at.x = r[0];
-        at.y = r[1];
-        at.z = r[2];
+        at.x = r0[0];
+        at.y = r0[1];
+        at.z = r0[2];
         at.xl = at.yl = at.zl = 0.0f;
         const float3 b = FIELD == MT_FIELD_MAP ? field_map(w, at) : field_map_nearest(w, at);
         Bm[0] = b.x;
@@ -318,8 +319,8 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
         cphi = -cphi;
     }
     // -- scattered momentum ps = p + sm1 p + P kf tv(u) (recomputed in FP32)
-    float ps[3] = {p[0], p[1], p[2]};
-    if (scat) scatter_fp32(p, sm1, kf, cphi, sphi, ps);
+    float ps[3] = {p0[0], p0[1], p0[2]};
+    if (scat) scatter_fp32(p0, sm10, kf0, cphi, sphi, ps);
     int blk = -1;
     float sc[3] = {1.0f, 1.0f, 1.0f};
     if (GEOM != MT_GEOM_VOXELS && FIELD != MT_FIELD_NONE && box >= 0) {
@@ -389,9 +390,11 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
     if (blk >= 0) acc.add(blk, Bb[0] * Bm[0], Bb[1] * Bm[1], Bb[2] * Bm[2], sacc);
     if (FIELD == MT_FIELD_MAP) {
         const float Bmb[3] = {sc[0] * Bb[0], sc[1] * Bb[1], sc[2] * Bb[2]};
-        field_map_jt(w, r, Bmb, rb);
+        field_map_jt(w, r0, Bmb, rb);
     }
     // -- scattering: ps = (1 + sm1) p + P kf tv(u), u = p / P, held draws (sm1, kf, phi)
+    const float(&p)[3] = p0;
+    const float sm1 = sm10, kf = kf0;
     if (!scat) {
         pb[0] = psb[0];
         pb[1] = psb[1];
