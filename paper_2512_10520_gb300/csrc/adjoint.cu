@@ -442,6 +442,12 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // FWD: the full-tape forward (finished muons stored, survivors appended to
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
+// gfin (recomputation only, may be null): dL/d(final state) [6][n].  The
+// backward is linear in it, so a muon whose six components are all zero has a
+// zero adjoint through every step and adds nothing to dL/dalpha: it is not
+// recomputed (its step count is set to 0).  With the acceptance loss that is
+// every stopped muon and every muon extrapolated 1.4 m or more outside the
+// acceptance (the sigmoids underflow to zero), most muons of a shield.
 // Resident blocks per SM of the recorded pass: 4 (64 registers; measured on
 // diff1e6 with the planes stored as soon as their values exist: checkpoint
 // backward 55.4 ms against 55.7 ms at 5 blocks, which spill 8 bytes).
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
               const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
               unsigned long long *tape_off, int64_t region_cap, unsigned int *flag, unsigned long long *work,
-              unsigned long long *wzero)
+              unsigned long long *wzero, const float *gfin, int64_t n)
 {
     __shared__ SmemWorld sw;
     const int64_t count = (int64_t)*cin;
@@ -494,7 +500,14 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
         float q = 0.0f;
         int k = 0;
         int64_t idx = 0;
-        if (i < count) {
+        bool zero_adjoint = false;
+        if (!FWD && gfin && i < count) {
+            const int64_t m = (int64_t)__float_as_int(in.w2[i].w);
+            zero_adjoint = gfin[m] == 0.0f && gfin[n + m] == 0.0f && gfin[2 * n + m] == 0.0f &&
+                           gfin[3 * n + m] == 0.0f && gfin[4 * n + m] == 0.0f && gfin[5 * n + m] == 0.0f;
+            if (zero_adjoint) reinterpret_cast<float *>(in.w3 + i)[3] = __int_as_float(0);
+        }
+        if (i < count && !zero_adjoint) {
             get_live(in, i, s, q, k, idx);
             tr.tid = i;
             const uint64_t id = (uint64_t)(rp.id_offset + idx);
@@ -561,6 +574,9 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
         const int ns = __float_as_int(ck.w3[i].w);
         float rb[3] = {adj[idx], adj[n + idx], adj[2 * n + idx]};
         float pb[3] = {adj[3 * n + idx], adj[4 * n + idx], adj[5 * n + idx]};
+        // a zero adjoint stays zero through the pass and adds nothing to dL/dalpha
+        if (rb[0] == 0.0f && rb[1] == 0.0f && rb[2] == 0.0f && pb[0] == 0.0f && pb[1] == 0.0f && pb[2] == 0.0f)
+            continue;
 #pragma unroll 1
         for (int j = ns - 1; j >= 0; --j) {
             const TapeEntry t = load_tape(tr, j);
@@ -699,7 +715,7 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
         tape_pass<GEOM, FIELD, true><<<grid, kBlock, 0, st>>>(
             w, soa, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
             live_buf_at(buf + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, K,
-            buf + T.region_off, toff + p, T.region_cap, flag, ctr + L.passes + 1 + p, nullptr);
+            buf + T.region_off, toff + p, T.region_cap, flag, ctr + L.passes + 1 + p, nullptr, nullptr, n);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -747,7 +763,7 @@ static int split_grid(const void *kernel, int per_sm_cap, int64_t work)
 // whose adjoint state it continues.
 template <int GEOM, int FIELD>
 static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
-                                 char *ck, float *adj, char *scratch)
+                                 char *ck, float *adj, char *scratch, const float *gfin)
 {
     const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
@@ -775,7 +791,7 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
         if (e != cudaSuccess) return;
         tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, aux>>>(
             w, mt_muon_soa{}, rp, lp, lp, ctr + p, nullptr, K, h + 256, reinterpret_cast<unsigned long long *>(h), cap,
-            reinterpret_cast<unsigned int *>(h + 64), wc, wc + 1);
+            reinterpret_cast<unsigned int *>(h + 64), wc, wc + 1, gfin, n);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev[p], aux);
     };
@@ -992,7 +1008,7 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
     char *tape = scratch;
     float *adj = dL_dinitial ? dL_dinitial : reinterpret_cast<float *>(scratch + tbytes);
     e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj, tape);
+    if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj, tape, dL_dfinal);
     if (e == cudaSuccess && alpha && n_block > 0) {
         const CkptLayout L = ckpt_layout(n, max_steps, ckpt_every);
         alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L.alpha_off), dL_dalpha,

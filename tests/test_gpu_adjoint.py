@@ -288,3 +288,44 @@ def test_tape_buffer_checks_and_autograd_mode():
             mt.acceptance_loss(fin).backward()
             grads.append(x.grad.cpu().numpy())
         np.testing.assert_allclose(grads[0], grads[1], rtol=1e-5, atol=1e-7 * np.abs(grads[1]).max())
+
+
+def test_zero_cotangents_are_skipped_exactly():
+    """The backward is linear in dL/d(final state), and a muon whose six components
+    are zero is neither recomputed nor reversed.  Check: with half the muons' rows
+    zeroed, dL/d(initial state) of those muons is exactly zero, and dL/dalpha is
+    additive over a split of the muons (each part skipping the other) and equals
+    the full-tape form's (whose reverse pass skips zero adjoints the same way)."""
+    import torch
+    import paper_2512_10520_gb300 as mt
+    wl = gen.workload("shield1e6", n=6000)
+    n, K = wl.n, 32
+    a = torch.as_tensor(_alpha(), dtype=torch.float32).cuda().contiguous()
+    rng = np.random.default_rng(9)
+    g_full = torch.as_tensor(rng.standard_normal((6, n)).astype(np.float32) * 1e-3).cuda()
+    part = torch.as_tensor(rng.random(n) < 0.5).cuda()
+    gA = (g_full * part).contiguous()
+    gB = (g_full * ~part).contiguous()
+    out = {}
+    with mt.World.from_workload(wl) as world:
+        ckpt = torch.empty(mt.mt_ckpt_bytes(n, wl.max_steps, K), dtype=torch.uint8, device="cuda")
+        dev = mt.muons_to_device(wl.muons)
+        mt.mt_transport_ckpt(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, K, ckpt)
+        for name, g in (("full", g_full.contiguous()), ("A", gA), ("B", gB)):
+            da = torch.empty_like(a)
+            gi = torch.empty((6, n), dtype=torch.float32, device="cuda")
+            mt.mt_adjoint_ckpt(world.handle, n, wl.step_len, wl.max_steps, wl.seed, a, K, ckpt, g, da, gi)
+            out[name] = (da.cpu().numpy().astype(np.float64), gi.cpu().numpy())
+        tape = torch.empty(mt.mt_tape_bytes(n, wl.max_steps, K), dtype=torch.uint8, device="cuda")
+        dev2 = mt.muons_to_device(wl.muons)
+        mt.mt_transport_tape(world.handle, dev2, wl.step_len, wl.max_steps, wl.seed, a, K, tape)
+        dt = torch.empty_like(a)
+        mt.mt_adjoint_tape(world.handle, n, wl.step_len, wl.max_steps, a, K, tape, gA, dt)
+        torch.cuda.synchronize()
+    pm = part.cpu().numpy()
+    assert np.all(out["A"][1][:, ~pm] == 0.0) and np.all(out["B"][1][:, pm] == 0.0)
+    np.testing.assert_array_equal(out["A"][1][:, pm], out["full"][1][:, pm])
+    gsum = out["A"][0] + out["B"][0]
+    assert np.linalg.norm(gsum - out["full"][0]) <= 1e-5 * np.linalg.norm(out["full"][0])
+    tp = dt.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(tp - out["A"][0]) <= 1e-5 * np.linalg.norm(out["A"][0])
