@@ -44,11 +44,12 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# the sources of the plain transport's kernels (compact_init, compact_pass) and their build flags
+# the sources of the plain transport's kernels (compact_init, compact_pass, sort_scan,
+# sort_scatter), of the world's device layout (api.cu) and their build flags
 _TRANSPORT_SOURCES = ("paper_2512_10520_gb300/csrc/step.cuh", "paper_2512_10520_gb300/csrc/compact.cuh",
                       "paper_2512_10520_gb300/csrc/compact.cu", "paper_2512_10520_gb300/csrc/transport.cu",
-                      "paper_2512_10520_gb300/csrc/mt_internal.cuh", "include/mt.h",
-                      "paper_2512_10520_gb300/_build.py")
+                      "paper_2512_10520_gb300/csrc/mt_internal.cuh", "paper_2512_10520_gb300/csrc/api.cu",
+                      "include/mt.h", "paper_2512_10520_gb300/_build.py")
 
 
 def _csrc_hash() -> str:
@@ -748,10 +749,12 @@ def run_mine(args):
 
     ev_k = []
     launch = {}
-    if args.mode != "auto" or args.blocks_per_sm or args.steps_per_pass:
+    if args.mode != "auto" or args.blocks_per_sm or args.steps_per_pass or args.order != "auto":
         launch = dict(mode={"auto": mt.MT_LAUNCH_AUTO, "static": mt.MT_LAUNCH_STATIC,
                             "persistent": mt.MT_LAUNCH_PERSISTENT, "compact": mt.MT_LAUNCH_COMPACT}[args.mode],
-                      blocks_per_sm=args.blocks_per_sm, steps_per_pass=args.steps_per_pass)
+                      blocks_per_sm=args.blocks_per_sm, steps_per_pass=args.steps_per_pass,
+                      order={"auto": mt.MT_ORDER_AUTO, "always": mt.MT_ORDER_ALWAYS,
+                             "never": mt.MT_ORDER_NEVER}[args.order])
 
     def one_step(timed: bool):
         reset()
@@ -913,7 +916,7 @@ def run_mine(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "plain", "launch": args.mode,
+            "config": {"workload": WORKLOAD, "form": "plain", "launch": args.mode, "order": args.order,
                        "blocks_per_sm": args.blocks_per_sm, "muons_per_gpu": n, "max_steps": wl.max_steps,
                        "muon_steps_per_batch_per_gpu": steps_per_batch, "muons_per_s": n * ws * args.steps / elapsed,
                        "l2": "inputs larger than L2 (field map 764 MB in HBM vs 129 MB L2); no flush",
@@ -947,6 +950,8 @@ def main(argv=None):
     ap.add_argument("--mode", default="auto", choices=["auto", "static", "persistent", "compact"])
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--steps-per-pass", type=int, default=0)
+    ap.add_argument("--order", default="auto", choices=["auto", "always", "never"],
+                    help="spatial order of the live list between passes (compacting transport with a field map)")
     ap.add_argument("--batch-instances", type=int, default=256, help="worlds in the batched form")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched form (one JSON line)")
     ap.add_argument("--no-shield1e8", action="store_true", help="skip the shield1e8 (1e8 muons) form")

@@ -259,19 +259,27 @@ mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, flo
  *  MT_LAUNCH_COMPACT    lockstep passes: every live muon advances steps_per_pass
  *                       steps (warps take 32-muon chunks of the live list from
  *                       a per-pass counter), then the survivors are compacted into a scratch
- *                       list (two 64-byte entries per muon plus 256 bytes, see
+ *                       list (two 64-byte entries per muon plus 256 bytes and
+ *                       the spatial order's 128 KB, see
  *                       mt_transport_workspace_bytes) for the next pass; n must
- *                       be below 2^31;
+ *                       be below 2^31.  With a field map the survivors can be
+ *                       reordered by the coarse xy cell of the map they stand
+ *                       in (a counting sort every second pass), so a warp's
+ *                       muons share their field-map corners; the order changes
+ *                       no result;
  *  MT_LAUNCH_AUTO       the fastest measured form: MT_LAUNCH_COMPACT with the
  *                       default pass length (the static grid for n >= 2^31). */
 enum { MT_LAUNCH_AUTO = 0, MT_LAUNCH_STATIC = 1, MT_LAUNCH_PERSISTENT = 2, MT_LAUNCH_COMPACT = 3 };
+enum { MT_ORDER_AUTO = 0, MT_ORDER_ALWAYS = 1, MT_ORDER_NEVER = 2 };
 typedef struct mt_launch_cfg {
     int32_t mode;             /* MT_LAUNCH_*                                              */
     int32_t blocks_per_sm;    /* 0 = as many as fit (occupancy calculator)                */
     int32_t steps_per_pass;   /* MT_LAUNCH_COMPACT: steps between compactions, 0 = the    */
                               /*   longest of 64, 48, 32, 24, 16 whose slab of the field  */
                               /*   map fits in 3/4 of L2 (64 without a map)               */
-    int32_t reserved;
+    int32_t order;            /* MT_LAUNCH_COMPACT, field maps: spatial order of the live */
+                              /*   list: MT_ORDER_AUTO (at least 2^19 muons), _ALWAYS,    */
+                              /*   _NEVER                                                 */
     void *workspace;          /* MT_LAUNCH_COMPACT: device scratch (256-byte aligned), or */
     int64_t workspace_bytes;  /*   NULL = taken from the stream-ordered allocator         */
 } mt_launch_cfg;
@@ -280,8 +288,8 @@ typedef struct mt_launch_cfg {
 int64_t mt_transport_workspace_bytes(int64_t n);
 
 /* mt_transport_scaled with an explicit launch shape (cfg may be NULL = auto).
- * Errors as mt_transport, plus MT_ERR_INVALID_ARG for an unknown mode, a
- * negative blocks_per_sm or steps_per_pass, a workspace that is too small or
+ * Errors as mt_transport, plus MT_ERR_INVALID_ARG for an unknown mode or
+ * order, a negative blocks_per_sm or steps_per_pass, a workspace that is too small or
  * not 256-byte aligned, or n >= 2^31 in compact mode; MT_ERR_OOM if the
  * stream-ordered allocation fails. */
 mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,

@@ -10,6 +10,7 @@ from ._binding import (  # noqa: F401
     mt_abi_version, mt_last_error, mt_create, mt_destroy, mt_device_bytes,
     mt_transport, mt_transport_scaled, mt_transport_cfg, mt_transport_workspace_bytes,
     MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT, MT_SAMPLER_ICDF, MT_SAMPLER_ALIAS,
+    MT_ORDER_AUTO, MT_ORDER_ALWAYS, MT_ORDER_NEVER,
     mt_transport_noalloc, MT_NOALLOC_MAX_MUONS,
     mt_ckpt_bytes, mt_transport_ckpt, mt_adjoint_ckpt, mt_transport_adjoint, mt_acceptance_loss,
     mt_tape_bytes, mt_transport_tape, mt_adjoint_tape,

@@ -75,10 +75,11 @@ AXES = {"linear": MT_AXES_LINEAR, "log": MT_AXES_LOG}
 
 class mt_launch_cfg(C.Structure):
     _fields_ = [("mode", C.c_int32), ("blocks_per_sm", C.c_int32), ("steps_per_pass", C.c_int32),
-                ("reserved", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64)]
+                ("order", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64)]
 
 
 MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT = 0, 1, 2, 3
+MT_ORDER_AUTO, MT_ORDER_ALWAYS, MT_ORDER_NEVER = 0, 1, 2
 
 
 MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL = 1, 2
@@ -372,7 +373,7 @@ def mt_transport_workspace_bytes(n: int) -> int:
 
 def mt_transport_cfg(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, alpha=None,
                      mode: int = MT_LAUNCH_AUTO, blocks_per_sm: int = 0, id_offset: int = 0, instance: int = 0,
-                     stream=None, steps_per_pass: int = 0, workspace=None) -> None:
+                     stream=None, steps_per_pass: int = 0, workspace=None, order: int = MT_ORDER_AUTO) -> None:
     """mt_transport with field scales (or None) and an explicit launch shape."""
     s = soa_struct(muons, id_offset, instance)
     n = int(muons["x"].numel())
@@ -384,7 +385,7 @@ def mt_transport_cfg(handle: int, muons: Dict, step_len: float, max_steps: int, 
         a_ptr, nb = None, 0
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(),
                                                            workspace.numel() * workspace.element_size())
-    cfg = mt_launch_cfg(int(mode), int(blocks_per_sm), int(steps_per_pass), 0, ws_ptr, int(ws_bytes))
+    cfg = mt_launch_cfg(int(mode), int(blocks_per_sm), int(steps_per_pass), int(order), ws_ptr, int(ws_bytes))
     _check(load_library().mt_transport_cfg(C.c_void_p(handle), C.byref(s), n, float(step_len), int(max_steps),
                                            int(seed) & 0xFFFFFFFFFFFFFFFF, C.c_void_p(a_ptr), int(nb), C.byref(cfg),
                                            C.c_void_p(_stream_ptr(stream))), "mt_transport_cfg")

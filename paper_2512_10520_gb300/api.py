@@ -56,10 +56,10 @@ class World:
 
     def transport(self, muons: Dict, step_len: float, max_steps: int, seed: int, id_offset: int = 0,
                   instance: int = 0, alpha=None, stream=None, mode: Optional[int] = None,
-                  blocks_per_sm: int = 0, steps_per_pass: int = 0, workspace=None) -> None:
-        if mode is not None or blocks_per_sm or steps_per_pass or workspace is not None:
+                  blocks_per_sm: int = 0, steps_per_pass: int = 0, workspace=None, order: int = 0) -> None:
+        if mode is not None or blocks_per_sm or steps_per_pass or workspace is not None or order:
             B.mt_transport_cfg(self.handle, muons, step_len, max_steps, seed, alpha, mode or 0, blocks_per_sm,
-                               id_offset, instance, stream, steps_per_pass, workspace)
+                               id_offset, instance, stream, steps_per_pass, workspace, order)
         elif alpha is None:
             B.mt_transport(self.handle, muons, step_len, max_steps, seed, id_offset, instance, stream)
         else:

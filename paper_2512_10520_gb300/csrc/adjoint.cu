@@ -442,12 +442,6 @@ __device__ __forceinline__ void reverse_step(const WorldParams &w, const SmemWor
 // FWD: the full-tape forward (finished muons stored, survivors appended to
 // `out`, as in compact_pass); otherwise the recomputation of one checkpointed
 // pass in the backward (nothing but the tape and the step counts is written).
-// gfin (recomputation only, may be null): dL/d(final state) [6][n].  The
-// backward is linear in it, so a muon whose six components are all zero has a
-// zero adjoint through every step and adds nothing to dL/dalpha: it is not
-// recomputed (its step count is set to 0).  With the acceptance loss that is
-// every stopped muon and every muon extrapolated 1.4 m or more outside the
-// acceptance (the sigmoids underflow to zero), most muons of a shield.
 // Resident blocks per SM of the recorded pass: 4 (64 registers; measured on
 // diff1e6 with the planes stored as soon as their values exist: checkpoint
 // backward 55.4 ms against 55.7 ms at 5 blocks, which spill 8 bytes).
@@ -471,7 +465,7 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
     tape_pass(const WorldParams w, const mt_muon_soa soa, const RunParams rp, LiveBuf in, LiveBuf out,
               const unsigned long long *cin, unsigned long long *cout, int S, char *tape_base,
               unsigned long long *tape_off, int64_t region_cap, unsigned int *flag, unsigned long long *work,
-              unsigned long long *wzero, const float *gfin, int64_t n)
+              unsigned long long *wzero)
 {
     __shared__ SmemWorld sw;
     const int64_t count = (int64_t)*cin;
@@ -500,14 +494,7 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
         float q = 0.0f;
         int k = 0;
         int64_t idx = 0;
-        bool zero_adjoint = false;
-        if (!FWD && gfin && i < count) {
-            const int64_t m = (int64_t)__float_as_int(in.w2[i].w);
-            zero_adjoint = gfin[m] == 0.0f && gfin[n + m] == 0.0f && gfin[2 * n + m] == 0.0f &&
-                           gfin[3 * n + m] == 0.0f && gfin[4 * n + m] == 0.0f && gfin[5 * n + m] == 0.0f;
-            if (zero_adjoint) reinterpret_cast<float *>(in.w3 + i)[3] = __int_as_float(0);
-        }
-        if (i < count && !zero_adjoint) {
+        if (i < count) {
             get_live(in, i, s, q, k, idx);
             tr.tid = i;
             const uint64_t id = (uint64_t)(rp.id_offset + idx);
@@ -678,7 +665,7 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
     if (e != cudaSuccess) return e;
     const int64_t need = (n + kBlock - 1) / kBlock;
     compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
-        w, soa, n, rp, live_buf_at(ck + L.lists_off, n), ctr);
+        w, soa, n, rp, live_buf_at(ck + L.lists_off, n), ctr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int grid = resident_grid((const void *)compact_pass<GEOM, FIELD>, n);
@@ -686,7 +673,7 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
         compact_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(
             w, soa, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
             live_buf_at(ck + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, nullptr,
-            ctr + L.passes + 1 + p, nullptr, K);
+            ctr + L.passes + 1 + p, nullptr, K, nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -707,7 +694,7 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
     if (e != cudaSuccess) return e;
     const int64_t need = (n + kBlock - 1) / kBlock;
     compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
-        w, soa, n, rp, live_buf_at(buf + L.lists_off, n), ctr);
+        w, soa, n, rp, live_buf_at(buf + L.lists_off, n), ctr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int grid = resident_grid((const void *)tape_pass<GEOM, FIELD, true>, n);
@@ -715,18 +702,61 @@ static cudaError_t tape_forward(const WorldParams &w, const mt_muon_soa &soa, in
         tape_pass<GEOM, FIELD, true><<<grid, kBlock, 0, st>>>(
             w, soa, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
             live_buf_at(buf + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, K,
-            buf + T.region_off, toff + p, T.region_cap, flag, ctr + L.passes + 1 + p, nullptr, nullptr, n);
+            buf + T.region_off, toff + p, T.region_cap, flag, ctr + L.passes + 1 + p, nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+// The entries of checkpointed list `in` (*cin of them) whose muon has a
+// nonzero cotangent in gfin = dL/d(final state) [6][n] (all entries when gfin
+// is null), appended to `out` at *cout.  The backward is linear in gfin, so a
+// muon whose six components are all zero keeps a zero adjoint through every
+// step and adds nothing to dL/dalpha: the backward leaves it out and its rows
+// of dL/d(initial state) keep the zeros they start from.  Under the acceptance
+// loss that is every stopped muon and every muon extrapolated 1.4 m or more
+// outside the acceptance (the sigmoids underflow to zero), most of a shield's.
+__global__ void __launch_bounds__(kBlock) select_live(LiveBuf in, const unsigned long long *cin, const float *gfin,
+                                                      int64_t n, LiveBuf out, unsigned long long *cout)
+{
+    const int64_t count = (int64_t)*cin;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool keep = false;
+        float4 a, b, c, d;
+        if (i < count) {
+            c = in.w2[i];
+            const int64_t m = (int64_t)__float_as_int(c.w);
+            keep = !gfin || gfin[m] != 0.0f || gfin[n + m] != 0.0f || gfin[2 * n + m] != 0.0f ||
+                   gfin[3 * n + m] != 0.0f || gfin[4 * n + m] != 0.0f || gfin[5 * n + m] != 0.0f;
+            if (keep) {
+                a = in.w0[i];
+                b = in.w1[i];
+                d = in.w3[i];
+            }
+        }
+        const int64_t slot = warp_append(cout, keep);
+        if (keep) {
+            out.w0[slot] = a;
+            out.w1[slot] = b;
+            out.w2[slot] = c;
+            out.w3[slot] = d;
+        }
+    }
+}
+
 // Scratch of the recompute form's backward: two slots, each a 256-byte header
 // (region offsets at bytes 0-15, the flag at 64, the recorded pass's and the
-// reverse pass's work counters at 128 and 136) and the tape of one pass of up
-// to n entries.  Pass p uses slot p % 2.
-static int64_t ckpt_slot_bytes(int64_t n, int K) { return 256 + tape_pass_bytes(n > 0 ? n : 1, K); }
+// reverse pass's work counters at 128 and 136, the selected entries' count at
+// 192), the tape of one pass of up to n entries, and the pass's selected list
+// (up to n entries).  Pass p uses slot p % 2.
+static int64_t ckpt_tape_cap(int64_t n, int K) { return round_up(tape_pass_bytes(n > 0 ? n : 1, K), 256); }
+static int64_t ckpt_slot_bytes(int64_t n, int K)
+{
+    return 256 + ckpt_tape_cap(n, K) + 4 * (n > 0 ? n : 1) * (int64_t)sizeof(float4);
+}
 static int64_t ckpt_scratch_bytes(int64_t n, int K) { return 2 * ckpt_slot_bytes(n, K); }
 
 // Resident blocks per SM of the two kernels of the checkpoint backward (0: as
@@ -769,12 +799,13 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
     double *dalpha = reinterpret_cast<double *>(ck + L.alpha_off);
     const int64_t slot = ckpt_slot_bytes(n, K);
-    const int64_t cap = tape_pass_bytes(n > 0 ? n : 1, K);
+    const int64_t cap = ckpt_tape_cap(n, K);
     cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
     for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemsetAsync(scratch + s * slot, 0, 256, st);
     if (e != cudaSuccess) return e;
     const int rgrid = split_grid((const void *)tape_pass<GEOM, FIELD, false>, MT_ADJ_REC_BLOCKS, n);
     const int agrid = split_grid((const void *)adjoint_pass<GEOM, FIELD>, MT_ADJ_SWEEP_BLOCKS, n);
+    const int sgrid = resident_grid((const void *)select_live, n);
     const int P = L.passes;
     cudaStream_t aux = nullptr;
     std::vector<cudaEvent_t> ev(2 * P + 1, nullptr);   // [0, P): recorded, [P, 2P): reversed, 2P: fork
@@ -783,25 +814,31 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * P], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[2 * P], 0);
     auto hdr = [&](int p) { return scratch + (p & 1) * slot; };
+    // segment p's entries with a nonzero cotangent, in its slot
+    auto selected = [&](int p) { return live_buf_at(hdr(p) + 256 + cap, n); };
     auto record = [&](int p) {
         char *h = hdr(p);
         unsigned long long *wc = reinterpret_cast<unsigned long long *>(h + 128);
-        const LiveBuf lp = live_buf_at(ck + L.lists_off + p * L.list_bytes, n);
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(h + 192);
+        const LiveBuf sel = selected(p);
         if (p + 2 < P && e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[P + p + 2], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), aux);
         if (e != cudaSuccess) return;
+        select_live<<<sgrid, kBlock, 0, aux>>>(live_buf_at(ck + L.lists_off + p * L.list_bytes, n), ctr + p, gfin, n,
+                                               sel, cnt);
         tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, aux>>>(
-            w, mt_muon_soa{}, rp, lp, lp, ctr + p, nullptr, K, h + 256, reinterpret_cast<unsigned long long *>(h), cap,
-            reinterpret_cast<unsigned int *>(h + 64), wc, wc + 1, gfin, n);
+            w, mt_muon_soa{}, rp, sel, sel, cnt, nullptr, K, h + 256, reinterpret_cast<unsigned long long *>(h), cap,
+            reinterpret_cast<unsigned int *>(h + 64), wc, wc + 1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev[p], aux);
     };
     auto reverse = [&](int p) {
         char *h = hdr(p);
         unsigned long long *wc = reinterpret_cast<unsigned long long *>(h + 128);
-        const LiveBuf lp = live_buf_at(ck + L.lists_off + p * L.list_bytes, n);
+        const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(h + 192);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[p], 0);
         if (e != cudaSuccess) return;
-        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, h + 256,
+        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, selected(p), cnt, adj, n, dalpha, h + 256,
                                                            reinterpret_cast<const unsigned long long *>(h),
                                                            reinterpret_cast<const unsigned int *>(h + 64), wc + 1, wc);
         e = cudaGetLastError();

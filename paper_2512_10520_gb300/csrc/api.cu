@@ -724,6 +724,26 @@ mt_status build_geometry(const mt_geometry_desc *g, const mt_field_desc *f, Worl
     return MT_OK;
 }
 
+// xy grid of the live list's spatial order: the map's xy cells merged 2 x 2
+// (measured on shield1e6 and tapered1e6 faster than single cells, whose
+// histogram is 4 times longer), or 4 x 4, ... until at most kSortBins remain.
+#ifndef MT_SORT_SHIFT_MIN
+#define MT_SORT_SHIFT_MIN 1
+#endif
+static void set_sort_grid(WorldParams &w)
+{
+    const int cx = w.fdims[0] - 1, cy = w.fdims[1] - 1;
+    w.sort_shift = 0;
+    w.sort_nx = 0;
+    w.sort_bins = 0;
+    if (cx < 1 || cy < 1) return;
+    int sh = MT_SORT_SHIFT_MIN;
+    while ((int64_t)(((cx - 1) >> sh) + 1) * (((cy - 1) >> sh) + 1) > kSortBins) ++sh;
+    w.sort_shift = sh;
+    w.sort_nx = ((cx - 1) >> sh) + 1;
+    w.sort_bins = w.sort_nx * (((cy - 1) >> sh) + 1);
+}
+
 // Field (validated) into w; a map is uploaded and repacked into x-adjacent node pairs.
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
 {
@@ -745,6 +765,7 @@ mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
             w.fspacing_lo[a] = 0.0f;
             w.finv[a] = 1.0f;
         }
+        set_sort_grid(w);
         return MT_OK;
     }
     if (f->kind != MT_FIELD_MAP) return MT_OK;
@@ -773,6 +794,7 @@ mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own)
         w.fspacing_lo[a] = 0.0f;
         w.finv[a] = (float)(1.0 / f->spacing[a]);
     }
+    set_sort_grid(w);
     return MT_OK;
 }
 

@@ -18,20 +18,35 @@
 
 namespace mt {
 
+// Counters (256 B), the two live lists, then the spatial order's histogram and
+// offsets (kSortBins each).
 int64_t compact_workspace_bytes(int64_t n)
 {
     const int64_t cap = n > 0 ? n : 1;
-    return 256 + 2 * 4 * cap * (int64_t)sizeof(float4);
+    return 256 + 2 * 4 * cap * (int64_t)sizeof(float4) + 2 * (int64_t)kSortBins * (int64_t)sizeof(unsigned);
 }
 
 template <int GEOM, int FIELD>
 static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
-                              cudaStream_t st, int S, int blocks_per_sm, char *ws)
+                              cudaStream_t st, int S, int blocks_per_sm, int order_mode, char *ws)
 {
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ws);
     LiveBuf buf[2] = {live_buf_at(ws + 256, n), live_buf_at(ws + 256 + 4 * n * (int64_t)sizeof(float4), n)};
+    unsigned *hist = reinterpret_cast<unsigned *>(ws + 256 + 2 * 4 * n * (int64_t)sizeof(float4));
+    unsigned *offs = hist + kSortBins;
     cudaError_t e = cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    // a muon that starts at step 0 needs ceil(max_steps / S) passes
+    const int passes = rp.max_steps > 0 ? (rp.max_steps + S - 1) / S : 1;
+    // Spatial order (maps only): the list is reordered after compact_init and
+    // after every MT_SORT_EVERY-th pass but the last.
+    const bool order = w.sort_bins > 0 && order_mode != MT_ORDER_NEVER &&
+                       (order_mode == MT_ORDER_ALWAYS || n >= MT_SORT_MIN_MUONS);
+    if (order) {
+        e = cudaFuncSetAttribute(sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)w.sort_bins * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+    }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -42,18 +57,32 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
     const int64_t need = (n + kBlock - 1) / kBlock;
     if (grid > need) grid = need;
     const int64_t init_grid = need < 65535 * 8 ? need : 65535 * 8;
-    compact_init<<<(unsigned)init_grid, kBlock, 0, st>>>(w, soa, n, rp, buf[0], ctr);
+    const int64_t scatter_grid = grid < (int64_t)sms * 8 ? (int64_t)sms * 8 : grid;
+    // scan the counts of the list just written to buf[src] and scatter it to the other list
+    auto reorder = [&](int src, const unsigned long long *cnt) {
+        sort_scan<<<1, 1024, kScanSmem, st>>>(hist, offs, w.sort_bins);
+        cudaError_t f = cudaGetLastError();
+        if (f != cudaSuccess) return f;
+        sort_scatter<<<(unsigned)scatter_grid, kBlock, 0, st>>>(w, buf[src], buf[src ^ 1], cnt, offs);
+        return cudaGetLastError();
+    };
+    // the current list is buf[cur]; a pass appends to the other one, which
+    // becomes current unless it is reordered back into buf[cur]
+    int cur = 0;
+    compact_init<<<(unsigned)init_grid, kBlock, 0, st>>>(w, soa, n, rp, buf[order ? 1 : 0], ctr, order ? hist : nullptr);
     e = cudaGetLastError();
+    if (e == cudaSuccess && order) e = reorder(1, ctr);
     if (e != cudaSuccess) return e;
-    // a muon that starts at step 0 needs ceil(max_steps / S) passes
-    const int passes = rp.max_steps > 0 ? (rp.max_steps + S - 1) / S : 1;
     for (int p = 0; p < passes; ++p) {
-        compact_pass<GEOM, FIELD><<<(unsigned)grid, kBlock, 0, st>>>(w, soa, rp, buf[p & 1], buf[(p + 1) & 1],
-                                                                     ctr + p % 3, ctr + (p + 1) % 3,
-                                                                     ctr + (p + 2) % 3, ctr + 3 + p % 3,
-                                                                     ctr + 3 + (p + 1) % 3, S);
+        const bool count = order && p + 1 < passes && (p + 1) % MT_SORT_EVERY == 0;
+        compact_pass<GEOM, FIELD><<<(unsigned)grid, kBlock, 0, st>>>(w, soa, rp, buf[cur], buf[cur ^ 1], ctr + p % 3,
+                                                                     ctr + (p + 1) % 3, ctr + (p + 2) % 3,
+                                                                     ctr + 3 + p % 3, ctr + 3 + (p + 1) % 3, S,
+                                                                     count ? hist : nullptr);
         e = cudaGetLastError();
+        if (e == cudaSuccess && count) e = reorder(cur ^ 1, ctr + (p + 1) % 3);
         if (e != cudaSuccess) return e;
+        if (!count) cur ^= 1;
     }
     return cudaSuccess;
 }
@@ -62,7 +91,8 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
 // then the scratch comes from the stream-ordered allocator and is returned on
 // the same stream.
 cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
-                           cudaStream_t st, int S, int blocks_per_sm, void *ws, int64_t ws_bytes, bool &ws_too_small)
+                           cudaStream_t st, int S, int blocks_per_sm, int order, void *ws, int64_t ws_bytes,
+                           bool &ws_too_small)
 {
     ws_too_small = false;
     const int64_t need = compact_workspace_bytes(n);
@@ -81,35 +111,35 @@ cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t
     cudaError_t e;
     if (w.geom_kind == MT_GEOM_BOXES) {
         if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
-            e = run_passes<MT_GEOM_BOXES, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_BOXES, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_MAP)
-            e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
-            e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_BOXES, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_BOX)
-            e = run_passes<MT_GEOM_BOXES, MT_FIELD_BOX>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_BOXES, MT_FIELD_BOX>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else
-            e = run_passes<MT_GEOM_BOXES, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_BOXES, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
     } else if (w.geom_kind == MT_GEOM_POLYHEDRA) {
         if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
-            e = run_passes<MT_GEOM_POLYHEDRA, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_POLYHEDRA, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_MAP)
-            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
-            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_BOX)
-            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_BOX>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_BOX>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else
-            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_POLYHEDRA, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
     } else {
         if (w.field_kind == MT_FIELD_MAP && w.field_per_stage)
-            e = run_passes<MT_GEOM_VOXELS, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_VOXELS, kFieldMapStaged>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_MAP)
-            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else if (w.field_kind == MT_FIELD_MAP_NEAREST)
-            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
         else
-            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, buf);
+            e = run_passes<MT_GEOM_VOXELS, MT_FIELD_NONE>(w, soa, n, rp, st, S, blocks_per_sm, order, buf);
     }
     if (own) {
         cudaError_t f = cudaFreeAsync(buf, st);
@@ -128,6 +158,8 @@ static cudaError_t preload_passes()
     cudaFuncAttributes a;
     cudaError_t e = cudaFuncGetAttributes(&a, compact_init);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, compact_pass<GEOM, FIELD>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sort_scan);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sort_scatter);
     return e;
 }
 

@@ -42,6 +42,10 @@ constexpr int kZSlabs = 256;   // z slabs of the box-candidate index
 // Field template value of the kernels for MT_FIELD_MAP with per_stage set.
 constexpr int kFieldMapStaged = 4;
 
+// Most bins of the live list's spatial order (keys 0 .. kSortBins - 1; a
+// multiple of 1024).
+constexpr int kSortBins = 16384;
+
 struct WorldParams {
     // geometry
     int32_t geom_kind;
@@ -85,6 +89,10 @@ struct WorldParams {
     float fspacing[3];
     float fspacing_lo[3];
     float finv[3];                 // trilinear map: 1 / node spacing in 1/m (field gradients)
+    // xy grid of the live list's spatial order (maps only): the key of a muon is
+    // (j >> sort_shift) * sort_nx + (i >> sort_shift) for its map cell (i, j),
+    // sort_shift >= 1; sort_bins = 0 leaves the list unordered
+    int32_t sort_shift, sort_nx, sort_bins;
     // histograms
     const HistRec *hist;
     const uint32_t *guide;

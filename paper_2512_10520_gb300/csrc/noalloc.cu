@@ -28,9 +28,11 @@ cudaError_t compact_preload(const WorldParams &w);
 
 namespace {
 
-constexpr size_t kNoAllocBytes = 256 + 2 * 4 * 16 * (size_t)MT_NOALLOC_MAX_MUONS;
+constexpr size_t kNoAllocBytes =
+    256 + 2 * 4 * 16 * (size_t)MT_NOALLOC_MAX_MUONS + 2 * (size_t)mt::kSortBins * sizeof(unsigned);
 
-// The compaction list (two 64-byte entries per muon) and its counters.
+// The compaction list (two 64-byte entries per muon), its counters, and the
+// histogram and offsets of its spatial order.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;

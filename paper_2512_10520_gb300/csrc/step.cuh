@@ -884,12 +884,15 @@ __device__ __forceinline__ int64_t warp_append(unsigned long long *ctr, bool kee
     return (int64_t)base + __popc(mask & ((1u << lane) - 1u));
 }
 
-__device__ __forceinline__ void put_live(const LiveBuf &b, int64_t i, const State &s, float q, int k, int64_t idx)
+// tag: the fourth word of w3 (the entry's rank within its key in the compacting
+// transport's spatial order; 0 elsewhere).
+__device__ __forceinline__ void put_live(const LiveBuf &b, int64_t i, const State &s, float q, int k, int64_t idx,
+                                         unsigned tag = 0u)
 {
     b.w0[i] = make_float4(s.x, s.y, s.z, q);
     b.w1[i] = make_float4(s.px, s.py, s.pz, __int_as_float(k));
     b.w2[i] = make_float4(s.xl, s.yl, s.zl, __int_as_float((int)idx));
-    b.w3[i] = make_float4(s.pxl, s.pyl, s.pzl, 0.0f);
+    b.w3[i] = make_float4(s.pxl, s.pyl, s.pzl, __uint_as_float(tag));
 }
 
 __device__ __forceinline__ void get_live(const LiveBuf &b, int64_t i, State &s, float &q, int &k, int64_t &idx)

@@ -143,7 +143,8 @@ static cudaError_t launch(const WorldParams &w, const mt_muon_soa &s, int64_t n,
 namespace mt {
 int64_t compact_workspace_bytes(int64_t n);
 cudaError_t launch_compact(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
-                           cudaStream_t st, int S, int blocks_per_sm, void *ws, int64_t ws_bytes, bool &ws_too_small);
+                           cudaStream_t st, int S, int blocks_per_sm, int order, void *ws, int64_t ws_bytes,
+                           bool &ws_too_small);
 }  // namespace mt
 
 using namespace mt;
@@ -233,9 +234,10 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     }
     mt_launch_cfg lc = {MT_LAUNCH_AUTO, 0, 0, 0, nullptr, 0};
     if (cfg) lc = *cfg;
-    if (lc.mode < MT_LAUNCH_AUTO || lc.mode > MT_LAUNCH_COMPACT || lc.blocks_per_sm < 0 || lc.steps_per_pass < 0) {
-        set_error("bad launch configuration (mode %d, blocks_per_sm %d, steps_per_pass %d)", lc.mode,
-                  lc.blocks_per_sm, lc.steps_per_pass);
+    if (lc.mode < MT_LAUNCH_AUTO || lc.mode > MT_LAUNCH_COMPACT || lc.blocks_per_sm < 0 || lc.steps_per_pass < 0 ||
+        lc.order < MT_ORDER_AUTO || lc.order > MT_ORDER_NEVER) {
+        set_error("bad launch configuration (mode %d, blocks_per_sm %d, steps_per_pass %d, order %d)", lc.mode,
+                  lc.blocks_per_sm, lc.steps_per_pass, lc.order);
         return MT_ERR_INVALID_ARG;
     }
     if (lc.mode == MT_LAUNCH_COMPACT && n >= (int64_t)1 << 31) {
@@ -260,7 +262,7 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
         bool small = false;
         e = launch_compact(w, *s, n, rp, cs,
                            lc.steps_per_pass > 0 ? lc.steps_per_pass : default_steps_per_pass(w, step_len),
-                           lc.blocks_per_sm,
+                           lc.blocks_per_sm, lc.order,
                            lc.workspace, lc.workspace_bytes, small);
         if (small) {
             set_error("workspace of %lld bytes at %p is too small or not 256-byte aligned (need %lld)",

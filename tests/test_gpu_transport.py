@@ -51,11 +51,21 @@ def test_shield1e6_subset_parity_and_ks(wl1_small):
 def test_shield1e6_full_size_sampled_parity():
     """The full 1e6-muon workload in the benchmark's launch configuration; the
     oracle recomputes a spread sample of muon ids one by one."""
+    import paper_2512_10520_gb300 as mt
+    import torch
     wl = gen.workload("shield1e6")
     gpu = gpu_transport(wl)
     idx = np.unique(np.linspace(0, wl.n - 1, 20000).astype(np.int64))
     ora = oracle.transport(oracle.world_of(wl), wl.muons, wl.step_len, wl.max_steps, wl.seed, index=idx)
     assert_parity(gpu, ora, idx)
+    # at this size the default call reorders the live list; without it every muon ends the same
+    with mt.World.from_workload(wl) as world:
+        dev = mt.muons_to_device(wl.muons)
+        world.transport(dev, wl.step_len, wl.max_steps, wl.seed, mode=mt.MT_LAUNCH_COMPACT, order=mt.MT_ORDER_NEVER)
+        torch.cuda.synchronize()
+        plain = mt.muons_to_host(dev)
+    for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+        np.testing.assert_array_equal(gpu[k], plain[k])
     # every muon ends in a valid terminal state
     assert set(np.unique(gpu["status"])) <= {1, 2, 3, 4}
     assert gpu["steps"].max() <= wl.max_steps
@@ -91,6 +101,35 @@ def test_launch_shapes_are_bit_identical(wl1_small):
     for o in outs[1:]:
         for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
             np.testing.assert_array_equal(outs[0][k], o[k])
+
+
+def test_spatial_order_is_bit_identical():
+    """The live list's spatial order (a counting sort of the survivors by their
+    coarse field-map cell between passes) changes only where a muon sits in the
+    list, so every result equals the unordered run's exactly: on the map with
+    boxes, on tapered solids, with the nearest-node map, after every pass length,
+    and in a caller's workspace of exactly mt_transport_workspace_bytes."""
+    import paper_2512_10520_gb300 as mt
+    import torch
+    cases = [(gen.workload("shield1e6", n=20000), 0), (gen.workload("shield1e6", n=20000), 7),
+             (gen.workload("shield1e6", n=20000), 1500), (gen.workload("tapered1e6", n=20000), 0),
+             (gen.workload("shield1e6", n=20000, field="nearest"), 0)]
+    for wl, spp in cases:
+        with mt.World.from_workload(wl) as world:
+            outs = []
+            for order in (mt.MT_ORDER_NEVER, mt.MT_ORDER_ALWAYS, mt.MT_ORDER_AUTO):
+                dev = mt.muons_to_device(wl.muons)
+                ws = torch.empty(mt.mt_transport_workspace_bytes(wl.n), dtype=torch.uint8, device="cuda")
+                world.transport(dev, wl.step_len, wl.max_steps, wl.seed, mode=mt.MT_LAUNCH_COMPACT,
+                                steps_per_pass=spp, workspace=ws, order=order)
+                torch.cuda.synchronize()
+                outs.append(mt.muons_to_host(dev))
+            for o in outs[1:]:
+                for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+                    np.testing.assert_array_equal(outs[0][k], o[k], err_msg=f"{wl.name} spp={spp} {k}")
+            with pytest.raises(mt.MtError):
+                world.transport(mt.muons_to_device(wl.muons), wl.step_len, wl.max_steps, wl.seed,
+                                mode=mt.MT_LAUNCH_COMPACT, order=3)
 
 
 def test_compact_mode_workspace_and_edge_cases(wl0):
