@@ -321,6 +321,10 @@ typedef struct mt_batch_cfg {
     int32_t use_graph;        /* 1 = capture the launch sequence in a CUDA graph once */
                               /*     per (workspace, sizes, arguments) and replay it  */
     int32_t staging;          /* MT_BATCH_STAGE_*; 0 = tuned / shared                 */
+    int32_t order;            /* field maps: spatial order of every instance's live   */
+                              /*   list between passes, as mt_launch_cfg.order        */
+                              /*   (MT_ORDER_AUTO: 2^19 muons or more in the batch)   */
+    int32_t reserved;         /* 0                                                    */
     void *workspace;          /* device scratch (256-byte aligned) of at least        */
     int64_t workspace_bytes;  /*   mt_batch_workspace_bytes, or NULL: stream-ordered  */
                               /*   scratch per call, or with use_graph the batch's    */

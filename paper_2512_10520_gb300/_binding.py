@@ -87,7 +87,8 @@ MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL = 1, 2
 
 class mt_batch_cfg(C.Structure):
     _fields_ = [("block", C.c_int32), ("steps_per_pass", C.c_int32), ("use_graph", C.c_int32),
-                ("staging", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64)]
+                ("staging", C.c_int32), ("order", C.c_int32), ("reserved", C.c_int32), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_int64)]
 
 
 class mt_muon_soa(C.Structure):
@@ -556,14 +557,16 @@ def _soas(muons_list, id_offsets, instances):
 
 def mt_transport_batched(batch: int, muons_list, step_len: float, max_steps: int, seed: int, block: int = 0,
                          steps_per_pass: int = 0, use_graph: bool = False, workspace=None, id_offsets=None,
-                         instances=None, stream=None, staging: int = 0) -> None:
+                         instances=None, stream=None, staging: int = 0, order: int = MT_ORDER_AUTO) -> None:
     """Transport instance i's muons (dict of CUDA tensors, in place) in world i, for every i.
     Muon ids are id_offsets[i] + m (default 0) and the Philox instance word is instances[i] (default i).
-    staging: MT_BATCH_STAGE_SHARED or MT_BATCH_STAGE_GLOBAL (0: the tuned one, else shared)."""
+    staging: MT_BATCH_STAGE_SHARED or MT_BATCH_STAGE_GLOBAL (0: the tuned one, else shared).
+    order: spatial order of the live lists (MT_ORDER_AUTO, _ALWAYS or _NEVER; results do not change)."""
     soas, n = _soas(muons_list, id_offsets, instances)
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(),
                                                            workspace.numel() * workspace.element_size())
-    cfg = mt_batch_cfg(int(block), int(steps_per_pass), int(bool(use_graph)), int(staging), ws_ptr, int(ws_bytes))
+    cfg = mt_batch_cfg(int(block), int(steps_per_pass), int(bool(use_graph)), int(staging), int(order), 0, ws_ptr,
+                       int(ws_bytes))
     _check(load_library().mt_transport_batched(C.c_void_p(batch), soas, n, float(step_len), int(max_steps),
                                                int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(cfg),
                                                C.c_void_p(_stream_ptr(stream))), "mt_transport_batched")

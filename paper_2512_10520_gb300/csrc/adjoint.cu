@@ -45,7 +45,7 @@ __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + 
 
 struct CkptLayout {
     int passes;
-    int64_t alpha_off, lists_off, list_bytes, total;
+    int64_t alpha_off, sort_off, lists_off, list_bytes, total;
 };
 
 static CkptLayout ckpt_layout(int64_t n, int32_t max_steps, int32_t K)
@@ -53,9 +53,11 @@ static CkptLayout ckpt_layout(int64_t n, int32_t max_steps, int32_t K)
     CkptLayout L;
     const int64_t cap = n > 0 ? n : 1;
     L.passes = max_steps > 0 ? (max_steps + K - 1) / K : 1;
-    // live counts of every pass, then the passes' work counters
+    // live counts of every pass, then the passes' work counters; dL/dalpha; the
+    // spatial order's counts and first slots; the live list of every pass
     L.alpha_off = round_up((int64_t)(L.passes + 1) * 16, 256);
-    L.lists_off = round_up(L.alpha_off + 3 * MT_MAX_BOXES * 8, 256);
+    L.sort_off = round_up(L.alpha_off + 3 * MT_MAX_BOXES * 8, 256);
+    L.lists_off = round_up(L.sort_off + 2 * (int64_t)kSortBins * (int64_t)sizeof(unsigned), 256);
     L.list_bytes = 4 * cap * (int64_t)sizeof(float4);
     L.total = L.lists_off + (L.passes + 1) * L.list_bytes;
     return L;
@@ -661,20 +663,42 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
 {
     const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
+    unsigned *hist = reinterpret_cast<unsigned *>(ck + L.sort_off), *offs = hist + kSortBins;
+    auto list = [&](int p) { return live_buf_at(ck + L.lists_off + p * L.list_bytes, n); };
+    // Spatial order of the saved lists (field maps, as the plain transport takes
+    // it): after compact_init and every MT_SORT_EVERY-th pass, survivors go to
+    // the list two ahead, still unused, and are scattered in key order into the
+    // next one.  The backward then reads every list in that order too.
+    const bool order = w.sort_bins > 0 && n >= MT_SORT_MIN_MUONS && L.passes > 1;
     cudaError_t e = cudaMemsetAsync(ck, 0, (size_t)L.lists_off, st);
+    if (e == cudaSuccess && order)
+        e = cudaFuncSetAttribute(sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = resident_grid((const void *)compact_pass<GEOM, FIELD>, n);
+    const int sgrid = grid < sms * 8 ? sms * 8 : grid;
+    auto reorder = [&](const LiveBuf &src, const LiveBuf &dst, const unsigned long long *cnt) {
+        sort_scan<<<1, 1024, kScanSmem, st>>>(hist, offs, w.sort_bins);
+        cudaError_t f = cudaGetLastError();
+        if (f != cudaSuccess) return f;
+        sort_scatter<<<sgrid, kBlock, 0, st>>>(w, src, dst, cnt, offs);
+        return cudaGetLastError();
+    };
     const int64_t need = (n + kBlock - 1) / kBlock;
     compact_init<<<(unsigned)(need < 65535 * 8 ? need : 65535 * 8), kBlock, 0, st>>>(
-        w, soa, n, rp, live_buf_at(ck + L.lists_off, n), ctr, nullptr);
+        w, soa, n, rp, list(order ? 1 : 0), ctr, order ? hist : nullptr);
     e = cudaGetLastError();
+    if (e == cudaSuccess && order) e = reorder(list(1), list(0), ctr);
     if (e != cudaSuccess) return e;
-    const int grid = resident_grid((const void *)compact_pass<GEOM, FIELD>, n);
     for (int p = 0; p < L.passes; ++p) {
-        compact_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(
-            w, soa, rp, live_buf_at(ck + L.lists_off + p * L.list_bytes, n),
-            live_buf_at(ck + L.lists_off + (p + 1) * L.list_bytes, n), ctr + p, ctr + p + 1, nullptr,
-            ctr + L.passes + 1 + p, nullptr, K, nullptr);
+        const bool count = order && p + 2 <= L.passes && (p + 1) % MT_SORT_EVERY == 0;
+        compact_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, soa, rp, list(p), list(count ? p + 2 : p + 1), ctr + p,
+                                                            ctr + p + 1, nullptr, ctr + L.passes + 1 + p, nullptr, K,
+                                                            count ? hist : nullptr);
         e = cudaGetLastError();
+        if (e == cudaSuccess && count) e = reorder(list(p + 2), list(p + 1), ctr + p + 1);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

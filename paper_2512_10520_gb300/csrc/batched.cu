@@ -74,6 +74,7 @@ struct BatchWs {
     unsigned int *queue;        // [1] next item
     unsigned long long *off;    // [n_inst + 1] region offsets
     mt_muon_soa *soa;           // [n_inst] caller arrays
+    unsigned *hist, *offs;      // [n_inst][kSortBins] each: the spatial order's counts and first slots
     char *live0, *live1;        // two live buffers of N entries
     int64_t N;
 };
@@ -95,6 +96,8 @@ static int64_t batch_ws_layout(int n_inst, int64_t N, BatchWs *ws, char *base)
     o = round256(o + ((int64_t)n_inst + 1) * 8);
     const int64_t c_soa = o;
     o = round256(o + (int64_t)n_inst * (int64_t)sizeof(mt_muon_soa));
+    const int64_t c_hist = o;
+    o = round256(o + 2 * (int64_t)n_inst * kSortBins * (int64_t)sizeof(unsigned));
     const int64_t cap = N > 0 ? N : 1;
     const int64_t c_l0 = o;
     o += 4 * cap * (int64_t)sizeof(float4);
@@ -107,6 +110,8 @@ static int64_t batch_ws_layout(int n_inst, int64_t N, BatchWs *ws, char *base)
         ws->queue = reinterpret_cast<unsigned int *>(base + c_q);
         ws->off = reinterpret_cast<unsigned long long *>(base + c_off);
         ws->soa = reinterpret_cast<mt_muon_soa *>(base + c_soa);
+        ws->hist = reinterpret_cast<unsigned *>(base + c_hist);
+        ws->offs = ws->hist + (int64_t)n_inst * kSortBins;
         ws->live0 = base + c_l0;
         ws->live1 = base + c_l1;
         ws->N = cap;
@@ -142,9 +147,17 @@ __device__ __forceinline__ int64_t warp_append_u32(unsigned int *ctr, bool keep)
 
 // Pack the live muons of every instance into its region of live buffer 0
 // (positions in the instance's frame).
+// Key of the spatial order in the batch's histogram: instance i's bins start at
+// i * kSortBins (an instance without a sort grid has the one key 0).
+__device__ __forceinline__ uint32_t batch_key(const WorldParams &w, int i, const State &s)
+{
+    return (uint32_t)i * (uint32_t)kSortBins + (w.sort_bins > 0 ? sort_key(w, s.x, s.y) : 0u);
+}
+
+// hist (if not null): each muon takes its rank within its key (spatial order).
 __global__ void __launch_bounds__(256) batch_init(const WorldParams *inst, const unsigned long long *off, int n_inst,
                                                   const mt_muon_soa *soa, RunParams rp, LiveBuf out,
-                                                  unsigned int *cnt)
+                                                  unsigned int *cnt, unsigned *hist)
 {
     const unsigned long long N = off[n_inst];
     const unsigned lane = threadIdx.x & 31u;
@@ -169,13 +182,56 @@ __global__ void __launch_bounds__(256) batch_init(const WorldParams *inst, const
         // lanes of one warp may straddle two instances: aggregate per instance
         const unsigned act = __ballot_sync(0xFFFFFFFFu, live);
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, live ? i : -1) & act;
+        int64_t slot = 0;
         if (live) {
             const int leader = __ffs(peers) - 1;
             unsigned int b0 = 0;
             if ((int)lane == leader) b0 = atomicAdd(&cnt[i], (unsigned)__popc(peers));
             b0 = __shfl_sync(peers, b0, leader);
-            const int64_t slot = (int64_t)off[i] + b0 + __popc(peers & ((1u << lane) - 1u));
-            put_live(out, slot, s, q, k, m);
+            slot = (int64_t)off[i] + b0 + __popc(peers & ((1u << lane) - 1u));
+        }
+        const unsigned rank = hist ? sort_rank(hist, live, live ? batch_key(inst[i], i, s) : 0u) : 0u;
+        if (live) put_live(out, slot, s, q, k, m, rank);
+    }
+}
+
+// Spatial order, step 2: one block per instance turns its counts into first slots.
+__global__ void __launch_bounds__(1024) batch_scan(const WorldParams *inst, unsigned *hist, unsigned *offs)
+{
+    extern __shared__ unsigned v[];   // [1024][kScanStride]
+    __shared__ unsigned wsum[32];
+    const int i = blockIdx.x;
+    const int bins = inst[i].sort_bins > 0 ? inst[i].sort_bins : 1;
+    scan_counts(hist + (int64_t)i * kSortBins, offs + (int64_t)i * kSortBins, bins, v, wsum);
+}
+
+// Spatial order, step 3: the live entries of every instance (cnt[i] of them at
+// off[i] in src) move to off[i] + first slot of their key + rank in dst.  A
+// key's ranks are 0 .. count - 1 by construction, so every slot lies in the
+// instance's live range; the test only keeps a broken count from writing
+// outside it.
+__global__ void __launch_bounds__(256) batch_scatter(const WorldParams *inst, const unsigned long long *off, int n_inst,
+                                                     const unsigned int *cnt, LiveBuf src, LiveBuf dst,
+                                                     const unsigned *offs)
+{
+    const unsigned long long N = off[n_inst];
+    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (unsigned long long)gridDim.x * blockDim.x) {
+        const int i = find_region(off, n_inst, g);
+        const unsigned long long e = g - off[i];
+        const unsigned int c = cnt[i];
+        if (e >= c) continue;
+        const float4 a = src.w0[g], b = src.w1[g], cc = src.w2[g], d = src.w3[g];
+        State s;
+        s.x = a.x;
+        s.y = a.y;
+        const unsigned long long pos = (unsigned long long)__ldg(offs + batch_key(inst[i], i, s)) + __float_as_uint(d.w);
+        if (pos < c) {
+            const unsigned long long to = off[i] + pos;
+            dst.w0[to] = a;
+            dst.w1[to] = b;
+            dst.w2[to] = cc;
+            dst.w3[to] = d;
         }
     }
 }
@@ -243,7 +299,7 @@ __global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / B
                                                    const unsigned long long *off, int n_inst, RunParams rp,
                                                    LiveBuf in, LiveBuf out, const unsigned int *cnt_in,
                                                    unsigned int *cnt_out, const unsigned int *cof,
-                                                   unsigned int *queue, unsigned int *sub, int S)
+                                                   unsigned int *queue, unsigned int *sub, int S, unsigned *hist)
 {
     __shared__ SmemWorld sw;
     __shared__ WorldParams wi;
@@ -333,14 +389,15 @@ __global__ void __launch_bounds__(BLOCK, batch_threads_per_sm<GEOM, FIELD>() / B
                     keep = true;
             }
             const int64_t slot = warp_append_u32(&cnt_out[i], keep);
-            if (keep) put_live(out, (int64_t)off[i] + slot, s, q, k, idx);
+            const unsigned rank = hist ? sort_rank(hist, keep, keep ? batch_key(wr, i, s) : 0u) : 0u;
+            if (keep) put_live(out, (int64_t)off[i] + slot, s, q, k, idx, rank);
         }
         __syncthreads();
     }
 }
 
 template <int GEOM, int FIELD, int BLOCK, int WS>
-static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
+static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S, bool order,
                              cudaStream_t st)
 {
     const LiveBuf L[2] = {live_buf_at(ws.live0, ws.N), live_buf_at(ws.live1, ws.N)};
@@ -354,55 +411,76 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     const int64_t ig = std::min<int64_t>(need < 1 ? 1 : need, 65535 * 8);
-    batch_init<<<(unsigned)ig, 256, 0, st>>>(b->d_inst, ws.off, n_inst, ws.soa, rp, L[0], ws.cnt);
-    cudaError_t e = cudaGetLastError();
+    const int64_t sg = std::min<int64_t>(need < 1 ? 1 : need, (int64_t)sms * 8);
+    cudaError_t e = cudaSuccess;
+    if (order) e = cudaMemsetAsync(ws.hist, 0, (size_t)n_inst * kSortBins * sizeof(unsigned), st);
+    // the live entries of the list just written to L[src] go to the other list in key order
+    auto reorder = [&](int src, const unsigned int *c) {
+        batch_scan<<<n_inst, 1024, kScanSmem, st>>>(b->d_inst, ws.hist, ws.offs);
+        cudaError_t f = cudaGetLastError();
+        if (f != cudaSuccess) return f;
+        batch_scatter<<<(unsigned)sg, 256, 0, st>>>(b->d_inst, ws.off, n_inst, c, L[src], L[src ^ 1], ws.offs);
+        return cudaGetLastError();
+    };
+    // the current list is L[cur]; a pass appends to the other one, which becomes
+    // current unless it is reordered back into L[cur]
+    int cur = 0;
+    if (e == cudaSuccess) {
+        batch_init<<<(unsigned)ig, 256, 0, st>>>(b->d_inst, ws.off, n_inst, ws.soa, rp, L[order ? 1 : 0], ws.cnt,
+                                                 order ? ws.hist : nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && order) e = reorder(1, ws.cnt);
     const int passes = rp.max_steps > 0 ? (rp.max_steps + S - 1) / S : 1;
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
         unsigned int *c_in = ws.cnt + (p % 3) * n_inst;
         unsigned int *c_out = ws.cnt + ((p + 1) % 3) * n_inst;
         unsigned int *c_zero = ws.cnt + ((p + 2) % 3) * n_inst;
+        const bool count = order && p + 1 < passes && (p + 1) % MT_SORT_EVERY == 0;
         batch_plan<<<1, 1024, 0, st>>>(c_in, c_zero, n_inst, BLOCK, ws.cof, ws.queue, ws.sub);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        batch_pass<GEOM, FIELD, BLOCK, WS><<<(unsigned)grid, BLOCK, 0, st>>>(b->d_inst, ws.soa, ws.off, n_inst, rp,
-                                                                        L[p & 1], L[(p + 1) & 1], c_in, c_out,
-                                                                        ws.cof, ws.queue, ws.sub, S);
+        batch_pass<GEOM, FIELD, BLOCK, WS><<<(unsigned)grid, BLOCK, 0, st>>>(
+            b->d_inst, ws.soa, ws.off, n_inst, rp, L[cur], L[cur ^ 1], c_in, c_out, ws.cof, ws.queue, ws.sub, S,
+            count ? ws.hist : nullptr);
         e = cudaGetLastError();
+        if (e == cudaSuccess && count) e = reorder(cur ^ 1, c_out);
+        if (!count) cur ^= 1;
     }
     return e;
 }
 
 template <int BLOCK, int WS>
 static cudaError_t dispatch_batch_ws(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int S,
-                                     cudaStream_t st)
+                                     bool order, cudaStream_t st)
 {
     const int f = b->field_kind;
     const bool staged = b->field_per_stage != 0;
 #define MT_BATCH_FIELDS(G)                                                                                     \
-    return f == MT_FIELD_MAP && staged ? run_batch<G, kFieldMapStaged, BLOCK, WS>(b, ws, n_inst, rp, S, st)      \
-           : f == MT_FIELD_MAP         ? run_batch<G, MT_FIELD_MAP, BLOCK, WS>(b, ws, n_inst, rp, S, st)         \
-           : f == MT_FIELD_MAP_NEAREST ? run_batch<G, MT_FIELD_MAP_NEAREST, BLOCK, WS>(b, ws, n_inst, rp, S, st) \
-           : f == MT_FIELD_BOX         ? run_batch<G, MT_FIELD_BOX, BLOCK, WS>(b, ws, n_inst, rp, S, st)         \
-                                       : run_batch<G, MT_FIELD_NONE, BLOCK, WS>(b, ws, n_inst, rp, S, st)
+    return f == MT_FIELD_MAP && staged ? run_batch<G, kFieldMapStaged, BLOCK, WS>(b, ws, n_inst, rp, S, order, st)      \
+           : f == MT_FIELD_MAP         ? run_batch<G, MT_FIELD_MAP, BLOCK, WS>(b, ws, n_inst, rp, S, order, st)         \
+           : f == MT_FIELD_MAP_NEAREST ? run_batch<G, MT_FIELD_MAP_NEAREST, BLOCK, WS>(b, ws, n_inst, rp, S, order, st) \
+           : f == MT_FIELD_BOX         ? run_batch<G, MT_FIELD_BOX, BLOCK, WS>(b, ws, n_inst, rp, S, order, st)         \
+                                       : run_batch<G, MT_FIELD_NONE, BLOCK, WS>(b, ws, n_inst, rp, S, order, st)
     if (b->geom_kind == MT_GEOM_BOXES) MT_BATCH_FIELDS(MT_GEOM_BOXES);
     if (b->geom_kind == MT_GEOM_POLYHEDRA) MT_BATCH_FIELDS(MT_GEOM_POLYHEDRA);
 #undef MT_BATCH_FIELDS
     if (f == MT_FIELD_MAP && staged)
-        return run_batch<MT_GEOM_VOXELS, kFieldMapStaged, BLOCK, WS>(b, ws, n_inst, rp, S, st);
-    if (f == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK, WS>(b, ws, n_inst, rp, S, st);
+        return run_batch<MT_GEOM_VOXELS, kFieldMapStaged, BLOCK, WS>(b, ws, n_inst, rp, S, order, st);
+    if (f == MT_FIELD_MAP) return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP, BLOCK, WS>(b, ws, n_inst, rp, S, order, st);
     if (f == MT_FIELD_MAP_NEAREST)
-        return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST, BLOCK, WS>(b, ws, n_inst, rp, S, st);
-    return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK, WS>(b, ws, n_inst, rp, S, st);
+        return run_batch<MT_GEOM_VOXELS, MT_FIELD_MAP_NEAREST, BLOCK, WS>(b, ws, n_inst, rp, S, order, st);
+    return run_batch<MT_GEOM_VOXELS, MT_FIELD_NONE, BLOCK, WS>(b, ws, n_inst, rp, S, order, st);
 }
 
 static cudaError_t dispatch_batch(mt_batch *b, const BatchWs &ws, int n_inst, const RunParams &rp, int block, int S,
-                                  int staging, cudaStream_t st)
+                                  int staging, bool order, cudaStream_t st)
 {
     if (staging == MT_BATCH_STAGE_GLOBAL)
-        return block == 128 ? dispatch_batch_ws<128, MT_BATCH_STAGE_GLOBAL>(b, ws, n_inst, rp, S, st)
-                            : dispatch_batch_ws<256, MT_BATCH_STAGE_GLOBAL>(b, ws, n_inst, rp, S, st);
-    return block == 128 ? dispatch_batch_ws<128, MT_BATCH_STAGE_SHARED>(b, ws, n_inst, rp, S, st)
-                        : dispatch_batch_ws<256, MT_BATCH_STAGE_SHARED>(b, ws, n_inst, rp, S, st);
+        return block == 128 ? dispatch_batch_ws<128, MT_BATCH_STAGE_GLOBAL>(b, ws, n_inst, rp, S, order, st)
+                            : dispatch_batch_ws<256, MT_BATCH_STAGE_GLOBAL>(b, ws, n_inst, rp, S, order, st);
+    return block == 128 ? dispatch_batch_ws<128, MT_BATCH_STAGE_SHARED>(b, ws, n_inst, rp, S, order, st)
+                        : dispatch_batch_ws<256, MT_BATCH_STAGE_SHARED>(b, ws, n_inst, rp, S, order, st);
 }
 
 }  // namespace mt
@@ -559,7 +637,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
         set_error("step_len must be positive and finite, max_steps >= 0");
         return MT_ERR_INVALID_ARG;
     }
-    mt_batch_cfg c = {0, 0, 0, 0, nullptr, 0};
+    mt_batch_cfg c = {0, 0, 0, 0, MT_ORDER_AUTO, 0, nullptr, 0};
     if (cfg) c = *cfg;
     int block = c.block ? c.block : (b->tuned_block ? b->tuned_block : 256);
     int S = c.steps_per_pass ? c.steps_per_pass : b->tuned_S;
@@ -570,9 +648,12 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     }
     int staging = c.staging ? c.staging : (b->tuned_staging ? b->tuned_staging : MT_BATCH_STAGE_SHARED);
     if ((block != 128 && block != 256) || S < 1 ||
-        (staging != MT_BATCH_STAGE_SHARED && staging != MT_BATCH_STAGE_GLOBAL)) {
-        set_error("batch launch: block must be 128 or 256, steps_per_pass >= 1 and staging %d or %d (got %d, %d, %d)",
-                  MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL, block, S, staging);
+        (staging != MT_BATCH_STAGE_SHARED && staging != MT_BATCH_STAGE_GLOBAL) || c.order < MT_ORDER_AUTO ||
+        c.order > MT_ORDER_NEVER) {
+        set_error("batch launch: block must be 128 or 256, steps_per_pass >= 1, staging %d or %d and order %d..%d "
+                  "(got %d, %d, %d, %d)",
+                  MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL, MT_ORDER_AUTO, MT_ORDER_NEVER, block, S, staging,
+                  c.order);
         return MT_ERR_INVALID_ARG;
     }
     std::vector<unsigned long long> off(b->n_inst + 1, 0);
@@ -590,6 +671,9 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     }
     const int64_t N = (int64_t)off[b->n_inst];
     const int64_t need = batch_ws_layout(b->n_inst, N, nullptr, nullptr);
+    // spatial order of the live lists (maps only; see compact.cuh)
+    const bool order = (b->field_kind == MT_FIELD_MAP || b->field_kind == MT_FIELD_MAP_NEAREST) &&
+                       c.order != MT_ORDER_NEVER && (c.order == MT_ORDER_ALWAYS || N >= MT_SORT_MIN_MUONS);
     if (c.workspace && (c.workspace_bytes < need || (reinterpret_cast<uintptr_t>(c.workspace) & 255u))) {
         set_error("batch workspace of %lld bytes too small or not 256-byte aligned (need %lld)",
                   (long long)c.workspace_bytes, (long long)need);
@@ -642,14 +726,15 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ws.soa, soas, sizeof(mt_muon_soa) * (size_t)b->n_inst, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.cnt, 0, 3 * (size_t)b->n_inst * sizeof(unsigned int), cs);
+    if (e == cudaSuccess && order) e = cudaFuncSetAttribute(batch_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
     if (e == cudaSuccess) {
         if (c.use_graph) {
             // capture the launch sequence once per (arguments) and replay it
-            std::vector<char> key(sizeof(void *) + 4 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 8);
+            std::vector<char> key(sizeof(void *) + 5 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 8);
             char *kp = key.data();
             memcpy(kp, &base, sizeof(void *));
             kp += sizeof(void *);
-            const int ints[4] = {block, S, max_steps, staging};
+            const int ints[5] = {block, S, max_steps, staging, order ? 1 : 0};
             memcpy(kp, ints, sizeof(ints));
             kp += sizeof(ints);
             memcpy(kp, &step_len, sizeof(float));
@@ -667,7 +752,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
                 cudaGraph_t gr = nullptr;
                 if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    cudaError_t le = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, cap);
+                    cudaError_t le = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, order, cap);
                     e = cudaStreamEndCapture(cap, &gr);
                     if (le != cudaSuccess) e = le;
                 }
@@ -678,7 +763,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
             }
             if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, cs);
         } else {
-            e = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, cs);
+            e = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, order, cs);
         }
     }
     if (own) {
@@ -710,7 +795,7 @@ mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t 
         M += m[i];
     }
     if (M == 0) {
-        if (best) *best = mt_batch_cfg{256, 64, 0, MT_BATCH_STAGE_SHARED, nullptr, 0};
+        if (best) *best = mt_batch_cfg{256, 64, 0, MT_BATCH_STAGE_SHARED, MT_ORDER_AUTO, 0, nullptr, 0};
         return MT_OK;
     }
     const size_t per = 4 * 6 + 1 + 4 + 1;   // bytes per muon over the nine arrays
@@ -761,7 +846,7 @@ mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t 
     const int Ss[5] = {32, 64, 128, 256, 512};
     const int stagings[2] = {MT_BATCH_STAGE_SHARED, MT_BATCH_STAGE_GLOBAL};
     float best_ms = 1e30f;
-    mt_batch_cfg bc = {256, 64, 0, MT_BATCH_STAGE_SHARED, nullptr, 0};
+    mt_batch_cfg bc = {256, 64, 0, MT_BATCH_STAGE_SHARED, MT_ORDER_AUTO, 0, nullptr, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -769,7 +854,7 @@ mt_status mt_batch_autotune(mt_batch *b, const mt_muon_soa *soas, const int64_t 
     for (int gi = 0; gi < 2 && e == cudaSuccess && st == MT_OK; ++gi)
     for (int bi = 0; bi < 2 && e == cudaSuccess && st == MT_OK; ++bi)
         for (int si_ = 0; si_ < 5 && e == cudaSuccess && st == MT_OK; ++si_) {
-            mt_batch_cfg c = {blocks[bi], Ss[si_], 0, stagings[gi], nullptr, 0};
+            mt_batch_cfg c = {blocks[bi], Ss[si_], 0, stagings[gi], MT_ORDER_AUTO, 0, nullptr, 0};
             for (int rep = 0; rep < 2 && e == cudaSuccess && st == MT_OK; ++rep) {   // warm-up, then timed
                 e = cudaMemcpyAsync(work, init, (size_t)M * per + 9 * 256, cudaMemcpyDeviceToDevice, cs);
                 if (e != cudaSuccess) break;

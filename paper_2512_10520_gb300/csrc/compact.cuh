@@ -76,16 +76,15 @@ __device__ __forceinline__ unsigned sort_rank(unsigned *hist, bool keep, uint32_
 }
 
 // One block of 1024 threads, bins <= kSortBins: offs = exclusive prefix sum of
-// hist[0 .. bins), and hist cleared for the next count.  The counts are staged
+// hist[0 .. bins), and hist cleared for the next count (v: 1024 * kScanStride
+// words of shared memory, wsum: 32).  The counts are staged
 // in shared memory (one coalesced sweep), each thread scans kSortBins / 1024
 // consecutive bins, and a block scan of the threads' totals joins them.
 constexpr int kScanPer = kSortBins / 1024;
 constexpr int kScanStride = kScanPer + 1;   // padded rows: no bank conflicts
 constexpr int kScanSmem = 1024 * kScanStride * (int)sizeof(unsigned);   // dynamic shared memory of sort_scan
-static __global__ void __launch_bounds__(1024) sort_scan(unsigned *hist, unsigned *offs, int bins)
+__device__ __forceinline__ void scan_counts(unsigned *hist, unsigned *offs, int bins, unsigned *v, unsigned *wsum)
 {
-    extern __shared__ unsigned v[];   // [1024][kScanStride]
-    __shared__ unsigned wsum[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 #pragma unroll
     for (int r = 0; r < kScanPer; ++r) {
@@ -131,6 +130,13 @@ static __global__ void __launch_bounds__(1024) sort_scan(unsigned *hist, unsigne
             hist[b] = 0u;
         }
     }
+}
+
+static __global__ void __launch_bounds__(1024) sort_scan(unsigned *hist, unsigned *offs, int bins)
+{
+    extern __shared__ unsigned v[];   // [1024][kScanStride]
+    __shared__ unsigned wsum[32];
+    scan_counts(hist, offs, bins, v, wsum);
 }
 
 // Move the *cnt entries of src to dst in key order: an entry goes to its key's

@@ -198,6 +198,25 @@ def test_world_staging_layouts_are_bit_identical(instances, batch, staging):
         _assert_same(_host(devs), ref)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_spatial_order_is_bit_identical(instances, batch, use_graph):
+    """Every instance's live list reordered by coarse map cell between passes
+    (a counting sort per instance, ragged and empty instances included) moves
+    entries only, so each instance ends exactly as without the order."""
+    import paper_2512_10520_gb300 as mt
+    devs = _dev(instances)
+    batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=256, steps_per_pass=16,
+                    order=mt.MT_ORDER_NEVER)
+    ref = _host(devs)
+    for S in (16, 64):
+        devs = _dev(instances)
+        batch.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=128, steps_per_pass=S,
+                        use_graph=use_graph, order=mt.MT_ORDER_ALWAYS)
+        _assert_same(_host(devs), ref)
+    with pytest.raises(mt.MtError):
+        batch.transport(_dev(instances), gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, order=5)
+
+
 def test_autotune_cache_reuses_the_tuned_shape(instances, batch, tmp_path, monkeypatch):
     """The second autotune of the same worlds, muons and arguments on the same GPU
     reads the JSON cache instead of timing again."""
