@@ -330,8 +330,9 @@ def time_block1e4_form(mt, dev, stream, reps=20, big=1_000_000, id_offset=0):
                     times.append(a.elapsed_time(b) / 1e3)
             t = float(np.median(times))
             steps = float(work["steps"].sum().item())
+            launches = mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps)
         out[key] = dict(muons=wl.n, value=steps / t, unit=UNIT, kernel_ms=1e3 * t, muon_steps=steps,
-                        muons_per_s=wl.n / t, launches_per_call=1 + (wl.max_steps + 63) // 64)
+                        muons_per_s=wl.n / t, launches_per_call=launches)
     out["value"] = out["as_specified"]["value"]
     out["unit"] = UNIT
     return out
@@ -787,13 +788,9 @@ def run_mine(args):
     elapsed = start.elapsed_time(stop) / 1e3
     elapsed = _barrier_max(elapsed, ws, dev)
     kernel_s = float(np.mean([a.elapsed_time(b) for a, b in ev_k])) / 1e3
-    # kernels of this library per transport call: the compacting form launches
-    # compact_init plus ceil(max_steps / steps_per_pass) compact_pass kernels
-    if args.mode in ("auto", "compact"):
-        spp = args.steps_per_pass or 64
-        launches_per_call = 1 + (wl.max_steps + spp - 1) // spp
-    else:
-        launches_per_call = 1
+    # kernels of this library per transport call, as the library plans them
+    launches_per_call = mt.mt_transport_launches(world.handle, n, wl.step_len, wl.max_steps,
+                                                 **{k: v for k, v in launch.items() if k != "blocks_per_sm"})
     total_steps = _barrier_sum(steps_per_batch * args.steps, ws, dev)
     value = total_steps / elapsed
 

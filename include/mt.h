@@ -275,8 +275,8 @@ typedef struct mt_launch_cfg {
     int32_t mode;             /* MT_LAUNCH_*                                              */
     int32_t blocks_per_sm;    /* 0 = as many as fit (occupancy calculator)                */
     int32_t steps_per_pass;   /* MT_LAUNCH_COMPACT: steps between compactions, 0 = the    */
-                              /*   longest of 64, 48, 32, 24, 16 whose slab of the field  */
-                              /*   map fits in 3/4 of L2 (64 without a map)               */
+                              /*   longest of 128, 96, 64, 48, 32, 24, 16 whose slab of   */
+                              /*   the field map fits in 3/4 of L2 (64 without a map)     */
     int32_t order;            /* MT_LAUNCH_COMPACT, field maps: spatial order of the live */
                               /*   list: MT_ORDER_AUTO (at least 2^19 muons), _ALWAYS,    */
                               /*   _NEVER                                                 */
@@ -286,6 +286,13 @@ typedef struct mt_launch_cfg {
 
 /* Scratch bytes MT_LAUNCH_COMPACT needs for n muons. */
 int64_t mt_transport_workspace_bytes(int64_t n);
+
+/* Number of kernel launches one mt_transport_cfg call with these arguments
+ * makes (the pass length and the spatial order as that call chooses them;
+ * cfg may be NULL = auto); -1 for a null handle or invalid arguments.
+ * Launches nothing. */
+int64_t mt_transport_launches(const mt_handle *h, int64_t n, float step_len, int32_t max_steps,
+                              const mt_launch_cfg *cfg);
 
 /* mt_transport_scaled with an explicit launch shape (cfg may be NULL = auto).
  * Errors as mt_transport, plus MT_ERR_INVALID_ARG for an unknown mode or

@@ -8,7 +8,7 @@ from ._binding import (  # noqa: F401
     MT_ALIVE, MT_STOPPED, MT_EXIT_Z, MT_EXIT_XY, MT_MAX_STEPS, MT_INVALID,
     MtError, declared_symbols, library_path, load_library,
     mt_abi_version, mt_last_error, mt_create, mt_destroy, mt_device_bytes,
-    mt_transport, mt_transport_scaled, mt_transport_cfg, mt_transport_workspace_bytes,
+    mt_transport, mt_transport_scaled, mt_transport_cfg, mt_transport_workspace_bytes, mt_transport_launches,
     MT_LAUNCH_AUTO, MT_LAUNCH_STATIC, MT_LAUNCH_PERSISTENT, MT_LAUNCH_COMPACT, MT_SAMPLER_ICDF, MT_SAMPLER_ALIAS,
     MT_ORDER_AUTO, MT_ORDER_ALWAYS, MT_ORDER_NEVER,
     mt_transport_noalloc, MT_NOALLOC_MAX_MUONS,

@@ -115,6 +115,7 @@ _SIGNATURES = {
     "mt_transport_cfg": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P,
                           C.c_int32, C.POINTER(mt_launch_cfg), _P], C.c_int),
     "mt_transport_workspace_bytes": ([C.c_int64], C.c_int64),
+    "mt_transport_launches": ([_P, C.c_int64, C.c_float, C.c_int32, C.POINTER(mt_launch_cfg)], C.c_int64),
     "mt_transport_noalloc": ([_P, C.POINTER(mt_muon_soa), C.c_int64, C.c_float, C.c_int32, C.c_uint64, _P],
                              C.c_int),
     "mt_ckpt_bytes": ([C.c_int64, C.c_int32, C.c_int32], C.c_int64),
@@ -370,6 +371,14 @@ def mt_transport_scaled(handle: int, muons: Dict, step_len: float, max_steps: in
 
 def mt_transport_workspace_bytes(n: int) -> int:
     return load_library().mt_transport_workspace_bytes(int(n))
+
+
+def mt_transport_launches(handle: int, n: int, step_len: float, max_steps: int, mode: int = MT_LAUNCH_AUTO,
+                          steps_per_pass: int = 0, order: int = MT_ORDER_AUTO) -> int:
+    """Kernel launches of one mt_transport_cfg call with these arguments (-1: invalid)."""
+    cfg = mt_launch_cfg(int(mode), 0, int(steps_per_pass), int(order), None, 0)
+    return int(load_library().mt_transport_launches(C.c_void_p(handle), int(n), float(step_len), int(max_steps),
+                                                    C.byref(cfg)))
 
 
 def mt_transport_cfg(handle: int, muons: Dict, step_len: float, max_steps: int, seed: int, alpha=None,

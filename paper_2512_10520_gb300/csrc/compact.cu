@@ -26,6 +26,32 @@ int64_t compact_workspace_bytes(int64_t n)
     return 256 + 2 * 4 * cap * (int64_t)sizeof(float4) + 2 * (int64_t)kSortBins * (int64_t)sizeof(unsigned);
 }
 
+// Launch plan of one compacting call: its passes, and whether the live list is
+// reordered (after compact_init and after the passes reorder_after names).
+CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode)
+{
+    CompactPlan pl;
+    // a muon that starts at step 0 needs ceil(max_steps / S) passes
+    pl.passes = max_steps > 0 ? (max_steps + S - 1) / S : 1;
+    pl.order = w.sort_bins > 0 && order_mode != MT_ORDER_NEVER &&
+               (order_mode == MT_ORDER_ALWAYS || n >= MT_SORT_MIN_MUONS);
+    return pl;
+}
+
+static bool reorder_after(const CompactPlan &pl, int p)
+{
+    return pl.order && p + 1 < pl.passes && (p + 1) % MT_SORT_EVERY == 0;
+}
+
+int64_t compact_launches(const CompactPlan &pl)
+{
+    int64_t c = 1 + pl.passes;
+    if (pl.order) c += 2;
+    for (int p = 0; p < pl.passes; ++p)
+        if (reorder_after(pl, p)) c += 2;
+    return c;
+}
+
 template <int GEOM, int FIELD>
 static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
                               cudaStream_t st, int S, int blocks_per_sm, int order_mode, char *ws)
@@ -36,12 +62,11 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
     unsigned *offs = hist + kSortBins;
     cudaError_t e = cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    // a muon that starts at step 0 needs ceil(max_steps / S) passes
-    const int passes = rp.max_steps > 0 ? (rp.max_steps + S - 1) / S : 1;
     // Spatial order (maps only): the list is reordered after compact_init and
     // after every MT_SORT_EVERY-th pass but the last.
-    const bool order = w.sort_bins > 0 && order_mode != MT_ORDER_NEVER &&
-                       (order_mode == MT_ORDER_ALWAYS || n >= MT_SORT_MIN_MUONS);
+    const CompactPlan plan = compact_plan(w, n, rp.max_steps, S, order_mode);
+    const int passes = plan.passes;
+    const bool order = plan.order;
     if (order) {
         e = cudaFuncSetAttribute(sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
         if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)w.sort_bins * sizeof(unsigned), st);
@@ -74,7 +99,7 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
     if (e == cudaSuccess && order) e = reorder(1, ctr);
     if (e != cudaSuccess) return e;
     for (int p = 0; p < passes; ++p) {
-        const bool count = order && p + 1 < passes && (p + 1) % MT_SORT_EVERY == 0;
+        const bool count = reorder_after(plan, p);
         compact_pass<GEOM, FIELD><<<(unsigned)grid, kBlock, 0, st>>>(w, soa, rp, buf[cur], buf[cur ^ 1], ctr + p % 3,
                                                                      ctr + (p + 1) % 3, ctr + (p + 2) % 3,
                                                                      ctr + 3 + p % 3, ctr + 3 + (p + 1) % 3, S,

@@ -167,5 +167,11 @@ mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own);
 mt_status build_geometry(const mt_geometry_desc *g, const mt_field_desc *f, WorldParams &w, DevOwner &own);
 mt_status build_field(const mt_field_desc *f, WorldParams &w, DevOwner &own);
 void noalloc_prepare(const WorldParams &w, int dev);   // noalloc.cu
+struct CompactPlan {   // compact.cu
+    int passes;
+    bool order;
+};
+CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);
+int64_t compact_launches(const CompactPlan &pl);
 int default_steps_per_pass(const WorldParams &w, float step_len);   // transport.cu
 }  // namespace mt

@@ -154,10 +154,13 @@ extern "C" int64_t mt_transport_workspace_bytes(int64_t n) { return compact_work
 namespace mt {
 // Default pass length of the compacting transport.  The muons in flight during
 // a pass span about S d of z, so the field map's working set is the node
-// layers of that slab; the longest S in {64, 48, 32, 24, 16} whose slab fits
-// in three quarters of L2 keeps the gathers L2 hits (measured on shield1e8,
-// 400 x 400 x 1200 map, 16M muons: S = 16 4.78e10 muon-steps/s, S = 64
-// 4.07e10; on shield1e6, 200 x 200 x 600, S = 64 is best and fits).
+// layers of that slab; the longest S in {128, 96, 64, 48, 32, 24, 16} whose
+// slab fits in three quarters of L2 keeps the gathers L2 hits (measured on
+// shield1e8, 400 x 400 x 1200 map, 16M muons: S = 16 4.78e10 muon-steps/s,
+// S = 64 4.07e10).  On shield1e6 (200 x 200 x 600) S = 128 fits; with the
+// live list's spatial order it is the fastest there, since the list is
+// reordered half as often (5.34e10 against 5.32e10 at 96, 5.30e10 at 64 and
+// 5.23e10 at 48).  Without a map the pass length is 64.
 int default_steps_per_pass(const WorldParams &w, float step_len)
 {
     if (w.field_kind != MT_FIELD_MAP && w.field_kind != MT_FIELD_MAP_NEAREST) return 64;
@@ -167,9 +170,12 @@ int default_steps_per_pass(const WorldParams &w, float step_len)
     const double layer = w.field_kind == MT_FIELD_MAP ? 32.0 * (w.fdims[0] - 1) * (double)w.fdims[1]
                                                       : 16.0 * w.fdims[0] * (double)w.fdims[1];
     const double sz = (double)w.frs_h[2] + (double)w.frs_l[2];
-    const int cand[5] = {64, 48, 32, 24, 16};
+    const int cand[7] = {128, 96, 64, 48, 32, 24, 16};
+    // the map read at every RK4 stage takes at most 64 steps (measured on
+    // shield1e6: 2.15e10 muon-steps/s against 2.00e10 at 128)
+    const int longest = w.field_per_stage ? 64 : 128;
     for (int S : cand)
-        if (layer * (S * (double)step_len / sz + 2.0) <= 0.75 * l2) return S;
+        if (S <= longest && layer * (S * (double)step_len / sz + 2.0) <= 0.75 * l2) return S;
     return 16;
 }
 }  // namespace mt
@@ -306,6 +312,24 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     }
     if (e != cudaSuccess) return cuda_fail(e, "transport launch");
     return MT_OK;
+}
+
+extern "C" int64_t mt_transport_launches(const mt_handle *h, int64_t n, float step_len, int32_t max_steps,
+                                         const mt_launch_cfg *cfg)
+{
+    if (!h || n < 0 || !(step_len > 0.0f) || !isfinite(step_len) || max_steps < 0) return -1;
+    mt_launch_cfg lc = {MT_LAUNCH_AUTO, 0, 0, 0, nullptr, 0};
+    if (cfg) lc = *cfg;
+    if (lc.mode < MT_LAUNCH_AUTO || lc.mode > MT_LAUNCH_COMPACT || lc.steps_per_pass < 0 ||
+        lc.order < MT_ORDER_AUTO || lc.order > MT_ORDER_NEVER)
+        return -1;
+    if (n == 0) return 0;
+    if (lc.mode == MT_LAUNCH_COMPACT || (lc.mode == MT_LAUNCH_AUTO && n < ((int64_t)1 << 31))) {
+        DeviceGuard g(h->device);
+        const int S = lc.steps_per_pass > 0 ? lc.steps_per_pass : default_steps_per_pass(h->w, step_len);
+        return compact_launches(compact_plan(h->w, n, max_steps, S, lc.order));
+    }
+    return 1;
 }
 
 extern "C" mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len,

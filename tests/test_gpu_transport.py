@@ -132,6 +132,32 @@ def test_spatial_order_is_bit_identical():
                                 mode=mt.MT_LAUNCH_COMPACT, order=3)
 
 
+def test_launch_count_query(wl0, wl1_small):
+    """mt_transport_launches reports one call's kernels: compact_init, the passes,
+    and a scan and a scatter per reorder of the live list (after compact_init and
+    every second pass but the last)."""
+    import paper_2512_10520_gb300 as mt
+    with mt.World.from_workload(wl0) as world:      # no map: never reordered
+        assert mt.mt_transport_launches(world.handle, wl0.n, wl0.step_len, wl0.max_steps) == 1 + 4
+        assert mt.mt_transport_launches(world.handle, wl0.n, wl0.step_len, wl0.max_steps,
+                                        order=mt.MT_ORDER_ALWAYS) == 1 + 4
+        assert mt.mt_transport_launches(world.handle, wl0.n, wl0.step_len, wl0.max_steps,
+                                        mode=mt.MT_LAUNCH_STATIC) == 1
+        assert mt.mt_transport_launches(world.handle, 0, wl0.step_len, wl0.max_steps) == 0
+        assert mt.mt_transport_launches(world.handle, wl0.n, -1.0, wl0.max_steps) == -1
+        assert mt.mt_transport_launches(world.handle, wl0.n, wl0.step_len, wl0.max_steps, order=7) == -1
+    wl = wl1_small
+    with mt.World.from_workload(wl) as world:
+        passes = (wl.max_steps + 6) // 7
+        assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=7) == 1 + passes
+        assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=7,
+                                        order=mt.MT_ORDER_ALWAYS) == 1 + passes + 2 + 2 * ((passes - 1) // 2)
+        auto = mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps)
+        never = mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps, order=mt.MT_ORDER_NEVER)
+        p = never - 1
+        assert auto == never + 2 + 2 * ((p - 1) // 2)
+
+
 def test_compact_mode_workspace_and_edge_cases(wl0):
     import paper_2512_10520_gb300 as mt
     import torch
