@@ -532,17 +532,21 @@ __global__ void __launch_bounds__(kBlock, tape_min_blocks<GEOM, FIELD>())
 // steps backwards (tape of the pass at tape_base + tape_off[0], column = list
 // entry), carrying (dL/dr, dL/dp) of muon idx in adj[6][n] and accumulating
 // dL/dalpha.  Nothing is done when *flag is set (the tape was not written).
+// cols (if not null): only the *sel_count entries cols[0 ..] of the list are
+// reversed (the full tape's entries with a nonzero cotangent).
 template <int GEOM, int FIELD>
 __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
     adjoint_pass(const WorldParams w, const RunParams rp, LiveBuf ck, const unsigned long long *count_p, float *adj,
                  int64_t n, double *dalpha, const char *tape_base, const unsigned long long *tape_off,
-                 const unsigned int *flag, unsigned long long *work, unsigned long long *wzero)
+                 const unsigned int *flag, unsigned long long *work, unsigned long long *wzero, const unsigned *cols,
+                 const unsigned long long *sel_count)
 {
     __shared__ SmemWorld sw;
     __shared__ float sacc[3][MT_MAX_BOXES];
     const int64_t count = (int64_t)*count_p;
+    const int64_t todo = cols ? (int64_t)*sel_count : count;
     if (wzero && blockIdx.x == 0 && threadIdx.x == 0) *wzero = 0ull;
-    if (count == 0 || *flag) return;
+    if (todo == 0 || *flag) return;
     stage_world(sw, w, rp);
     for (int t = threadIdx.x; t < 3 * MT_MAX_BOXES; t += blockDim.x) (&sacc[0][0])[t] = 0.0f;
     __syncthreads();
@@ -554,9 +558,10 @@ __global__ void __launch_bounds__(kBlock, MT_ADJ_MIN_BLOCKS)
         unsigned long long b = 0;
         if (lane == 0) b = atomicAdd(work, 32ull);
         const int64_t base = (int64_t)__shfl_sync(0xFFFFFFFFu, b, 0);
-        if (base >= count) break;
-        const int64_t i = base + lane;
-        if (i >= count) continue;
+        if (base >= todo) break;
+        const int64_t li = base + lane;
+        if (li >= todo) continue;
+        const int64_t i = cols ? (int64_t)cols[li] : li;
         tr.tid = i;
         const float q = ck.w0[i].w;
         const int64_t idx = __float_as_int(ck.w2[i].w);
@@ -771,6 +776,27 @@ __global__ void __launch_bounds__(kBlock) select_live(LiveBuf in, const unsigned
     }
 }
 
+// The positions in list `in` (*cin entries) of the muons with a nonzero
+// cotangent in gfin (see select_live), appended to cols at *cout: the full
+// tape's backward reverses those columns only.
+__global__ void __launch_bounds__(kBlock) select_cols(LiveBuf in, const unsigned long long *cin, const float *gfin,
+                                                      int64_t n, unsigned *cols, unsigned long long *cout)
+{
+    const int64_t count = (int64_t)*cin;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool keep = false;
+        if (i < count) {
+            const int64_t m = (int64_t)__float_as_int(in.w2[i].w);
+            keep = gfin[m] != 0.0f || gfin[n + m] != 0.0f || gfin[2 * n + m] != 0.0f || gfin[3 * n + m] != 0.0f ||
+                   gfin[4 * n + m] != 0.0f || gfin[5 * n + m] != 0.0f;
+        }
+        const int64_t slot = warp_append(cout, keep);
+        if (keep) cols[slot] = (unsigned)i;
+    }
+}
+
 // Scratch of the recompute form's backward: two slots, each a 256-byte header
 // (region offsets at bytes 0-15, the flag at 64, the recorded pass's and the
 // reverse pass's work counters at 128 and 136, the selected entries' count at
@@ -864,7 +890,8 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
         if (e != cudaSuccess) return;
         adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, selected(p), cnt, adj, n, dalpha, h + 256,
                                                            reinterpret_cast<const unsigned long long *>(h),
-                                                           reinterpret_cast<const unsigned int *>(h + 64), wc + 1, wc);
+                                                           reinterpret_cast<const unsigned int *>(h + 64), wc + 1, wc,
+                                                           nullptr, nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ev[P + p], st);
     };
@@ -882,9 +909,17 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
     return e;
 }
 
+// scratch: the selected columns of one pass (n u32) and the passes' counts of
+// them (L.passes u64), see tape_backward_scratch_bytes.
+static int64_t tape_backward_scratch_bytes(int64_t n, int32_t max_steps, int K)
+{
+    const CkptLayout L = ckpt_layout(n, max_steps, K);
+    return round_up((n > 0 ? n : 1) * 4, 256) + round_up((int64_t)L.passes * 8, 256);
+}
+
 template <int GEOM, int FIELD>
 static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
-                                 char *buf, float *adj, char *)
+                                 char *buf, float *adj, char *scratch, const float *gfin)
 {
     const TapeLayout T = tape_layout(n, rp.max_steps, K);
     const CkptLayout &L = T.ck;
@@ -897,11 +932,17 @@ static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParam
     cudaError_t e = cudaMemsetAsync(dalpha, 0, 3 * MT_MAX_BOXES * sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(wc, 0, (size_t)(L.passes + 1) * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    unsigned *cols = reinterpret_cast<unsigned *>(scratch);
+    unsigned long long *sel = reinterpret_cast<unsigned long long *>(scratch + round_up((n > 0 ? n : 1) * 4, 256));
+    if (e == cudaSuccess) e = cudaMemsetAsync(sel, 0, (size_t)L.passes * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
     const int grid = resident_grid((const void *)adjoint_pass<GEOM, FIELD>, n);
+    const int sgrid = resident_grid((const void *)select_cols, n);
     for (int p = L.passes - 1; p >= 0; --p) {
-        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, live_buf_at(buf + L.lists_off + p * L.list_bytes, n),
-                                                          ctr + p, adj, n, dalpha, buf + T.region_off, toff + p, flag,
-                                                          wc + p, nullptr);
+        const LiveBuf lp = live_buf_at(buf + L.lists_off + p * L.list_bytes, n);
+        select_cols<<<sgrid, kBlock, 0, st>>>(lp, ctr + p, gfin, n, cols, sel + p);
+        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, buf + T.region_off,
+                                                          toff + p, flag, wc + p, nullptr, cols, sel + p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1173,16 +1214,18 @@ extern "C" mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, in
         }
         return MT_OK;
     }
+    // scratch: the selected columns, then the adjoint state unless the caller
+    // takes dL/d(initial state)
     float *adj = dL_dinitial;
+    const int64_t cbytes = tape_backward_scratch_bytes(n, max_steps, steps_per_pass);
     char *scratch = nullptr;
-    cudaError_t e = cudaSuccess;
-    if (!adj) {
-        e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)(6 * n * sizeof(float)), st);
-        if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
-        adj = reinterpret_cast<float *>(scratch);
-    }
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch),
+                                    (size_t)(cbytes + (adj ? 0 : 6 * n * (int64_t)sizeof(float))), st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
+    if (!adj) adj = reinterpret_cast<float *>(scratch + cbytes);
     e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = MT_DISPATCH(tape_backward, w, n, rp, st, steps_per_pass, (char *)tape, adj, nullptr);
+    if (e == cudaSuccess)
+        e = MT_DISPATCH(tape_backward, w, n, rp, st, steps_per_pass, (char *)tape, adj, scratch, dL_dfinal);
     if (e == cudaSuccess && alpha && n_block > 0) {
         const TapeLayout T = tape_layout(n, max_steps, steps_per_pass);
         alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)tape + T.ck.alpha_off), dL_dalpha,
