@@ -372,8 +372,13 @@ void DevOwner::release()
 mt_status build_hist(const mt_hist_desc *hd, WorldParams &w, DevOwner &own)
 {
     const int ncell = hd->nf * hd->ntheta;
+    // At least four guide slots per cell, up to 32K: a slot that holds a cell
+    // boundary sends its draws to the binary search, and a warp waits for its
+    // longest search.  Measured on shield1e6 (8192 cells): one slot per cell
+    // 5.33e10 muon-steps/s, two 5.39e10, four 5.42e10, eight 5.42e10 (the guide
+    // rows of its 192 histograms grow from 6 to 24 MB at four).
     int gbits = 12;
-    while ((1 << gbits) < ncell && gbits < 15) ++gbits;   // at least one guide slot per cell up to 32K
+    while ((1 << gbits) < 4 * ncell && gbits < 15) ++gbits;
     std::vector<HistRec> rec;
     std::vector<uint32_t> guide;
     std::vector<uint2> pairs;
