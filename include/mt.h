@@ -266,7 +266,12 @@ mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, flo
  *                       reordered by the coarse xy cell of the map they stand
  *                       in (a counting sort every second pass), so a warp's
  *                       muons share their field-map corners; the order changes
- *                       no result;
+ *                       no result.  A call of 2^19 muons or more runs as two
+ *                       groups of half the muons, each with its own list, the
+ *                       second on a stream the call creates (forked from and
+ *                       joined back to `stream` with events, released when its
+ *                       work is done), so one group's passes fill the SMs the
+ *                       other's pass tails leave idle; the workspace holds both;
  *  MT_LAUNCH_AUTO       the fastest measured form: MT_LAUNCH_COMPACT with the
  *                       default pass length (the static grid for n >= 2^31). */
 enum { MT_LAUNCH_AUTO = 0, MT_LAUNCH_STATIC = 1, MT_LAUNCH_PERSISTENT = 2, MT_LAUNCH_COMPACT = 3 };
@@ -310,7 +315,10 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
  * steps_per_pass steps; a device work queue hands items naming an instance to
  * a resident grid whose blocks stage that instance's world in shared memory,
  * and the block's warps take 32-muon chunks of the instance until none are
- * left; survivors are compacted per instance between passes.  The paper
+ * left; survivors are compacted per instance between passes.  From 2^19
+ * muons in all and two instances, the instances run as two groups of about
+ * equal muon counts, each its own launch sequence, the second on a stream
+ * the call creates (forked from and joined back to `stream`).  The paper
  * runs one geometry per launch; scanning many magnet configurations is the
  * design-optimisation use it motivates (Sec. Introduction).
  * ------------------------------------------------------------------------- */

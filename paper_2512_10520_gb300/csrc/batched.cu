@@ -22,10 +22,15 @@
 #include "compact.cuh"
 
 // Resident threads per SM the compiler must allow for in batch_pass (register
-// budget: 1024 threads = 64 registers; measured on worlds256, 256 instances with
-// warp chunks: 730 ms against 752 ms at 768 threads = 80 registers).  The
+// budget).  Voxel worlds: 1280 threads = 48 registers, no spill (measured on
+// worlds256, 256 instances with the spatial order: 594.6 ms against 623.9 ms
+// at 1024 threads = 64 registers).  Box worlds keep 1024 (at 48 registers they
+// spill 4-16 bytes; earlier, 1024 threads 730 ms against 752 ms at 768).  The
 // variants that spill at 64 registers (per-stage field reads; polyhedra) keep
 // 768.
+#ifndef MT_BATCH_THREADS_PER_SM_VOXELS
+#define MT_BATCH_THREADS_PER_SM_VOXELS 1280
+#endif
 #ifndef MT_BATCH_THREADS_PER_SM
 #define MT_BATCH_THREADS_PER_SM 1024
 #endif
@@ -38,7 +43,8 @@ template <int GEOM, int FIELD>
 constexpr int batch_threads_per_sm()
 {
     return (GEOM == MT_GEOM_POLYHEDRA || FIELD == kFieldMapStaged) ? MT_BATCH_THREADS_PER_SM_WIDE
-                                                                   : MT_BATCH_THREADS_PER_SM;
+           : GEOM == MT_GEOM_VOXELS                                 ? MT_BATCH_THREADS_PER_SM_VOXELS
+                                                                    : MT_BATCH_THREADS_PER_SM;
 }
 }  // namespace mt
 
@@ -77,7 +83,36 @@ struct BatchWs {
     unsigned *hist, *offs;      // [n_inst][kSortBins] each: the spatial order's counts and first slots
     char *live0, *live1;        // two live buffers of N entries
     int64_t N;
+    const WorldParams *inst;    // device table of this group's instances
 };
+
+// Instance groups of one batched call: with MT_BATCH_GROUP_MIN_MUONS muons or
+// more and at least two instances, the instances [0, s) and [s, n_inst) run as
+// two independent batches on two streams (the split s makes their muon counts
+// as even as it can), so one group's passes fill the SMs the other's pass
+// tails leave idle, as the plain transport's two muon groups do.
+#ifndef MT_BATCH_GROUP_MIN_MUONS
+#define MT_BATCH_GROUP_MIN_MUONS (1 << 19)
+#endif
+
+// Returns the number of groups (1 or 2); split = first instance of group 1.
+static int batch_groups(int n_inst, const int64_t *n, int &split)
+{
+    int64_t N = 0;
+    for (int i = 0; i < n_inst; ++i) N += n[i] > 0 ? n[i] : 0;
+    split = n_inst;
+    if (n_inst < 2 || N < MT_BATCH_GROUP_MIN_MUONS) return 1;
+    int64_t run = 0, best = -1;
+    for (int s = 1; s < n_inst; ++s) {
+        run += n[s - 1] > 0 ? n[s - 1] : 0;
+        const int64_t d = run * 2 > N ? run * 2 - N : N - run * 2;
+        if (best < 0 || d < best) {
+            best = d;
+            split = s;
+        }
+    }
+    return 2;
+}
 
 static int64_t round256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
@@ -416,17 +451,17 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
     if (order) e = cudaMemsetAsync(ws.hist, 0, (size_t)n_inst * kSortBins * sizeof(unsigned), st);
     // the live entries of the list just written to L[src] go to the other list in key order
     auto reorder = [&](int src, const unsigned int *c) {
-        batch_scan<<<n_inst, 1024, kScanSmem, st>>>(b->d_inst, ws.hist, ws.offs);
+        batch_scan<<<n_inst, 1024, kScanSmem, st>>>(ws.inst, ws.hist, ws.offs);
         cudaError_t f = cudaGetLastError();
         if (f != cudaSuccess) return f;
-        batch_scatter<<<(unsigned)sg, 256, 0, st>>>(b->d_inst, ws.off, n_inst, c, L[src], L[src ^ 1], ws.offs);
+        batch_scatter<<<(unsigned)sg, 256, 0, st>>>(ws.inst, ws.off, n_inst, c, L[src], L[src ^ 1], ws.offs);
         return cudaGetLastError();
     };
     // the current list is L[cur]; a pass appends to the other one, which becomes
     // current unless it is reordered back into L[cur]
     int cur = 0;
     if (e == cudaSuccess) {
-        batch_init<<<(unsigned)ig, 256, 0, st>>>(b->d_inst, ws.off, n_inst, ws.soa, rp, L[order ? 1 : 0], ws.cnt,
+        batch_init<<<(unsigned)ig, 256, 0, st>>>(ws.inst, ws.off, n_inst, ws.soa, rp, L[order ? 1 : 0], ws.cnt,
                                                  order ? ws.hist : nullptr);
         e = cudaGetLastError();
     }
@@ -441,7 +476,7 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
         batch_pass<GEOM, FIELD, BLOCK, WS><<<(unsigned)grid, BLOCK, 0, st>>>(
-            b->d_inst, ws.soa, ws.off, n_inst, rp, L[cur], L[cur ^ 1], c_in, c_out, ws.cof, ws.queue, ws.sub, S,
+            ws.inst, ws.soa, ws.off, n_inst, rp, L[cur], L[cur ^ 1], c_in, c_out, ws.cof, ws.queue, ws.sub, S,
             count ? ws.hist : nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess && count) e = reorder(cur ^ 1, c_out);
@@ -621,9 +656,16 @@ int64_t mt_batch_device_bytes(const mt_batch *b)
 int64_t mt_batch_workspace_bytes(const mt_batch *b, const int64_t *n)
 {
     if (!b || !n) return -1;
-    int64_t N = 0;
-    for (int i = 0; i < b->n_inst; ++i) N += n[i] > 0 ? n[i] : 0;
-    return batch_ws_layout(b->n_inst, N, nullptr, nullptr);
+    int split = 0;
+    const int G = batch_groups(b->n_inst, n, split);
+    int64_t bytes = 0;
+    for (int g = 0; g < G; ++g) {
+        const int i0 = g == 0 ? 0 : split, i1 = G == 1 || g == 1 ? b->n_inst : split;
+        int64_t N = 0;
+        for (int i = i0; i < i1; ++i) N += n[i] > 0 ? n[i] : 0;
+        bytes += round256(batch_ws_layout(i1 - i0, N, nullptr, nullptr));
+    }
+    return bytes;
 }
 
 mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64_t *n, float step_len,
@@ -670,7 +712,16 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
         off[i + 1] = off[i] + (unsigned long long)n[i];
     }
     const int64_t N = (int64_t)off[b->n_inst];
-    const int64_t need = batch_ws_layout(b->n_inst, N, nullptr, nullptr);
+    // instance groups (see batch_groups) and their workspaces, one after the other
+    int split = b->n_inst;
+    const int G = batch_groups(b->n_inst, n, split);
+    int gi0[2] = {0, split}, gi1[2] = {G == 1 ? b->n_inst : split, b->n_inst};
+    int64_t gN[2] = {0, 0}, gws[2] = {0, 0};
+    for (int g = 0; g < G; ++g) {
+        gN[g] = (int64_t)(off[gi1[g]] - off[gi0[g]]);
+        gws[g] = round256(batch_ws_layout(gi1[g] - gi0[g], gN[g], nullptr, nullptr));
+    }
+    const int64_t need = gws[0] + gws[1];
     // spatial order of the live lists (maps only; see compact.cuh)
     const bool order = (b->field_kind == MT_FIELD_MAP || b->field_kind == MT_FIELD_MAP_NEAREST) &&
                        c.order != MT_ORDER_NEVER && (c.order == MT_ORDER_ALWAYS || N >= MT_SORT_MIN_MUONS);
@@ -710,8 +761,11 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
         if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
         own = true;
     }
-    BatchWs ws{};
-    batch_ws_layout(b->n_inst, N, &ws, base);
+    BatchWs ws[2]{};
+    for (int g = 0; g < G; ++g) {
+        batch_ws_layout(gi1[g] - gi0[g], gN[g], &ws[g], base + (g ? gws[0] : 0));
+        ws[g].inst = b->d_inst + gi0[g];
+    }
     RunParams rp;
     rp.d = step_len;
     rp.kd = (float)(0.299792458 * (double)step_len);
@@ -721,20 +775,47 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     rp.n_block = 0;
     rp.instance = 0;
     rp.id_offset = 0;
-    // per-call inputs: region offsets, the instances' arrays, cleared counters
-    e = cudaMemcpyAsync(ws.off, off.data(), off.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ws.soa, soas, sizeof(mt_muon_soa) * (size_t)b->n_inst, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws.cnt, 0, 3 * (size_t)b->n_inst * sizeof(unsigned int), cs);
+    // per-call inputs of each group: region offsets from its first instance,
+    // its instances' arrays, cleared counters
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const int ni = gi1[g] - gi0[g];
+        std::vector<unsigned long long> og(ni + 1);
+        for (int i = 0; i <= ni; ++i) og[i] = off[gi0[g] + i] - off[gi0[g]];
+        e = cudaMemcpyAsync(ws[g].off, og.data(), og.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws[g].soa, soas + gi0[g], sizeof(mt_muon_soa) * (size_t)ni, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ws[g].cnt, 0, 3 * (size_t)ni * sizeof(unsigned int), cs);
+    }
     if (e == cudaSuccess && order) e = cudaFuncSetAttribute(batch_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+    // both groups' launch sequences on s0: group 1 on the second stream `aux`,
+    // forked from s0 and joined back into it (aux is created before and
+    // destroyed after any graph capture of this sequence)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (e == cudaSuccess && G == 2) e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess && G == 2) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && G == 2) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    auto launch_groups = [&](cudaStream_t s0) -> cudaError_t {
+        if (G == 1) return dispatch_batch(b, ws[0], gi1[0] - gi0[0], rp, block, S, staging, order, s0);
+        // fork before either group's work, so that the two run side by side
+        cudaError_t f = cudaEventRecord(fork, s0);
+        if (f == cudaSuccess) f = cudaStreamWaitEvent(aux, fork, 0);
+        if (f == cudaSuccess) f = dispatch_batch(b, ws[0], gi1[0] - gi0[0], rp, block, S, staging, order, s0);
+        if (f == cudaSuccess) f = dispatch_batch(b, ws[1], gi1[1] - gi0[1], rp, block, S, staging, order, aux);
+        // joined also after an error, so nothing on aux outlives the scratch
+        cudaError_t j = cudaEventRecord(join, aux);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s0, join, 0);
+        if (j != cudaSuccess && f == cudaSuccess) f = j;
+        return f;
+    };
     if (e == cudaSuccess) {
         if (c.use_graph) {
             // capture the launch sequence once per (arguments) and replay it
-            std::vector<char> key(sizeof(void *) + 5 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 8);
+            std::vector<char> key(sizeof(void *) + 6 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 16);
             char *kp = key.data();
             memcpy(kp, &base, sizeof(void *));
             kp += sizeof(void *);
-            const int ints[5] = {block, S, max_steps, staging, order ? 1 : 0};
+            const int ints[6] = {block, S, max_steps, staging, order ? 1 : 0, split};
             memcpy(kp, ints, sizeof(ints));
             kp += sizeof(ints);
             memcpy(kp, &step_len, sizeof(float));
@@ -742,6 +823,8 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
             memcpy(kp, &seed, sizeof(uint64_t));
             kp += sizeof(uint64_t);
             memcpy(kp, &N, sizeof(int64_t));
+            kp += sizeof(int64_t);
+            memcpy(kp, &gN[0], sizeof(int64_t));
             if (!b->graph || b->graph_key != key) {
                 if (b->graph) {
                     cudaGraphExecDestroy(b->graph);
@@ -752,7 +835,7 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
                 cudaGraph_t gr = nullptr;
                 if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    cudaError_t le = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, order, cap);
+                    cudaError_t le = launch_groups(cap);
                     e = cudaStreamEndCapture(cap, &gr);
                     if (le != cudaSuccess) e = le;
                 }
@@ -763,9 +846,13 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
             }
             if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, cs);
         } else {
-            e = dispatch_batch(b, ws, b->n_inst, rp, block, S, staging, order, cs);
+            e = launch_groups(cs);
         }
     }
+    // released once their work is done
+    if (join) cudaEventDestroy(join);
+    if (fork) cudaEventDestroy(fork);
+    if (aux) cudaStreamDestroy(aux);
     if (own) {
         const cudaError_t f = cudaFreeAsync(base, cs);
         if (e == cudaSuccess) e = f;

@@ -172,6 +172,6 @@ struct CompactPlan {   // compact.cu
     bool order;
 };
 CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);
-int64_t compact_launches(const CompactPlan &pl);
+int64_t compact_call_launches(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);
 int default_steps_per_pass(const WorldParams &w, float step_len);   // transport.cu
 }  // namespace mt

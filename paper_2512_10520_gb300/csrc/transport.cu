@@ -327,7 +327,7 @@ extern "C" int64_t mt_transport_launches(const mt_handle *h, int64_t n, float st
     if (lc.mode == MT_LAUNCH_COMPACT || (lc.mode == MT_LAUNCH_AUTO && n < ((int64_t)1 << 31))) {
         DeviceGuard g(h->device);
         const int S = lc.steps_per_pass > 0 ? lc.steps_per_pass : default_steps_per_pass(h->w, step_len);
-        return compact_launches(compact_plan(h->w, n, max_steps, S, lc.order));
+        return compact_call_launches(h->w, n, max_steps, S, lc.order);
     }
     return 1;
 }

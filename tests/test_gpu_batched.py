@@ -198,6 +198,39 @@ def test_world_staging_layouts_are_bit_identical(instances, batch, staging):
         _assert_same(_host(devs), ref)
 
 
+def test_two_instance_groups_are_bit_identical(hist):
+    """From 2^19 muons a batched call runs its instances as two groups of about
+    equal muon counts on two streams: each instance ends exactly as a separate
+    mt_transport call, with and without a CUDA graph, in a caller's workspace of
+    exactly mt_batch_workspace_bytes."""
+    import torch
+    import paper_2512_10520_gb300 as mt
+    sizes = [200_000, 1, 250_000, 0, 150_000]
+    insts = [gen.batched_instance(40 + i, n=n) for i, n in enumerate(sizes)]
+    assert sum(sizes) >= 1 << 19
+    ids = [10**6 * i for i in range(len(insts))]
+    words = list(range(len(insts)))
+    ref = _separate(hist, insts, ids, words)
+    with mt.Batch(hist, len(insts)) as b:
+        for i, inst in enumerate(insts):
+            b.set_instance(i, inst["geometry"], inst["field"])
+        for use_graph in (False, True, True):
+            devs = _dev(insts)
+            b.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, block=128,
+                        steps_per_pass=64, use_graph=use_graph, id_offsets=ids, instances=words)
+            _assert_same(_host(devs), ref)
+        n = [d["x"].numel() for d in _dev(insts)]
+        nbytes = b.workspace_bytes(n)
+        devs = _dev(insts)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        b.transport(devs, gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED, workspace=ws,
+                    id_offsets=ids, instances=words)
+        _assert_same(_host(devs), ref)
+        with pytest.raises(mt.MtError):
+            b.transport(_dev(insts), gen.BATCH_STEP_LEN, gen.BATCH_MAX_STEPS, gen.BATCH_SEED,
+                        workspace=ws[: nbytes - 256], id_offsets=ids, instances=words)
+
+
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_spatial_order_is_bit_identical(instances, batch, use_graph):
     """Every instance's live list reordered by coarse map cell between passes

@@ -152,10 +152,42 @@ def test_launch_count_query(wl0, wl1_small):
         assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=7) == 1 + passes
         assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=7,
                                         order=mt.MT_ORDER_ALWAYS) == 1 + passes + 2 + 2 * ((passes - 1) // 2)
-        auto = mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps)
-        never = mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps, order=mt.MT_ORDER_NEVER)
-        p = never - 1
-        assert auto == never + 2 + 2 * ((p - 1) // 2)
+        # at the default pass length; from 2^19 muons a call is two groups of half the muons
+        p = mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps) - 1
+        assert mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps,
+                                        order=mt.MT_ORDER_NEVER) == 2 * (1 + p)
+        assert mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps) == \
+            2 * (1 + p + 2 + 2 * ((p - 1) // 2))
+
+
+def test_two_muon_groups_are_bit_identical():
+    """From 2^19 muons a compacting call runs as two halves on two streams (an odd
+    count splits unevenly): every muon ends as in the single-kernel static grid,
+    with and without the spatial order, in a caller's workspace of exactly
+    mt_transport_workspace_bytes."""
+    import paper_2512_10520_gb300 as mt
+    import torch
+    wl = gen.workload("shield1e6", n=(1 << 19) + 3)
+    with mt.World.from_workload(wl) as world:
+        ref = mt.muons_to_device(wl.muons)
+        world.transport(ref, wl.step_len, wl.max_steps, wl.seed, mode=mt.MT_LAUNCH_STATIC)
+        torch.cuda.synchronize()
+        ref = mt.muons_to_host(ref)
+        nbytes = mt.mt_transport_workspace_bytes(wl.n)
+        assert nbytes > mt.mt_transport_workspace_bytes((1 << 19) - 1) + 64 * 4
+        for order in (mt.MT_ORDER_AUTO, mt.MT_ORDER_NEVER):
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            dev = mt.muons_to_device(wl.muons)
+            world.transport(dev, wl.step_len, wl.max_steps, wl.seed, mode=mt.MT_LAUNCH_COMPACT, workspace=ws,
+                            order=order)
+            torch.cuda.synchronize()
+            out = mt.muons_to_host(dev)
+            for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+                np.testing.assert_array_equal(out[k], ref[k], err_msg=f"order {order}, field {k}")
+        with pytest.raises(mt.MtError):
+            world.transport(mt.muons_to_device(wl.muons), wl.step_len, wl.max_steps, wl.seed,
+                            mode=mt.MT_LAUNCH_COMPACT, workspace=torch.empty(nbytes - 256, dtype=torch.uint8,
+                                                                             device="cuda"))
 
 
 def test_compact_mode_workspace_and_edge_cases(wl0):
