@@ -264,7 +264,7 @@ mt_status mt_transport_scaled(mt_handle *h, const mt_muon_soa *s, int64_t n, flo
  *                       mt_transport_workspace_bytes) for the next pass; n must
  *                       be below 2^31.  With a field map the survivors can be
  *                       reordered by the coarse xy cell of the map they stand
- *                       in (a counting sort every second pass), so a warp's
+ *                       in (a counting sort about every 64 steps), so a warp's
  *                       muons share their field-map corners; the order changes
  *                       no result.  A call of 2^19 muons or more runs as two
  *                       groups of half the muons, each with its own list, the

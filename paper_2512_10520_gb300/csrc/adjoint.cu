@@ -671,7 +671,7 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
     unsigned *hist = reinterpret_cast<unsigned *>(ck + L.sort_off), *offs = hist + kSortBins;
     auto list = [&](int p) { return live_buf_at(ck + L.lists_off + p * L.list_bytes, n); };
     // Spatial order of the saved lists (field maps, as the plain transport takes
-    // it): after compact_init and every MT_SORT_EVERY-th pass, survivors go to
+    // it): after compact_init and every sort_every(K)-th pass, survivors go to
     // the list two ahead, still unused, and are scattered in key order into the
     // next one.  The backward then reads every list in that order too.
     const bool order = w.sort_bins > 0 && n >= MT_SORT_MIN_MUONS && L.passes > 1;
@@ -698,7 +698,7 @@ static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, in
     if (e == cudaSuccess && order) e = reorder(list(1), list(0), ctr);
     if (e != cudaSuccess) return e;
     for (int p = 0; p < L.passes; ++p) {
-        const bool count = order && p + 2 <= L.passes && (p + 1) % MT_SORT_EVERY == 0;
+        const bool count = order && p + 2 <= L.passes && (p + 1) % sort_every(K) == 0;
         compact_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, soa, rp, list(p), list(count ? p + 2 : p + 1), ctr + p,
                                                             ctr + p + 1, nullptr, ctr + L.passes + 1 + p, nullptr, K,
                                                             count ? hist : nullptr);

@@ -471,7 +471,7 @@ static cudaError_t run_batch(mt_batch *b, const BatchWs &ws, int n_inst, const R
         unsigned int *c_in = ws.cnt + (p % 3) * n_inst;
         unsigned int *c_out = ws.cnt + ((p + 1) % 3) * n_inst;
         unsigned int *c_zero = ws.cnt + ((p + 2) % 3) * n_inst;
-        const bool count = order && p + 1 < passes && (p + 1) % MT_SORT_EVERY == 0;
+        const bool count = order && p + 1 < passes && (p + 1) % sort_every(S) == 0;
         batch_plan<<<1, 1024, 0, st>>>(c_in, c_zero, n_inst, BLOCK, ws.cof, ws.queue, ws.sub);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;

@@ -77,12 +77,13 @@ CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, 
     pl.passes = max_steps > 0 ? (max_steps + S - 1) / S : 1;
     pl.order = w.sort_bins > 0 && order_mode != MT_ORDER_NEVER &&
                (order_mode == MT_ORDER_ALWAYS || n >= MT_SORT_MIN_MUONS);
+    pl.every = sort_every(S);
     return pl;
 }
 
 static bool reorder_after(const CompactPlan &pl, int p)
 {
-    return pl.order && p + 1 < pl.passes && (p + 1) % MT_SORT_EVERY == 0;
+    return pl.order && p + 1 < pl.passes && (p + 1) % pl.every == 0;
 }
 
 static int64_t compact_launches(const CompactPlan &pl)
@@ -116,7 +117,7 @@ static cudaError_t run_passes(const WorldParams &w, const mt_muon_soa &soa, int6
     cudaError_t e = cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     // Spatial order (maps only): the list is reordered after compact_init and
-    // after every MT_SORT_EVERY-th pass but the last.
+    // after every sort_every(S)-th pass but the last.
     const CompactPlan plan = compact_plan(w, n, rp.max_steps, S, order_mode);
     const int passes = plan.passes;
     const bool order = plan.order;

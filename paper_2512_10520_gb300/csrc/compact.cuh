@@ -40,17 +40,24 @@ namespace mt {
 // key's first slot plus its rank.  A muon's result does not depend on its
 // place in the list, so the order changes the speed only.
 //
-// Measured (GB300, muon-steps/s; the order after every pass / every second
-// pass): shield1e6 1e6 muons +2.2 % / +2.8 %, tapered1e6 +9.2 % / +7.9 %,
-// 262144 muons -1.2 % / +0.2 %, 65536 muons -14 % / -10 % (the scan and the
-// scatter cost about 40 us per reorder whatever the size).  So the list is
-// reordered after every second pass, in calls of at least 2^19 muons.
-#ifndef MT_SORT_EVERY
-#define MT_SORT_EVERY 2
+// Measured (GB300, muon-steps/s; 64-step passes, the order after every pass /
+// every second pass): shield1e6 1e6 muons +2.2 % / +2.8 %, tapered1e6 +9.2 % /
+// +7.9 %, 262144 muons -1.2 % / +0.2 %, 65536 muons -14 % / -10 % (the scan and
+// the scatter cost about 40 us per reorder whatever the size).  With two muon
+// groups and 128-step passes, a reorder after every pass is the faster on
+// shield1e6 (5.80 against 5.72e10; every third pass 5.67e10).  So the list
+// is reordered about every MT_SORT_STEPS steps (after every pass of 64 steps
+// or more, every second of 32, every fourth of 16), in calls of at least
+// 2^19 muons.
+#ifndef MT_SORT_STEPS
+#define MT_SORT_STEPS 64
 #endif
 #ifndef MT_SORT_MIN_MUONS
 #define MT_SORT_MIN_MUONS (1 << 19)
 #endif
+
+// Passes between reorders for passes of S steps.
+__host__ __device__ constexpr int sort_every(int S) { return S >= MT_SORT_STEPS ? 1 : (MT_SORT_STEPS + S - 1) / S; }
 
 __device__ __forceinline__ uint32_t sort_key(const WorldParams &w, float uh, float vh)
 {

@@ -170,6 +170,7 @@ void noalloc_prepare(const WorldParams &w, int dev);   // noalloc.cu
 struct CompactPlan {   // compact.cu
     int passes;
     bool order;
+    int every;   // passes between reorders
 };
 CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);
 int64_t compact_call_launches(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);

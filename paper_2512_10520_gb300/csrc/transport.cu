@@ -157,10 +157,10 @@ namespace mt {
 // layers of that slab; the longest S in {128, 96, 64, 48, 32, 24, 16} whose
 // slab fits in three quarters of L2 keeps the gathers L2 hits (measured on
 // shield1e8, 400 x 400 x 1200 map, 16M muons: S = 16 4.78e10 muon-steps/s,
-// S = 64 4.07e10).  On shield1e6 (200 x 200 x 600) S = 128 fits; with the
-// live list's spatial order it is the fastest there, since the list is
-// reordered half as often (5.34e10 against 5.32e10 at 96, 5.30e10 at 64 and
-// 5.23e10 at 48).  Without a map the pass length is 64.
+// S = 64 4.07e10).  On shield1e6 (200 x 200 x 600) S = 128 fits and is among
+// the fastest: with the live list reordered after every pass and two muon
+// groups, 5.80e10 muon-steps/s at 128 and at 96, 5.74e10 at 64 and 5.76e10
+// at 160.  Without a map the pass length is 64.
 int default_steps_per_pass(const WorldParams &w, float step_len)
 {
     if (w.field_kind != MT_FIELD_MAP && w.field_kind != MT_FIELD_MAP_NEAREST) return 64;

@@ -148,16 +148,21 @@ def test_launch_count_query(wl0, wl1_small):
         assert mt.mt_transport_launches(world.handle, wl0.n, wl0.step_len, wl0.max_steps, order=7) == -1
     wl = wl1_small
     with mt.World.from_workload(wl) as world:
+        # a reorder about every 64 steps: after every 10th pass of 7 steps
         passes = (wl.max_steps + 6) // 7
         assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=7) == 1 + passes
         assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=7,
-                                        order=mt.MT_ORDER_ALWAYS) == 1 + passes + 2 + 2 * ((passes - 1) // 2)
-        # at the default pass length; from 2^19 muons a call is two groups of half the muons
+                                        order=mt.MT_ORDER_ALWAYS) == 1 + passes + 2 + 2 * ((passes - 1) // 10)
+        assert mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps, steps_per_pass=64,
+                                        order=mt.MT_ORDER_ALWAYS) == 1 + 24 + 2 + 2 * 23
+        # at the default pass length (64 steps or more for this map: a reorder after
+        # every pass); from 2^19 muons a call is two groups of half the muons
         p = mt.mt_transport_launches(world.handle, wl.n, wl.step_len, wl.max_steps) - 1
+        assert p <= 24
         assert mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps,
                                         order=mt.MT_ORDER_NEVER) == 2 * (1 + p)
         assert mt.mt_transport_launches(world.handle, 1 << 20, wl.step_len, wl.max_steps) == \
-            2 * (1 + p + 2 + 2 * ((p - 1) // 2))
+            2 * (1 + p + 2 + 2 * (p - 1))
 
 
 def test_two_muon_groups_are_bit_identical():
