@@ -167,3 +167,19 @@ def test_offline_and_edges_host_checks(lib):
     assert st == B.MT_ERR_INVALID_ARG
     st = lib.mt_build_histograms(None, 1, 1, None, 4, 4, 0.2, 0.02, 10, 1, None, None, None)
     assert st == B.MT_ERR_INVALID_ARG
+
+
+def test_compact_workspace_layout(lib):
+    """mt_transport_workspace_bytes: one group below 2^19 muons (256 B of
+    counters, two 64-byte live entries per muon, the spatial order's two
+    16384-word arrays, rounded up to 256 B); from 2^19 muons two groups of
+    n // 2 and n - n // 2 muons, each laid out the same way."""
+    def group(n):
+        b = 256 + 2 * 64 * max(n, 1) + 2 * 16384 * 4
+        return (b + 255) // 256 * 256
+    for n in (0, 1, 777, 65536, (1 << 19) - 1):
+        assert mt.mt_transport_workspace_bytes(n) == group(n), n
+    for n in (1 << 19, (1 << 19) + 3, 10**6, (1 << 31) - 1):
+        assert mt.mt_transport_workspace_bytes(n) == group(n // 2) + group(n - n // 2), n
+    # the no-allocation entry point's fixed array holds one group at its capacity
+    assert mt.mt_transport_workspace_bytes(mt.MT_NOALLOC_MAX_MUONS) == group(mt.MT_NOALLOC_MAX_MUONS)
