@@ -660,7 +660,91 @@ static int resident_grid(const void *kernel, int64_t work)
     return (int)(grid < 1 ? 1 : grid);
 }
 
-int64_t ckpt_bytes(int64_t n, int32_t max_steps, int32_t K) { return ckpt_layout(n, max_steps, K).total; }
+// Muon groups of the checkpointing form, as in the plain transport: from
+// MT_CKPT_GROUP_MIN_MUONS muons, the muons [0, n/2) and [n/2, n) are two
+// checkpointed transports of their own (each with its own layout in the
+// checkpoint buffer, one after the other), run side by side on two streams in
+// the forward and again in the backward, whose recorded and reverse passes
+// leave most of the SMs' warp slots free.
+#ifndef MT_CKPT_GROUP_MIN_MUONS
+#define MT_CKPT_GROUP_MIN_MUONS (1 << 19)
+#endif
+
+struct CkptGroups {
+    int G;
+    int64_t n[2];      // muons of each group
+    int64_t start[2];  // first muon of each group
+    int64_t off[2];    // byte offset of each group's layout in the checkpoint buffer
+};
+
+static CkptGroups ckpt_groups(int64_t n, int32_t max_steps, int32_t K)
+{
+    CkptGroups g;
+    g.G = n >= MT_CKPT_GROUP_MIN_MUONS ? 2 : 1;
+    g.n[0] = g.G == 2 ? n / 2 : n;
+    g.n[1] = n - g.n[0];
+    g.start[0] = 0;
+    g.start[1] = g.n[0];
+    g.off[0] = 0;
+    g.off[1] = round_up(ckpt_layout(g.n[0], max_steps, K).total, 256);
+    return g;
+}
+
+int64_t ckpt_bytes(int64_t n, int32_t max_steps, int32_t K)
+{
+    const CkptGroups g = ckpt_groups(n, max_steps, K);
+    int64_t b = 0;
+    for (int i = 0; i < g.G; ++i) b += round_up(ckpt_layout(g.n[i], max_steps, K).total, 256);
+    return b;
+}
+
+// The muons [off, ...) of s as a SoA of their own (their ids follow from rp).
+static mt_muon_soa soa_from(const mt_muon_soa &s, int64_t off)
+{
+    mt_muon_soa p = s;
+    p.x = s.x + off;
+    p.y = s.y + off;
+    p.z = s.z + off;
+    p.px = s.px + off;
+    p.py = s.py + off;
+    p.pz = s.pz + off;
+    p.q = s.q + off;
+    p.steps = s.steps + off;
+    p.status = s.status + off;
+    return p;
+}
+
+// A second stream forked from st; join() makes st wait for everything given
+// to it, also after an error, and releases stream and events once their work
+// is done.
+struct Fork {
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join_ev = nullptr;
+    cudaError_t begin(cudaStream_t st)
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
+        return e;
+    }
+    cudaError_t join(cudaStream_t st)
+    {
+        cudaError_t e = cudaSuccess;
+        if (aux && join_ev) {
+            e = cudaEventRecord(join_ev, aux);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join_ev, 0);
+            if (e != cudaSuccess) cudaStreamSynchronize(aux);
+        }
+        if (join_ev) cudaEventDestroy(join_ev);
+        if (fork) cudaEventDestroy(fork);
+        if (aux) cudaStreamDestroy(aux);
+        aux = nullptr;
+        fork = join_ev = nullptr;
+        return e;
+    }
+};
 
 template <int GEOM, int FIELD>
 static cudaError_t ckpt_forward(const WorldParams &w, const mt_muon_soa &soa, int64_t n, const RunParams &rp,
@@ -843,7 +927,7 @@ static int split_grid(const void *kernel, int per_sm_cap, int64_t work)
 // whose adjoint state it continues.
 template <int GEOM, int FIELD>
 static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
-                                 char *ck, float *adj, char *scratch, const float *gfin)
+                                 char *ck, float *adj, char *scratch, const float *gfin, int64_t ld)
 {
     const CkptLayout L = ckpt_layout(n, rp.max_steps, K);
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(ck);
@@ -874,7 +958,7 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
         if (p + 2 < P && e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[P + p + 2], 0);
         if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), aux);
         if (e != cudaSuccess) return;
-        select_live<<<sgrid, kBlock, 0, aux>>>(live_buf_at(ck + L.lists_off + p * L.list_bytes, n), ctr + p, gfin, n,
+        select_live<<<sgrid, kBlock, 0, aux>>>(live_buf_at(ck + L.lists_off + p * L.list_bytes, n), ctr + p, gfin, ld,
                                                sel, cnt);
         tape_pass<GEOM, FIELD, false><<<rgrid, kBlock, 0, aux>>>(
             w, mt_muon_soa{}, rp, sel, sel, cnt, nullptr, K, h + 256, reinterpret_cast<unsigned long long *>(h), cap,
@@ -888,7 +972,7 @@ static cudaError_t ckpt_backward(const WorldParams &w, int64_t n, const RunParam
         const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(h + 192);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[p], 0);
         if (e != cudaSuccess) return;
-        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, selected(p), cnt, adj, n, dalpha, h + 256,
+        adjoint_pass<GEOM, FIELD><<<agrid, kBlock, 0, st>>>(w, rp, selected(p), cnt, adj, ld, dalpha, h + 256,
                                                            reinterpret_cast<const unsigned long long *>(h),
                                                            reinterpret_cast<const unsigned int *>(h + 64), wc + 1, wc,
                                                            nullptr, nullptr);
@@ -949,11 +1033,12 @@ static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParam
     return cudaSuccess;
 }
 
-// dL/dalpha as float; NaN when the forward ran out of tape (flag set).
-__global__ void alpha_out(const double *src, float *dst, int m, const unsigned int *flag)
+// dL/dalpha as float (the sum of two groups' accumulators when src1 is not
+// null); NaN when the forward ran out of tape (flag set).
+__global__ void alpha_out(const double *src, const double *src1, float *dst, int m, const unsigned int *flag)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < m) dst[t] = (flag && *flag) ? __int_as_float(0x7FC00000) : (float)src[t];
+    if (t < m) dst[t] = (flag && *flag) ? __int_as_float(0x7FC00000) : (float)(src[t] + (src1 ? src1[t] : 0.0));
 }
 
 #define MT_DISPATCH_FIELDS(FN, G, ...)                                                  \
@@ -1061,7 +1146,24 @@ extern "C" mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64
     if (n == 0) return MT_OK;
     DevGuard g(h->device);
     const WorldParams &w = h->w;
-    const cudaError_t e = MT_DISPATCH(ckpt_forward, w, *s, n, rp, (cudaStream_t)stream, ckpt_every, (char *)ckpt);
+    cudaStream_t st = (cudaStream_t)stream;
+    const CkptGroups G = ckpt_groups(n, max_steps, ckpt_every);
+    cudaError_t e;
+    if (G.G == 1) {
+        e = MT_DISPATCH(ckpt_forward, w, *s, n, rp, st, ckpt_every, (char *)ckpt);
+    } else {
+        Fork f;
+        e = f.begin(st);
+        if (e == cudaSuccess) e = MT_DISPATCH(ckpt_forward, w, *s, G.n[0], rp, st, ckpt_every, (char *)ckpt);
+        if (e == cudaSuccess) {
+            RunParams r1 = rp;
+            r1.id_offset += G.start[1];
+            e = MT_DISPATCH(ckpt_forward, w, soa_from(*s, G.start[1]), G.n[1], r1, f.aux, ckpt_every,
+                            (char *)ckpt + G.off[1]);
+        }
+        const cudaError_t j = f.join(st);
+        if (e == cudaSuccess) e = j;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "checkpointing transport");
     return MT_OK;
 }
@@ -1102,18 +1204,41 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
     }
     // scratch: the tape of the reverse sweep, and the adjoint state unless the
     // caller asked for dL/d(initial state) in place
-    const int64_t tbytes = ckpt_scratch_bytes(n, ckpt_every);
+    // each group its own tape slots; the adjoint state [6][n] is shared, group
+    // 1's rows starting at its first muon
+    const CkptGroups G = ckpt_groups(n, max_steps, ckpt_every);
+    const int64_t tb0 = round_up(ckpt_scratch_bytes(G.n[0], ckpt_every), 256);
+    const int64_t tbytes = tb0 + (G.G == 2 ? ckpt_scratch_bytes(G.n[1], ckpt_every) : 0);
     const int64_t abytes = dL_dinitial ? 0 : ((6 * n * (int64_t)sizeof(float) + 255) & ~(int64_t)255);
+    const int64_t aoff = round_up(tbytes, 256);
     char *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)(tbytes + abytes), st);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)(aoff + abytes), st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
-    char *tape = scratch;
-    float *adj = dL_dinitial ? dL_dinitial : reinterpret_cast<float *>(scratch + tbytes);
+    float *adj = dL_dinitial ? dL_dinitial : reinterpret_cast<float *>(scratch + aoff);
     e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj, tape, dL_dfinal);
+    if (e == cudaSuccess && G.G == 1) {
+        e = MT_DISPATCH(ckpt_backward, w, n, rp, st, ckpt_every, (char *)ckpt, adj, scratch, dL_dfinal, n);
+    } else if (e == cudaSuccess) {
+        Fork f;
+        e = f.begin(st);
+        if (e == cudaSuccess)
+            e = MT_DISPATCH(ckpt_backward, w, G.n[0], rp, st, ckpt_every, (char *)ckpt, adj, scratch, dL_dfinal, n);
+        if (e == cudaSuccess) {
+            RunParams r1 = rp;
+            r1.id_offset += G.start[1];
+            e = MT_DISPATCH(ckpt_backward, w, G.n[1], r1, f.aux, ckpt_every, (char *)ckpt + G.off[1],
+                            adj + G.start[1], scratch + tb0, dL_dfinal + G.start[1], n);
+        }
+        const cudaError_t j = f.join(st);
+        if (e == cudaSuccess) e = j;
+    }
     if (e == cudaSuccess && alpha && n_block > 0) {
-        const CkptLayout L = ckpt_layout(n, max_steps, ckpt_every);
-        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L.alpha_off), dL_dalpha,
+        const CkptLayout L0 = ckpt_layout(G.n[0], max_steps, ckpt_every);
+        const double *a1 = nullptr;
+        if (G.G == 2)
+            a1 = reinterpret_cast<const double *>((char *)ckpt + G.off[1] +
+                                                  ckpt_layout(G.n[1], max_steps, ckpt_every).alpha_off);
+        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L0.alpha_off), a1, dL_dalpha,
                                      3 * n_block, nullptr);
         e = cudaGetLastError();
     }
@@ -1228,7 +1353,7 @@ extern "C" mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, in
         e = MT_DISPATCH(tape_backward, w, n, rp, st, steps_per_pass, (char *)tape, adj, scratch, dL_dfinal);
     if (e == cudaSuccess && alpha && n_block > 0) {
         const TapeLayout T = tape_layout(n, max_steps, steps_per_pass);
-        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)tape + T.ck.alpha_off), dL_dalpha,
+        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)tape + T.ck.alpha_off), nullptr, dL_dalpha,
                                      3 * n_block, reinterpret_cast<const unsigned int *>((char *)tape + T.flag_off));
         e = cudaGetLastError();
     }
