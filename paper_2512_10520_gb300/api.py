@@ -121,8 +121,9 @@ class Batch:
         """(block, steps_per_pass, staging) fastest on a sample of every instance
         (mt_batch_autotune); later transports use it unless told otherwise.  With
         cache, the result is kept in a JSON file keyed by a fingerprint of the
-        worlds, tables, muon counts and run arguments and by the GPU's name, and a
-        later call with the same key reuses it without timing anything."""
+        worlds, tables, muon counts, run arguments and library sources and by the
+        GPU's name, and a later call with the same key reuses it without timing
+        anything."""
         key = None
         if cache:
             import torch
@@ -130,8 +131,9 @@ class Batch:
             for w in self._worlds:
                 h.update(w)
             counts = [int(m["x"].numel()) if hasattr(m["x"], "numel") else len(m["x"]) for m in muons_list]
+            from . import _build
             h.update(json.dumps([counts, float(step_len), int(max_steps), int(seed), int(sample_per_instance),
-                                 B.mt_abi_version()]).encode())
+                                 B.mt_abi_version(), _build.source_digest()]).encode())
             key = f"{h.hexdigest()[:24]}|{torch.cuda.get_device_name()}"
             with _tune_lock:
                 try:
