@@ -33,20 +33,6 @@ def _stale(target: str, deps: List[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def source_digest() -> str:
-    """Hash of the library's sources, headers and compile flags: a tuned launch
-    shape cached for one build is not reused by another."""
-    import hashlib
-    h = hashlib.sha1(" ".join(ARCH).encode())
-    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
-    files += sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
-    for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 def build(force: bool = False, verbose: bool = False, extra_flags: Optional[List[str]] = None,
           out_path: Optional[str] = None, obj_dir: Optional[str] = None) -> str:
     """Compile every CUDA translation unit (in parallel) and link libmt.so; returns its path.

@@ -18,6 +18,20 @@ _TUNE_CACHE = os.environ.get("MT_AUTOTUNE_CACHE",
 _tune_lock = threading.Lock()
 
 
+def source_digest() -> str:
+    """Hash of the library's sources, headers and target architecture: a tuned
+    launch shape cached for one build is not reused by another."""
+    from . import _build
+    h = hashlib.sha1(" ".join(_build.ARCH).encode())
+    files = sorted(os.path.join(_build.CSRC, f) for f in os.listdir(_build.CSRC) if f.endswith((".cu", ".cuh", ".h")))
+    files += sorted(os.path.join(_build.INCLUDE, f) for f in os.listdir(_build.INCLUDE) if f.endswith(".h"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _fingerprint(h, obj) -> None:
     """Feed a descriptor dict (numbers, strings, arrays) into hash h: scalars and
     shapes exactly, large arrays through a strided sample plus their sums."""
@@ -131,9 +145,8 @@ class Batch:
             for w in self._worlds:
                 h.update(w)
             counts = [int(m["x"].numel()) if hasattr(m["x"], "numel") else len(m["x"]) for m in muons_list]
-            from . import _build
             h.update(json.dumps([counts, float(step_len), int(max_steps), int(seed), int(sample_per_instance),
-                                 B.mt_abi_version(), _build.source_digest()]).encode())
+                                 B.mt_abi_version(), source_digest()]).encode())
             key = f"{h.hexdigest()[:24]}|{torch.cuda.get_device_name()}"
             with _tune_lock:
                 try:
