@@ -406,8 +406,11 @@ int64_t mt_ckpt_bytes(int64_t n, int32_t max_steps, int32_t ckpt_every);
 /* Checkpointing forward: exactly mt_transport_scaled (same results), keeping
  * the state of every muon alive at steps 0, K, 2K, ... in `ckpt` (device,
  * 256-byte aligned, at least mt_ckpt_bytes bytes, caller-owned and reused by
- * mt_adjoint_ckpt).  Errors as mt_transport_scaled, plus MT_ERR_INVALID_ARG for
- * K outside [1, 64], n >= 2^31 or a checkpoint buffer too small / unaligned. */
+ * mt_adjoint_ckpt).  From 2^19 muons the two halves of the muons are
+ * checkpointed as two groups side by side, the second on a stream the call
+ * creates (forked from and joined back to `stream`), each with its own part of
+ * `ckpt`.  Errors as mt_transport_scaled, plus MT_ERR_INVALID_ARG for K
+ * outside [1, 64], n >= 2^31 or a checkpoint buffer too small / unaligned. */
 mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64_t n, float step_len, int32_t max_steps,
                             uint64_t seed, const float *alpha, int32_t n_block, int32_t ckpt_every, void *ckpt,
                             int64_t ckpt_bytes, void *stream);
@@ -418,11 +421,14 @@ mt_status mt_transport_ckpt(mt_handle *h, const mt_muon_soa *s, int64_t n, float
  * py, pz) of the final state (SoA rows).  dL_dalpha: device [n_block][3],
  * overwritten.  dL_dinitial (may be NULL): device [6][n], receives dL/d(initial
  * state) in the same layout.  The checkpoint buffer's header is used as the
- * gradient accumulator, and each checkpoint's list entries record the step
- * counts of their segment.  Scratch (the tape of one K-step segment, 56 K n
- * bytes, plus 6n floats when dL_dinitial is NULL) comes from the stream-ordered
- * allocator.  Errors: MT_ERR_INVALID_ARG for null or
- * inconsistent arguments, MT_ERR_OOM, MT_ERR_CUDA. */
+ * gradient accumulator; its lists are only read.  Only the muons whose six
+ * dL_dfinal components are not all zero are recomputed and reversed (the
+ * backward is linear in dL_dfinal); the others' rows of dL_dinitial are 0.  The
+ * two muon groups of mt_transport_ckpt run side by side as in the forward.
+ * Scratch (per group two slots, each the tape of one K-step segment, 56 K n
+ * bytes, and a list of 64 n bytes, plus 6n floats when dL_dinitial is NULL)
+ * comes from the stream-ordered allocator.  Errors: MT_ERR_INVALID_ARG for
+ * null or inconsistent arguments, MT_ERR_OOM, MT_ERR_CUDA. */
 mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, int32_t max_steps, uint64_t seed,
                           const float *alpha, int32_t n_block, int32_t ckpt_every, void *ckpt, int64_t ckpt_bytes,
                           int64_t id_offset, int32_t instance, const float *dL_dfinal, float *dL_dinitial,
@@ -461,8 +467,10 @@ mt_status mt_transport_tape(mt_handle *h, const mt_muon_soa *s, int64_t n, float
 
 /* Backward from the tape of one mt_transport_tape call (same n, step_len,
  * max_steps, alpha values, steps_per_pass).  dL_dfinal, dL_dinitial and
- * dL_dalpha as in mt_adjoint_ckpt.  Scratch (6n floats when dL_dinitial is
- * NULL) comes from the stream-ordered allocator. */
+ * dL_dalpha as in mt_adjoint_ckpt; only the muons whose dL_dfinal is not all
+ * zero are reversed.  Scratch (their list positions in one pass, 4n bytes,
+ * plus 6n floats when dL_dinitial is NULL) comes from the stream-ordered
+ * allocator. */
 mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, int32_t max_steps, const float *alpha,
                           int32_t n_block, int32_t steps_per_pass, void *tape, int64_t tape_bytes,
                           const float *dL_dfinal, float *dL_dinitial, float *dL_dalpha, void *stream);
