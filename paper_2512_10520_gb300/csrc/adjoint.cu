@@ -1003,7 +1003,7 @@ static int64_t tape_backward_scratch_bytes(int64_t n, int32_t max_steps, int K)
 
 template <int GEOM, int FIELD>
 static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParams &rp, cudaStream_t st, int K,
-                                 char *buf, float *adj, char *scratch, const float *gfin)
+                                 char *buf, float *adj, char *scratch, const float *gfin, int64_t ld)
 {
     const TapeLayout T = tape_layout(n, rp.max_steps, K);
     const CkptLayout &L = T.ck;
@@ -1024,8 +1024,8 @@ static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParam
     const int sgrid = resident_grid((const void *)select_cols, n);
     for (int p = L.passes - 1; p >= 0; --p) {
         const LiveBuf lp = live_buf_at(buf + L.lists_off + p * L.list_bytes, n);
-        select_cols<<<sgrid, kBlock, 0, st>>>(lp, ctr + p, gfin, n, cols, sel + p);
-        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, n, dalpha, buf + T.region_off,
+        select_cols<<<sgrid, kBlock, 0, st>>>(lp, ctr + p, gfin, ld, cols, sel + p);
+        adjoint_pass<GEOM, FIELD><<<grid, kBlock, 0, st>>>(w, rp, lp, ctr + p, adj, ld, dalpha, buf + T.region_off,
                                                           toff + p, flag, wc + p, nullptr, cols, sel + p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1035,10 +1035,12 @@ static cudaError_t tape_backward(const WorldParams &w, int64_t n, const RunParam
 
 // dL/dalpha as float (the sum of two groups' accumulators when src1 is not
 // null); NaN when the forward ran out of tape (flag set).
-__global__ void alpha_out(const double *src, const double *src1, float *dst, int m, const unsigned int *flag)
+__global__ void alpha_out(const double *src, const double *src1, float *dst, int m, const unsigned int *flag,
+                          const unsigned int *flag1)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < m) dst[t] = (flag && *flag) ? __int_as_float(0x7FC00000) : (float)(src[t] + (src1 ? src1[t] : 0.0));
+    const bool bad = (flag && *flag) || (flag1 && *flag1);
+    if (t < m) dst[t] = bad ? __int_as_float(0x7FC00000) : (float)(src[t] + (src1 ? src1[t] : 0.0));
 }
 
 #define MT_DISPATCH_FIELDS(FN, G, ...)                                                  \
@@ -1239,7 +1241,7 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
             a1 = reinterpret_cast<const double *>((char *)ckpt + G.off[1] +
                                                   ckpt_layout(G.n[1], max_steps, ckpt_every).alpha_off);
         alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)ckpt + L0.alpha_off), a1, dL_dalpha,
-                                     3 * n_block, nullptr);
+                                     3 * n_block, nullptr, nullptr);
         e = cudaGetLastError();
     }
     const cudaError_t f = cudaFreeAsync(scratch, st);
@@ -1248,10 +1250,25 @@ extern "C" mt_status mt_adjoint_ckpt(mt_handle *h, int64_t n, float step_len, in
     return MT_OK;
 }
 
+// The full-tape form's muon groups: those of the checkpoint form, each with its
+// own tape layout in the buffer, one after the other.
+static int64_t tape_group_off(const CkptGroups &g, int32_t max_steps, int K)
+{
+    return round_up(tape_layout(g.n[0], max_steps, K).total, 256);
+}
+
+static int64_t tape_bytes(int64_t n, int32_t max_steps, int K)
+{
+    const CkptGroups g = ckpt_groups(n, max_steps, K);
+    int64_t b = 0;
+    for (int i = 0; i < g.G; ++i) b += round_up(tape_layout(g.n[i], max_steps, K).total, 256);
+    return b;
+}
+
 extern "C" int64_t mt_tape_bytes(int64_t n, int32_t max_steps, int32_t steps_per_pass)
 {
     if (steps_per_pass < 1 || steps_per_pass > kTapeMax || n < 0 || max_steps < 0) return -1;
-    return tape_layout(n, max_steps, steps_per_pass).total;
+    return tape_bytes(n, max_steps, steps_per_pass);
 }
 
 namespace {
@@ -1266,7 +1283,7 @@ mt_status check_tape(int64_t n, int32_t max_steps, int32_t K, const void *buf, i
         set_error("n = %lld outside [0, 2^31)", (long long)n);
         return MT_ERR_INVALID_ARG;
     }
-    const int64_t need = tape_layout(n, max_steps, K).total;
+    const int64_t need = tape_bytes(n, max_steps, K);
     if (!buf || (reinterpret_cast<uintptr_t>(buf) & 255u) || bytes < need) {
         set_error("tape buffer %p of %lld bytes: need %lld bytes, 256-byte aligned", buf, (long long)bytes,
                   (long long)need);
@@ -1301,7 +1318,24 @@ extern "C" mt_status mt_transport_tape(mt_handle *h, const mt_muon_soa *s, int64
     if (n == 0) return MT_OK;
     DevGuard g(h->device);
     const WorldParams &w = h->w;
-    const cudaError_t e = MT_DISPATCH(tape_forward, w, *s, n, rp, (cudaStream_t)stream, steps_per_pass, (char *)tape);
+    cudaStream_t st = (cudaStream_t)stream;
+    const CkptGroups G = ckpt_groups(n, max_steps, steps_per_pass);
+    cudaError_t e;
+    if (G.G == 1) {
+        e = MT_DISPATCH(tape_forward, w, *s, n, rp, st, steps_per_pass, (char *)tape);
+    } else {
+        Fork f;
+        e = f.begin(st);
+        if (e == cudaSuccess) e = MT_DISPATCH(tape_forward, w, *s, G.n[0], rp, st, steps_per_pass, (char *)tape);
+        if (e == cudaSuccess) {
+            RunParams r1 = rp;
+            r1.id_offset += G.start[1];
+            e = MT_DISPATCH(tape_forward, w, soa_from(*s, G.start[1]), G.n[1], r1, f.aux, steps_per_pass,
+                            (char *)tape + tape_group_off(G, max_steps, steps_per_pass));
+        }
+        const cudaError_t j = f.join(st);
+        if (e == cudaSuccess) e = j;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "taped transport");
     return MT_OK;
 }
@@ -1342,19 +1376,42 @@ extern "C" mt_status mt_adjoint_tape(mt_handle *h, int64_t n, float step_len, in
     // scratch: the selected columns, then the adjoint state unless the caller
     // takes dL/d(initial state)
     float *adj = dL_dinitial;
-    const int64_t cbytes = tape_backward_scratch_bytes(n, max_steps, steps_per_pass);
+    const CkptGroups G = ckpt_groups(n, max_steps, steps_per_pass);
+    const int64_t cb0 = round_up(tape_backward_scratch_bytes(G.n[0], max_steps, steps_per_pass), 256);
+    const int64_t cbytes = cb0 + (G.G == 2 ? tape_backward_scratch_bytes(G.n[1], max_steps, steps_per_pass) : 0);
+    const int64_t aoff = round_up(cbytes, 256);
     char *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch),
-                                    (size_t)(cbytes + (adj ? 0 : 6 * n * (int64_t)sizeof(float))), st);
+                                    (size_t)(aoff + (adj ? 0 : 6 * n * (int64_t)sizeof(float))), st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
-    if (!adj) adj = reinterpret_cast<float *>(scratch + cbytes);
+    if (!adj) adj = reinterpret_cast<float *>(scratch + aoff);
     e = cudaMemcpyAsync(adj, dL_dfinal, 6 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-        e = MT_DISPATCH(tape_backward, w, n, rp, st, steps_per_pass, (char *)tape, adj, scratch, dL_dfinal);
+    char *tape1 = (char *)tape + (G.G == 2 ? tape_group_off(G, max_steps, steps_per_pass) : 0);
+    if (e == cudaSuccess && G.G == 1) {
+        e = MT_DISPATCH(tape_backward, w, n, rp, st, steps_per_pass, (char *)tape, adj, scratch, dL_dfinal, n);
+    } else if (e == cudaSuccess) {
+        Fork f;
+        e = f.begin(st);
+        if (e == cudaSuccess)
+            e = MT_DISPATCH(tape_backward, w, G.n[0], rp, st, steps_per_pass, (char *)tape, adj, scratch, dL_dfinal, n);
+        if (e == cudaSuccess)
+            e = MT_DISPATCH(tape_backward, w, G.n[1], rp, f.aux, steps_per_pass, tape1, adj + G.start[1],
+                            scratch + cb0, dL_dfinal + G.start[1], n);
+        const cudaError_t j = f.join(st);
+        if (e == cudaSuccess) e = j;
+    }
     if (e == cudaSuccess && alpha && n_block > 0) {
-        const TapeLayout T = tape_layout(n, max_steps, steps_per_pass);
-        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)tape + T.ck.alpha_off), nullptr, dL_dalpha,
-                                     3 * n_block, reinterpret_cast<const unsigned int *>((char *)tape + T.flag_off));
+        const TapeLayout T0 = tape_layout(G.n[0], max_steps, steps_per_pass);
+        const double *a1 = nullptr;
+        const unsigned int *f1 = nullptr;
+        if (G.G == 2) {
+            const TapeLayout T1 = tape_layout(G.n[1], max_steps, steps_per_pass);
+            a1 = reinterpret_cast<const double *>(tape1 + T1.ck.alpha_off);
+            f1 = reinterpret_cast<const unsigned int *>(tape1 + T1.flag_off);
+        }
+        alpha_out<<<1, 128, 0, st>>>(reinterpret_cast<const double *>((char *)tape + T0.ck.alpha_off), a1, dL_dalpha,
+                                     3 * n_block, reinterpret_cast<const unsigned int *>((char *)tape + T0.flag_off),
+                                     f1);
         e = cudaGetLastError();
     }
     if (scratch) {

@@ -331,42 +331,54 @@ def test_zero_cotangents_are_skipped_exactly():
     assert np.linalg.norm(tp - out["A"][0]) <= 1e-5 * np.linalg.norm(out["A"][0])
 
 
-def test_two_muon_groups_in_the_checkpoint_form():
-    """From 2^19 muons the checkpointing forward and its backward run as two
-    groups of half the muons on two streams, each with its own checkpoints and
-    tape slots.  The forward's final states equal the static grid's bit for bit;
-    dL/d(initial state) equals the one-group full-tape form's bit for bit (the
-    same reverse sweep over the same recorded steps); dL/dalpha, a sum in
-    another order, to 1e-5."""
+def test_two_muon_groups_in_the_differentiable_forms():
+    """From 2^19 muons the checkpoint and full-tape forms run as two groups of half
+    the muons on two streams, each with its own checkpoints (or tape) and scratch.
+    The forward's final states equal the static grid's bit for bit; each half's
+    dL/d(initial state) equals a separate one-group call on that half alone (its
+    muons' ids offset as in the whole) bit for bit, in both forms; dL/dalpha, a
+    sum in another order, to 1e-5."""
     import torch
     import paper_2512_10520_gb300 as mt
     wl = gen.workload("shield1e6", n=(1 << 19) + 5)
     n, K = wl.n, 32
+    n0 = n // 2
     a = torch.as_tensor(_alpha(), dtype=torch.float32).cuda().contiguous()
+
+    def run(world, lo, hi, g_all, tape):
+        mu = {k: v[lo:hi].copy() for k, v in wl.muons.items()}
+        m = hi - lo
+        dev = mt.muons_to_device(mu)
+        da = torch.empty_like(a)
+        gi = torch.empty((6, m), dtype=torch.float32, device="cuda")
+        g = g_all[:, lo:hi].contiguous()
+        if tape:
+            buf = torch.empty(mt.mt_tape_bytes(m, wl.max_steps, K), dtype=torch.uint8, device="cuda")
+            mt.mt_transport_tape(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, K, buf, id_offset=lo)
+            mt.mt_adjoint_tape(world.handle, m, wl.step_len, wl.max_steps, a, K, buf, g, da, gi)
+        else:
+            buf = torch.empty(mt.mt_ckpt_bytes(m, wl.max_steps, K), dtype=torch.uint8, device="cuda")
+            mt.mt_transport_ckpt(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, K, buf, id_offset=lo)
+            mt.mt_adjoint_ckpt(world.handle, m, wl.step_len, wl.max_steps, wl.seed, a, K, buf, g, da, gi,
+                               id_offset=lo)
+        torch.cuda.synchronize()
+        del buf
+        return dev, da.cpu().numpy().astype(np.float64), gi.cpu().numpy()
+
     with mt.World.from_workload(wl) as world:
         ref = mt.muons_to_device(wl.muons)
         world.transport(ref, wl.step_len, wl.max_steps, wl.seed, alpha=a, mode=mt.MT_LAUNCH_STATIC)
-        ckpt = torch.empty(mt.mt_ckpt_bytes(n, wl.max_steps, K), dtype=torch.uint8, device="cuda")
-        dev = mt.muons_to_device(wl.muons)
-        mt.mt_transport_ckpt(world.handle, dev, wl.step_len, wl.max_steps, wl.seed, a, K, ckpt)
-        torch.cuda.synchronize()
-        for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
-            assert torch.equal(ref[k], dev[k]), k
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         g = torch.empty((6, n), dtype=torch.float32, device="cuda")
-        mt.mt_acceptance_loss(dev, loss, g)
-        da = torch.empty_like(a)
-        gi = torch.empty((6, n), dtype=torch.float32, device="cuda")
-        mt.mt_adjoint_ckpt(world.handle, n, wl.step_len, wl.max_steps, wl.seed, a, K, ckpt, g, da, gi)
-        del ckpt
-        tape = torch.empty(mt.mt_tape_bytes(n, wl.max_steps, K), dtype=torch.uint8, device="cuda")
-        dev2 = mt.muons_to_device(wl.muons)
-        mt.mt_transport_tape(world.handle, dev2, wl.step_len, wl.max_steps, wl.seed, a, K, tape)
-        dt = torch.empty_like(a)
-        gt = torch.empty((6, n), dtype=torch.float32, device="cuda")
-        mt.mt_adjoint_tape(world.handle, n, wl.step_len, wl.max_steps, a, K, tape, g, dt, gt)
+        mt.mt_acceptance_loss(ref, loss, g)
         torch.cuda.synchronize()
-    assert int((g != 0).any(0).sum().item()) > 1000
-    np.testing.assert_array_equal(gi.cpu().numpy(), gt.cpu().numpy())
-    d1, d2 = da.cpu().numpy().astype(np.float64), dt.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(d1 - d2) <= 1e-5 * np.linalg.norm(d2)
+        assert int((g != 0).any(0).sum().item()) > 1000
+        for tape in (False, True):
+            dev, da, gi = run(world, 0, n, g, tape)
+            for k in ("x", "y", "z", "px", "py", "pz", "steps", "status"):
+                assert torch.equal(ref[k], dev[k]), (tape, k)
+            _, da0, gi0 = run(world, 0, n0, g, tape)
+            _, da1, gi1 = run(world, n0, n, g, tape)
+            np.testing.assert_array_equal(gi[:, :n0], gi0, err_msg=f"tape={tape}, first half")
+            np.testing.assert_array_equal(gi[:, n0:], gi1, err_msg=f"tape={tape}, second half")
+            assert np.linalg.norm(da - (da0 + da1)) <= 1e-5 * np.linalg.norm(da), tape
