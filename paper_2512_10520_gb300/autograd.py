@@ -119,8 +119,8 @@ def transport_differentiable(world, muons: Dict, alpha, step_len: float, max_ste
     takes the tape when it needs at most half of the free device memory.  With
     the acceptance loss, whose cotangent is zero for most muons of a shield, the
     checkpoint form is the faster (10^6 muons on a GB300: forward + backward 1.5x
-    the plain transport, against 2.4x with the tape); with a cotangent on every
-    muon the tape form is."""
+    the plain transport, against 2.0x with the tape); with a cotangent on every
+    muon the tape form is (2.8x, against 4.0x)."""
     out = MuonTransportFn.apply(alpha, world, muons, step_len, max_steps, seed, ckpt_every, id_offset, instance,
                                 tape)
     return dict(zip(_FIELDS + ("steps", "status"), out))
