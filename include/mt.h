@@ -281,7 +281,8 @@ typedef struct mt_launch_cfg {
     int32_t blocks_per_sm;    /* 0 = as many as fit (occupancy calculator)                */
     int32_t steps_per_pass;   /* MT_LAUNCH_COMPACT: steps between compactions, 0 = the    */
                               /*   longest of 128, 96, 64, 48, 32, 24, 16 whose slab of   */
-                              /*   the field map fits in 3/4 of L2 (64 without a map)     */
+                              /*   the field map fits in 3/4 of L2, or in 2.5 L2 when the */
+                              /*   live list is ordered (64 without a map)                */
     int32_t order;            /* MT_LAUNCH_COMPACT, field maps: spatial order of the live */
                               /*   list: MT_ORDER_AUTO (at least 2^19 muons), _ALWAYS,    */
                               /*   _NEVER                                                 */

@@ -683,11 +683,8 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     if (cfg) c = *cfg;
     int block = c.block ? c.block : (b->tuned_block ? b->tuned_block : 256);
     int S = c.steps_per_pass ? c.steps_per_pass : b->tuned_S;
-    if (!S) {   // untuned: the plain transport's choice for the instance with the largest map layers
-        S = 64;
-        for (int i = 0; i < b->n_inst; ++i)
-            if (b->is_set[i]) S = std::min(S, default_steps_per_pass(b->inst[i], step_len));
-    }
+    const bool untuned = !S;
+    if (untuned) S = 64;   // lowered below, once the call's order is known
     int staging = c.staging ? c.staging : (b->tuned_staging ? b->tuned_staging : MT_BATCH_STAGE_SHARED);
     if ((block != 128 && block != 256) || S < 1 ||
         (staging != MT_BATCH_STAGE_SHARED && staging != MT_BATCH_STAGE_GLOBAL) || c.order < MT_ORDER_AUTO ||
@@ -725,6 +722,9 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     // spatial order of the live lists (maps only; see compact.cuh)
     const bool order = (b->field_kind == MT_FIELD_MAP || b->field_kind == MT_FIELD_MAP_NEAREST) &&
                        c.order != MT_ORDER_NEVER && (c.order == MT_ORDER_ALWAYS || N >= MT_SORT_MIN_MUONS);
+    if (untuned)   // the plain transport's choice for the instance with the largest map layers
+        for (int i = 0; i < b->n_inst; ++i)
+            if (b->is_set[i]) S = std::min(S, default_steps_per_pass(b->inst[i], step_len, order));
     if (c.workspace && (c.workspace_bytes < need || (reinterpret_cast<uintptr_t>(c.workspace) & 255u))) {
         set_error("batch workspace of %lld bytes too small or not 256-byte aligned (need %lld)",
                   (long long)c.workspace_bytes, (long long)need);

@@ -68,6 +68,11 @@ static int resolve_order(const WorldParams &w, int64_t n, int order_mode)
     return MT_ORDER_NEVER;
 }
 
+bool call_ordered(const WorldParams &w, int64_t n, int order_mode)
+{
+    return resolve_order(w, n, order_mode) == MT_ORDER_ALWAYS;
+}
+
 // Launch plan of one compacting call: its passes, and whether the live list is
 // reordered (after compact_init and after the passes reorder_after names).
 CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode)

@@ -174,5 +174,7 @@ struct CompactPlan {   // compact.cu
 };
 CompactPlan compact_plan(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);
 int64_t compact_call_launches(const WorldParams &w, int64_t n, int max_steps, int S, int order_mode);
-int default_steps_per_pass(const WorldParams &w, float step_len);   // transport.cu
+// whether a compacting call of n muons reorders its live list (compact.cu)
+bool call_ordered(const WorldParams &w, int64_t n, int order_mode);
+int default_steps_per_pass(const WorldParams &w, float step_len, bool ordered);   // transport.cu
 }  // namespace mt

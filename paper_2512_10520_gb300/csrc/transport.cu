@@ -155,13 +155,17 @@ namespace mt {
 // Default pass length of the compacting transport.  The muons in flight during
 // a pass span about S d of z, so the field map's working set is the node
 // layers of that slab; the longest S in {128, 96, 64, 48, 32, 24, 16} whose
-// slab fits in three quarters of L2 keeps the gathers L2 hits (measured on
-// shield1e8, 400 x 400 x 1200 map, 16M muons: S = 16 4.78e10 muon-steps/s,
-// S = 64 4.07e10).  On shield1e6 (200 x 200 x 600) S = 128 fits and is among
-// the fastest: with the live list reordered after every pass and two muon
-// groups, 5.80e10 muon-steps/s at 128 and at 96, 5.74e10 at 64 and 5.76e10
-// at 160.  Without a map the pass length is 64.
-int default_steps_per_pass(const WorldParams &w, float step_len)
+// slab fits the L2 budget keeps the gathers L2 hits.  Without the spatial
+// order the budget is three quarters of L2 (measured on shield1e8, 400 x 400
+// x 1200 map, 16M muons, unordered: S = 16 4.78e10 muon-steps/s, S = 64
+// 4.07e10).  With it the warps in flight hold neighbouring map columns, so at
+// any moment they touch only part of the slab and the budget is 2.5 L2
+// (shield1e8, ordered: S = 16 5.48e10, 32 5.67e10, 48 5.68e10, 64 5.78e10,
+// 96 5.74e10, 128 5.66e10; S = 64 is a 290 MB slab).  On shield1e6 (200 x 200
+// x 600) S = 128 fits either budget and is among the fastest: ordered, with
+// two muon groups, 5.80e10 muon-steps/s at 128 and at 96, 5.74e10 at 64 and
+// 5.76e10 at 160.  Without a map the pass length is 64.
+int default_steps_per_pass(const WorldParams &w, float step_len, bool ordered)
 {
     if (w.field_kind != MT_FIELD_MAP && w.field_kind != MT_FIELD_MAP_NEAREST) return 64;
     int dev = 0, l2 = 0;
@@ -170,12 +174,13 @@ int default_steps_per_pass(const WorldParams &w, float step_len)
     const double layer = w.field_kind == MT_FIELD_MAP ? 32.0 * (w.fdims[0] - 1) * (double)w.fdims[1]
                                                       : 16.0 * w.fdims[0] * (double)w.fdims[1];
     const double sz = (double)w.frs_h[2] + (double)w.frs_l[2];
+    const double budget = (ordered ? 2.5 : 0.75) * l2;
     const int cand[7] = {128, 96, 64, 48, 32, 24, 16};
     // the map read at every RK4 stage takes at most 64 steps (measured on
     // shield1e6: 2.15e10 muon-steps/s against 2.00e10 at 128)
     const int longest = w.field_per_stage ? 64 : 128;
     for (int S : cand)
-        if (S <= longest && layer * (S * (double)step_len / sz + 2.0) <= 0.75 * l2) return S;
+        if (S <= longest && layer * (S * (double)step_len / sz + 2.0) <= budget) return S;
     return 16;
 }
 }  // namespace mt
@@ -267,7 +272,8 @@ extern "C" mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_
     if (lc.mode == MT_LAUNCH_COMPACT || (lc.mode == MT_LAUNCH_AUTO && n < ((int64_t)1 << 31))) {
         bool small = false;
         e = launch_compact(w, *s, n, rp, cs,
-                           lc.steps_per_pass > 0 ? lc.steps_per_pass : default_steps_per_pass(w, step_len),
+                           lc.steps_per_pass > 0 ? lc.steps_per_pass
+                                              : default_steps_per_pass(w, step_len, call_ordered(w, n, lc.order)),
                            lc.blocks_per_sm, lc.order,
                            lc.workspace, lc.workspace_bytes, small);
         if (small) {
@@ -326,7 +332,8 @@ extern "C" int64_t mt_transport_launches(const mt_handle *h, int64_t n, float st
     if (n == 0) return 0;
     if (lc.mode == MT_LAUNCH_COMPACT || (lc.mode == MT_LAUNCH_AUTO && n < ((int64_t)1 << 31))) {
         DeviceGuard g(h->device);
-        const int S = lc.steps_per_pass > 0 ? lc.steps_per_pass : default_steps_per_pass(h->w, step_len);
+        const int S = lc.steps_per_pass > 0 ? lc.steps_per_pass
+                                           : default_steps_per_pass(h->w, step_len, call_ordered(h->w, n, lc.order));
         return compact_call_launches(h->w, n, max_steps, S, lc.order);
     }
     return 1;
