@@ -317,9 +317,11 @@ mt_status mt_transport_cfg(mt_handle *h, const mt_muon_soa *s, int64_t n, float 
  * a resident grid whose blocks stage that instance's world in shared memory,
  * and the block's warps take 32-muon chunks of the instance until none are
  * left; survivors are compacted per instance between passes.  From 2^19
- * muons in all and two instances, the instances run as two groups of about
- * equal muon counts, each its own launch sequence, the second on a stream
- * the call creates (forked from and joined back to `stream`).  The paper
+ * muons in all, the call runs as two groups of about equal muon counts, each
+ * its own launch sequence, the second on a stream the call creates (forked
+ * from and joined back to `stream`).  The groups split at an instance
+ * boundary when one leaves them within 1/16 of the muons of each other, else
+ * inside the instance at the midpoint (a single instance included).  The paper
  * runs one geometry per launch; scanning many magnet configurations is the
  * design-optimisation use it motivates (Sec. Introduction).
  * ------------------------------------------------------------------------- */

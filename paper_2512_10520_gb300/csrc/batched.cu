@@ -87,22 +87,33 @@ struct BatchWs {
 };
 
 // Instance groups of one batched call: with MT_BATCH_GROUP_MIN_MUONS muons or
-// more and at least two instances, the instances [0, s) and [s, n_inst) run as
-// two independent batches on two streams (the split s makes their muon counts
-// as even as it can), so one group's passes fill the SMs the other's pass
-// tails leave idle, as the plain transport's two muon groups do.
+// more the call runs as two independent batches of about equal muon counts on
+// two streams, so one group's passes fill the SMs the other's pass tails
+// leave idle, as the plain transport's two muon groups do.  The groups split
+// at the instance boundary nearest to half the muons when that leaves them
+// within N/16 of each other; otherwise the instance holding muon N/2 is cut
+// there, its first `cut` muons in group 0 and the rest in group 1 (a muon's
+// draws depend only on its instance word and id, so results are the same).
 #ifndef MT_BATCH_GROUP_MIN_MUONS
 #define MT_BATCH_GROUP_MIN_MUONS (1 << 19)
 #endif
 
-// Returns the number of groups (1 or 2); split = first instance of group 1.
-static int batch_groups(int n_inst, const int64_t *n, int &split)
+struct BatchSplit {
+    int G = 1;
+    int i0[2] = {0, 0}, i1[2] = {0, 0};   // instances [i0, i1) of each group
+    int s = 0;                             // first instance of group 1
+    int64_t cut = 0;                       // > 0: muons of instance s in group 0
+};
+
+static BatchSplit batch_groups(int n_inst, const int64_t *n)
 {
+    BatchSplit sp;
+    sp.i1[0] = n_inst;
     int64_t N = 0;
     for (int i = 0; i < n_inst; ++i) N += n[i] > 0 ? n[i] : 0;
-    split = n_inst;
-    if (n_inst < 2 || N < MT_BATCH_GROUP_MIN_MUONS) return 1;
+    if (n_inst < 1 || N < MT_BATCH_GROUP_MIN_MUONS) return sp;
     int64_t run = 0, best = -1;
+    int split = n_inst;
     for (int s = 1; s < n_inst; ++s) {
         run += n[s - 1] > 0 ? n[s - 1] : 0;
         const int64_t d = run * 2 > N ? run * 2 - N : N - run * 2;
@@ -111,7 +122,35 @@ static int batch_groups(int n_inst, const int64_t *n, int &split)
             split = s;
         }
     }
-    return 2;
+    sp.G = 2;
+    sp.i1[1] = n_inst;
+    if (best >= 0 && best <= N / 16) {
+        sp.s = split;
+        sp.i1[0] = sp.i0[1] = split;
+        return sp;
+    }
+    const int64_t h = N / 2;
+    int64_t o = 0;
+    int s = 0;
+    for (; s < n_inst; ++s) {
+        const int64_t ns = n[s] > 0 ? n[s] : 0;
+        if (o + ns > h) break;
+        o += ns;
+    }
+    // o <= h < o + n[s], and h > 0, so s > 0 when the cut is 0
+    sp.s = s;
+    sp.cut = h - o;
+    sp.i0[1] = s;
+    sp.i1[0] = sp.cut > 0 ? s + 1 : s;
+    return sp;
+}
+
+// Muons of instance i (i0[g] <= i < i1[g]) in group g.
+static int64_t group_count(const BatchSplit &sp, int g, int i, const int64_t *n)
+{
+    const int64_t ni = n[i] > 0 ? n[i] : 0;
+    if (sp.G == 1 || sp.cut == 0 || i != sp.s) return ni;
+    return g == 0 ? sp.cut : ni - sp.cut;
 }
 
 static int64_t round256(int64_t x) { return (x + 255) & ~(int64_t)255; }
@@ -656,14 +695,12 @@ int64_t mt_batch_device_bytes(const mt_batch *b)
 int64_t mt_batch_workspace_bytes(const mt_batch *b, const int64_t *n)
 {
     if (!b || !n) return -1;
-    int split = 0;
-    const int G = batch_groups(b->n_inst, n, split);
+    const BatchSplit sp = batch_groups(b->n_inst, n);
     int64_t bytes = 0;
-    for (int g = 0; g < G; ++g) {
-        const int i0 = g == 0 ? 0 : split, i1 = G == 1 || g == 1 ? b->n_inst : split;
+    for (int g = 0; g < sp.G; ++g) {
         int64_t N = 0;
-        for (int i = i0; i < i1; ++i) N += n[i] > 0 ? n[i] : 0;
-        bytes += round256(batch_ws_layout(i1 - i0, N, nullptr, nullptr));
+        for (int i = sp.i0[g]; i < sp.i1[g]; ++i) N += group_count(sp, g, i, n);
+        bytes += round256(batch_ws_layout(sp.i1[g] - sp.i0[g], N, nullptr, nullptr));
     }
     return bytes;
 }
@@ -710,12 +747,12 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     }
     const int64_t N = (int64_t)off[b->n_inst];
     // instance groups (see batch_groups) and their workspaces, one after the other
-    int split = b->n_inst;
-    const int G = batch_groups(b->n_inst, n, split);
-    int gi0[2] = {0, split}, gi1[2] = {G == 1 ? b->n_inst : split, b->n_inst};
+    const BatchSplit sp = batch_groups(b->n_inst, n);
+    const int G = sp.G;
+    const int *gi0 = sp.i0, *gi1 = sp.i1;
     int64_t gN[2] = {0, 0}, gws[2] = {0, 0};
     for (int g = 0; g < G; ++g) {
-        gN[g] = (int64_t)(off[gi1[g]] - off[gi0[g]]);
+        for (int i = gi0[g]; i < gi1[g]; ++i) gN[g] += group_count(sp, g, i, n);
         gws[g] = round256(batch_ws_layout(gi1[g] - gi0[g], gN[g], nullptr, nullptr));
     }
     const int64_t need = gws[0] + gws[1];
@@ -779,11 +816,26 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     // its instances' arrays, cleared counters
     for (int g = 0; g < G && e == cudaSuccess; ++g) {
         const int ni = gi1[g] - gi0[g];
-        std::vector<unsigned long long> og(ni + 1);
-        for (int i = 0; i <= ni; ++i) og[i] = off[gi0[g] + i] - off[gi0[g]];
+        std::vector<unsigned long long> og(ni + 1, 0);
+        std::vector<mt_muon_soa> sg(soas + gi0[g], soas + gi1[g]);
+        for (int i = 0; i < ni; ++i) og[i + 1] = og[i] + (unsigned long long)group_count(sp, g, gi0[g] + i, n);
+        if (g == 1 && sp.cut > 0) {   // the second part of the cut instance: its muons from `cut` on
+            mt_muon_soa &p = sg[0];
+            const int64_t c0 = sp.cut;
+            p.x += c0;
+            p.y += c0;
+            p.z += c0;
+            p.px += c0;
+            p.py += c0;
+            p.pz += c0;
+            p.q += c0;
+            p.steps += c0;
+            p.status += c0;
+            p.id_offset += c0;
+        }
         e = cudaMemcpyAsync(ws[g].off, og.data(), og.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ws[g].soa, soas + gi0[g], sizeof(mt_muon_soa) * (size_t)ni, cudaMemcpyHostToDevice, cs);
+            e = cudaMemcpyAsync(ws[g].soa, sg.data(), sizeof(mt_muon_soa) * (size_t)ni, cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(ws[g].cnt, 0, 3 * (size_t)ni * sizeof(unsigned int), cs);
     }
     if (e == cudaSuccess && order) e = cudaFuncSetAttribute(batch_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
@@ -811,11 +863,11 @@ mt_status mt_transport_batched(mt_batch *b, const mt_muon_soa *soas, const int64
     if (e == cudaSuccess) {
         if (c.use_graph) {
             // capture the launch sequence once per (arguments) and replay it
-            std::vector<char> key(sizeof(void *) + 6 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 16);
+            std::vector<char> key(sizeof(void *) + 7 * sizeof(int) + sizeof(float) + sizeof(uint64_t) + 16);
             char *kp = key.data();
             memcpy(kp, &base, sizeof(void *));
             kp += sizeof(void *);
-            const int ints[6] = {block, S, max_steps, staging, order ? 1 : 0, split};
+            const int ints[7] = {block, S, max_steps, staging, order ? 1 : 0, G == 2 ? sp.s : -1, sp.cut > 0 ? 1 : 0};
             memcpy(kp, ints, sizeof(ints));
             kp += sizeof(ints);
             memcpy(kp, &step_len, sizeof(float));

@@ -198,14 +198,19 @@ def test_world_staging_layouts_are_bit_identical(instances, batch, staging):
         _assert_same(_host(devs), ref)
 
 
-def test_two_instance_groups_are_bit_identical(hist):
-    """From 2^19 muons a batched call runs its instances as two groups of about
-    equal muon counts on two streams: each instance ends exactly as a separate
-    mt_transport call, with and without a CUDA graph, in a caller's workspace of
-    exactly mt_batch_workspace_bytes."""
+@pytest.mark.parametrize("sizes", [
+    [200_000, 1, 250_000, 0, 150_000],   # no boundary within N/16 of half: instance 2 is cut
+    [300_000, 1, 0, 290_000],            # split at the boundary after instance 0
+    [600_000],                           # one instance, cut in half
+])
+def test_two_instance_groups_are_bit_identical(hist, sizes):
+    """From 2^19 muons a batched call runs as two groups of about equal muon
+    counts on two streams, split at an instance boundary or inside the middle
+    instance: each instance ends exactly as a separate mt_transport call, with
+    and without a CUDA graph, in a caller's workspace of exactly
+    mt_batch_workspace_bytes."""
     import torch
     import paper_2512_10520_gb300 as mt
-    sizes = [200_000, 1, 250_000, 0, 150_000]
     insts = [gen.batched_instance(40 + i, n=n) for i, n in enumerate(sizes)]
     assert sum(sizes) >= 1 << 19
     ids = [10**6 * i for i in range(len(insts))]
