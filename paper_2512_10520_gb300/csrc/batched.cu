@@ -24,15 +24,15 @@
 // Resident threads per SM the compiler must allow for in batch_pass (register
 // budget).  Voxel worlds: 1280 threads = 48 registers, no spill (measured on
 // worlds256, 256 instances with the spatial order: 594.6 ms against 623.9 ms
-// at 1024 threads = 64 registers).  Box worlds keep 1024 (at 48 registers they
-// spill 4-16 bytes; earlier, 1024 threads 730 ms against 752 ms at 768).  The
-// variants that spill at 64 registers (per-stage field reads; polyhedra) keep
-// 768.
+// at 1024 threads = 64 registers).  Box worlds take 1280 too although they
+// spill 4-16 bytes there (shield1e8 as one instance of 10^8 muons: 2081 ms
+// against 2129 ms at 1024).  The variants that spill at 64 registers
+// (per-stage field reads; polyhedra) keep 768.
 #ifndef MT_BATCH_THREADS_PER_SM_VOXELS
 #define MT_BATCH_THREADS_PER_SM_VOXELS 1280
 #endif
 #ifndef MT_BATCH_THREADS_PER_SM
-#define MT_BATCH_THREADS_PER_SM 1024
+#define MT_BATCH_THREADS_PER_SM 1280
 #endif
 #ifndef MT_BATCH_THREADS_PER_SM_WIDE
 #define MT_BATCH_THREADS_PER_SM_WIDE 768
